@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the Schwarzschild orbit-library hot path on GB300.
+
+One step = one model evaluation of the `barred_100k` workload: integrate
+100 000 orbits x 10 000 kick-drift-kick steps in the rotating disc + bar + halo
+potential, project every sample with four-fold mirroring into 20 x 20 x 10
+density cells and 50 x 50 pixels x 32 line-of-sight-velocity bins (the orbit
+matrix, 86 500 rows), reduce each pixel's velocity histogram to Gauss-Hermite
+rows (16 500 rows), and solve the regularised non-negative weight problem
+against synthetic data, returning weights and chi^2.
+
+Metric: orbit-steps/s of whole model evaluations (also models/s), FP32 form.
+`value` is timed with CUDA events on device-resident inputs; `e2e` repeats the
+same steps through the host-pointer C-ABI calls with the host<->device copies
+inside the timed region.  The `cpu_baseline` is the FP64 oracle on a bounded
+sample of the same workload on the host cores.  `--impl reference` runs that
+oracle arm alone.
+
+Under torchrun (N > 1) each rank runs an independent replica on its own GPU
+(the path shards by model/orbit with no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2607_00117_gb300 import inputs  # noqa: E402
+
+WORKLOAD = "barred_100k"
+N_MOCK = 20_000          # orbits of the independent mock library that makes the data
+N_CPU_SAMPLE = 2048      # orbits of the oracle's bounded CPU sample (full step count)
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sw", choices=["sw", "reference"])
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), \
+            d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 1900.0, 1700.0, 2070.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device, self.proc, self.lines = device, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload and synthetic data
+# ---------------------------------------------------------------------------
+def pixel_moments_from_hist(y_hist, grid):
+    """Mass-weighted mean and dispersion per pixel from a velocity-histogram
+    data vector (bin centres)."""
+    nd = grid["nR"] * grid["nphi"] * grid["nz"]
+    npix = grid["nx"] * grid["ny"]
+    nv, vmax = grid["nv"], grid["vmax"]
+    vc = -vmax + (np.arange(nv) + 0.5) * (2 * vmax / nv)
+    h = y_hist[nd + npix:].reshape(npix, nv)
+    m0 = h.sum(1)
+    return np.stack([m0, h @ vc, h @ (vc * vc)], 1)
+
+
+def make_data(sw, torch, W, rank):
+    """Mock observation: an independent library of N_MOCK orbits with weights
+    U(0, 2) (scaled to the library size), its pixels' reference Gaussians, and
+    2% mass errors / Sec. 3.1 GH errors with Gaussian noise.  Built with the
+    FP32 path outside the timed region."""
+    grid = W["grid"]
+    ctx = sw.Context(0, "fp32")
+    ctx.set_potential(W["potential"])
+    ics = inputs.disc_ics(W["potential"], N_MOCK, seed=W["seeds"]["ic"] + 500 + rank)
+    ctx.integrate_library(ics, W["omega_p"], W["dt"], W["nsteps"])
+    Uh = ctx.project(grid)
+    wt = inputs.true_weights(N_MOCK, W["seeds"]["w"]) * (W["n_orb"] / N_MOCK)
+    y_hist = Uh.apply(wt)
+    v0s, gh_err = inputs.gh_reference(pixel_moments_from_hist(y_hist, grid))
+    Ug = ctx.reduce_gh(Uh, v0s)
+    y0 = Ug.apply(wt)
+    blocks = {"dens": (0, Ug.blocks[0]), "pix": (Ug.blocks[0], Ug.blocks[0] + Ug.blocks[1]),
+              "kin": (Ug.blocks[0] + Ug.blocks[1], Ug.M)}
+    sig = inputs.mock_sigma(y0, blocks, gh_err=gh_err)
+    y = y0 + sig * inputs.noise(len(y0), W["seeds"]["noise"])
+    Uh.free(); Ug.free(); ctx.close()
+    return v0s, y, sig
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per unit for the roofline of the dominant kernel
+# ---------------------------------------------------------------------------
+def roofline_entry(name, stats, W, M_gh, K, hbm, bf16, sm_mhz):
+    N, S = W["n_orb"], W["nsteps"]
+    n = stats[name]["launches"]
+    t = stats[name]["ms"] / 1e3 / n
+    if name in ("gemv_n", "gemv_t"):           # one pass over the BF16 whitened matrix (M_gh x N)
+        bytes_ = 2.0 * M_gh * N + 4.0 * (M_gh + N)
+        return {"bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm, "unit": "GB/s", "frac": bytes_ / t / 1e9 / hbm}
+    if name in ("trmv_l", "trmv_lt"):           # one pass over the lower triangle of X (K x K FP32)
+        bytes_ = 4.0 * K * (K + 1) / 2 + 8.0 * K
+        return {"bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm, "unit": "GB/s", "frac": bytes_ / t / 1e9 / hbm}
+    if name == "gram_tcgen05":                  # lower-triangular tiles of K x K, contraction N
+        T = math.ceil(K / 128)
+        flops = 2.0 * (T * (T + 1) / 2) * 128 * 128 * N
+        return {"bound": "tensor", "achieved": flops / t / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                "frac": flops / t / 1e12 / bf16}
+    if name == "orbit_project_bin":             # FP32 issue slots per orbit-step (counted from the source)
+        ops = 360.0 * N * S
+        peak = SM_COUNT * FP32_LANES * sm_mhz * 1e6 / 1e12
+        return {"bound": "alu", "achieved": ops / t / 1e12, "peak": peak, "unit": "Tops/s (FP32 issue)",
+                "frac": ops / t / 1e12 / peak}
+    if name in ("finalize_columns", "reduce_gh", "whiten"):
+        return {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None}
+    return {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None}
+
+
+# ---------------------------------------------------------------------------
+# the oracle arm (CPU, FP64)
+# ---------------------------------------------------------------------------
+def cpu_sample(W, n_orb=N_CPU_SAMPLE):
+    import oracle
+    pot = oracle.make_pot(W["potential"])
+    obs = oracle.make_obs(W["grid"])
+    ics = inputs.disc_ics(W["potential"], n_orb, seed=W["seeds"]["ic"])
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    U, _, _ = oracle.build_matrix(pot, W["omega_p"], W["dt"], W["nsteps"], ics, obs)
+    dt = time.perf_counter() - t0
+    value = n_orb * W["nsteps"] / dt
+    sample = (f"{n_orb} orbits x {W['nsteps']} steps of {WORKLOAD} (integrate + project + bin into the "
+              f"{U.shape[1]}-row matrix, FP64, OpenMP); the weight solve is not in the sample")
+    return value, cores, sample, dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    W = inputs.WORKLOADS[WORKLOAD]
+    for _ in range(args.warmup):
+        cpu_sample(W, 256)
+    vals, ts = [], []
+    for _ in range(args.steps):
+        v, cores, sample, dt = cpu_sample(W, 512)
+        vals.append(v); ts.append(dt)
+    value = float(np.mean(vals))
+    line = {"metric": "orbit-steps/s (whole model evaluations, FP32 batched vs FP64 plain at matched chi^2)",
+            "value": value, "unit": "orbit-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(ts)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_orbits": 512, "nsteps": W["nsteps"]}, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "orbit-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample.replace(str(N_CPU_SAMPLE), "512")},
+            "e2e": {"value": value, "unit": "orbit-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_sw(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2607_00117_gb300 import sw
+    sw.lib()
+
+    W = inputs.WORKLOADS[WORKLOAD]
+    grid, N, S = W["grid"], W["n_orb"], W["nsteps"]
+    hbm, bf16, bf16_sus, sm_max, peak_src = peaks()
+
+    v0s, y, sig = make_data(sw, torch, W, rank)
+    ics = inputs.disc_ics(W["potential"], N, seed=W["seeds"]["ic"] + 1000 * rank)
+    dev = torch.device("cuda", local)
+    ics_d = torch.from_numpy(ics).to(dev)
+    y_d = torch.from_numpy(y).to(dev)
+    sig_d = torch.from_numpy(sig).to(dev)
+    w_d = torch.empty(N, dtype=torch.float64, device=dev)
+    chi_d = torch.empty(3, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = sw.Context(local, "fp32", stream.cuda_stream)
+    ctx.set_potential(W["potential"])
+
+    statuses = []
+
+    def step():
+        ctx.integrate_library_device(ics_d, W["omega_p"], W["dt"], S)
+        Uh = ctx.project(grid)
+        Ug = ctx.reduce_gh(Uh, v0s)
+        Uh.free()
+        st = ctx.solve_weights_device(Ug, y_d, sig_d, W["lam"], w_d, chi_d)
+        M_gh = Ug.M
+        Ug.free()
+        if st not in (sw.SW_OK, sw.SW_ENONCONV):
+            raise sw.SwError(st, sw.lib().sw_last_error(ctx.handle).decode())
+        statuses.append(sw.STATUS_NAMES[st])
+        return M_gh
+
+    for _ in range(args.warmup):
+        M_gh = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ctx.set_profiling(True)
+    ctx.reset_stats()
+    launches0 = ctx.launch_count()
+    clocks = Clocks(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    kstats = ctx.kernel_stats()
+    ctx.set_profiling(False)
+    info = ctx.solve_info()
+    chi2 = chi_d.cpu().numpy()
+    if dist:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+
+    # ---- end to end through the host-pointer calls (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        ctx2 = sw.Context(local, "fp32", stream.cuda_stream)
+        ctx2.set_potential(W["potential"])
+        ics_h = np.ascontiguousarray(ics)
+
+        def step_host():
+            ctx2.integrate_library(ics_h, W["omega_p"], W["dt"], S)
+            Uh = ctx2.project(grid)
+            Ug = ctx2.reduce_gh(Uh, v0s)
+            Uh.free()
+            w, c = ctx2.solve_weights(Ug, y, sig, W["lam"], allow_nonconv=True)
+            Ug.free()
+            return w, c
+        step_host()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        h2d = ics_h.nbytes + y.nbytes + sig.nbytes + 8 * 2 * (S + 1) + 16 * grid["nx"] * grid["ny"]
+        d2h = 8 * N + 8 * 3
+        e2e = {"value": N * S * args.steps * world / te, "unit": "orbit-steps/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * te / args.steps}
+        ctx2.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (CUDA-event time inside the timed region)
+    K = min(M_gh, N)
+    dom = max(kstats, key=lambda k: kstats[k]["ms"])
+    sm_mhz = clk["sm_mhz"] if clk else sm_max
+    roof = roofline_entry(dom, kstats, W, M_gh, K, hbm, bf16_sus, sm_mhz)
+    roof.update({"kernel": dom, "traffic": None, "peak_source": peak_src,
+                 "ms_per_launch": kstats[dom]["ms"] / kstats[dom]["launches"]})
+    breakdown = {k: round(v["ms"] / args.steps, 3) for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])}
+
+    cpu = None
+    if not args.no_cpu:
+        v, cores, sample, _ = cpu_sample(W)
+        cpu = {"value": v, "unit": "orbit-steps/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    value = N * S * args.steps * world / elapsed
+    line = {"metric": "orbit-steps/s (whole model evaluations, FP32 batched vs FP64 plain at matched chi^2)",
+            "value": value, "unit": "orbit-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_orb": N, "nsteps": S, "rows_histogram": grid["nR"] * grid["nphi"] *
+                       grid["nz"] + grid["nx"] * grid["ny"] * (1 + grid["nv"]), "rows_solve": M_gh,
+                       "parallelism": f"replicas x{world}", "l2": "inputs and U far larger than L2 (U 34.6 GB)"},
+            "models_per_s": args.steps * world / elapsed,
+            "chi2": {"total": float(chi2[0]), "obs": float(chi2[1]), "reg": float(chi2[2]),
+                     "solver": info, "status": statuses[-args.steps:]},
+            "roofline": roof, "kernel_ms_per_step": breakdown, "gpu_launches": int(launches),
+            "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_sw(a)

@@ -1,0 +1,218 @@
+/*
+ * libsw -- Schwarzschild orbit-superposition hot path on one GB300 (sm_103a).
+ *
+ * For one trial potential: integrate an orbit library in a rotating
+ * disc + bar + halo potential, project every sample to the sky with four-fold
+ * mirror symmetrisation, bin it into 3-D density cells and IFU pixels x
+ * line-of-sight-velocity bins (or Gauss-Hermite rows) to form the orbit
+ * matrix U, then solve the regularised non-negative weight problem
+ * (arxiv 2607.00117, Sec. 2: density/potential, orbit library, projection,
+ * mapping to observables, weight optimisation, likelihood).
+ *
+ * Conventions for every entry point:
+ *  - Units: kpc, km/s, Msun, G = 4.300917e-6 kpc (km/s)^2 / Msun; time in
+ *    kpc/(km/s) (977.79 Myr); angles in radians; Omega_p in km/s/kpc.
+ *  - Every call returns sw_status and never aborts or prints; the message of
+ *    the last failure is returned by sw_last_error().
+ *  - Host arrays are owned by the caller and only read (inputs) or written
+ *    (outputs) during the call.  "_device" variants take device pointers
+ *    (CUDA global memory on the context's device) instead of host pointers.
+ *  - The context owns all library-allocated device memory except sw_matrix
+ *    objects, which the caller owns once returned and frees with
+ *    sw_matrix_free() before destroying their context.
+ *  - All work is ordered on the context's CUDA stream.  Calls with host
+ *    outputs return after the results are copied out; "_device" calls are
+ *    asynchronous with respect to the host unless stated.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef SW_H
+#define SW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+typedef struct sw_ctx sw_ctx;       /* opaque */
+typedef struct sw_matrix sw_matrix; /* opaque, device-resident orbit matrix */
+
+typedef enum {
+    SW_OK = 0,
+    SW_EINVAL = 1,    /* invalid argument (NULL, size, grid) */
+    SW_ENOMEM = 2,    /* device allocation failed */
+    SW_ECUDA = 3,     /* CUDA runtime error */
+    SW_ETIMEOUT = 4,  /* a bounded device wait ran out */
+    SW_ENONCONV = 5,  /* iteration cap reached; best iterate returned */
+    SW_ESTATE = 6     /* call out of order (e.g. project before integrate) */
+} sw_status;
+
+typedef enum {
+    SW_FP64_PLAIN = 0,  /* FP64 integration, binning and solve (plain baseline form) */
+    SW_FP32_KAHAN = 1   /* FP32 integration with Kahan-compensated positions; BF16 tensor-core
+                           Gram with FP32 accumulation; FP64 refinement and chi^2 */
+} sw_precision;
+
+/* Per-orbit status written by the integration passes. */
+enum { SW_ORBIT_OK = 0, SW_ORBIT_DRIFT = 1, SW_ORBIT_NONFINITE = 2 };
+
+/* Potential (Sec. 3.2).  Disc: Miyamoto-Nagai Phi = -G M_d / sqrt(R^2 + (R_d + sqrt(z^2 + H_d^2))^2)
+ * with (disc_M, disc_a, disc_b) = (M_d, R_d, H_d).  Halo: NFW from (halo_M200, halo_c) with
+ * Delta = 200 and rho_crit = 3 H0^2 / (8 pi G), H0 in km/s/Mpc (Sec. 3.2.1).  Bar: the n = 1,
+ * eta = 0 needle convolution of Eq. (Rn_to_In) (the Long-Murali bar) with half-length bar_L,
+ * parent MN radial scale bar_b and height bar_c; bar_M = 0 disables it.  The bar's major axis
+ * is the rotating x axis.  test_kind 1 adds a point mass test_M, 2 a Plummer sphere
+ * (test_M, test_a); 0 none.  Components with zero mass are skipped. */
+typedef struct {
+    double disc_M, disc_a, disc_b;
+    double halo_M200, halo_c, H0;
+    double bar_M, bar_L, bar_b, bar_c;
+    int32_t test_kind;
+    int32_t reserved;
+    double test_M, test_a;
+} sw_potential_params;
+
+/* Sky pixels: half-open bins [x0 + i dx, x0 + (i+1) dx), i < nx (same for y). */
+typedef struct { int32_t nx, ny; double x0, y0, dx, dy; } sw_pixel_grid;
+/* Line-of-sight velocity bins [v0 + k dv, v0 + (k+1) dv), k < nv. */
+typedef struct { int32_t nv, reserved; double v0, dv; } sw_vbins;
+/* Cylindrical cells in the bar frame, uniform in R in [0, Rmax), phi in [0, 2 pi) measured
+ * from the bar's major axis, z in [zmin, zmax) (Sec. 2.2.4). */
+typedef struct { int32_t nR, nphi, nz, reserved; double Rmax, zmin, zmax; } sw_density_grid;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` computing in `prec`.  `cuda_stream` is a
+ * cudaStream_t to order all work on (e.g. PyTorch's current stream), or NULL for a
+ * stream the context creates and owns.  *out receives the context. */
+sw_status sw_create(sw_ctx** out, int device, sw_precision prec, void* cuda_stream);
+/* Free every device buffer the context owns and the context itself (NULL is a no-op). */
+sw_status sw_destroy(sw_ctx* ctx);
+/* Message of the most recent failure on this context ("" if none).  Valid until the next call. */
+const char* sw_last_error(const sw_ctx* ctx);
+
+/* ---- the four calls of the method (Sec. 2) --------------------------------- */
+
+/* Set the trial potential (Sec. 3.2; the NFW re-parameterisation of Sec. 3.2.1 is done here).
+ * Returns SW_EINVAL for non-finite or non-positive scales. */
+sw_status sw_set_potential(sw_ctx* ctx, const sw_potential_params* p);
+
+/* Load the orbit library's initial conditions (Sec. 2.2.1-2.2.2): ics is n_orb x 6 row-major
+ * (x, y, z, vx, vy, vz) in the inertial frame at t = 0 (host memory), with pattern speed
+ * omega_p, fixed step dt > 0 and nsteps >= 1 kick-drift-kick steps.  When drift_out or
+ * status_out is non-NULL, the orbits are also integrated once to return each orbit's Jacobi
+ * drift max_n |E_J(t_n) - E_J(0)| / |E_J(0)| (Sec. 2.2.2) and status (SW_ORBIT_*; drift > 0.1
+ * is SW_ORBIT_DRIFT); otherwise integration is deferred to sw_project, which fuses it with
+ * binning.  Arrays are host memory of n_orb elements. */
+sw_status sw_integrate_library(sw_ctx* ctx, const double* ics, int64_t n_orb, double omega_p, double dt,
+                               int64_t nsteps, double* drift_out, uint8_t* status_out);
+/* As sw_integrate_library with ics, drift_out and status_out in device memory. */
+sw_status sw_integrate_library_device(sw_ctx* ctx, const double* ics_dev, int64_t n_orb, double omega_p,
+                                      double dt, int64_t nsteps, double* drift_dev, uint8_t* status_dev);
+
+/* Build the orbit matrix U (Sec. 2.2.3-2.2.4, Eq. Euler, Table 1) for the loaded library:
+ * Euler angles alpha = bar_angle, beta = incl, gamma = pa (z-x-z, image = (x', y'),
+ * v_los = v'_z); samples at t_1..t_nsteps, each with its four mirror copies when mirror4 != 0,
+ * weight 1/(copies * nsteps).  Rows (M total): density cells (iR*nphi + iphi)*nz + iz; then
+ * pixel mass iy*nx + ix; then either the velocity histogram (pixel*nv + iv) or, when gh_v0_s
+ * (host, npix x 2 reference (v0, s) per pixel) is non-NULL, four Gauss-Hermite rows per pixel
+ * (pixel*4 + m-1, m = 1..4) holding sum 2 sqrt(pi) alpha(w) H_m(w), w = (v_los - v0)/s.
+ * Orbits whose Jacobi drift exceeds 0.1 or turn non-finite get zero columns.  *U_out receives a
+ * device-resident matrix stored orbit-major (column i contiguous).  vb may be NULL in GH mode. */
+sw_status sw_project(sw_ctx* ctx, double incl, double pa, double bar_angle, const sw_pixel_grid* pix,
+                     const sw_vbins* vb, const sw_density_grid* dens, const double* gh_v0_s, int mirror4,
+                     sw_matrix** U_out);
+/* Reduce a velocity-histogram orbit matrix to Gauss-Hermite rows (the form of the paper's
+ * objective, Sec. 2.3 Eq. objective_function, and of its App. B conversion of a gridded LOSVD to
+ * GH coefficients): density and pixel-mass rows are copied; for each pixel p and m = 1..4 the row
+ * (p, m) is sum_k U[(p, k)] 2 sqrt(pi) alpha(w_k) H_m(w_k) with w_k = (v_k - v0_p)/s_p and v_k the
+ * centre of velocity bin k (midpoint quadrature of the orbit's LOSVD).  gh_v0_s: host npix x 2
+ * (v0, s > 0).  *U_gh_out receives a new matrix (rows nd + 5 npix, GH layout as in sw_project);
+ * U_hist is unchanged. */
+sw_status sw_reduce_gh(sw_ctx* ctx, const sw_matrix* U_hist, const double* gh_v0_s, sw_matrix** U_gh_out);
+/* Drift and status per orbit from the last sw_project (host arrays of n_orb, nullable). */
+sw_status sw_project_stats(sw_ctx* ctx, double* drift_out, uint8_t* status_out);
+
+/* Solve min_w 1/2 ||(U w - data) / errors||^2 + (lambda / N) ||w||^2 subject to w >= 0
+ * (Sec. 2.3, Eq. objective_function in its compact NNLS form) by ADMM on the Gram of the
+ * whitened matrix, followed by refinement with FP64 residuals against the stored U until the
+ * KKT conditions hold.  data, errors: M host values (errors > 0); weights_out: N host values;
+ * chi2_out: host [chi2_total, chi2_obs, reg] with chi2_total = ||(U w - data)/errors||^2,
+ * chi2_obs the same without the density rows (Sec. 2.4) and reg = (lambda/N)||w||^2.
+ * Returns SW_ENONCONV (with the best iterate) when the iteration caps are reached. */
+sw_status sw_solve_weights(sw_ctx* ctx, const sw_matrix* U, const double* data, const double* errors,
+                           double lambda, double* weights_out, double* chi2_out);
+/* As sw_solve_weights with data, errors, weights_out and chi2_out in device memory. */
+sw_status sw_solve_weights_device(sw_ctx* ctx, const sw_matrix* U, const double* data_dev,
+                                  const double* errors_dev, double lambda, double* weights_dev,
+                                  double* chi2_dev);
+
+/* Solver diagnostics of the last solve: out[0] ADMM iterations, out[1] refinement rounds,
+ * out[2] final KKT projected-gradient infinity norm (scaled by max |U~^T y~|), out[3] 1 if the
+ * Gram was formed in constraint space (M x M), 0 if in orbit space (N x N), out[4] number of
+ * exact active-set (polish) solves, out[5] 1 if the KKT tolerance was met (0: chi^2 stable). */
+sw_status sw_solve_info(sw_ctx* ctx, double* out6);
+
+/* ---- orbit matrix --------------------------------------------------------- */
+
+/* Shape (rows M, orbits N) and row blocks: blocks3 = {density rows, pixel rows, kinematic rows}. */
+sw_status sw_matrix_shape(const sw_matrix* U, int64_t* M, int64_t* N, int64_t* blocks3);
+/* Copy U to host as double, orbit-major: host_out[i * M + row] (N * M values). */
+sw_status sw_matrix_copy(const sw_matrix* U, double* host_out);
+/* Model observables for weights w: y_out = U w (host w of N values, host y_out of M values;
+ * FP64 accumulation over the stored matrix), e.g. the best-fit maps of a solve. */
+sw_status sw_matrix_apply(const sw_matrix* U, const double* w, double* y_out);
+/* Free a matrix returned by sw_project (NULL is a no-op).  May be called before or after
+ * sw_destroy of its context: a destroyed context's bookkeeping lives until its last matrix
+ * is freed. */
+sw_status sw_matrix_free(sw_matrix* U);
+
+/* ---- diagnostics and test hooks -------------------------------------------- */
+
+/* Trajectories of n orbits (host ics, n x 6) under the context's potential and precision with
+ * pattern speed omega_p and step dt: out is host n x (nsteps + 1) x 6 (inertial x, v at t_n). */
+sw_status sw_trajectory(sw_ctx* ctx, const double* ics, int64_t n, double omega_p, double dt, int64_t nsteps,
+                        double* out);
+/* Static bar-frame potential and acceleration of the context's potential at n host points
+ * (n x 3), in the context's precision: phi_out n, acc_out n x 3 (host). */
+sw_status sw_potential_eval(sw_ctx* ctx, const double* xyz, int64_t n, double* phi_out, double* acc_out);
+
+/* Per-kernel CUDA-event timing: when enabled every kernel launch of this context is bracketed by
+ * events on the context's stream.  sw_kernel_stats synchronises the stream and returns, for
+ * kernel index k (0 <= k < sw_kernel_count()), its name, launch count and total milliseconds
+ * since the last reset; sw_reset_stats clears them.  sw_launch_count returns the number of
+ * kernels this context has launched since its creation (timing on or off). */
+sw_status sw_set_profiling(sw_ctx* ctx, int enable);
+int sw_kernel_count(void);
+sw_status sw_kernel_stats(sw_ctx* ctx, int k, const char** name, int64_t* launches, double* total_ms);
+sw_status sw_reset_stats(sw_ctx* ctx);
+int64_t sw_launch_count(const sw_ctx* ctx);
+
+/* Tunables (value semantics in parentheses); unknown keys return SW_EINVAL:
+ *  "ej_every" (>= 1)        steps between Jacobi-energy checks in sw_project (default 1 in FP64, 8 in FP32)
+ *  "admm_max_iter" (>= 1)   ADMM iteration cap per run (default 400; a run also stops when its residual
+ *                           has not halved over five checks)
+ *  "admm_tol" (> 0)         ADMM stopping tolerance (default 1e-6)
+ *  "refine_max" (>= 0)      refinement rounds with FP64 residuals (default 8)
+ *  "kkt_tol" (> 0)          KKT tolerance relative to max |U~^T y~| (default 1e-6)
+ *  "check_every" (>= 1)     ADMM iterations between convergence checks (default 20)
+ *  "admm_rho" (> 0)         ADMM penalty of orbit i is admm_rho * ||column i of U~||^2 when the Gram is
+ *                           in orbit space (default 0.01)
+ *  "admm_rho_cspace" (> 0)  the same for the constraint-space (Woodbury) form (default 1)
+ *  "admm_alpha" (0, 2)      ADMM over-relaxation (default 1.6)
+ *  "chi2_tol" (>= 0)        refinement also stops when chi^2 changes by less than this, relative (1e-7)
+ *  "polish_max" (>= 0)      largest support the exact active-set polish handles (default 6000; 0 = off)
+ *  "polish_solves" (>= 0)   cap on reduced solves of one polish (default 60)
+ *  "gram_tensor_cores" (0/1) tcgen05 BF16 Gram in the FP32 form (default 1) */
+sw_status sw_set_option(sw_ctx* ctx, const char* key, double value);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+#ifdef __cplusplus
+}
+#endif
+#endif /* SW_H */

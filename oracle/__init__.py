@@ -251,6 +251,25 @@ def _gh_arg(obs: Obs, gh_v0s):
     return _dp(a)
 
 
+def reduce_gh(U_orbit_major: np.ndarray, nd: int, npix: int, nv: int, vmin: float, dv: float,
+              gh_v0s: np.ndarray) -> np.ndarray:
+    """Velocity-histogram rows -> Gauss-Hermite rows: row (p, m) = sum_k
+    U[(p, k)] * (2 sqrt(pi) alpha H_m)(w_k), w_k = (v_k - v0_p)/s_p at bin
+    centres v_k (the GH weights of Eq. GH applied to the gridded LOSVD, as the
+    paper's App. B does before comparing with data).  Input and output are
+    orbit-major (N, rows)."""
+    N = U_orbit_major.shape[0]
+    out = np.zeros((N, nd + 5 * npix))
+    out[:, :nd + npix] = U_orbit_major[:, :nd + npix]
+    vc = vmin + (np.arange(nv) + 0.5) * dv
+    for p in range(npix):
+        v0, s = gh_v0s[p]
+        W = np.array([gh_weights((v - v0) / s)[1:] for v in vc])          # (nv, 4)
+        hist = U_orbit_major[:, nd + npix + p * nv: nd + npix + (p + 1) * nv]
+        out[:, nd + npix + 4 * p: nd + npix + 4 * p + 4] = hist @ W
+    return out
+
+
 def set_threads(n: int) -> None:
     lib().orc_set_threads(int(n))
 

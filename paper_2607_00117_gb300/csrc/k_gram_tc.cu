@@ -1,0 +1,301 @@
+// Gram matrix of the whitened orbit matrix on the 5th-generation tensor cores
+// (the dense normal-equation contraction of the weight solve, Sec. 2.3):
+// C = A A^T with A (K x ldA, BF16, row-major = K-major operands), FP32
+// accumulation in tensor memory.  Only tiles on or below the diagonal are
+// computed; the Cholesky factorisation reads the lower triangle only.
+//
+// One CTA per 128 x 128 output tile.  Warp 0 issues TMA loads (128-byte
+// swizzle) of the two 128-row operand panels, 64 BF16 of the contraction per
+// stage, through a 4-stage mbarrier ring; warp 1 allocates 128 TMEM columns
+// and a single thread issues tcgen05.mma (M = 128, N = 128, K = 16) four times
+// per stage, committing each stage back to the producer; warps 2-5 read the
+// accumulator with tcgen05.ld and store FP32 rows.  Every wait is bounded by
+// a wall-clock deadline: on expiry the kernel records an error code, drains
+// its own copies, frees TMEM and returns.
+#include "sw_linalg.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+namespace sw {
+
+namespace gtc {
+
+constexpr int BM = 128, BN = 128, BKC = 64;  // tile rows/cols, BF16 per stage (128 bytes)
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BKC * 2, B_BYTES = BN * BKC * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int THREADS = 192;
+constexpr uint32_t TMEM_COLS = 128;
+constexpr uint64_t WAIT_NS = 4000000000ull;  // 4 s per wait
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
+{
+    if (mbar_try(b, parity)) return true;
+    const uint64_t t0 = now_ns();
+    while (!mbar_try(b, parity))
+        if (now_ns() - t0 > WAIT_NS) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            su32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+// K-major, 128-byte-swizzled UMMA shared-memory descriptor: 8-row atoms of
+// 128 bytes stacked at 1024-byte stride; start address in 16-byte units.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;            // descriptor version
+    d |= (uint64_t)2 << 61;            // SWIZZLE_128B
+    return d;
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N, M.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1) k_gram(const __grid_constant__ CUtensorMap map, int64_t K, int nk,
+                                                     float* __restrict__ C, int* err)
+{
+    extern __shared__ unsigned char smraw[];
+    // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
+    unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accum = empty + STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    // lower-triangular tile (ti >= tj) from the linear block index
+    const int64_t t = blockIdx.x;
+    int64_t ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    const int64_t tj = t - ti * (ti + 1) / 2;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        int issued = 0;
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % STAGES;
+            const uint32_t ph = (uint32_t)(kc / STAGES) & 1u;
+            if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
+                *abort_flag = 1;
+                break;
+            }
+            unsigned char* sa = base + s * STAGE_BYTES;
+            mbar_expect_tx(&full[s], STAGE_BYTES);
+            tma_load_2d(sa, &map, kc * BKC, (int)(ti * BM), &full[s]);
+            tma_load_2d(sa + A_BYTES, &map, kc * BKC, (int)(tj * BN), &full[s]);
+            issued = kc + 1;
+        }
+        if (*abort_flag) {
+            // drain this CTA's copies still in flight before leaving
+            for (int kc = issued - STAGES < 0 ? 0 : issued - STAGES; kc < issued; ++kc)
+                mbar_wait(&full[kc % STAGES], (uint32_t)(kc / STAGES) & 1u);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        const uint32_t idesc = idesc_bf16(BM, BN);
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % STAGES;
+            const uint32_t ph = (uint32_t)(kc / STAGES) & 1u;
+            if (*abort_flag || !mbar_wait(&full[s], ph)) {
+                *abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = su32(base + s * STAGE_BYTES);
+            const uint64_t da = smem_desc(sa), db = smem_desc(sa + A_BYTES);
+#pragma unroll
+            for (int k = 0; k < BKC / 16; ++k)
+                umma(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (kc | k) != 0);
+            umma_commit(&empty[s]);
+        }
+        umma_commit(accum);
+    } else if (warp >= 2) {
+        // ---- epilogue: TMEM -> registers -> global (lower tiles only)
+        const bool ok = mbar_wait(accum, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) *abort_flag = 1;
+        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        const int64_t gi = ti * BM + q * 32 + lane;
+        if (ok && !*abort_flag) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                const int64_t gj0 = tj * BN + c0;
+                if (gi < K) {
+                    float* dst = C + (size_t)gi * K + gj0;
+                    if (gj0 + 32 <= K && (K & 3) == 0) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4)
+                            *reinterpret_cast<float4*>(dst + j) =
+                                make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                            __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+                    } else {
+                        for (int j = 0; j < 32; ++j)
+                            if (gj0 + j < K) dst[j] = __uint_as_float(v[j]);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) atomicExch(err, 1);
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static bool encoder()
+{
+    if (g_encode) return true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return false;
+    }
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return true;
+}
+
+}  // namespace gtc
+
+bool gram_tc_available() { return gtc::encoder(); }
+
+cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, int64_t K, int64_t ldA, float* C, int* d_err)
+{
+    using namespace gtc;
+    if (K <= 0) return cudaSuccess;
+    if ((ldA % BKC) != 0 || ((uintptr_t)A & 15) != 0 || !encoder()) return cudaErrorInvalidValue;
+    if (K > 0x7fffff00LL || ldA > 0x7fffff00LL) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)ldA, (cuuint64_t)K};
+    cuuint64_t strides[1] = {(cuuint64_t)ldA * 2};
+    cuuint32_t box[2] = {BKC, BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)A, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int64_t T = (K + BM - 1) / BM;
+    const int64_t tiles = T * (T + 1) / 2;
+    const int nk = (int)(ldA / BKC);
+    LaunchTimer lt(ctx, K_GRAM_TC);
+    k_gram<<<(unsigned)tiles, THREADS, SMEM_BYTES, ctx_stream(ctx)>>>(map, K, nk, C, d_err);
+    return cudaGetLastError();
+}
+
+}  // namespace sw

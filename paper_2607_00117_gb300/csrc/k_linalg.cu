@@ -1,0 +1,954 @@
+// Dense linear algebra of the weight solve (arxiv 2607.00117 Sec. 2.3):
+// whitening, blocked Cholesky of the shifted Gram, explicit inverse of the
+// Cholesky factor, HBM-bound matrix-vector products, the fused ADMM update,
+// and FP64 residual / gradient / chi^2 passes over the stored orbit matrix.
+#include "sw_linalg.cuh"
+
+namespace sw {
+
+// ---------------------------------------------------------------------------
+// conversions
+// ---------------------------------------------------------------------------
+template <typename AT> __device__ __forceinline__ AT to_a(float v);
+template <> __device__ __forceinline__ __nv_bfloat16 to_a<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ float to_a<float>(float v) { return v; }
+template <typename AT> __device__ __forceinline__ AT to_a_d(double v);
+template <> __device__ __forceinline__ double to_a_d<double>(double v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 to_a_d<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
+template <> __device__ __forceinline__ float to_a_d<float>(double v) { return (float)v; }
+
+__device__ __forceinline__ float from_a(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float from_a(float v) { return v; }
+__device__ __forceinline__ double from_a(double v) { return v; }
+
+// ---------------------------------------------------------------------------
+// Whitening: A~ = diag(1/sigma) U diag(cs) (cs: per-orbit column scale),
+// written K-major for the Gram.
+// Orbit space: A[i * ldA + r] (rows are orbits, contraction over constraints).
+// Constraint space: A[r * ldA + i] (rows are constraints, contraction over orbits).
+// Padding columns up to ldA are zero.
+// ---------------------------------------------------------------------------
+template <typename T, typename AT>
+__global__ void k_whiten_orbit(const T* __restrict__ U, int64_t M, int64_t N, const double* __restrict__ inv_sig,
+                               const double* __restrict__ cs, AT* __restrict__ A, int64_t ldA)
+{
+    for (int64_t i = blockIdx.x; i < N; i += gridDim.x) {
+        const T* col = U + (size_t)i * M;
+        AT* row = A + (size_t)i * ldA;
+        const double c = cs[i];
+        for (int64_t r = threadIdx.x; r < ldA; r += blockDim.x)
+            row[r] = r < M ? to_a_d<AT>((double)col[r] * inv_sig[r] * c) : to_a_d<AT>(0.0);
+    }
+}
+
+template <typename T, typename AT>
+__global__ void k_whiten_transpose(const T* __restrict__ U, int64_t M, int64_t N, const double* __restrict__ inv_sig,
+                                   const double* __restrict__ cs, AT* __restrict__ A, int64_t ldA)
+{
+    __shared__ double tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int k = ty; k < 32; k += 8) {
+        int64_t i = i0 + k, r = r0 + tx;
+        tile[k][tx] = (i < N && r < M) ? (double)U[(size_t)i * M + r] * inv_sig[r] * cs[i] : 0.0;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        int64_t r = r0 + k, i = i0 + tx;
+        if (r < M && i < ldA) A[(size_t)r * ldA + i] = to_a_d<AT>(tile[tx][k]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SIMT GEMM: C[m x n] = beta C + alpha A op(B); A row-major m x k; BT: B is
+// n x k row-major (C = A B^T), else k x n row-major (C = A B).  LOWER skips
+// 64 x 64 tiles that lie strictly above the diagonal of the global matrix
+// (global row - global col = tile row - tile col + diag_off).
+// ---------------------------------------------------------------------------
+template <typename T, bool BT, bool LOWER>
+__global__ void __launch_bounds__(256) k_gemm(int64_t m, int64_t n, int64_t k, T alpha, const T* __restrict__ A,
+                                              int64_t lda, const T* __restrict__ B, int64_t ldb, T beta,
+                                              T* __restrict__ C, int64_t ldc, int64_t diag_off)
+{
+    constexpr int BM = 64, BN = 64, BK = 16;
+    const int64_t bm = (int64_t)blockIdx.y * BM, bn = (int64_t)blockIdx.x * BN;
+    if (LOWER && bm + BM - 1 + diag_off < bn) return;
+    __shared__ T As[BK][BM + 4];
+    __shared__ T Bs[BK][BN + 4];
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int64_t k0 = 0; k0 < k; k0 += BK) {
+        {   // A tile: 64 rows x 16 k; thread -> row t/4, k (t%4)*4 .. +4
+            int r = t >> 2, kq = (t & 3) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int64_t gr = bm + r, gk = k0 + kq + q;
+                As[kq + q][r] = (gr < m && gk < k) ? A[(size_t)gr * lda + gk] : T(0);
+            }
+        }
+        if (BT) {
+            int r = t >> 2, kq = (t & 3) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int64_t gc = bn + r, gk = k0 + kq + q;
+                Bs[kq + q][r] = (gc < n && gk < k) ? B[(size_t)gc * ldb + gk] : T(0);
+            }
+        } else {
+            int kk = t >> 4, cq = (t & 15) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int64_t gc = bn + cq + q, gk = k0 + kk;
+                Bs[kk][cq + q] = (gc < n && gk < k) ? B[(size_t)gk * ldb + gc] : T(0);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t gr = bm + ty * 4 + i;
+        if (gr >= m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t gc = bn + tx * 4 + j;
+            if (gc >= n) continue;
+            T* c = C + (size_t)gr * ldc + gc;
+            *c = (beta == T(0) ? T(0) : beta * *c) + alpha * acc[i][j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky pieces (block size NB = 64).
+// ---------------------------------------------------------------------------
+constexpr int NB = 64;
+
+// In-place Cholesky of the bs x bs diagonal block at (j0, j0).  A pivot that
+// is not positive records its global index + 1 in *info and is replaced by a
+// tiny positive value so the factorisation can finish.
+template <typename T>
+__global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t ld, int64_t j0, int bs, int* info)
+{
+    extern __shared__ unsigned char smraw[];
+    T (*a)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);
+    const int t = threadIdx.x;
+    for (int e = t; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        a[i][j] = (i < bs && j <= i) ? G[(size_t)(j0 + i) * ld + j0 + j] : T(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < bs; ++j) {
+        if (t == 0) {
+            T d = a[j][j];
+            if (!(d > T(0))) {
+                if (info) atomicCAS(info, 0, (int)(j0 + j + 1));
+                d = T(1e-30);
+            }
+            a[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        for (int i = j + 1 + t; i < bs; i += blockDim.x) a[i][j] /= a[j][j];
+        __syncthreads();
+        const int rem = bs - j - 1;
+        for (int e = t; e < rem * rem; e += blockDim.x) {
+            int i = j + 1 + e / rem, l = j + 1 + e % rem;
+            if (l <= i) a[i][l] -= a[i][j] * a[l][j];
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        if (i < bs && j <= i) G[(size_t)(j0 + i) * ld + j0 + j] = a[i][j];
+    }
+}
+
+// Rows below the diagonal block: A[i, j0:j0+bs] <- A[i, j0:j0+bs] L_kk^{-T}.
+template <typename T>
+__global__ void __launch_bounds__(64) k_trsm_panel(T* __restrict__ G, int64_t ld, int64_t j0, int bs, int64_t r0,
+                                                   int64_t r1)
+{
+    extern __shared__ unsigned char smraw[];
+    T (*L)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);
+    T (*X)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw + sizeof(T) * NB * (NB + 1));
+    const int t = threadIdx.x;
+    const int64_t rb = r0 + (int64_t)blockIdx.x * NB;
+    for (int e = t; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        L[i][j] = (i < bs && j <= i) ? G[(size_t)(j0 + i) * ld + j0 + j] : T(0);
+        int64_t gr = rb + i;
+        X[i][j] = (gr < r1 && j < bs) ? G[(size_t)gr * ld + j0 + j] : T(0);
+    }
+    __syncthreads();
+    // thread t solves row t: x_c = (a_c - sum_{l<c} x_l L[c][l]) / L[c][c]
+    for (int c = 0; c < bs; ++c) {
+        T s = X[t][c];
+        for (int l = 0; l < c; ++l) s -= X[t][l] * L[c][l];
+        X[t][c] = s / L[c][c];
+    }
+    __syncthreads();
+    for (int e = t; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        int64_t gr = rb + i;
+        if (gr < r1 && j < bs) G[(size_t)gr * ld + j0 + j] = X[i][j];
+    }
+}
+
+// Inverse of the lower-triangular bs x bs diagonal block: D = L_kk^{-1}
+// (full NB x NB storage, zeros above the diagonal and outside bs).
+template <typename T>
+__global__ void __launch_bounds__(64) k_trinv_diag(const T* __restrict__ G, int64_t ld, int64_t j0, int bs,
+                                                   T* __restrict__ D)
+{
+    extern __shared__ unsigned char smraw[];
+    T (*L)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);
+    T (*X)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw + sizeof(T) * NB * (NB + 1));
+    const int t = threadIdx.x;
+    for (int e = t; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        L[i][j] = (i < bs && j <= i) ? G[(size_t)(j0 + i) * ld + j0 + j] : T(0);
+        X[i][j] = T(0);
+    }
+    __syncthreads();
+    // thread t computes column t of the inverse by forward substitution
+    if (t < bs) {
+        X[t][t] = T(1) / L[t][t];
+        for (int i = t + 1; i < bs; ++i) {
+            T s = T(0);
+            for (int l = t; l < i; ++l) s += L[i][l] * X[l][t];
+            X[i][t] = -s / L[i][i];
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < NB * NB; e += blockDim.x) D[e] = X[e / NB][e % NB];
+}
+
+// Block row k of X (rows j0..j0+bs, columns 0..ncols): X_k <- D X_k.
+template <typename T>
+__global__ void __launch_bounds__(64) k_trmm_diag(T* __restrict__ X, int64_t ld, int64_t j0, int bs, int64_t ncols,
+                                                  const T* __restrict__ D)
+{
+    extern __shared__ unsigned char smraw[];
+    T (*Dm)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);
+    T (*S)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw + sizeof(T) * NB * (NB + 1));
+    const int t = threadIdx.x;
+    const int64_t c0 = (int64_t)blockIdx.x * NB;
+    for (int e = t; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        Dm[i][j] = D[e];
+        int64_t gc = c0 + j;
+        S[i][j] = (i < bs && gc < ncols) ? X[(size_t)(j0 + i) * ld + gc] : T(0);
+    }
+    __syncthreads();
+    // thread t owns column t of the slab (S is a private copy, so writing X is safe)
+    const int64_t gc = c0 + t;
+    if (gc >= ncols) return;
+    for (int i = 0; i < bs; ++i) {
+        T s = T(0);
+        for (int l = 0; l <= i; ++l) s += Dm[i][l] * S[l][t];
+        X[(size_t)(j0 + i) * ld + gc] = s;
+    }
+}
+
+template <typename T>
+__global__ void k_set_identity(T* __restrict__ X, int64_t K)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < K * K; e += (int64_t)gridDim.x * blockDim.x)
+        X[e] = (e / K == e % K) ? T(1) : T(0);
+}
+
+template <typename T>
+__global__ void k_shift_diag(T* __restrict__ G, int64_t K, double shift)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x)
+        G[(size_t)i * K + i] += (T)shift;
+}
+
+template <typename T>
+__global__ void k_trace(const T* __restrict__ G, int64_t K, double* out)
+{
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x)
+        s += (double)G[(size_t)i * K + i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// ---------------------------------------------------------------------------
+// Matrix-vector products on row-major A (rows x cols, leading dim lda).
+// rowdot: y[r] = alpha * sum_c A[r, c] x[c] + beta * y[r]   (one warp per row)
+// colcomb: y[c] += alpha * sum_r A[r, c] x[r]               (threads over
+//          columns, blockIdx.y splits the rows; partial sums by atomics)
+// lower: only c <= r contributes.
+// ---------------------------------------------------------------------------
+template <typename AT, typename XT, typename YT, typename ACC>
+__global__ void __launch_bounds__(256) k_rowdot(const AT* __restrict__ A, int64_t rows, int64_t cols, int64_t lda,
+                                                const XT* __restrict__ x, YT* __restrict__ y, double alpha,
+                                                double beta, int lower)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < rows; r += nwarp) {
+        const AT* a = A + (size_t)r * lda;
+        const int64_t n = lower ? (r + 1 < cols ? r + 1 : cols) : cols;
+        ACC s = ACC(0);
+        if constexpr (sizeof(AT) == 2) {
+            const __nv_bfloat162* a2 = reinterpret_cast<const __nv_bfloat162*>(a);
+            const int64_t n2 = n >> 1;
+            for (int64_t c = lane; c < n2; c += 32) {
+                float2 v = __bfloat1622float2(a2[c]);
+                s += (ACC)v.x * (ACC)x[2 * c] + (ACC)v.y * (ACC)x[2 * c + 1];
+            }
+            if ((n & 1) && lane == 0) s += (ACC)from_a(a[n - 1]) * (ACC)x[n - 1];
+        } else {
+            for (int64_t c = lane; c < n; c += 32) s += (ACC)from_a(a[c]) * (ACC)x[c];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) y[r] = (YT)(alpha * (double)s + (beta == 0.0 ? 0.0 : beta * (double)y[r]));
+    }
+}
+
+template <typename AT, typename XT, typename YT, typename ACC>
+__global__ void __launch_bounds__(256) k_colcomb(const AT* __restrict__ A, int64_t rows, int64_t cols, int64_t lda,
+                                                 const XT* __restrict__ x, YT* __restrict__ y, double alpha,
+                                                 int64_t rows_per_split, int lower)
+{
+    const int64_t c2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // column pair index
+    const int64_t c = 2 * c2;
+    if (c >= cols) return;
+    const int64_t r0 = (int64_t)blockIdx.y * rows_per_split;
+    int64_t r1 = r0 + rows_per_split;
+    if (r1 > rows) r1 = rows;
+    int64_t rs = r0;
+    if (lower && rs < c) rs = c;
+    ACC s0 = ACC(0), s1 = ACC(0);
+    const bool two = c + 1 < cols;
+    for (int64_t r = rs; r < r1; ++r) {
+        const AT* a = A + (size_t)r * lda + c;
+        ACC xr = (ACC)x[r];
+        if constexpr (sizeof(AT) == 2) {
+            if (two) {
+                float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(a));
+                s0 += (ACC)v.x * xr;
+                s1 += (ACC)v.y * xr;
+            } else {
+                s0 += (ACC)from_a(a[0]) * xr;
+            }
+        } else {
+            s0 += (ACC)from_a(a[0]) * xr;
+            if (two && (!lower || r >= c + 1)) s1 += (ACC)from_a(a[1]) * xr;
+        }
+    }
+    if (lower && sizeof(AT) == 2) {
+        // bf16 triangular use does not occur; keep the general path exact
+    }
+    if (r1 > rs) {
+        atomicAdd(&y[c], (YT)(alpha * (double)s0));
+        if (two) atomicAdd(&y[c + 1], (YT)(alpha * (double)s1));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ADMM (Sec. 2.3) with a per-orbit penalty P = diag(rho_i): the quadratic step
+// w = (H~ + P)^{-1} (q' + P (z - u)) is applied as w = s o y with
+// s = (2 lam/N + rho_i)^{-1/2} (see sw_solve.cu), then, over-relaxed by alpha,
+// z = max(0, alpha w + (1 - alpha) z + u), u += alpha w + (1 - alpha) z_old - z,
+// and the next scaled right-hand side rs = s o (q' + P (z - u)).
+// Constraint space passes v and forms y = rs - v.
+// stats (nullable): max |w - z| d, max |z - z_prev| d, max z d (float bits),
+// with d_i = ||column i of U~||, i.e. in units of the equilibrated problem.
+// ---------------------------------------------------------------------------
+template <typename GT>
+__global__ void k_admm_update(int64_t N, const GT* __restrict__ y, const GT* __restrict__ v,
+                              const GT* __restrict__ sc, const GT* __restrict__ rho_i, const GT* __restrict__ d,
+                              const GT* __restrict__ qp, GT alpha, GT* __restrict__ rs, GT* __restrict__ z,
+                              GT* __restrict__ u, unsigned* stats)
+{
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const GT si = sc[i];
+        const GT w = v ? si * (rs[i] - v[i]) : si * y[i];
+        const GT zo = z[i], uo = u[i];
+        const GT wh = alpha * w + (GT(1) - alpha) * zo;
+        GT zn = wh + uo;
+        zn = zn > GT(0) ? zn : GT(0);
+        const GT un = uo + wh - zn;
+        z[i] = zn;
+        u[i] = un;
+        rs[i] = si * (qp[i] + rho_i[i] * (zn - un));
+        const GT di = d[i];
+        m0 = fmaxf(m0, (float)(fabs((double)(w - zn)) * (double)di));
+        m1 = fmaxf(m1, (float)(fabs((double)(zn - zo)) * (double)di));
+        m2 = fmaxf(m2, (float)((double)zn * (double)di));
+    }
+    if (!stats) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(stats + 0, __float_as_uint(m0));
+        atomicMax(stats + 1, __float_as_uint(m1));
+        atomicMax(stats + 2, __float_as_uint(m2));
+    }
+}
+
+// rs = s o (q' + P (z - u)) (initialisation)
+template <typename GT>
+__global__ void k_admm_init(int64_t N, const GT* __restrict__ qp, const GT* __restrict__ z, const GT* __restrict__ u,
+                            const GT* __restrict__ sc, const GT* __restrict__ rho_i, GT* __restrict__ rs)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        rs[i] = sc[i] * (qp[i] + rho_i[i] * (z[i] - u[i]));
+}
+
+// Per-orbit ADMM scaling from the exact column norms h_i = ||U~ e_i||^2:
+// rho_i = rho h_i, Lambda_i = 2 lam/N + rho_i (floored), s_i = Lambda_i^{-1/2}.
+template <typename GT>
+__global__ void k_admm_scales(int64_t N, const double* __restrict__ h, double two_lam_n, double rho, double floor_,
+                              double* __restrict__ s64, GT* __restrict__ s, GT* __restrict__ rho_i, GT* __restrict__ d)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double hi = h[i];
+        double lam_i = two_lam_n + rho * hi;
+        if (!(lam_i > floor_)) lam_i = 1.0;   // an empty orbit with lambda = 0: its column is zero
+        double si = 1.0 / sqrt(lam_i);
+        s64[i] = si;
+        s[i] = (GT)si;
+        rho_i[i] = (GT)(rho * hi);
+        d[i] = (GT)sqrt(hi);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 passes over the stored orbit matrix (orbit-major, column i at U + i M).
+// ---------------------------------------------------------------------------
+// acc[r] += sum_i U[i, r] w[i]   (threads over rows r, blockIdx.y splits orbits)
+template <typename T>
+__global__ void __launch_bounds__(256) k_u_times_w(const T* __restrict__ U, int64_t M, int64_t N,
+                                                   const double* __restrict__ w, double* __restrict__ acc,
+                                                   int64_t orbits_per_split)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    const int64_t i0 = (int64_t)blockIdx.y * orbits_per_split;
+    int64_t i1 = i0 + orbits_per_split;
+    if (i1 > N) i1 = N;
+    double s = 0.0;
+    for (int64_t i = i0; i < i1; ++i) {
+        double wi = w[i];
+        if (wi != 0.0) s += (double)U[(size_t)i * M + r] * wi;
+    }
+    if (i1 > i0) atomicAdd(acc + r, s);
+}
+
+// e[r] = (y[r] - acc[r]) * inv_sig[r]; also xs[r] = e[r] * inv_sig[r].
+__global__ void k_residual(int64_t M, const double* __restrict__ y, const double* __restrict__ acc,
+                           const double* __restrict__ inv_sig, double* __restrict__ e, double* __restrict__ xs)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < M; r += (int64_t)gridDim.x * blockDim.x) {
+        double v = (y[r] - acc[r]) * inv_sig[r];
+        e[r] = v;
+        xs[r] = v * inv_sig[r];
+    }
+}
+
+// out[i] = sum_r U[i, r] xs[r]  (one warp per orbit)
+template <typename T>
+__global__ void __launch_bounds__(256) k_ut_times_x(const T* __restrict__ U, int64_t M, int64_t N,
+                                                    const double* __restrict__ xs, double* __restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < N; i += nwarp) {
+        const T* col = U + (size_t)i * M;
+        double s = 0.0;
+        for (int64_t r = lane; r < M; r += 32) s += (double)col[r] * xs[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[i] = s;
+    }
+}
+
+// h[i] = sum_r (U[i, r] inv_sig[r])^2  (one warp per orbit)
+template <typename T>
+__global__ void __launch_bounds__(256) k_colnorm2(const T* __restrict__ U, int64_t M, int64_t N,
+                                                  const double* __restrict__ inv_sig, double* __restrict__ h)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < N; i += nwarp) {
+        const T* col = U + (size_t)i * M;
+        double s = 0.0;
+        for (int64_t r = lane; r < M; r += 32) {
+            double v = (double)col[r] * inv_sig[r];
+            s += v * v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) h[i] = s;
+    }
+}
+
+// KKT of min 1/2 w^T H w - q^T w, w >= 0 with the exact gradient
+// grad = H w - q = -(U~^T e) + (2 lam / N) w  (e = y~ - U~ w):
+// projected gradient pg = grad where w > 0, min(grad, 0) where w = 0.
+// out: g_neg[i] = U~^T e - (2 lam/N) w (the negative gradient) and atomic max |pg| (float bits)
+__global__ void k_kkt(int64_t N, const double* __restrict__ ute, const double* __restrict__ w, double two_lam_n,
+                      double* __restrict__ gneg, unsigned long long* pgmax)
+{
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double g = ute[i] - two_lam_n * w[i];
+        gneg[i] = g;
+        double grad = -g;
+        double pg = w[i] > 0.0 ? grad : fmin(grad, 0.0);
+        m = fmax(m, fabs(pg));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(pgmax, (unsigned long long)__double_as_longlong(m));
+}
+
+// chi2 parts: [sum e^2, sum_{r >= nd} e^2] and reg sum w^2
+__global__ void k_chi2(int64_t M, int64_t nd, const double* __restrict__ e, int64_t N, const double* __restrict__ w,
+                       double* __restrict__ out3)
+{
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < M; r += (int64_t)gridDim.x * blockDim.x) {
+        double v = e[r] * e[r];
+        a += v;
+        if (r >= nd) b += v;
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        c += w[i] * w[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out3 + 0, a);
+        atomicAdd(out3 + 1, b);
+        atomicAdd(out3 + 2, c);
+    }
+}
+
+// inv_sig = 1/sigma, yt = y / sigma (both FP64); flags a non-positive sigma.
+__global__ void k_prep_data(int64_t M, const double* __restrict__ sigma, const double* __restrict__ y,
+                            double* __restrict__ inv_sig, double* __restrict__ ys, int* bad)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < M; r += (int64_t)gridDim.x * blockDim.x) {
+        double s = sigma[r];
+        if (!(s > 0.0) || !isfinite(s) || !isfinite(y[r])) { atomicExch(bad, 1); s = 1.0; }
+        inv_sig[r] = 1.0 / s;
+        ys[r] = y[r] / s * (1.0 / s);   // y / sigma^2, the weight of U in q = U~^T y~
+    }
+}
+
+// elementwise helpers
+template <typename A, typename B>
+__global__ void k_convert(int64_t n, const A* __restrict__ a, B* __restrict__ b)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (B)a[i];
+}
+
+// q' = t / s + g + (2 lam / N) w with t = A^T A (w / s) the Gram-precision
+// product of the column-scaled matrix; warm start z = w, u = P^{-1} g.
+template <typename GT>
+__global__ void k_refine_rhs(int64_t N, const GT* __restrict__ t, const double* __restrict__ gneg,
+                             const double* __restrict__ w, const double* __restrict__ s64, double two_lam_n,
+                             const GT* __restrict__ rho_i, GT* __restrict__ qp, GT* __restrict__ z, GT* __restrict__ u)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        qp[i] = (GT)((double)t[i] / s64[i] + gneg[i] + two_lam_n * w[i]);
+        z[i] = (GT)w[i];
+        const double ri = (double)rho_i[i];
+        u[i] = (GT)(ri > 0.0 ? gneg[i] / ri : 0.0);
+    }
+}
+
+// out = a / b elementwise (double in, GT out)
+template <typename GT>
+__global__ void k_div_to(int64_t n, const double* __restrict__ a, const double* __restrict__ b, GT* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (GT)(a[i] / b[i]);
+}
+
+// R[k, r] = U[idx[k], r] * inv_sig[r]  (rows of the whitened matrix, FP64)
+template <typename T>
+__global__ void k_gather_rows(const T* __restrict__ U, int64_t M, const int64_t* __restrict__ idx, int64_t nP,
+                              const double* __restrict__ inv_sig, double* __restrict__ R)
+{
+    for (int64_t k = blockIdx.x; k < nP; k += gridDim.x) {
+        const T* col = U + (size_t)idx[k] * M;
+        double* row = R + (size_t)k * M;
+        for (int64_t r = threadIdx.x; r < M; r += blockDim.x) row[r] = (double)col[r] * inv_sig[r];
+    }
+}
+
+__global__ void k_gather_vec(const double* __restrict__ a, const int64_t* __restrict__ idx, int64_t n,
+                             double* __restrict__ out)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = a[idx[k]];
+}
+
+// ===========================================================================
+// host launchers
+// ===========================================================================
+static inline unsigned cap_grid(int64_t n, int b, int64_t cap = 1 << 20)
+{
+    int64_t g = (n + b - 1) / b;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+template <typename T, typename AT>
+cudaError_t whiten(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* inv_sig, const double* cs, AT* A,
+                   int64_t ldA, bool orbit_space)
+{
+    LaunchTimer lt(ctx, K_WHITEN);
+    if (orbit_space) {
+        k_whiten_orbit<T, AT><<<cap_grid(N, 1, 65536), 256, 0, ctx_stream(ctx)>>>(U, M, N, inv_sig, cs, A, ldA);
+    } else {
+        dim3 grid((unsigned)((ldA + 31) / 32), (unsigned)((M + 31) / 32));
+        k_whiten_transpose<T, AT><<<grid, dim3(32, 8), 0, ctx_stream(ctx)>>>(U, M, N, inv_sig, cs, A, ldA);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t colnorm2(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* inv_sig, double* h)
+{
+    LaunchTimer lt(ctx, K_MISC);
+    k_colnorm2<T><<<cap_grid(N * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, inv_sig, h);
+    return cudaGetLastError();
+}
+
+template <typename GT>
+cudaError_t admm_scales(sw_ctx* ctx, int64_t N, const double* h, double two_lam_n, double rho, double floor_,
+                        double* s64, GT* s, GT* rho_i, GT* d)
+{
+    LaunchTimer lt(ctx, K_MISC);
+    k_admm_scales<GT><<<cap_grid(N, 256, 4096), 256, 0, ctx_stream(ctx)>>>(N, h, two_lam_n, rho, floor_, s64, s,
+                                                                           rho_i, d);
+    return cudaGetLastError();
+}
+
+template <typename GT>
+cudaError_t div_to(sw_ctx* ctx, int64_t n, const double* a, const double* b, GT* out)
+{
+    LaunchTimer lt(ctx, K_MISC);
+    k_div_to<GT><<<cap_grid(n, 256, 4096), 256, 0, ctx_stream(ctx)>>>(n, a, b, out);
+    return cudaGetLastError();
+}
+
+template <typename T, bool BT, bool LOWER>
+cudaError_t gemm(sw_ctx* ctx, int kid, int64_t m, int64_t n, int64_t k, T alpha, const T* A, int64_t lda, const T* B,
+                 int64_t ldb, T beta, T* C, int64_t ldc, int64_t diag_off)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    LaunchTimer lt(ctx, kid);
+    dim3 grid((unsigned)((n + 63) / 64), (unsigned)((m + 63) / 64));
+    k_gemm<T, BT, LOWER><<<grid, 256, 0, ctx_stream(ctx)>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, diag_off);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static size_t smem2() { return 2 * sizeof(T) * NB * (NB + 1); }
+
+template <typename T>
+cudaError_t cholesky(sw_ctx* ctx, T* G, int64_t K, int* d_info)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<T>());
+        cudaFuncSetAttribute(k_trsm_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<T>());
+        attr_set = true;
+    }
+    cudaStream_t st = ctx_stream(ctx);
+    for (int64_t j0 = 0; j0 < K; j0 += NB) {
+        int bs = (int)(K - j0 < NB ? K - j0 : NB);
+        {
+            LaunchTimer lt(ctx, K_POTRF_DIAG);
+            k_potrf_diag<T><<<1, 256, smem2<T>() / 2, st>>>(G, K, j0, bs, d_info);
+        }
+        int64_t r0 = j0 + bs, r1 = K;
+        if (r1 > r0) {
+            {
+                LaunchTimer lt(ctx, K_TRSM_PANEL);
+                k_trsm_panel<T><<<(unsigned)((r1 - r0 + NB - 1) / NB), 64, smem2<T>(), st>>>(G, K, j0, bs, r0, r1);
+            }
+            // trailing lower update: G[r0:, r0:] -= P P^T with P = G[r0:, j0:j0+bs]
+            cudaError_t e = gemm<T, true, true>(ctx, K_SYRK_UPDATE, r1 - r0, r1 - r0, bs, T(-1), G + (size_t)r0 * K + j0,
+                                                K, G + (size_t)r0 * K + j0, K, T(1), G + (size_t)r0 * K + r0, K, 0);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaGetLastError();
+}
+
+// X = L^{-1} for the lower-triangular Cholesky factor L stored in G.
+template <typename T>
+cudaError_t tri_inverse(sw_ctx* ctx, const T* G, T* X, T* D, int64_t K)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_trinv_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<T>());
+        cudaFuncSetAttribute(k_trmm_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<T>());
+        attr_set = true;
+    }
+    cudaStream_t st = ctx_stream(ctx);
+    {
+        LaunchTimer lt(ctx, K_MISC);
+        k_set_identity<T><<<cap_grid(K * K, 256, 65536), 256, 0, st>>>(X, K);
+    }
+    for (int64_t j0 = 0; j0 < K; j0 += NB) {
+        int bs = (int)(K - j0 < NB ? K - j0 : NB);
+        int64_t ncols = j0 + bs;
+        {
+            LaunchTimer lt(ctx, K_TRINV_DIAG);
+            k_trinv_diag<T><<<1, 64, smem2<T>(), st>>>(G, K, j0, bs, D);
+        }
+        {
+            LaunchTimer lt(ctx, K_TRINV_DIAG);
+            k_trmm_diag<T><<<(unsigned)((ncols + NB - 1) / NB), 64, smem2<T>(), st>>>(X, K, j0, bs, ncols, D);
+        }
+        int64_t r0 = j0 + bs;
+        if (r0 < K) {
+            cudaError_t e = gemm<T, false, false>(ctx, K_TRINV_UPDATE, K - r0, ncols, bs, T(-1), G + (size_t)r0 * K + j0,
+                                                  K, X + (size_t)j0 * K, K, T(1), X + (size_t)r0 * K, K, 0);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t shift_and_trace(sw_ctx* ctx, T* G, int64_t K, double* d_trace, double shift)
+{
+    LaunchTimer lt(ctx, K_SHIFT);
+    if (d_trace) k_trace<T><<<cap_grid(K, 256, 1024), 256, 0, ctx_stream(ctx)>>>(G, K, d_trace);
+    else k_shift_diag<T><<<cap_grid(K, 256, 1024), 256, 0, ctx_stream(ctx)>>>(G, K, shift);
+    return cudaGetLastError();
+}
+
+template <typename AT, typename XT, typename YT, typename ACC>
+cudaError_t rowdot(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t cols, int64_t lda, const XT* x, YT* y,
+                   double alpha, double beta, bool lower)
+{
+    if (rows <= 0) return cudaSuccess;
+    LaunchTimer lt(ctx, kid);
+    k_rowdot<AT, XT, YT, ACC><<<cap_grid(rows * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(A, rows, cols, lda, x,
+                                                                                               y, alpha, beta, lower);
+    return cudaGetLastError();
+}
+
+// y must be pre-initialised (it is accumulated into)
+template <typename AT, typename XT, typename YT, typename ACC>
+cudaError_t colcomb(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t cols, int64_t lda, const XT* x, YT* y,
+                    double alpha, bool lower)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    LaunchTimer lt(ctx, kid);
+    int64_t pairs = (cols + 1) / 2;
+    unsigned gx = (unsigned)((pairs + 255) / 256);
+    // enough blocks to fill the GPU several times over, rows split evenly
+    int64_t want = (152 * 16 + gx - 1) / gx;
+    if (want < 1) want = 1;
+    int64_t rps = (rows + want - 1) / want;
+    if (rps < 32) rps = 32;
+    unsigned gy = (unsigned)((rows + rps - 1) / rps);
+    k_colcomb<AT, XT, YT, ACC><<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(A, rows, cols, lda, x, y, alpha, rps, lower);
+    return cudaGetLastError();
+}
+
+template <typename GT>
+cudaError_t admm_update(sw_ctx* ctx, int64_t N, const GT* y, const GT* v, const GT* s, const GT* rho_i, const GT* d,
+                        const GT* qp, double alpha, GT* rs, GT* z, GT* u, unsigned* stats)
+{
+    LaunchTimer lt(ctx, K_ADMM_UPDATE);
+    k_admm_update<GT><<<cap_grid(N, 256, 152 * 8), 256, 0, ctx_stream(ctx)>>>(N, y, v, s, rho_i, d, qp, (GT)alpha,
+                                                                              rs, z, u, stats);
+    return cudaGetLastError();
+}
+
+template <typename GT>
+cudaError_t admm_init(sw_ctx* ctx, int64_t N, const GT* qp, const GT* z, const GT* u, const GT* s, const GT* rho_i,
+                      GT* rs)
+{
+    LaunchTimer lt(ctx, K_MISC);
+    k_admm_init<GT><<<cap_grid(N, 256, 152 * 8), 256, 0, ctx_stream(ctx)>>>(N, qp, z, u, s, rho_i, rs);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t u_times_w(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* w, double* acc)
+{
+    LaunchTimer lt(ctx, K_RESID);
+    unsigned gx = (unsigned)((M + 255) / 256);
+    int64_t want = (152 * 16 + gx - 1) / gx;
+    if (want < 1) want = 1;
+    int64_t ops = (N + want - 1) / want;
+    if (ops < 16) ops = 16;
+    unsigned gy = (unsigned)((N + ops - 1) / ops);
+    k_u_times_w<T><<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(U, M, N, w, acc, ops);
+    return cudaGetLastError();
+}
+
+cudaError_t residual(sw_ctx* ctx, int64_t M, const double* y, const double* acc, const double* inv_sig, double* e,
+                     double* xs)
+{
+    LaunchTimer lt(ctx, K_RESID);
+    k_residual<<<cap_grid(M, 256, 4096), 256, 0, ctx_stream(ctx)>>>(M, y, acc, inv_sig, e, xs);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t ut_times_x(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* xs, double* out)
+{
+    LaunchTimer lt(ctx, K_GRAD);
+    k_ut_times_x<T><<<cap_grid(N * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xs, out);
+    return cudaGetLastError();
+}
+
+cudaError_t kkt(sw_ctx* ctx, int64_t N, const double* ute, const double* w, double two_lam_n, double* gneg,
+                unsigned long long* pgmax)
+{
+    LaunchTimer lt(ctx, K_GRAD);
+    k_kkt<<<cap_grid(N, 256, 4096), 256, 0, ctx_stream(ctx)>>>(N, ute, w, two_lam_n, gneg, pgmax);
+    return cudaGetLastError();
+}
+
+cudaError_t chi2(sw_ctx* ctx, int64_t M, int64_t nd, const double* e, int64_t N, const double* w, double* out3)
+{
+    LaunchTimer lt(ctx, K_CHI2);
+    int64_t mx = M > N ? M : N;
+    k_chi2<<<cap_grid(mx, 256, 4096), 256, 0, ctx_stream(ctx)>>>(M, nd, e, N, w, out3);
+    return cudaGetLastError();
+}
+
+cudaError_t prep_data(sw_ctx* ctx, int64_t M, const double* sigma, const double* y, double* inv_sig, double* ys,
+                      int* bad)
+{
+    LaunchTimer lt(ctx, K_MISC);
+    k_prep_data<<<cap_grid(M, 256, 4096), 256, 0, ctx_stream(ctx)>>>(M, sigma, y, inv_sig, ys, bad);
+    return cudaGetLastError();
+}
+
+template <typename A, typename B>
+cudaError_t convert(sw_ctx* ctx, int64_t n, const A* a, B* b)
+{
+    LaunchTimer lt(ctx, K_MISC);
+    k_convert<A, B><<<cap_grid(n, 256, 4096), 256, 0, ctx_stream(ctx)>>>(n, a, b);
+    return cudaGetLastError();
+}
+
+template <typename GT>
+cudaError_t refine_rhs(sw_ctx* ctx, int64_t N, const GT* t, const double* gneg, const double* w, const double* s64,
+                       double two_lam_n, const GT* rho_i, GT* qp, GT* z, GT* u)
+{
+    LaunchTimer lt(ctx, K_MISC);
+    k_refine_rhs<GT><<<cap_grid(N, 256, 4096), 256, 0, ctx_stream(ctx)>>>(N, t, gneg, w, s64, two_lam_n, rho_i, qp, z,
+                                                                          u);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gather_rows(sw_ctx* ctx, const T* U, int64_t M, const int64_t* idx, int64_t nP, const double* inv_sig,
+                        double* R)
+{
+    if (nP <= 0) return cudaSuccess;
+    LaunchTimer lt(ctx, K_MISC);
+    k_gather_rows<T><<<cap_grid(nP, 1, 65536), 256, 0, ctx_stream(ctx)>>>(U, M, idx, nP, inv_sig, R);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_vec(sw_ctx* ctx, const double* a, const int64_t* idx, int64_t n, double* out)
+{
+    if (n <= 0) return cudaSuccess;
+    LaunchTimer lt(ctx, K_MISC);
+    k_gather_vec<<<cap_grid(n, 256, 4096), 256, 0, ctx_stream(ctx)>>>(a, idx, n, out);
+    return cudaGetLastError();
+}
+
+// ---- explicit instantiations -------------------------------------------------
+template cudaError_t gather_rows<float>(sw_ctx*, const float*, int64_t, const int64_t*, int64_t, const double*,
+                                        double*);
+template cudaError_t gather_rows<double>(sw_ctx*, const double*, int64_t, const int64_t*, int64_t, const double*,
+                                         double*);
+#define SW_WH(T, AT) \
+    template cudaError_t whiten<T, AT>(sw_ctx*, const T*, int64_t, int64_t, const double*, const double*, AT*, int64_t, bool);
+SW_WH(float, __nv_bfloat16)
+SW_WH(float, float)
+SW_WH(double, double)
+template cudaError_t gemm<float, true, true>(sw_ctx*, int, int64_t, int64_t, int64_t, float, const float*, int64_t,
+                                             const float*, int64_t, float, float*, int64_t, int64_t);
+template cudaError_t gemm<double, true, true>(sw_ctx*, int, int64_t, int64_t, int64_t, double, const double*,
+                                              int64_t, const double*, int64_t, double, double*, int64_t, int64_t);
+template cudaError_t cholesky<float>(sw_ctx*, float*, int64_t, int*);
+template cudaError_t cholesky<double>(sw_ctx*, double*, int64_t, int*);
+template cudaError_t tri_inverse<float>(sw_ctx*, const float*, float*, float*, int64_t);
+template cudaError_t tri_inverse<double>(sw_ctx*, const double*, double*, double*, int64_t);
+template cudaError_t shift_and_trace<float>(sw_ctx*, float*, int64_t, double*, double);
+template cudaError_t shift_and_trace<double>(sw_ctx*, double*, int64_t, double*, double);
+template cudaError_t rowdot<__nv_bfloat16, float, float, float>(sw_ctx*, int, const __nv_bfloat16*, int64_t, int64_t,
+                                                               int64_t, const float*, float*, double, double, bool);
+template cudaError_t colcomb<__nv_bfloat16, float, float, float>(sw_ctx*, int, const __nv_bfloat16*, int64_t,
+                                                                int64_t, int64_t, const float*, float*, double, bool);
+template cudaError_t rowdot<float, float, float, float>(sw_ctx*, int, const float*, int64_t, int64_t, int64_t,
+                                                       const float*, float*, double, double, bool);
+template cudaError_t colcomb<float, float, float, float>(sw_ctx*, int, const float*, int64_t, int64_t, int64_t,
+                                                        const float*, float*, double, bool);
+template cudaError_t rowdot<double, double, double, double>(sw_ctx*, int, const double*, int64_t, int64_t, int64_t,
+                                                           const double*, double*, double, double, bool);
+template cudaError_t colcomb<double, double, double, double>(sw_ctx*, int, const double*, int64_t, int64_t, int64_t,
+                                                            const double*, double*, double, bool);
+#define SW_GT(GT)                                                                                                  \
+    template cudaError_t admm_update<GT>(sw_ctx*, int64_t, const GT*, const GT*, const GT*, const GT*, const GT*,   \
+                                         const GT*, double, GT*, GT*, GT*, unsigned*);                             \
+    template cudaError_t admm_init<GT>(sw_ctx*, int64_t, const GT*, const GT*, const GT*, const GT*, const GT*, GT*); \
+    template cudaError_t admm_scales<GT>(sw_ctx*, int64_t, const double*, double, double, double, double*, GT*, GT*, \
+                                         GT*);                                                                     \
+    template cudaError_t refine_rhs<GT>(sw_ctx*, int64_t, const GT*, const double*, const double*, const double*,   \
+                                        double, const GT*, GT*, GT*, GT*);                                         \
+    template cudaError_t div_to<GT>(sw_ctx*, int64_t, const double*, const double*, GT*);
+SW_GT(float)
+SW_GT(double)
+template cudaError_t u_times_w<float>(sw_ctx*, const float*, int64_t, int64_t, const double*, double*);
+template cudaError_t u_times_w<double>(sw_ctx*, const double*, int64_t, int64_t, const double*, double*);
+template cudaError_t ut_times_x<float>(sw_ctx*, const float*, int64_t, int64_t, const double*, double*);
+template cudaError_t ut_times_x<double>(sw_ctx*, const double*, int64_t, int64_t, const double*, double*);
+template cudaError_t colnorm2<float>(sw_ctx*, const float*, int64_t, int64_t, const double*, double*);
+template cudaError_t colnorm2<double>(sw_ctx*, const double*, int64_t, int64_t, const double*, double*);
+template cudaError_t convert<double, float>(sw_ctx*, int64_t, const double*, float*);
+template cudaError_t convert<float, double>(sw_ctx*, int64_t, const float*, double*);
+template cudaError_t convert<double, double>(sw_ctx*, int64_t, const double*, double*);
+
+}  // namespace sw

@@ -1,0 +1,105 @@
+// Context and matrix objects behind the opaque C-ABI handles (internal).
+#pragma once
+#include "sw_common.cuh"
+
+#include <string>
+#include <vector>
+
+struct sw_matrix;
+
+namespace sw {
+
+struct Options {
+    int ej_every = 1;            // Jacobi-energy check interval (steps) in the projection pass
+    int admm_max_iter = 400;     // ADMM iteration cap per run
+    double admm_tol = 1e-6;      // ADMM stop: ||w-z||inf, rho||z-z_prev||inf <= tol * max(1, ||z||inf)
+    int refine_max = 8;          // refinement rounds with FP64 residuals
+    double kkt_tol = 1e-6;       // KKT stop: ||P(grad)||inf <= kkt_tol * max|q|
+    int check_every = 20;        // ADMM iterations between host convergence checks
+    double admm_rho = 0.01;      // ADMM penalty relative to each orbit's Gram diagonal (orbit space)
+    double admm_rho_cs = 1.0;    // the same in constraint space (the Woodbury form cancels digits for small rho)
+    double admm_alpha = 1.6;     // over-relaxation
+    double chi2_tol = 1e-7;      // refinement also stops once chi^2 changes by less than this (relative)
+    int polish_max = 6000;       // largest support solved exactly by the active-set polish (0: off)
+    int polish_solves = 60;      // cap on reduced solves per polish
+    bool gram_tc = true;         // tcgen05 BF16 Gram (FP32 path); false: SIMT FP32 Gram
+};
+
+// Device workspace of the weight solve, sized for the largest problem seen.
+struct SolveWS {
+    void* A = nullptr; size_t A_cap = 0;          // whitened matrix (BF16 or FP64), K-major for the Gram
+    void* G = nullptr; size_t G_cap = 0;          // K x K Gram, Cholesky factor in place
+    void* X = nullptr; size_t X_cap = 0;          // K x K inverse of the Cholesky factor
+    void* D = nullptr; size_t D_cap = 0;          // nb x nb diagonal-block scratch
+    void* vec = nullptr; size_t vec_cap = 0;      // vectors
+    void* R = nullptr; size_t R_cap = 0;          // polish: gathered whitened rows (FP64)
+    void* H = nullptr; size_t H_cap = 0;          // polish: reduced normal matrix (FP64)
+    void* Hi = nullptr; size_t Hi_cap = 0;        // polish: inverse of its Cholesky factor
+    void* pv = nullptr; size_t pv_cap = 0;        // polish: index list and vectors
+    const sw_matrix* A_of = nullptr;              // which matrix A was built from
+    void release();
+    void forget_matrix(const sw_matrix* U) { if (A_of == U) A_of = nullptr; }
+};
+
+struct LaunchRec {
+    int id;
+    cudaEvent_t a, b;
+};
+
+}  // namespace sw
+
+struct sw_ctx {
+    int device = 0;
+    sw_precision prec = SW_FP32_KAHAN;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    sw::Options opt;
+    // potential
+    sw_potential_params pot{};
+    bool has_pot = false;
+    double Mdm = 0.0, rs = 1.0;
+    // orbit library
+    int64_t n_orb = 0, nsteps = 0;
+    double omega = 0.0, dt = 0.0;
+    bool has_lib = false;
+    void* d_soa = nullptr; size_t soa_cap = 0;
+    void* d_cs = nullptr; size_t cs_cap = 0;
+    double* d_aos = nullptr; size_t aos_cap = 0;
+    double* d_drift = nullptr; size_t drift_cap = 0;
+    uint8_t* d_status = nullptr; size_t status_cap = 0;
+    unsigned long long* d_stats = nullptr;
+    void* d_ghtab = nullptr; size_t ghtab_cap = 0;
+    int64_t last_proj_n = 0;
+    // solve
+    sw::SolveWS solve_ws;
+    double solve_info[6] = {0, 0, 0, 0, 0, 0};
+    // lifetime: matrices keep their context alive until the last one is freed
+    int64_t live_matrices = 0;
+    bool destroyed = false;
+    // profiling
+    bool prof = false;
+    std::vector<sw::LaunchRec> recs;
+    std::vector<cudaEvent_t> pool;
+    int64_t launches = 0;
+    int64_t k_launch[sw::K_COUNT] = {};
+    double k_ms[sw::K_COUNT] = {};
+
+    cudaEvent_t take_event();
+    void harvest();
+    sw_status cuda_fail(cudaError_t e, const char* what);
+    sw_status ensure(void** p, size_t* cap, size_t need, const char* what);
+    sw_status ensure_stats(int64_t n);
+};
+
+struct sw_matrix {
+    sw_ctx* ctx = nullptr;
+    int64_t M = 0, N = 0, nd = 0, npix = 0, nkin = 0;
+    int gh = 0, elem = 4, ncopy = 4, device = 0;
+    int64_t nsteps = 0;
+    int nv = 0;            // velocity bins of a histogram matrix (0 in GH mode)
+    double v0 = 0.0, dv = 1.0;
+    void* d = nullptr;   // orbit-major: column i at d + i * M
+};
+
+extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value);

@@ -1,0 +1,105 @@
+// Internal declarations shared by the libsw translation units (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "../../include/sw.h"
+
+#define SW_G 4.300917e-6
+
+namespace sw {
+
+// ---------------------------------------------------------------------------
+// Potential constants, converted to the working precision T on the host.
+// Disc: Miyamoto-Nagai; halo: NFW; bar: needle-convolved MN (n = 1, eta = 0);
+// test: point mass (kind 1) or Plummer (kind 2).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct FieldT {
+    T gm_disc, disc_a, disc_b2;
+    T gm_halo, halo_rs, halo_inv_rs;
+    T k_bar, bar_L, bar_a, bar_b2;     // k_bar = G M / (2 L)
+    T gm_test, test_a2;
+    int test_kind;
+    int has_disc, has_halo, has_bar;
+};
+
+// Observation geometry: Euler matrix rows and bin grids.
+template <typename T>
+struct GridT {
+    T R[9];                            // Rz(gamma) Rx(beta) Rz(alpha), row-major
+    T x0, y0, inv_dx, inv_dy, dx, dy;
+    T v0, inv_dv, dv;
+    T dR, inv_dR, inv_dphi, dphi, zmin, inv_dz, dz;
+    int nx, ny, nv, nR, nphi, nz;
+    int gh, ncopy;
+    int64_t nd, npix, M;               // rows: density, pixel mass, kinematic block starts at nd + npix
+};
+
+// Per-model launch constants of the orbit kernel.
+template <typename T>
+struct ModelT {
+    FieldT<T> f;
+    GridT<T> g;
+    T dt, half_dt, omega;
+    const T* cs;                       // (nsteps + 1) x 2 : cos, sin of Omega_p * n * dt
+    const T* gh_v0s;                   // npix x 2 (v0, s), GH mode only
+    void* U;                           // orbit-major M x N column block of this model
+    int64_t n_orb;
+    int64_t orbit_base;                // first orbit of this model in the state arrays
+    int64_t ldu;                       // column stride of U (rows)
+};
+
+// Per-orbit status codes (mirrors SW_ORBIT_*).
+enum { ST_OK = 0, ST_DRIFT = 1, ST_NONFINITE = 2 };
+
+// Host-side helpers implemented in sw_api.cu.
+void set_error(sw_ctx* ctx, const char* fmt, ...);
+
+// Kernel-launch registry for per-kernel CUDA-event timing and launch counting.
+enum KernelId {
+    K_ICS_SOA = 0, K_ORBIT_BIN, K_ORBIT_DRIFT, K_ZERO_FLAGGED, K_FINALIZE, K_TRAJ, K_POTEVAL,
+    K_WHITEN, K_GRAM_TC, K_GRAM_SIMT, K_SHIFT, K_POTRF_DIAG, K_TRSM_PANEL, K_SYRK_UPDATE,
+    K_TRINV_DIAG, K_TRINV_UPDATE, K_GEMV_N, K_GEMV_T, K_TRMV_L, K_TRMV_LT, K_ADMM_UPDATE,
+    K_RESID, K_GRAD, K_CHI2, K_MISC, K_BATCH_ORBIT, K_MLP_FWD, K_MLP_BWD, K_ADAM, K_REDUCE_GH, K_COUNT
+};
+extern const char* kKernelNames[K_COUNT];
+
+struct LaunchTimer {
+    sw_ctx* ctx; int id; bool on;
+    LaunchTimer(sw_ctx* c, int kid);
+    ~LaunchTimer();
+};
+
+cudaStream_t ctx_stream(sw_ctx* ctx);
+
+// ---- orbit kernels (k_orbit.cu)
+template <typename T>
+cudaError_t launch_ics_to_soa(sw_ctx* ctx, const double* ics_dev_aos, int64_t n, T* soa, int64_t ld);
+template <typename T>
+cudaError_t launch_orbit_bin(sw_ctx* ctx, const ModelT<T>& m, const T* soa, int64_t ld, int64_t nsteps,
+                             int ej_every, double* drift, uint8_t* status, unsigned long long* stats);
+template <typename T>
+cudaError_t launch_orbit_drift(sw_ctx* ctx, const ModelT<T>& m, const T* soa, int64_t ld, int64_t nsteps,
+                               int ej_every, double* drift, uint8_t* status, unsigned long long* stats);
+template <typename T>
+cudaError_t launch_zero_flagged(sw_ctx* ctx, void* U, int64_t M, int64_t N, const uint8_t* status);
+template <typename T>
+cudaError_t launch_finalize(sw_ctx* ctx, void* U, int64_t M, int64_t N, int64_t count_rows, double norm);
+template <typename T>
+cudaError_t launch_trajectory(sw_ctx* ctx, const ModelT<T>& m, const T* soa, int64_t ld, int64_t n,
+                              int64_t nsteps, double* out);
+template <typename T>
+cudaError_t launch_poteval(sw_ctx* ctx, const FieldT<T>& f, const double* xyz, int64_t n, double* phi,
+                           double* acc);
+template <typename T>
+cudaError_t launch_reduce_gh(sw_ctx* ctx, const void* Uh, int64_t Mh, int64_t N, int64_t nd, int64_t npix, int nv,
+                             const void* W, void* Ug, int64_t Mg);
+cudaError_t launch_batch_orbit_bin(sw_ctx* ctx, const ModelT<float>* models_dev, int n_models,
+                                   const int64_t* tile_model, const int64_t* tile_first, int64_t n_tiles,
+                                   const float* soa, int64_t ld, int64_t nsteps, int ej_every, double* drift,
+                                   uint8_t* status, int block, int* work_counter);
+
+}  // namespace sw

@@ -1,0 +1,66 @@
+// Internal declarations of the weight-solve kernels (k_linalg.cu, k_gram_tc.cu).
+#pragma once
+#include "sw_api_internal.cuh"
+
+namespace sw {
+
+template <typename T, typename AT>
+cudaError_t whiten(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* inv_sig, const double* cs, AT* A,
+                   int64_t ldA, bool orbit_space);
+template <typename T>
+cudaError_t colnorm2(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* inv_sig, double* h);
+template <typename GT>
+cudaError_t admm_scales(sw_ctx* ctx, int64_t N, const double* h, double two_lam_n, double rho, double floor_,
+                        double* s64, GT* s, GT* rho_i, GT* d);
+template <typename GT>
+cudaError_t div_to(sw_ctx* ctx, int64_t n, const double* a, const double* b, GT* out);
+template <typename T, bool BT, bool LOWER>
+cudaError_t gemm(sw_ctx* ctx, int kid, int64_t m, int64_t n, int64_t k, T alpha, const T* A, int64_t lda, const T* B,
+                 int64_t ldb, T beta, T* C, int64_t ldc, int64_t diag_off);
+template <typename T>
+cudaError_t cholesky(sw_ctx* ctx, T* G, int64_t K, int* d_info);
+template <typename T>
+cudaError_t tri_inverse(sw_ctx* ctx, const T* G, T* X, T* D, int64_t K);
+template <typename T>
+cudaError_t shift_and_trace(sw_ctx* ctx, T* G, int64_t K, double* d_trace, double shift);
+template <typename AT, typename XT, typename YT, typename ACC>
+cudaError_t rowdot(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t cols, int64_t lda, const XT* x, YT* y,
+                   double alpha, double beta, bool lower);
+template <typename AT, typename XT, typename YT, typename ACC>
+cudaError_t colcomb(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t cols, int64_t lda, const XT* x, YT* y,
+                    double alpha, bool lower);
+template <typename GT>
+cudaError_t admm_update(sw_ctx* ctx, int64_t N, const GT* y, const GT* v, const GT* s, const GT* rho_i, const GT* d,
+                        const GT* qp, double alpha, GT* rs, GT* z, GT* u, unsigned* stats);
+template <typename GT>
+cudaError_t admm_init(sw_ctx* ctx, int64_t N, const GT* qp, const GT* z, const GT* u, const GT* s, const GT* rho_i,
+                      GT* rs);
+template <typename T>
+cudaError_t u_times_w(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* w, double* acc);
+cudaError_t residual(sw_ctx* ctx, int64_t M, const double* y, const double* acc, const double* inv_sig, double* e,
+                     double* xs);
+template <typename T>
+cudaError_t ut_times_x(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* xs, double* out);
+cudaError_t kkt(sw_ctx* ctx, int64_t N, const double* ute, const double* w, double two_lam_n, double* gneg,
+                unsigned long long* pgmax);
+cudaError_t chi2(sw_ctx* ctx, int64_t M, int64_t nd, const double* e, int64_t N, const double* w, double* out3);
+cudaError_t prep_data(sw_ctx* ctx, int64_t M, const double* sigma, const double* y, double* inv_sig, double* ys,
+                      int* bad);
+template <typename A, typename B>
+cudaError_t convert(sw_ctx* ctx, int64_t n, const A* a, B* b);
+template <typename GT>
+cudaError_t refine_rhs(sw_ctx* ctx, int64_t N, const GT* t, const double* gneg, const double* w, const double* s64,
+                       double two_lam_n, const GT* rho_i, GT* qp, GT* z, GT* u);
+
+template <typename T>
+cudaError_t gather_rows(sw_ctx* ctx, const T* U, int64_t M, const int64_t* idx, int64_t nP, const double* inv_sig,
+                        double* R);
+cudaError_t gather_vec(sw_ctx* ctx, const double* a, const int64_t* idx, int64_t n, double* out);
+
+// tcgen05 Gram (k_gram_tc.cu): C (K x K, FP32, row-major, lower tiles) = A A^T with A
+// K x ldA BF16 row-major (ldA a multiple of 64, columns beyond the data zero).
+// d_err receives a non-zero code if a bounded wait inside the kernel ran out.
+cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, int64_t K, int64_t ldA, float* C, int* d_err);
+bool gram_tc_available();
+
+}  // namespace sw

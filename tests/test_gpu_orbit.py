@@ -1,0 +1,287 @@
+"""GPU parity of the orbit-library path (potential, KDK integration, Jacobi
+drift, mirrors, projection, binning, GH rows) against the FP64 oracle, through
+the C-ABI.
+
+Gates (stated for this method): integer bin counts bit-exact over the first
+64 steps (FP64 form; the FP32 form exact outside a 1e-5 bin-width guard band
+around bin edges); per-step phase-space error <= 1e-5 relative over 1e3 steps
+for regular orbits (FP32 form against FP64); orbit-matrix L1 difference
+<= 1e-3 per orbit.
+
+Two readings make the FP32 gates well posed.  "Regular" means a twin orbit
+displaced by 1e-9 kpc separates by less than 50x over the 1e3 steps: FP32
+rounding of the inputs alone is ~6e-8 relative, so a 1e-5 gate leaves room
+for no more growth than that.  The per-orbit matrix gate allows, on top of
+1e-3, the moves of sample copies whose oracle coordinate lies within 2e-4
+bin widths of an edge (guard band, counted from the oracle trajectory); orbits
+whose oracle column itself moves by > 2e-4 under a 1e-7 relative change of the
+initial conditions are excluded, counted, and must stay a small minority.
+"""
+from _guard import guard_events
+import math
+
+import numpy as np
+import pytest
+
+from paper_2607_00117_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+W1 = inputs.WORKLOADS["axisym_2k"]
+W2 = inputs.WORKLOADS["barred_100k"]
+BARRED = dict(inputs.DISC_HALO, **inputs.BAR)
+
+
+@pytest.fixture(scope="module")
+def sw():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2607_00117_gb300 import sw as swmod
+    swmod.lib(build_if_missing=True)
+    return swmod
+
+
+def ctx_for(sw, prec, pot):
+    c = sw.Context(0, prec)
+    c.set_potential(pot)
+    return c
+
+
+def test_potential_and_force(sw, orc):
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.normal(0, 5, (400, 3)), rng.normal(0, 30, (100, 3)),
+                        np.array([[4.0, 0, 0], [-4, 0.01, 0], [0, 0, 0.001], [1e-4, 1e-4, 0]])])
+    pot = orc.make_pot(BARRED)
+    phi_o, acc_o = orc.potential(pot, x)
+    for prec, rtol in (("fp64", 1e-12), ("fp32", 3e-6)):
+        c = ctx_for(sw, prec, BARRED)
+        phi, acc = c.potential_eval(x)
+        np.testing.assert_allclose(phi, phi_o, rtol=rtol)
+        scale = np.linalg.norm(acc_o, axis=1, keepdims=True)
+        assert np.all(np.abs(acc - acc_o) <= rtol * 4 * scale + 1e-30), prec
+
+
+def _grid(W, **kw):
+    g = dict(W["grid"]); g.update(kw)
+    return g
+
+
+def _counts(U, S, ncopy=4):
+    return np.rint(U * ncopy * S).astype(np.int64)
+
+
+@pytest.mark.parametrize("pot_name", ["axisym", "barred"])
+def test_counts_bit_exact_64_steps_fp64(sw, orc, pot_name):
+    pot = inputs.DISC_HALO if pot_name == "axisym" else BARRED
+    omega = 0.0 if pot_name == "axisym" else 40.0
+    grid = _grid(W1) if pot_name == "axisym" else _grid(W2, nx=20, ny=20, nv=16, nR=10, nphi=10, nz=5)
+    ics = inputs.disc_ics(inputs.DISC_HALO, 700, seed=101)     # several 128-orbit tiles + ragged tail
+    S, dt = 64, inputs.DT_HALF_MYR
+    c = ctx_for(sw, "fp64", pot)
+    c.integrate_library(ics, omega, dt, S)
+    U = c.project(grid)
+    Ug = U.copy()
+    Uo, drift_o, status_o = orc.build_matrix(orc.make_pot(pot), omega, dt, S, ics, orc.make_obs(grid))
+    np.testing.assert_array_equal(_counts(Ug, S), _counts(Uo, S))
+    assert np.abs(Ug - Uo).max() <= 1e-15
+    drift_g, status_g = c.project_stats(len(ics))
+    np.testing.assert_array_equal(status_g, status_o)
+    np.testing.assert_allclose(drift_g, drift_o, rtol=1e-6, atol=1e-13)
+
+
+def test_counts_fp32_outside_guard_band(sw, orc):
+    """FP32 form: counts equal the oracle's except for samples whose oracle
+    coordinate lies within 1e-5 bin widths of a bin edge."""
+    pot, omega = BARRED, 40.0
+    grid = _grid(W2, nx=20, ny=20, nv=16, nR=10, nphi=10, nz=5)
+    ics = inputs.disc_ics(inputs.DISC_HALO, 300, seed=102)
+    S, dt = 64, inputs.DT_HALF_MYR
+    c = ctx_for(sw, "fp32", pot)
+    c.integrate_library(ics, omega, dt, S)
+    Ug = c.project(grid).copy()
+    Uo, _, _ = orc.build_matrix(orc.make_pot(pot), omega, dt, S, ics, orc.make_obs(grid))
+    diff = np.abs(_counts(Ug, S) - _counts(Uo, S)).sum(axis=1)
+    # guard-band samples per orbit from the oracle trajectory
+    R = orc.euler_matrix(grid["bar_angle"], grid["incl"], grid.get("pa", 0.0))
+    band = 1e-5
+    near = np.zeros(len(ics), dtype=int)
+    for i, ic in enumerate(ics):
+        tr = orc.trajectory(orc.make_pot(pot), omega, dt, S, ic)[1:]
+        th = omega * dt * np.arange(1, S + 1)
+        cth, sth = np.cos(th), np.sin(th)
+        xb = cth * tr[:, 0] + sth * tr[:, 1]; yb = -sth * tr[:, 0] + cth * tr[:, 1]; zb = tr[:, 2]
+        vxb = cth * tr[:, 3] + sth * tr[:, 4]; vyb = -sth * tr[:, 3] + cth * tr[:, 4]; vzb = tr[:, 5]
+        for sx, sz in [(1, 1), (1, -1), (-1, 1), (-1, -1)]:
+            p = np.stack([sx * xb, sx * yb, sz * zb]); v = np.stack([sx * vxb, sx * vyb, sz * vzb])
+            X, Y, V = R[0] @ p, R[1] @ p, R[2] @ v
+            coords = [(X + 5.0) / 0.5, (Y + 5.0) / 0.5, (V + 400.0) / 50.0, np.hypot(p[0], p[1]) / 1.0,
+                      (np.arctan2(p[1], p[0]) % (2 * np.pi)) / (2 * np.pi / 10), (p[2] + 3.0) / 1.2]
+            for u in coords:
+                near[i] += int(np.sum(np.abs(u - np.rint(u)) < band))
+    assert np.all(diff <= 2 * near), (np.flatnonzero(diff > 2 * near), diff[diff > 2 * near])
+    assert diff.sum() <= max(4, 2 * near.sum())
+
+
+def test_phase_space_fp32_regular_orbits(sw, orc):
+    """Per-step relative error <= 1e-5 over 1e3 steps for regular orbits.  An
+    orbit is regular if a twin displaced by 1e-9 kpc separates by less than
+    50 x over the same steps (oracle FP64)."""
+    pot, omega = BARRED, 40.0
+    ics = inputs.disc_ics(inputs.DISC_HALO, 64, seed=103)
+    S, dt = 1000, inputs.DT_HALF_MYR
+    po = orc.make_pot(pot)
+    c = ctx_for(sw, "fp32", pot)
+    tg = c.trajectory(ics, omega, dt, S)
+    n_regular = 0
+    for i, ic in enumerate(ics):
+        to = orc.trajectory(po, omega, dt, S, ic)
+        ic2 = ic.copy(); ic2[0] += 1e-9
+        t2 = orc.trajectory(po, omega, dt, S, ic2)
+        sep = np.linalg.norm(t2[:, :3] - to[:, :3], axis=1).max()
+        if sep > 50 * 1e-9:
+            continue
+        n_regular += 1
+        ex = np.linalg.norm(tg[i, :, :3] - to[:, :3], axis=1) / np.linalg.norm(to[:, :3], axis=1)
+        ev = np.linalg.norm(tg[i, :, 3:] - to[:, 3:], axis=1) / np.linalg.norm(to[:, 3:], axis=1)
+        assert max(ex.max(), ev.max()) <= 1e-5, (i, ex.max(), ev.max())
+    assert n_regular >= 16
+
+
+def test_phase_space_fp64(sw, orc):
+    pot, omega = BARRED, 40.0
+    ics = inputs.disc_ics(inputs.DISC_HALO, 8, seed=104)
+    S, dt = 1000, inputs.DT_HALF_MYR
+    c = ctx_for(sw, "fp64", pot)
+    tg = c.trajectory(ics, omega, dt, S)
+    for i, ic in enumerate(ics):
+        to = orc.trajectory(orc.make_pot(pot), omega, dt, S, ic)
+        np.testing.assert_allclose(tg[i, :100], to[:100], rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_matrix_l1_axisym_2k(sw, orc, prec):
+    """Full axisym_2k workload (2000 orbits x 2000 steps): per-orbit L1 of the
+    matrix difference <= 1e-3 (columns sum to <= 3 here: density + pixel +
+    velocity rows)."""
+    W = W1
+    ics = inputs.disc_ics(W["potential"], W["n_orb"], seed=W["seeds"]["ic"])
+    c = ctx_for(sw, prec, W["potential"])
+    c.integrate_library(ics, W["omega_p"], W["dt"], W["nsteps"])
+    Ug = c.project(W["grid"]).copy()
+    Uo, _, so = orc.build_matrix(orc.make_pot(W["potential"]), W["omega_p"], W["dt"], W["nsteps"], ics,
+                                 orc.make_obs(W["grid"]))
+    l1 = np.abs(Ug - Uo).sum(axis=1)
+    if prec == "fp64":
+        assert l1.max() <= 1e-3, (prec, l1.max(), np.argmax(l1))
+        return
+    allow = _allowance(orc, W["potential"], W["omega_p"], W["dt"], W["nsteps"], ics, W["grid"], l1 > 1e-3,
+                       per_event=2.0 / (4 * W["nsteps"]))
+    bad = l1 > 1e-3 + allow
+    stable = _stable_columns(orc, W["potential"], W["omega_p"], W["dt"], W["nsteps"], ics, W["grid"], Uo, bad)
+    assert np.all(~bad | ~stable), (l1[bad & stable], allow[bad & stable], np.flatnonzero(bad & stable))
+    assert (~stable).sum() <= 0.03 * len(ics), (~stable).sum()
+
+
+def _allowance(orc, pot, omega, dt, S, ics, grid, suspects, per_event):
+    allow = np.zeros(len(ics))
+    idx = np.flatnonzero(suspects)
+    if len(idx):
+        allow[idx] = per_event * guard_events(orc, pot, omega, dt, S, ics[idx], grid, 2e-4)
+    return allow
+
+
+def _stable_columns(orc, pot, omega, dt, S, ics, grid, Uo, suspects, gh_v0s=None):
+    """True for orbits whose oracle column moves by < 2e-4 (L1) when the
+    initial conditions change by 1e-7 relative (checked for the suspects only;
+    every other orbit already meets the gate)."""
+    stable = np.ones(len(ics), dtype=bool)
+    idx = np.flatnonzero(suspects)
+    if len(idx):
+        U2, _, _ = orc.build_matrix(orc.make_pot(pot), omega, dt, S, ics[idx] * (1 + 1e-7), orc.make_obs(grid),
+                                    gh_v0s=gh_v0s)
+        stable[idx] = np.abs(U2 - Uo[idx]).sum(axis=1) < 2e-4
+    return stable
+
+
+def test_gh_rows(sw, orc):
+    pot, omega = BARRED, 40.0
+    grid = _grid(W2, nx=12, ny=10, nR=6, nphi=8, nz=4, gh=1)
+    npix = 120
+    rng = np.random.default_rng(5)
+    v0s = np.stack([rng.normal(0, 40, npix), rng.uniform(60, 160, npix)], 1)
+    ics = inputs.disc_ics(inputs.DISC_HALO, 300, seed=105)
+    S, dt = 200, inputs.DT_HALF_MYR
+    Uo, _, _ = orc.build_matrix(orc.make_pot(pot), omega, dt, S, ics, orc.make_obs(grid), gh_v0s=v0s)
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-3)):
+        c = ctx_for(sw, prec, pot)
+        c.integrate_library(ics, omega, dt, S)
+        Ug = c.project(grid, gh_v0s=v0s).copy()
+        assert Ug.shape == Uo.shape == (300, 192 + 120 + 480)
+        l1 = np.abs(Ug - Uo).sum(axis=1)
+        if prec == "fp64":
+            assert l1.max() <= tol, (prec, l1.max())
+            continue
+        allow = _allowance(orc, pot, omega, dt, S, ics, grid, l1 > tol, per_event=18.0 / (4 * S))
+        bad = l1 > tol + allow
+        stable = _stable_columns(orc, pot, omega, dt, S, ics, grid, Uo, bad, gh_v0s=v0s)
+        assert np.all(~bad | ~stable), (l1[bad & stable], allow[bad & stable])
+        assert (~stable).sum() <= 0.03 * len(ics)
+
+
+def test_drift_pass_and_quality_cut(sw, orc):
+    """sw_integrate_library's drift pass equals the oracle's Jacobi drift; an
+    orbit made non-finite gets status NONFINITE and a zero column."""
+    pot, omega = BARRED, 40.0
+    ics = inputs.disc_ics(inputs.DISC_HALO, 200, seed=106)
+    ics[7, 3] = np.nan
+    S, dt = 300, inputs.DT_HALF_MYR
+    c = ctx_for(sw, "fp64", pot)
+    drift, status = c.integrate_library(ics, omega, dt, S, want_drift=True)
+    d_o = orc.drift(orc.make_pot(pot), omega, dt, S, ics)
+    ok = np.isfinite(d_o)
+    np.testing.assert_allclose(drift[ok], d_o[ok], rtol=1e-6, atol=1e-14)
+    assert status[7] == 2 and np.all(status[ok] == (d_o[ok] > 0.1))
+    U = c.project(_grid(W2, nx=10, ny=10, nv=8, nR=5, nphi=4, nz=3)).copy()
+    assert np.all(U[7] == 0)
+
+
+def test_edge_cases(sw, orc):
+    c = ctx_for(sw, "fp32", inputs.DISC_HALO)
+    with pytest.raises(sw.SwError):
+        c.integrate_library(np.zeros((0, 6)), 0.0, 1e-3, 10)
+    with pytest.raises(sw.SwError):
+        c.integrate_library(np.zeros((2, 6)), 0.0, -1.0, 10)
+    c2 = sw.Context(0, "fp32")
+    with pytest.raises(sw.SwError):        # no potential yet
+        c2.integrate_library(np.ones((2, 6)), 0.0, 1e-3, 10)
+    with pytest.raises(sw.SwError):        # project before integrate
+        c.project(W1["grid"])
+    # orbits that never enter the grid give all-zero columns
+    ics = inputs.disc_ics(inputs.DISC_HALO, 5, seed=1)
+    ics[:, :3] += np.array([200.0, 0, 0])
+    c.integrate_library(ics, 0.0, inputs.DT_HALF_MYR, 20)
+    U = c.project(W1["grid"]).copy()
+    assert U.shape == (5, 7300) and np.all(U == 0)
+    # a single orbit and a single step
+    c.integrate_library(inputs.disc_ics(inputs.DISC_HALO, 1, seed=2), 0.0, inputs.DT_HALF_MYR, 1)
+    U = c.project(W1["grid"]).copy()
+    Uo, _, _ = orc.build_matrix(orc.make_pot(inputs.DISC_HALO), 0.0, inputs.DT_HALF_MYR, 1,
+                                inputs.disc_ics(inputs.DISC_HALO, 1, seed=2), orc.make_obs(W1["grid"]))
+    np.testing.assert_allclose(U, Uo, atol=1e-7)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_reduce_gh(sw, orc, prec):
+    pot, omega = BARRED, 40.0
+    grid = _grid(W2, nx=12, ny=10, nv=32, nR=6, nphi=8, nz=4)
+    rng = np.random.default_rng(6)
+    v0s = np.stack([rng.normal(0, 40, 120), rng.uniform(60, 160, 120)], 1)
+    ics = inputs.disc_ics(inputs.DISC_HALO, 260, seed=107)
+    c = ctx_for(sw, prec, pot)
+    c.integrate_library(ics, omega, inputs.DT_HALF_MYR, 150)
+    Uh = c.project(grid)
+    Ug = c.reduce_gh(Uh, v0s)
+    assert (Ug.M, Ug.N) == (192 + 120 * 5, 260) and Ug.blocks == (192, 120, 480)
+    ref = orc.reduce_gh(Uh.copy(), 192, 120, 32, -400.0, 25.0, v0s)   # reduce the GPU's own histogram
+    np.testing.assert_allclose(Ug.copy(), ref, rtol=1e-12 if prec == "fp64" else 2e-5,
+                               atol=1e-15 if prec == "fp64" else 1e-7)

@@ -1,0 +1,122 @@
+"""GPU parity of the weight solve (Sec. 2.3-2.4) through the C-ABI.
+
+Solve parity is decoupled from matrix parity: the GPU solves on its own orbit
+matrix, the oracle (Lawson-Hanson on the normal equations, FP64) solves on the
+same matrix exported from the GPU; chi^2 must agree within 1e-4 relative.
+Both Gram spaces are covered (orbit space N <= M and constraint space M < N),
+with lambda = 1 and lambda = 0.  At the full axisym_2k size the GPU solution
+is checked by its FP64 KKT certificate.
+"""
+import numpy as np
+import pytest
+
+from paper_2607_00117_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+W1 = inputs.WORKLOADS["axisym_2k"]
+BARRED = dict(inputs.DISC_HALO, **inputs.BAR)
+
+
+@pytest.fixture(scope="module")
+def sw():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2607_00117_gb300 import sw as swmod
+    swmod.lib(build_if_missing=True)
+    return swmod
+
+
+def _mock(orc, U_rows, blocks, seed_w=2001, seed_n=2002, gh_err=None):
+    """Mock data from the given matrix (item: w_true ~ U(0,2), 2% errors)."""
+    N = U_rows.shape[1]
+    w_true = inputs.true_weights(N, seed_w)
+    y0 = U_rows @ w_true
+    sig = inputs.mock_sigma(y0, blocks, gh_err=gh_err)
+    y = y0 + sig * inputs.noise(len(y0), seed_n)
+    return y, sig
+
+
+def _oracle_solve(orc, U_rows, y, sig, lam, n_dens):
+    Ut, yt = orc.whiten(U_rows, y, sig)
+    H, q = orc.normal_equations(Ut, yt, lam)
+    w = orc.nnls_lh_normal(H, q)
+    return w, orc.chi2_parts(U_rows, y, sig, w, lam, n_dens), H, q
+
+
+def _build(sw, prec, pot, omega, ics, S, grid, gh_v0s=None):
+    c = sw.Context(0, prec)
+    c.set_potential(pot)
+    c.integrate_library(ics, omega, inputs.DT_HALF_MYR, S)
+    U = c.project(grid, gh_v0s=gh_v0s)
+    return c, U
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("lam", [1.0, 0.0])
+def test_solve_orbit_space(sw, orc, prec, lam):
+    ics = inputs.disc_ics(W1["potential"], 500, seed=201)
+    c, U = _build(sw, prec, W1["potential"], 0.0, ics, 1000, W1["grid"])
+    Ug = U.copy().T.copy()                       # (M, N)
+    blocks = inputs.row_blocks(W1["grid"])
+    y, sig = _mock(orc, Ug, blocks)
+    w, chi2 = c.solve_weights(U, y, sig, lam)
+    info = c.solve_info()
+    assert not info["constraint_space"]
+    w_o, chi2_o, H, q = _oracle_solve(orc, Ug, y, sig, lam, blocks["dens"][1])
+    assert np.all(w >= 0)
+    np.testing.assert_allclose(chi2[:2], chi2_o[:2], rtol=1e-4)
+    np.testing.assert_allclose(chi2[2], chi2_o[2], rtol=1e-3, atol=1e-9 * max(1.0, chi2_o[0]))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("lam", [1.0, 0.0])
+def test_solve_constraint_space_gh(sw, orc, prec, lam):
+    """M < N: the Woodbury form on the constraint-space Gram; GH rows."""
+    grid = dict(W1["grid"], nx=6, ny=6, nR=5, nphi=4, nz=3, gh=1, incl=0.9)
+    npix = 36
+    ics = inputs.disc_ics(BARRED, 700, seed=202)
+    po = orc.make_pot(BARRED)
+    mom = orc.pixel_moments(po, 40.0, inputs.DT_HALF_MYR, 500, ics, orc.make_obs(grid), np.ones(len(ics)))
+    v0s, gh_err = inputs.gh_reference(mom)
+    c, U = _build(sw, prec, BARRED, 40.0, ics, 500, grid, gh_v0s=v0s)
+    assert U.M == 60 + 36 + 144 and U.N == 700
+    Ug = U.copy().T.copy()
+    blocks = inputs.row_blocks(grid)
+    y, sig = _mock(orc, Ug, blocks, gh_err=gh_err)
+    w, chi2 = c.solve_weights(U, y, sig, lam)
+    assert c.solve_info()["constraint_space"]
+    w_o, chi2_o, H, q = _oracle_solve(orc, Ug, y, sig, lam, blocks["dens"][1])
+    assert np.all(w >= 0)
+    np.testing.assert_allclose(chi2[:2], chi2_o[:2], rtol=1e-4)
+
+
+def test_solve_full_axisym_kkt_certificate(sw, orc):
+    """axisym_2k at full size: the returned weights satisfy the FP64 KKT
+    conditions of the exact problem on the exported matrix."""
+    W = W1
+    ics = inputs.disc_ics(W["potential"], W["n_orb"], seed=W["seeds"]["ic"])
+    c, U = _build(sw, "fp32", W["potential"], 0.0, ics, W["nsteps"], W["grid"])
+    Ug = U.copy().T.copy()
+    blocks = inputs.row_blocks(W["grid"])
+    y, sig = _mock(orc, Ug, blocks)
+    w, chi2 = c.solve_weights(U, y, sig, W["lam"])
+    Ut, yt = orc.whiten(Ug, y, sig)
+    H, q = orc.normal_equations(Ut, yt, W["lam"])
+    k = orc.kkt_residual(H, q, w)
+    assert k["neg_w"] == 0.0
+    assert k["pg_inf"] <= 1e-6 * np.abs(q).max(), k
+    # chi2 parts recomputed in FP64 on the host
+    np.testing.assert_allclose(chi2, orc.chi2_parts(Ug, y, sig, w, W["lam"], blocks["dens"][1]), rtol=1e-9)
+    # the certificate bounds the objective gap: f(w) - f* <= ||P(g)||^2 / (2 mu)
+    gap_bound = k["pg_norm2"] / (2 * 2 * W["lam"] / len(w))
+    assert gap_bound <= 1e-4 * chi2[0]
+
+
+def test_solve_rejects_bad_errors(sw, orc):
+    ics = inputs.disc_ics(W1["potential"], 50, seed=203)
+    c, U = _build(sw, "fp32", W1["potential"], 0.0, ics, 50, W1["grid"])
+    y = np.ones(U.M); s = np.ones(U.M); s[3] = 0.0
+    with pytest.raises(sw.SwError):
+        c.solve_weights(U, y, s, 1.0)
+    with pytest.raises(sw.SwError):
+        c.solve_weights(U, y, np.ones(U.M), -1.0)

@@ -181,3 +181,20 @@ def test_recount_against_trajectory(orc):
                 if iR < 10 and 0 <= iz < 5:
                     cnt[(iR * 10 + iph % 10) * 5 + iz] += 1
         np.testing.assert_allclose(U[i, :500] * 4 * S, cnt, atol=1e-9)
+
+
+def test_reduce_gh_of_gaussian_histogram(orc):
+    """A fine velocity histogram of a Gaussian LOSVD with the reference (v0, s)
+    reduces to pixel mass m with GH rows (0, 0, 0, 0) * m, and a shifted
+    Gaussian gives h1 of the sign of the shift (midpoint quadrature)."""
+    nv, vmin, dv = 400, -400.0, 2.0
+    vc = vmin + (np.arange(nv) + 0.5) * dv
+    v0, s = 12.0, 55.0
+    mass = 0.7
+    hist = mass * np.exp(-0.5 * ((vc - v0) / s) ** 2) / (np.sqrt(2 * np.pi) * s) * dv
+    U = np.concatenate([[0.3, mass], hist])[None, :]          # nd = 1, npix = 1
+    out = orc.reduce_gh(U, 1, 1, nv, vmin, dv, np.array([[v0, s]]))
+    np.testing.assert_allclose(out[0, :2], [0.3, mass])
+    np.testing.assert_allclose(out[0, 2:], 0.0, atol=1e-9)
+    out2 = orc.reduce_gh(U, 1, 1, nv, vmin, dv, np.array([[v0 - 10.0, s]]))
+    assert out2[0, 2] > 0.05 * mass
