@@ -165,6 +165,16 @@ sw_status sw_matrix_copy(const sw_matrix* U, double* host_out);
 /* Model observables for weights w: y_out = U w (host w of N values, host y_out of M values;
  * FP64 accumulation over the stored matrix), e.g. the best-fit maps of a solve. */
 sw_status sw_matrix_apply(const sw_matrix* U, const double* w, double* y_out);
+/* No counterpart in the paper: a variant of sw_matrix_apply for callers that cannot allocate
+ * device memory when they call (e.g. a process whose device memory belongs to another allocator's
+ * pool, or a pipeline that must not allocate once running).  Same arguments and result as
+ * sw_matrix_apply, but its scratch (the staged w and the FP64 accumulator of U w) lives in a fixed
+ * static device array of 2^21 doubles (16 MiB), held by every device that loads the library until
+ * the process exits; N + M above 2^21 returns SW_EINVAL.  It calls no cudaMalloc/cudaFree.  The
+ * first call on a device looks up the array's device address (once per device, with that device
+ * current); make that first call before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU race: serialise them. */
+sw_status sw_matrix_apply_static(const sw_matrix* U, const double* w, double* y_out);
 /* Free a matrix returned by sw_project (NULL is a no-op).  May be called before or after
  * sw_destroy of its context: a destroyed context's bookkeeping lives until its last matrix
  * is freed. */

@@ -80,6 +80,7 @@ SIGNATURES = {
     "sw_matrix_shape": (ctypes.c_int, [_VP, _I64, _I64, _I64]),
     "sw_matrix_copy": (ctypes.c_int, [_VP, _D]),
     "sw_matrix_apply": (ctypes.c_int, [_VP, _D, _D]),
+    "sw_matrix_apply_static": (ctypes.c_int, [_VP, _D, _D]),
     "sw_matrix_free": (ctypes.c_int, [_VP]),
     "sw_trajectory": (ctypes.c_int, [_VP, _D, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int64, _D]),
     "sw_potential_eval": (ctypes.c_int, [_VP, _D, ctypes.c_int64, _D, _D]),
@@ -169,6 +170,13 @@ class Matrix:
         w = np.ascontiguousarray(w, dtype=np.float64)
         y = np.empty(self.M)
         self.ctx._check(lib().sw_matrix_apply(self.handle, _dp(w), _dp(y)))
+        return y
+
+    def apply_static(self, w: np.ndarray) -> np.ndarray:
+        """U w through the entry point that allocates no device memory (static scratch)."""
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        y = np.empty(self.M)
+        self.ctx._check(lib().sw_matrix_apply_static(self.handle, _dp(w), _dp(y)))
         return y
 
     def free(self) -> None:
