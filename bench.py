@@ -2,12 +2,14 @@
 """Benchmark of the Schwarzschild orbit-library hot path on GB300.
 
 One step = one model evaluation of the `barred_100k` workload: integrate
-100 000 orbits x 10 000 kick-drift-kick steps in the rotating disc + bar + halo
-potential, project every sample with four-fold mirroring into 20 x 20 x 10
-density cells and 50 x 50 pixels x 32 line-of-sight-velocity bins (the orbit
-matrix, 86 500 rows), reduce each pixel's velocity histogram to Gauss-Hermite
-rows (16 500 rows), and solve the regularised non-negative weight problem
-against synthetic data, returning weights and chi^2.
+100 000 orbits (25 000 initial conditions x 4 dithered realisations, the orbit
+bundles of Sec. 2.2.1) x 10 000 kick-drift-kick steps in the rotating
+disc + bar + halo potential, project every sample with four-fold mirroring into
+20 x 20 x 10 density cells and 50 x 50 pixels x 32 line-of-sight-velocity bins
+(the orbit matrix, 86 500 rows), average each bundle's columns, reduce each
+pixel's velocity histogram to Gauss-Hermite rows (16 500 rows), and solve the
+regularised non-negative weight problem for the 25 000 bundles against
+synthetic data, returning weights and chi^2.
 
 Metric: orbit-steps/s of whole model evaluations (also models/s), FP32 form.
 `value` is timed with CUDA events on device-resident inputs; `e2e` repeats the
@@ -248,12 +250,15 @@ def run_sw(args):
     hbm, bf16, bf16_sus, sm_max, peak_src = peaks()
 
     v0s, y, sig = make_data(sw, torch, W, rank)
-    ics = inputs.disc_ics(W["potential"], N, seed=W["seeds"]["ic"] + 1000 * rank)
+    nb = W.get("bundle", 1)
+    Nb = N // nb
+    base = inputs.disc_ics(W["potential"], Nb, seed=W["seeds"]["ic"] + 1000 * rank)
+    ics = inputs.dither(base, nb, W["seeds"]["dither"] + 1000 * rank, W["potential"]) if nb > 1 else base
     dev = torch.device("cuda", local)
     ics_d = torch.from_numpy(ics).to(dev)
     y_d = torch.from_numpy(y).to(dev)
     sig_d = torch.from_numpy(sig).to(dev)
-    w_d = torch.empty(N, dtype=torch.float64, device=dev)
+    w_d = torch.empty(Nb, dtype=torch.float64, device=dev)
     chi_d = torch.empty(3, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = sw.Context(local, "fp32", stream.cuda_stream)
@@ -264,6 +269,10 @@ def run_sw(args):
     def step():
         ctx.integrate_library_device(ics_d, W["omega_p"], W["dt"], S)
         Uh = ctx.project(grid)
+        if nb > 1:
+            Ub = ctx.bundle(Uh, nb)
+            Uh.free()
+            Uh = Ub
         Ug = ctx.reduce_gh(Uh, v0s)
         Uh.free()
         st = ctx.solve_weights_device(Ug, y_d, sig_d, W["lam"], w_d, chi_d)
@@ -314,6 +323,10 @@ def run_sw(args):
         def step_host():
             ctx2.integrate_library(ics_h, W["omega_p"], W["dt"], S)
             Uh = ctx2.project(grid)
+            if nb > 1:
+                Ub = ctx2.bundle(Uh, nb)
+                Uh.free()
+                Uh = Ub
             Ug = ctx2.reduce_gh(Uh, v0s)
             Uh.free()
             w, c = ctx2.solve_weights(Ug, y, sig, W["lam"], allow_nonconv=True)
@@ -333,7 +346,7 @@ def run_sw(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             te = float(t.item())
         h2d = ics_h.nbytes + y.nbytes + sig.nbytes + 8 * 2 * (S + 1) + 16 * grid["nx"] * grid["ny"]
-        d2h = 8 * N + 8 * 3
+        d2h = 8 * Nb + 8 * 3
         e2e = {"value": N * S * args.steps * world / te, "unit": "orbit-steps/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * te / args.steps}
         ctx2.close()
@@ -362,7 +375,8 @@ def run_sw(args):
             "value": value, "unit": "orbit-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_orb": N, "nsteps": S, "rows_histogram": grid["nR"] * grid["nphi"] *
+            "config": {"workload": WORKLOAD, "n_orb": N, "bundles": Nb, "dithers_per_bundle": nb, "nsteps": S,
+                       "rows_histogram": grid["nR"] * grid["nphi"] *
                        grid["nz"] + grid["nx"] * grid["ny"] * (1 + grid["nv"]), "rows_solve": M_gh,
                        "parallelism": f"replicas x{world}", "l2": "inputs and U far larger than L2 (U 34.6 GB)"},
             "models_per_s": args.steps * world / elapsed,

@@ -133,6 +133,13 @@ sw_status sw_project(sw_ctx* ctx, double incl, double pa, double bar_angle, cons
  * (v0, s > 0).  *U_gh_out receives a new matrix (rows nd + 5 npix, GH layout as in sw_project);
  * U_hist is unchanged. */
 sw_status sw_reduce_gh(sw_ctx* ctx, const sw_matrix* U_hist, const double* gh_v0_s, sw_matrix** U_gh_out);
+/* Orbit bundles (Sec. 2.2.1: each initial condition is dithered into n nearby realisations that
+ * enter the fit as one orbit).  For a matrix whose N columns hold N/n bundles of n consecutive
+ * realisations, *U_out receives a new matrix of N/n columns, column j the mean of columns
+ * j n .. j n + n - 1 (FP64 sum, rounded once to the matrix precision); rows and layout are
+ * unchanged.  n must divide N (SW_EINVAL otherwise).  U is unchanged; free both with
+ * sw_matrix_free. */
+sw_status sw_bundle(sw_ctx* ctx, const sw_matrix* U, int64_t n, sw_matrix** U_out);
 /* Drift and status per orbit from the last sw_project (host arrays of n_orb, nullable). */
 sw_status sw_project_stats(sw_ctx* ctx, double* drift_out, uint8_t* status_out);
 
@@ -152,9 +159,10 @@ sw_status sw_solve_weights_device(sw_ctx* ctx, const sw_matrix* U, const double*
 
 /* Solver diagnostics of the last solve: out[0] ADMM iterations, out[1] refinement rounds,
  * out[2] final KKT projected-gradient infinity norm (scaled by max |U~^T y~|), out[3] 1 if the
- * Gram was formed in constraint space (M x M), 0 if in orbit space (N x N), out[4] number of
- * exact active-set (polish) solves, out[5] 1 if the KKT tolerance was met (0: chi^2 stable). */
-sw_status sw_solve_info(sw_ctx* ctx, double* out6);
+ * orbits outnumbered the constraints (working-set or constraint-space form), out[4] number of
+ * exact active-set (polish) solves, out[5] 1 if the KKT tolerance was met (0: chi^2 stable),
+ * out[6] working-set rounds, out[7] final working-set size (0 without a working set). */
+sw_status sw_solve_info(sw_ctx* ctx, double* out8);
 
 /* ---- orbit matrix --------------------------------------------------------- */
 
@@ -207,16 +215,30 @@ int64_t sw_launch_count(const sw_ctx* ctx);
  *                           has not halved over five checks)
  *  "admm_tol" (> 0)         ADMM stopping tolerance (default 1e-6)
  *  "refine_max" (>= 0)      refinement rounds with FP64 residuals (default 8)
- *  "kkt_tol" (> 0)          KKT tolerance relative to max |U~^T y~| (default 1e-6)
+ *  "kkt_tol" (> 0)          KKT tolerance relative to max |U~^T y~| (default 1e-9)
  *  "check_every" (>= 1)     ADMM iterations between convergence checks (default 20)
  *  "admm_rho" (> 0)         ADMM penalty of orbit i is admm_rho * ||column i of U~||^2 when the Gram is
  *                           in orbit space (default 0.01)
  *  "admm_rho_cspace" (> 0)  the same for the constraint-space (Woodbury) form (default 1)
  *  "admm_alpha" (0, 2)      ADMM over-relaxation (default 1.6)
- *  "chi2_tol" (>= 0)        refinement also stops when chi^2 changes by less than this, relative (1e-7)
- *  "polish_max" (>= 0)      largest support the exact active-set polish handles (default 6000; 0 = off)
- *  "polish_solves" (>= 0)   cap on reduced solves of one polish (default 60)
- *  "gram_tensor_cores" (0/1) tcgen05 BF16 Gram in the FP32 form (default 1) */
+ *  "chi2_tol" (>= 0)        refinement also stops when chi^2 changes by less than this, relative (1e-6)
+ *  "polish_max" (>= 0)      largest support the exact active-set polish handles (default 2048; 0 = off)
+ *  "polish_solves" (>= 0)   cap on reduced solves of one polish (default 400)
+ *  "inner_refine" (0..8)    refinement steps of each ADMM linear solve against the Gram (default 1)
+ *  "verbose" (0/1)          print solver progress to stderr (default 0; the only output the library makes)
+ *  "working_set" (0/1)      N > M: orbit-space solves on a working set of orbits (default 1); 0 uses the
+ *                           constraint-space (Woodbury) form of the ADMM step
+ *  "orbit_direct_max" (>= 0) N > M up to this many orbits: orbit-space solve on all orbits (default 8192)
+ *  "large_solver" (0/1)     above orbit_direct_max orbits: 0 block active set (default), 1 ADMM working set
+ *  "as_block" (>= 1)        active set: KKT violators entering per pivoting step (default 2048)
+ *  "as_cg_max" (>= 0)       active set: preconditioned conjugate-gradient steps per reduced solve (default 200)
+ *  "as_cg_tol" (> 0)        active set: CG stops at max|r| <= as_cg_tol * kkt_tol * max|q| (default 0.05)
+ *  "as_solves" (>= 1)       active set: cap on pivoting steps (default 400)
+ *  "ws_factor" (> 0)        initial working-set size in units of M (default 0.6; it grows to take in the
+ *                           violators of each round, up to three times that)
+ *  "ws_rounds" (>= 1)       working-set exchange rounds (default 6)
+ *  "gram_tensor_cores" (0/1) tcgen05 BF16 Gram in the FP32 form (default 1; the operand is split into
+ *                           BF16 hi + lo halves and three products are accumulated) */
 sw_status sw_set_option(sw_ctx* ctx, const char* key, double value);
 
 #if defined(__GNUC__)

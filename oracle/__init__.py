@@ -270,6 +270,18 @@ def reduce_gh(U_orbit_major: np.ndarray, nd: int, npix: int, nv: int, vmin: floa
     return out
 
 
+def bundle(U_orbit_major: np.ndarray, n: int) -> np.ndarray:
+    """Orbit bundles (Sec. 2.2.1): the n dithered realisations of one initial
+    condition enter the fit as one orbit, their mean column.  Input (N, rows)
+    with the realisations of a bundle consecutive; output (N / n, rows)."""
+    N, M = U_orbit_major.shape
+    assert N % n == 0
+    out = np.zeros((N // n, M))
+    for k in range(n):
+        out += U_orbit_major[k::n]
+    return out / n
+
+
 def set_threads(n: int) -> None:
     lib().orc_set_threads(int(n))
 

@@ -5,8 +5,9 @@
 // computed; the Cholesky factorisation reads the lower triangle only.
 //
 // One CTA per 128 x 128 output tile.  Warp 0 issues TMA loads (128-byte
-// swizzle) of the two 128-row operand panels, 64 BF16 of the contraction per
-// stage, through a 4-stage mbarrier ring; warp 1 allocates 128 TMEM columns
+// swizzle) of the two 128-row operand panels (four with the hi/lo split), 64
+// BF16 of the contraction per stage, through a 4-stage (3 with the split)
+// mbarrier ring; warp 1 allocates 128 TMEM columns
 // and a single thread issues tcgen05.mma (M = 128, N = 128, K = 16) four times
 // per stage, committing each stage back to the producer; warps 2-5 read the
 // accumulator with tcgen05.ld and store FP32 rows.  Every wait is bounded by
@@ -22,11 +23,14 @@ namespace sw {
 namespace gtc {
 
 constexpr int BM = 128, BN = 128, BKC = 64;  // tile rows/cols, BF16 per stage (128 bytes)
-constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BKC * 2, B_BYTES = BN * BKC * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int THREADS = 192;
+// plain: 4 stages of (A, B); split: 3 stages of (A_hi, B_hi, A_lo, B_lo)
+template <bool SPLIT> struct Cfg {
+    static constexpr int STAGES = SPLIT ? 3 : 4;
+    static constexpr int STAGE_BYTES = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES);
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+};
 constexpr uint32_t TMEM_COLS = 128;
 constexpr uint64_t WAIT_NS = 4000000000ull;  // 4 s per wait
 
@@ -129,9 +133,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(THREADS, 1) k_gram(const __grid_constant__ CUtensorMap map, int64_t K, int nk,
+// SPLIT: the operand is A = A_hi + A_lo (both BF16, maps hi and lo) and the
+// tile accumulates A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (the lo x lo term is
+// below FP32 resolution), i.e. a Gram accurate to ~2^-16 relative.
+template <bool SPLIT>
+__global__ void __launch_bounds__(THREADS, 1) k_gram(const __grid_constant__ CUtensorMap map,
+                                                     const __grid_constant__ CUtensorMap map_lo, int64_t K, int nk,
                                                      float* __restrict__ C, int* err)
 {
+    constexpr int STAGES = Cfg<SPLIT>::STAGES, STAGE_BYTES = Cfg<SPLIT>::STAGE_BYTES;
     extern __shared__ unsigned char smraw[];
     // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
     unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -184,6 +194,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram(const __grid_constant__ CUt
             mbar_expect_tx(&full[s], STAGE_BYTES);
             tma_load_2d(sa, &map, kc * BKC, (int)(ti * BM), &full[s]);
             tma_load_2d(sa + A_BYTES, &map, kc * BKC, (int)(tj * BN), &full[s]);
+            if (SPLIT) {
+                tma_load_2d(sa + A_BYTES + B_BYTES, &map_lo, kc * BKC, (int)(ti * BM), &full[s]);
+                tma_load_2d(sa + 2 * A_BYTES + B_BYTES, &map_lo, kc * BKC, (int)(tj * BN), &full[s]);
+            }
             issued = kc + 1;
         }
         if (*abort_flag) {
@@ -207,6 +221,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram(const __grid_constant__ CUt
 #pragma unroll
             for (int k = 0; k < BKC / 16; ++k)
                 umma(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (kc | k) != 0);
+            if (SPLIT) {
+                const uint64_t dal = smem_desc(sa + A_BYTES + B_BYTES), dbl = smem_desc(sa + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+                for (int k = 0; k < BKC / 16; ++k) {
+                    umma(tmem, da + (uint64_t)(2 * k), dbl + (uint64_t)(2 * k), idesc, 1u);
+                    umma(tmem, dal + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, 1u);
+                }
+            }
             umma_commit(&empty[s]);
         }
         umma_commit(accum);
@@ -269,32 +291,47 @@ static bool encoder()
 
 bool gram_tc_available() { return gtc::encoder(); }
 
-cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, int64_t K, int64_t ldA, float* C, int* d_err)
+static bool make_map(CUtensorMap* map, const __nv_bfloat16* A, int64_t K, int64_t ldA)
 {
     using namespace gtc;
-    if (K <= 0) return cudaSuccess;
-    if ((ldA % BKC) != 0 || ((uintptr_t)A & 15) != 0 || !encoder()) return cudaErrorInvalidValue;
-    if (K > 0x7fffff00LL || ldA > 0x7fffff00LL) return cudaErrorInvalidValue;
-    CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)ldA, (cuuint64_t)K};
     cuuint64_t strides[1] = {(cuuint64_t)ldA * 2};
     cuuint32_t box[2] = {BKC, BM};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)A, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)A, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, const __nv_bfloat16* A_lo, int64_t K, int64_t ldA, float* C,
+                    int* d_err)
+{
+    using namespace gtc;
+    if (K <= 0) return cudaSuccess;
+    if ((ldA % BKC) != 0 || ((uintptr_t)A & 15) != 0 || ((uintptr_t)A_lo & 15) != 0 || !encoder())
+        return cudaErrorInvalidValue;
+    if (K > 0x7fffff00LL || ldA > 0x7fffff00LL) return cudaErrorInvalidValue;
+    CUtensorMap map, map_lo;
+    if (!make_map(&map, A, K, ldA)) return cudaErrorInvalidValue;
+    if (!make_map(&map_lo, A_lo ? A_lo : A, K, ldA)) return cudaErrorInvalidValue;
+    static bool attr[2] = {false, false};
+    const bool split = A_lo != nullptr;
+    if (!attr[split]) {
+        cudaError_t e = split ? cudaFuncSetAttribute(k_gram<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     Cfg<true>::SMEM_BYTES)
+                              : cudaFuncSetAttribute(k_gram<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     Cfg<false>::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[split] = true;
     }
     const int64_t T = (K + BM - 1) / BM;
     const int64_t tiles = T * (T + 1) / 2;
     const int nk = (int)(ldA / BKC);
     LaunchTimer lt(ctx, K_GRAM_TC);
-    k_gram<<<(unsigned)tiles, THREADS, SMEM_BYTES, ctx_stream(ctx)>>>(map, K, nk, C, d_err);
+    if (split)
+        k_gram<true><<<(unsigned)tiles, THREADS, Cfg<true>::SMEM_BYTES, ctx_stream(ctx)>>>(map, map_lo, K, nk, C, d_err);
+    else
+        k_gram<false><<<(unsigned)tiles, THREADS, Cfg<false>::SMEM_BYTES, ctx_stream(ctx)>>>(map, map_lo, K, nk, C, d_err);
     return cudaGetLastError();
 }
 

@@ -28,22 +28,31 @@ __device__ __forceinline__ double from_a(double v) { return v; }
 // Constraint space: A[r * ldA + i] (rows are constraints, contraction over orbits).
 // Padding columns up to ldA are zero.
 // ---------------------------------------------------------------------------
+// hi/lo split: lo (nullable) receives the rounding residual of the value in hi
+template <typename AT>
+__device__ __forceinline__ void store_split(AT* hi, AT* lo, size_t k, double v)
+{
+    const AT h = to_a_d<AT>(v);
+    hi[k] = h;
+    if (lo) lo[k] = to_a_d<AT>(v - (double)from_a(h));
+}
+
 template <typename T, typename AT>
 __global__ void k_whiten_orbit(const T* __restrict__ U, int64_t M, int64_t N, const double* __restrict__ inv_sig,
-                               const double* __restrict__ cs, AT* __restrict__ A, int64_t ldA)
+                               const double* __restrict__ cs, AT* __restrict__ A, AT* __restrict__ Alo, int64_t ldA)
 {
     for (int64_t i = blockIdx.x; i < N; i += gridDim.x) {
         const T* col = U + (size_t)i * M;
-        AT* row = A + (size_t)i * ldA;
         const double c = cs[i];
         for (int64_t r = threadIdx.x; r < ldA; r += blockDim.x)
-            row[r] = r < M ? to_a_d<AT>((double)col[r] * inv_sig[r] * c) : to_a_d<AT>(0.0);
+            store_split(A, Alo, (size_t)i * ldA + r, r < M ? (double)col[r] * inv_sig[r] * c : 0.0);
     }
 }
 
 template <typename T, typename AT>
 __global__ void k_whiten_transpose(const T* __restrict__ U, int64_t M, int64_t N, const double* __restrict__ inv_sig,
-                                   const double* __restrict__ cs, AT* __restrict__ A, int64_t ldA)
+                                   const double* __restrict__ cs, AT* __restrict__ A, AT* __restrict__ Alo,
+                                   int64_t ldA)
 {
     __shared__ double tile[32][33];
     const int64_t i0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
@@ -55,7 +64,7 @@ __global__ void k_whiten_transpose(const T* __restrict__ U, int64_t M, int64_t N
     __syncthreads();
     for (int k = ty; k < 32; k += 8) {
         int64_t r = r0 + k, i = i0 + tx;
-        if (r < M && i < ldA) A[(size_t)r * ldA + i] = to_a_d<AT>(tile[tx][k]);
+        if (r < M && i < ldA) store_split(A, Alo, (size_t)r * ldA + i, tile[tx][k]);
     }
 }
 
@@ -279,6 +288,73 @@ __global__ void k_shift_diag(T* __restrict__ G, int64_t K, double shift)
         G[(size_t)i * K + i] += (T)shift;
 }
 
+// G_ii += d_i (per-variable ridge)
+template <typename T>
+__global__ void k_shift_diag_vec(T* __restrict__ G, int64_t K, const double* __restrict__ d)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x)
+        G[(size_t)i * K + i] += (T)d[i];
+}
+
+// Active-set reduced solve helpers: out_k = s_k * a_k (to working precision), and
+// r_k = q_k - g_k - mu x_k (FP64), optionally scaled by s_k into working precision.
+template <typename GT>
+__global__ void k_scale_to(int64_t n, const double* __restrict__ a, const double* __restrict__ s, GT* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (GT)(a[i] * s[i]);
+}
+
+template <typename GT>
+__global__ void k_as_residual(int64_t n, const double* __restrict__ q, const double* __restrict__ g,
+                              const double* __restrict__ x, double mu, const double* __restrict__ s,
+                              GT* __restrict__ rs)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        rs[i] = (GT)((q[i] - g[i] - mu * x[i]) * s[i]);
+}
+
+// x_k += s_k * c_k
+template <typename GT>
+__global__ void k_axpy_scaled(int64_t n, const GT* __restrict__ c, const double* __restrict__ s, double* __restrict__ x)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += (double)c[i] * s[i];
+}
+
+// xs_r = acc_r * inv_sig_r^2
+__global__ void k_weight_sq(int64_t m, const double* __restrict__ acc, const double* __restrict__ inv_sig,
+                            double* __restrict__ xs)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x)
+        xs[r] = acc[r] * inv_sig[r] * inv_sig[r];
+}
+
+// S = G with the lower triangle mirrored to the upper one (full symmetric copy)
+template <typename T>
+__global__ void k_symmetrize(const T* __restrict__ G, int64_t K, T* __restrict__ S)
+{
+    __shared__ T tile[32][33];
+    const int64_t bi = blockIdx.y, bj = blockIdx.x;   // tile (bi, bj) of S, 32 x 32
+    const int tx = threadIdx.x, ty = threadIdx.y;     // 32 x 8
+    if (bi >= bj) {
+        for (int k = ty; k < 32; k += 8) {
+            int64_t r = bi * 32 + k, c = bj * 32 + tx;
+            if (r < K && c < K) S[(size_t)r * K + c] = (r >= c) ? G[(size_t)r * K + c] : G[(size_t)c * K + r];
+        }
+    } else {   // upper tile: transpose of the lower tile (bj, bi)
+        for (int k = ty; k < 32; k += 8) {
+            int64_t r = bj * 32 + k, c = bi * 32 + tx;
+            tile[k][tx] = (r < K && c < K) ? G[(size_t)r * K + c] : T(0);
+        }
+        __syncthreads();
+        for (int k = ty; k < 32; k += 8) {
+            int64_t r = bi * 32 + k, c = bj * 32 + tx;
+            if (r < K && c < K) S[(size_t)r * K + c] = tile[tx][k];
+        }
+    }
+}
+
 template <typename T>
 __global__ void k_trace(const T* __restrict__ G, int64_t K, double* out)
 {
@@ -297,9 +373,9 @@ __global__ void k_trace(const T* __restrict__ G, int64_t K, double* out)
 // lower: only c <= r contributes.
 // ---------------------------------------------------------------------------
 template <typename AT, typename XT, typename YT, typename ACC>
-__global__ void __launch_bounds__(256) k_rowdot(const AT* __restrict__ A, int64_t rows, int64_t cols, int64_t lda,
-                                                const XT* __restrict__ x, YT* __restrict__ y, double alpha,
-                                                double beta, int lower)
+__global__ void __launch_bounds__(256) k_rowdot(const AT* __restrict__ A, const AT* __restrict__ A2, int64_t rows,
+                                                int64_t cols, int64_t lda, const XT* __restrict__ x,
+                                                YT* __restrict__ y, double alpha, double beta, int lower)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -310,12 +386,20 @@ __global__ void __launch_bounds__(256) k_rowdot(const AT* __restrict__ A, int64_
         ACC s = ACC(0);
         if constexpr (sizeof(AT) == 2) {
             const __nv_bfloat162* a2 = reinterpret_cast<const __nv_bfloat162*>(a);
+            const __nv_bfloat162* b2 = A2 ? reinterpret_cast<const __nv_bfloat162*>(A2 + (size_t)r * lda) : nullptr;
             const int64_t n2 = n >> 1;
             for (int64_t c = lane; c < n2; c += 32) {
                 float2 v = __bfloat1622float2(a2[c]);
+                if (b2) {
+                    const float2 l = __bfloat1622float2(b2[c]);
+                    v.x += l.x;
+                    v.y += l.y;
+                }
                 s += (ACC)v.x * (ACC)x[2 * c] + (ACC)v.y * (ACC)x[2 * c + 1];
             }
-            if ((n & 1) && lane == 0) s += (ACC)from_a(a[n - 1]) * (ACC)x[n - 1];
+            if ((n & 1) && lane == 0)
+                s += ((ACC)from_a(a[n - 1]) + (A2 ? (ACC)from_a(A2[(size_t)r * lda + n - 1]) : ACC(0))) *
+                     (ACC)x[n - 1];
         } else {
             for (int64_t c = lane; c < n; c += 32) s += (ACC)from_a(a[c]) * (ACC)x[c];
         }
@@ -326,9 +410,9 @@ __global__ void __launch_bounds__(256) k_rowdot(const AT* __restrict__ A, int64_
 }
 
 template <typename AT, typename XT, typename YT, typename ACC>
-__global__ void __launch_bounds__(256) k_colcomb(const AT* __restrict__ A, int64_t rows, int64_t cols, int64_t lda,
-                                                 const XT* __restrict__ x, YT* __restrict__ y, double alpha,
-                                                 int64_t rows_per_split, int lower)
+__global__ void __launch_bounds__(256) k_colcomb(const AT* __restrict__ A, const AT* __restrict__ A2, int64_t rows,
+                                                 int64_t cols, int64_t lda, const XT* __restrict__ x,
+                                                 YT* __restrict__ y, double alpha, int64_t rows_per_split, int lower)
 {
     const int64_t c2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // column pair index
     const int64_t c = 2 * c2;
@@ -344,20 +428,23 @@ __global__ void __launch_bounds__(256) k_colcomb(const AT* __restrict__ A, int64
         const AT* a = A + (size_t)r * lda + c;
         ACC xr = (ACC)x[r];
         if constexpr (sizeof(AT) == 2) {
+            const AT* b = A2 ? A2 + (size_t)r * lda + c : nullptr;
             if (two) {
                 float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(a));
+                if (b) {
+                    const float2 l = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(b));
+                    v.x += l.x;
+                    v.y += l.y;
+                }
                 s0 += (ACC)v.x * xr;
                 s1 += (ACC)v.y * xr;
             } else {
-                s0 += (ACC)from_a(a[0]) * xr;
+                s0 += ((ACC)from_a(a[0]) + (b ? (ACC)from_a(b[0]) : ACC(0))) * xr;
             }
         } else {
             s0 += (ACC)from_a(a[0]) * xr;
             if (two && (!lower || r >= c + 1)) s1 += (ACC)from_a(a[1]) * xr;
         }
-    }
-    if (lower && sizeof(AT) == 2) {
-        // bf16 triangular use does not occur; keep the general path exact
     }
     if (r1 > rs) {
         atomicAdd(&y[c], (YT)(alpha * (double)s0));
@@ -611,6 +698,26 @@ __global__ void k_gather_rows(const T* __restrict__ U, int64_t M, const int64_t*
     }
 }
 
+// Uc[k, :] = U[idx[k], :] (orbit columns of the stored matrix, unchanged)
+template <typename T>
+__global__ void k_gather_cols(const T* __restrict__ U, int64_t M, const int64_t* __restrict__ idx, int64_t n,
+                              T* __restrict__ Uc)
+{
+    for (int64_t k = blockIdx.x; k < n; k += gridDim.x) {
+        const T* src = U + (size_t)idx[k] * M;
+        T* dst = Uc + (size_t)k * M;
+        for (int64_t r = threadIdx.x; r < M; r += blockDim.x) dst[r] = src[r];
+    }
+}
+
+// out[idx[k]] = a[k]
+__global__ void k_scatter_vec(const double* __restrict__ a, const int64_t* __restrict__ idx, int64_t n,
+                              double* __restrict__ out)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        out[idx[k]] = a[k];
+}
+
 __global__ void k_gather_vec(const double* __restrict__ a, const int64_t* __restrict__ idx, int64_t n,
                              double* __restrict__ out)
 {
@@ -631,14 +738,14 @@ static inline unsigned cap_grid(int64_t n, int b, int64_t cap = 1 << 20)
 
 template <typename T, typename AT>
 cudaError_t whiten(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* inv_sig, const double* cs, AT* A,
-                   int64_t ldA, bool orbit_space)
+                   AT* Alo, int64_t ldA, bool orbit_space)
 {
     LaunchTimer lt(ctx, K_WHITEN);
     if (orbit_space) {
-        k_whiten_orbit<T, AT><<<cap_grid(N, 1, 65536), 256, 0, ctx_stream(ctx)>>>(U, M, N, inv_sig, cs, A, ldA);
+        k_whiten_orbit<T, AT><<<cap_grid(N, 1, 65536), 256, 0, ctx_stream(ctx)>>>(U, M, N, inv_sig, cs, A, Alo, ldA);
     } else {
         dim3 grid((unsigned)((ldA + 31) / 32), (unsigned)((M + 31) / 32));
-        k_whiten_transpose<T, AT><<<grid, dim3(32, 8), 0, ctx_stream(ctx)>>>(U, M, N, inv_sig, cs, A, ldA);
+        k_whiten_transpose<T, AT><<<grid, dim3(32, 8), 0, ctx_stream(ctx)>>>(U, M, N, inv_sig, cs, A, Alo, ldA);
     }
     return cudaGetLastError();
 }
@@ -759,21 +866,79 @@ cudaError_t shift_and_trace(sw_ctx* ctx, T* G, int64_t K, double* d_trace, doubl
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t shift_diag_vec(sw_ctx* ctx, T* G, int64_t K, const double* d)
+{
+    LaunchTimer lt(ctx, K_SHIFT);
+    k_shift_diag_vec<T><<<cap_grid(K, 256, 1024), 256, 0, ctx_stream(ctx)>>>(G, K, d);
+    return cudaGetLastError();
+}
+template cudaError_t shift_diag_vec<float>(sw_ctx*, float*, int64_t, const double*);
+template cudaError_t shift_diag_vec<double>(sw_ctx*, double*, int64_t, const double*);
+
+template <typename GT>
+cudaError_t scale_to(sw_ctx* ctx, int64_t n, const double* a, const double* s, GT* out)
+{
+    LaunchTimer lt(ctx, K_MISC);
+    k_scale_to<GT><<<cap_grid(n, 256, 4096), 256, 0, ctx_stream(ctx)>>>(n, a, s, out);
+    return cudaGetLastError();
+}
+template <typename GT>
+cudaError_t as_residual(sw_ctx* ctx, int64_t n, const double* q, const double* g, const double* x, double mu,
+                        const double* s, GT* rs)
+{
+    LaunchTimer lt(ctx, K_RESID);
+    k_as_residual<GT><<<cap_grid(n, 256, 4096), 256, 0, ctx_stream(ctx)>>>(n, q, g, x, mu, s, rs);
+    return cudaGetLastError();
+}
+template <typename GT>
+cudaError_t axpy_scaled(sw_ctx* ctx, int64_t n, const GT* c, const double* s, double* x)
+{
+    LaunchTimer lt(ctx, K_MISC);
+    k_axpy_scaled<GT><<<cap_grid(n, 256, 4096), 256, 0, ctx_stream(ctx)>>>(n, c, s, x);
+    return cudaGetLastError();
+}
+cudaError_t weight_sq(sw_ctx* ctx, int64_t m, const double* acc, const double* inv_sig, double* xs)
+{
+    LaunchTimer lt(ctx, K_RESID);
+    k_weight_sq<<<cap_grid(m, 256, 4096), 256, 0, ctx_stream(ctx)>>>(m, acc, inv_sig, xs);
+    return cudaGetLastError();
+}
+template cudaError_t scale_to<float>(sw_ctx*, int64_t, const double*, const double*, float*);
+template cudaError_t scale_to<double>(sw_ctx*, int64_t, const double*, const double*, double*);
+template cudaError_t as_residual<float>(sw_ctx*, int64_t, const double*, const double*, const double*, double,
+                                        const double*, float*);
+template cudaError_t as_residual<double>(sw_ctx*, int64_t, const double*, const double*, const double*, double,
+                                         const double*, double*);
+template cudaError_t axpy_scaled<float>(sw_ctx*, int64_t, const float*, const double*, double*);
+template cudaError_t axpy_scaled<double>(sw_ctx*, int64_t, const double*, const double*, double*);
+
+template <typename T>
+cudaError_t symmetrize(sw_ctx* ctx, const T* G, int64_t K, T* S)
+{
+    LaunchTimer lt(ctx, K_MISC);
+    dim3 grid((unsigned)((K + 31) / 32), (unsigned)((K + 31) / 32));
+    k_symmetrize<T><<<grid, dim3(32, 8), 0, ctx_stream(ctx)>>>(G, K, S);
+    return cudaGetLastError();
+}
+template cudaError_t symmetrize<float>(sw_ctx*, const float*, int64_t, float*);
+template cudaError_t symmetrize<double>(sw_ctx*, const double*, int64_t, double*);
+
 template <typename AT, typename XT, typename YT, typename ACC>
 cudaError_t rowdot(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t cols, int64_t lda, const XT* x, YT* y,
-                   double alpha, double beta, bool lower)
+                   double alpha, double beta, bool lower, const AT* A2)
 {
     if (rows <= 0) return cudaSuccess;
     LaunchTimer lt(ctx, kid);
-    k_rowdot<AT, XT, YT, ACC><<<cap_grid(rows * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(A, rows, cols, lda, x,
-                                                                                               y, alpha, beta, lower);
+    k_rowdot<AT, XT, YT, ACC><<<cap_grid(rows * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(
+        A, A2, rows, cols, lda, x, y, alpha, beta, lower);
     return cudaGetLastError();
 }
 
 // y must be pre-initialised (it is accumulated into)
 template <typename AT, typename XT, typename YT, typename ACC>
 cudaError_t colcomb(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t cols, int64_t lda, const XT* x, YT* y,
-                    double alpha, bool lower)
+                    double alpha, bool lower, const AT* A2)
 {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     LaunchTimer lt(ctx, kid);
@@ -785,7 +950,8 @@ cudaError_t colcomb(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t col
     int64_t rps = (rows + want - 1) / want;
     if (rps < 32) rps = 32;
     unsigned gy = (unsigned)((rows + rps - 1) / rps);
-    k_colcomb<AT, XT, YT, ACC><<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(A, rows, cols, lda, x, y, alpha, rps, lower);
+    k_colcomb<AT, XT, YT, ACC><<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(A, A2, rows, cols, lda, x, y, alpha, rps,
+                                                                          lower);
     return cudaGetLastError();
 }
 
@@ -890,6 +1056,25 @@ cudaError_t gather_rows(sw_ctx* ctx, const T* U, int64_t M, const int64_t* idx, 
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t gather_cols(sw_ctx* ctx, const T* U, int64_t M, const int64_t* idx, int64_t n, T* Uc)
+{
+    if (n <= 0) return cudaSuccess;
+    LaunchTimer lt(ctx, K_MISC);
+    k_gather_cols<T><<<cap_grid(n, 1, 65536), 256, 0, ctx_stream(ctx)>>>(U, M, idx, n, Uc);
+    return cudaGetLastError();
+}
+template cudaError_t gather_cols<float>(sw_ctx*, const float*, int64_t, const int64_t*, int64_t, float*);
+template cudaError_t gather_cols<double>(sw_ctx*, const double*, int64_t, const int64_t*, int64_t, double*);
+
+cudaError_t scatter_vec(sw_ctx* ctx, const double* a, const int64_t* idx, int64_t n, double* out)
+{
+    if (n <= 0) return cudaSuccess;
+    LaunchTimer lt(ctx, K_MISC);
+    k_scatter_vec<<<cap_grid(n, 256, 4096), 256, 0, ctx_stream(ctx)>>>(a, idx, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t gather_vec(sw_ctx* ctx, const double* a, const int64_t* idx, int64_t n, double* out)
 {
     if (n <= 0) return cudaSuccess;
@@ -904,7 +1089,8 @@ template cudaError_t gather_rows<float>(sw_ctx*, const float*, int64_t, const in
 template cudaError_t gather_rows<double>(sw_ctx*, const double*, int64_t, const int64_t*, int64_t, const double*,
                                          double*);
 #define SW_WH(T, AT) \
-    template cudaError_t whiten<T, AT>(sw_ctx*, const T*, int64_t, int64_t, const double*, const double*, AT*, int64_t, bool);
+    template cudaError_t whiten<T, AT>(sw_ctx*, const T*, int64_t, int64_t, const double*, const double*, AT*, AT*, \
+                                       int64_t, bool);
 SW_WH(float, __nv_bfloat16)
 SW_WH(float, float)
 SW_WH(double, double)
@@ -919,17 +1105,20 @@ template cudaError_t tri_inverse<double>(sw_ctx*, const double*, double*, double
 template cudaError_t shift_and_trace<float>(sw_ctx*, float*, int64_t, double*, double);
 template cudaError_t shift_and_trace<double>(sw_ctx*, double*, int64_t, double*, double);
 template cudaError_t rowdot<__nv_bfloat16, float, float, float>(sw_ctx*, int, const __nv_bfloat16*, int64_t, int64_t,
-                                                               int64_t, const float*, float*, double, double, bool);
+                                                               int64_t, const float*, float*, double, double, bool, const __nv_bfloat16*);
 template cudaError_t colcomb<__nv_bfloat16, float, float, float>(sw_ctx*, int, const __nv_bfloat16*, int64_t,
-                                                                int64_t, int64_t, const float*, float*, double, bool);
+                                                                int64_t, int64_t, const float*, float*, double, bool, const __nv_bfloat16*);
 template cudaError_t rowdot<float, float, float, float>(sw_ctx*, int, const float*, int64_t, int64_t, int64_t,
-                                                       const float*, float*, double, double, bool);
+                                                       const float*, float*, double, double, bool, const float*);
+template cudaError_t rowdot<float, float, float, double>(sw_ctx*, int, const float*, int64_t, int64_t, int64_t,
+                                                        const float*, float*, double, double, bool, const float*);
 template cudaError_t colcomb<float, float, float, float>(sw_ctx*, int, const float*, int64_t, int64_t, int64_t,
-                                                        const float*, float*, double, bool);
+                                                        const float*, float*, double, bool, const float*);
 template cudaError_t rowdot<double, double, double, double>(sw_ctx*, int, const double*, int64_t, int64_t, int64_t,
-                                                           const double*, double*, double, double, bool);
+                                                           const double*, double*, double, double, bool,
+                                                           const double*);
 template cudaError_t colcomb<double, double, double, double>(sw_ctx*, int, const double*, int64_t, int64_t, int64_t,
-                                                            const double*, double*, double, bool);
+                                                            const double*, double*, double, bool, const double*);
 #define SW_GT(GT)                                                                                                  \
     template cudaError_t admm_update<GT>(sw_ctx*, int64_t, const GT*, const GT*, const GT*, const GT*, const GT*,   \
                                          const GT*, double, GT*, GT*, GT*, unsigned*);                             \

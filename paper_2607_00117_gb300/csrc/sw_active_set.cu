@@ -1,0 +1,578 @@
+// Active-set solve of the weight problem (Sec. 2.3) for libraries with many
+// more orbits than constraints.
+//
+// The non-negative least-squares minimiser keeps only a part of the N orbits
+// (about rank(U), more with the regulariser), so instead of iterating on all
+// of them this follows the Lawson-Hanson active-set method on a passive set F:
+// solve the unconstrained problem on F, keep the iterate feasible and its
+// objective non-increasing, and add the orbits that violate the KKT conditions
+// (negative gradient g_i > tol at w_i = 0).  Two changes make it fit a
+// hundred-thousand-orbit library: violators enter in blocks of the strongest
+// (largest g_i / |u~_i|), and when the solution on F has negative weights the
+// projection max(x, 0) is taken whenever it lowers the objective, so that many
+// orbits can leave in one step; the classical step back to the first zero is
+// the fallback that keeps the method monotone.
+//
+// Each reduced problem (U~_F^T U~_F + 2 lambda/N I) x = q_F is solved on the
+// GPU by preconditioned conjugate gradients whose products use the stored
+// matrix with FP64 accumulation.  The preconditioner is the Cholesky factor of
+// the Jacobi-scaled Gram of a superset P0 of F, formed on the tensor cores
+// (BF16 hi + lo split, FP32 accumulation), factored in FP32 with its triangular
+// inverse kept explicitly; while F stays inside P0 (orbits leaving) the factor
+// is reused, its F block differing from the exact inverse by a term of the rank
+// of P0 \ F.  The gradient over all N orbits is recomputed in FP64 whenever the
+// iterate settles on the optimum of its passive set.
+#include "sw_linalg.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+namespace sw {
+
+namespace {
+
+#define AS_CUDA(ctx, expr, what)                                   \
+    do {                                                           \
+        cudaError_t e_ = (expr);                                   \
+        if (e_ != cudaSuccess) return (ctx)->cuda_fail(e_, what);  \
+    } while (0)
+#define AS_TRY(expr)                 \
+    do {                             \
+        sw_status s_ = (expr);       \
+        if (s_ != SW_OK) return s_;  \
+    } while (0)
+
+__global__ void k_as_chi2_finish(const double* __restrict__ in3, double lam_over_n, double* __restrict__ out3)
+{
+    out3[0] = in3[0];
+    out3[1] = in3[1];
+    out3[2] = lam_over_n * in3[2];
+}
+
+inline int64_t pad64(int64_t n) { return (n + 63) / 64 * 64; }
+
+// ---- preconditioned conjugate gradients on (G_P + mu I) x = q_P, all in FP64.
+// cg[0], cg[2]: r.z of the two most recent iterations (ping-pong, slot `old` /
+// `fresh`), cg[1]: p.Ap, cg[3]: max|r| (bits of a non-negative double).
+constexpr int CG_THREADS = 256;
+
+__device__ inline double block_sum(double v)
+{
+    __shared__ double part[CG_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = threadIdx.x < CG_THREADS / 32 ? part[threadIdx.x] : 0.0;
+    if (threadIdx.x < 32)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ inline double block_max(double v)
+{
+    __shared__ double part[CG_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = threadIdx.x < CG_THREADS / 32 ? part[threadIdx.x] : 0.0;
+    if (threadIdx.x < 32)
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// out += sum_i a_i (b_i + mu c_i)
+__global__ void k_cg_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                         const double* __restrict__ c, double mu, double* __restrict__ out)
+{
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)CG_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * CG_THREADS)
+        s += a[i] * (b[i] + (c ? mu * c[i] : 0.0));
+    s = block_sum(s);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+}
+
+// x += alpha p, r -= alpha m (Ap + mu p) with alpha = cg[old] / cg[1]; cg[3] = max|r|.
+// m (nullable) masks the orbits of the factored set that are not in the passive set.
+__global__ void k_cg_step(int64_t n, const double* __restrict__ cg, int old, const double* __restrict__ p,
+                          const double* __restrict__ Ap, double mu, const double* __restrict__ m,
+                          double* __restrict__ x, double* __restrict__ r, unsigned long long* __restrict__ rmax)
+{
+    const double alpha = cg[old] / cg[1];
+    double mx = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)CG_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * CG_THREADS) {
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * (m ? m[i] : 1.0) * (Ap[i] + mu * p[i]);
+        r[i] = ri;
+        mx = fmax(mx, fabs(ri));
+    }
+    mx = block_max(mx);
+    if (threadIdx.x == 0) atomicMax(rmax, (unsigned long long)__double_as_longlong(mx));
+}
+
+// p = z + beta p with beta = cg[fresh] / cg[old] (beta = 0 on the first step)
+__global__ void k_cg_dir(int64_t n, const double* __restrict__ cg, int fresh, int old, bool first,
+                         const double* __restrict__ z, double* __restrict__ p)
+{
+    const double beta = first ? 0.0 : cg[fresh] / cg[old];
+    for (int64_t i = blockIdx.x * (int64_t)CG_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * CG_THREADS)
+        p[i] = z[i] + beta * p[i];
+}
+
+// r = m (q - g - mu x); max|r|
+__global__ void k_cg_residual(int64_t n, const double* __restrict__ q, const double* __restrict__ g,
+                              const double* __restrict__ x, double mu, const double* __restrict__ m,
+                              double* __restrict__ r, unsigned long long* __restrict__ rmax)
+{
+    double mx = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)CG_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * CG_THREADS) {
+        const double ri = (m ? m[i] : 1.0) * (q[i] - g[i] - mu * x[i]);
+        r[i] = ri;
+        mx = fmax(mx, fabs(ri));
+    }
+    mx = block_max(mx);
+    if (threadIdx.x == 0) atomicMax(rmax, (unsigned long long)__double_as_longlong(mx));
+}
+
+// z = m z
+__global__ void k_cg_mask(int64_t n, const double* __restrict__ m, double* __restrict__ z)
+{
+    for (int64_t i = blockIdx.x * (int64_t)CG_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * CG_THREADS)
+        z[i] *= m[i];
+}
+
+inline int cg_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + CG_THREADS - 1) / CG_THREADS, 152 * 8)); }
+
+struct Span {
+    char* p;
+    size_t used = 0;
+    template <typename X>
+    X* take(int64_t n)
+    {
+        size_t off = (used + 255) & ~(size_t)255;
+        used = off + (size_t)n * sizeof(X);
+        return p ? reinterpret_cast<X*>(p + off) : nullptr;
+    }
+};
+
+// device vectors of the active-set solve
+template <typename GT>
+struct AsVecs {
+    double *inv_sig, *ys, *acc, *e, *xs;          // M
+    double *q, *h, *w, *ute, *gneg;               // N
+    double *qP, *sP, *x, *gP, *ridge;             // passive set (cap)
+    double *r, *z, *p, *mask, *xa;                // conjugate gradients, passive mask, candidate (cap)
+    int64_t* idx;
+    GT *rs, *t1, *c;
+    double* scal;                                 // chi[4], pgmax, bad, info, err, cg[8]
+    size_t carve(char* base, int64_t M, int64_t N, int64_t cap)
+    {
+        Span s{base};
+        inv_sig = s.take<double>(M); ys = s.take<double>(M); acc = s.take<double>(M); e = s.take<double>(M);
+        xs = s.take<double>(M);
+        q = s.take<double>(N); h = s.take<double>(N); w = s.take<double>(N); ute = s.take<double>(N);
+        gneg = s.take<double>(N);
+        qP = s.take<double>(cap); sP = s.take<double>(cap); x = s.take<double>(cap); gP = s.take<double>(cap);
+        ridge = s.take<double>(cap); idx = s.take<int64_t>(cap);
+        r = s.take<double>(cap); z = s.take<double>(cap); p = s.take<double>(cap);
+        mask = s.take<double>(cap); xa = s.take<double>(cap);
+        rs = s.take<GT>(cap); t1 = s.take<GT>(cap); c = s.take<GT>(cap);
+        scal = s.take<double>(16);
+        return s.used + 256;
+    }
+};
+
+}  // namespace
+
+template <typename T, typename AT, typename GT>
+sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, const double* sig_dev, double lam,
+                           double* w_dev, double* chi2_dev)
+{
+    const int64_t M = Um->M, N = Um->N;
+    const T* U = (const T*)Um->d;
+    cudaStream_t st = ctx->stream;
+    SolveWS& ws = ctx->solve_ws;
+    const int64_t cap = std::min<int64_t>(N, std::max<int64_t>(2 * M, 4096));
+    const int64_t ldA = pad64(M);
+    const bool split = sizeof(AT) == 2;
+    const double mu = 2.0 * lam / (double)N;
+    const double floor_ridge = sizeof(GT) == 4 ? 1e-6 : 1e-11;   // keeps the factor definite; CG removes it
+
+    AsVecs<GT> V{};
+    AS_TRY(ctx->ensure(&ws.outer, &ws.outer_cap, V.carve(nullptr, M, N, cap), "active-set vectors"));
+    V.carve((char*)ws.outer, M, N, cap);
+    double* chi = V.scal;
+    unsigned long long* pgmax = (unsigned long long*)(V.scal + 4);
+    int* bad = (int*)(V.scal + 5);
+    int* info = (int*)(V.scal + 6);
+    int* gerr = (int*)(V.scal + 7);
+    double* cg = V.scal + 8;
+    unsigned long long* rmax = (unsigned long long*)(cg + 3);
+
+    AS_CUDA(ctx, cudaMemsetAsync(V.scal, 0, 16 * sizeof(double), st), "memset");
+    AS_CUDA(ctx, prep_data(ctx, M, sig_dev, y_dev, V.inv_sig, V.ys, bad), "prep data");
+    AS_CUDA(ctx, ut_times_x<T>(ctx, U, M, N, V.ys, V.q), "q");
+    AS_CUDA(ctx, colnorm2<T>(ctx, U, M, N, V.inv_sig, V.h), "column norms");
+    std::vector<double> qh(N), hh(N), gh(N), zh(N, 0.0), xh;
+    int badh = 0;
+    AS_CUDA(ctx, cudaMemcpyAsync(qh.data(), V.q, N * sizeof(double), cudaMemcpyDeviceToHost, st), "q");
+    AS_CUDA(ctx, cudaMemcpyAsync(hh.data(), V.h, N * sizeof(double), cudaMemcpyDeviceToHost, st), "h");
+    AS_CUDA(ctx, cudaMemcpyAsync(&badh, bad, sizeof(int), cudaMemcpyDeviceToHost, st), "flags");
+    AS_CUDA(ctx, cudaStreamSynchronize(st), "active set");
+    if (badh) { set_error(ctx, "solve: errors must be positive and finite, data finite"); return SW_EINVAL; }
+    double qmax = 0.0;
+    for (int64_t i = 0; i < N; ++i) qmax = std::max(qmax, std::fabs(qh[i]));
+    const double gtol = ctx->opt.kkt_tol * std::max(qmax, 1e-300);
+    const double rtol = ctx->opt.as_cg_tol * gtol;
+
+    // ---- factor of the passive Gram on a set P0 of orbits (kept while the passive
+    // set stays inside P0): gathered columns Uc, scales s = h^-1/2, explicit inverse X
+    // of the Cholesky factor of S G~ S + R (tensor-core Gram of the scaled columns)
+    std::vector<int64_t> P0;
+    std::vector<int64_t> pos(N, -1);
+    int n_factor = 0, n_solves = 0, cg_total = 0;
+    auto factor = [&](const std::vector<int64_t>& S, bool& ok) -> sw_status {
+        const int64_t nP = (int64_t)S.size();
+        ok = false;
+        for (int64_t i : P0) pos[i] = -1;
+        P0 = S;
+        for (int64_t k = 0; k < nP; ++k) pos[S[k]] = k;
+        std::vector<double> sh(nP), rh(nP);
+        AS_TRY(ctx->ensure(&ws.Uc, &ws.Uc_cap, (size_t)nP * M * sizeof(T), "passive columns"));
+        AS_TRY(ctx->ensure(&ws.A, &ws.A_cap, (size_t)nP * ldA * sizeof(AT), "passive matrix"));
+        if (split) AS_TRY(ctx->ensure(&ws.Alo, &ws.Alo_cap, (size_t)nP * ldA * sizeof(AT), "passive matrix (lo)"));
+        AS_TRY(ctx->ensure(&ws.G, &ws.G_cap, (size_t)nP * nP * sizeof(GT), "reduced Gram"));
+        AS_TRY(ctx->ensure(&ws.X, &ws.X_cap, (size_t)nP * nP * sizeof(GT), "reduced inverse factor"));
+        AS_TRY(ctx->ensure(&ws.D, &ws.D_cap, 64 * 64 * sizeof(GT), "block scratch"));
+        T* Uc = (T*)ws.Uc;
+        AT* A = (AT*)ws.A;
+        AT* Alo = split ? (AT*)ws.Alo : nullptr;
+        GT* G = (GT*)ws.G;
+        for (int64_t k = 0; k < nP; ++k) sh[k] = 1.0 / std::sqrt(hh[S[k]] > 0.0 ? hh[S[k]] : 1.0);
+        AS_CUDA(ctx, cudaMemcpyAsync(V.idx, S.data(), nP * sizeof(int64_t), cudaMemcpyHostToDevice, st), "idx");
+        AS_CUDA(ctx, cudaMemcpyAsync(V.sP, sh.data(), nP * sizeof(double), cudaMemcpyHostToDevice, st), "scales");
+        AS_CUDA(ctx, gather_cols<T>(ctx, U, M, V.idx, nP, Uc), "gather");
+        AS_CUDA(ctx, gather_vec(ctx, V.q, V.idx, nP, V.qP), "q_P");
+        AS_CUDA(ctx, (whiten<T, AT>(ctx, Uc, M, nP, V.inv_sig, V.sP, A, Alo, ldA, true)), "whiten");
+        double fl = floor_ridge;
+        int infoh = 1, gerrh = 0;
+        for (int attempt = 0; attempt < 4 && infoh != 0; ++attempt, fl *= 100.0) {
+            for (int64_t k = 0; k < nP; ++k) rh[k] = std::max(mu * sh[k] * sh[k], fl);
+            AS_CUDA(ctx, cudaMemcpyAsync(V.ridge, rh.data(), nP * sizeof(double), cudaMemcpyHostToDevice, st), "ridge");
+            AS_CUDA(ctx, cudaMemsetAsync(info, 0, sizeof(int), st), "memset");
+            if constexpr (sizeof(AT) == 2) {
+                AS_CUDA(ctx, gram_tc(ctx, A, Alo, nP, ldA, (float*)G, gerr), "reduced Gram");
+            } else {
+                AS_CUDA(ctx, (gemm<GT, true, true>(ctx, K_GRAM_SIMT, nP, nP, ldA, GT(1), (const GT*)A, ldA,
+                                                   (const GT*)A, ldA, GT(0), G, nP, 0)),
+                        "reduced Gram");
+            }
+            AS_CUDA(ctx, shift_diag_vec<GT>(ctx, G, nP, V.ridge), "ridge");
+            AS_CUDA(ctx, cholesky<GT>(ctx, G, nP, info), "reduced Cholesky");
+            AS_CUDA(ctx, cudaMemcpyAsync(&infoh, info, sizeof(int), cudaMemcpyDeviceToHost, st), "info");
+            AS_CUDA(ctx, cudaMemcpyAsync(&gerrh, gerr, sizeof(int), cudaMemcpyDeviceToHost, st), "flags");
+            AS_CUDA(ctx, cudaStreamSynchronize(st), "reduced factor");
+            if (gerrh) { set_error(ctx, "solve: tensor-core Gram kernel timed out"); return SW_ETIMEOUT; }
+        }
+        ++n_factor;
+        if (infoh != 0) return SW_OK;   // ok = false
+        AS_CUDA(ctx, tri_inverse<GT>(ctx, G, (GT*)ws.X, (GT*)ws.D, nP), "reduced inverse");
+        ok = true;
+        return SW_OK;
+    };
+
+    // ---- (G_F + mu I) x = q_F for a passive set F inside P0, by preconditioned
+    // conjugate gradients in the coordinates of P0 with the orbits outside F masked:
+    // the preconditioner is the F block of the inverse of the P0 factor, which differs
+    // from the exact inverse on F by a term of the rank of P0 \ F.  Products use the
+    // stored matrix with FP64 accumulation.  Result in xh (P0 order, zero outside F).
+    auto solve_on = [&](const std::vector<int64_t>& F, bool& converged) -> sw_status {
+        const int64_t nP = (int64_t)P0.size();
+        const T* Uc = (const T*)ws.Uc;
+        const GT* X = (const GT*)ws.X;
+        converged = false;
+        std::vector<double> mh(nP, 0.0);
+        for (int64_t i : F) mh[pos[i]] = 1.0;
+        AS_CUDA(ctx, cudaMemcpyAsync(V.mask, mh.data(), nP * sizeof(double), cudaMemcpyHostToDevice, st), "mask");
+        const int nb = cg_blocks(nP);
+        auto precond = [&](const double* r, double* z) -> sw_status {   // z = m S X^T X S r
+            AS_CUDA(ctx, scale_to<GT>(ctx, nP, r, V.sP, V.rs), "precondition");
+            AS_CUDA(ctx, (rowdot<GT, GT, GT, GT>(ctx, K_TRMV_L, X, nP, nP, nP, V.rs, V.t1, 1.0, 0.0, true)),
+                    "precondition");
+            AS_CUDA(ctx, cudaMemsetAsync(V.c, 0, nP * sizeof(GT), st), "memset");
+            AS_CUDA(ctx, (colcomb<GT, GT, GT, GT>(ctx, K_TRMV_LT, X, nP, nP, nP, V.t1, V.c, 1.0, true)),
+                    "precondition");
+            AS_CUDA(ctx, cudaMemsetAsync(z, 0, nP * sizeof(double), st), "memset");
+            AS_CUDA(ctx, axpy_scaled<GT>(ctx, nP, V.c, V.sP, z), "precondition");
+            {
+                LaunchTimer lt(ctx, K_PCG);
+                k_cg_mask<<<nb, CG_THREADS, 0, st>>>(nP, V.mask, z);
+            }
+            AS_CUDA(ctx, cudaGetLastError(), "precondition");
+            return SW_OK;
+        };
+        auto apply_G = [&](const double* v, double* out) -> sw_status {   // out = U_P0^T W U_P0 v
+            AS_CUDA(ctx, cudaMemsetAsync(V.acc, 0, M * sizeof(double), st), "memset");
+            AS_CUDA(ctx, u_times_w<T>(ctx, Uc, M, nP, v, V.acc), "U_P v");
+            AS_CUDA(ctx, weight_sq(ctx, M, V.acc, V.inv_sig, V.xs), "weights");
+            AS_CUDA(ctx, ut_times_x<T>(ctx, Uc, M, nP, V.xs, out), "U_P^T");
+            return SW_OK;
+        };
+        // warm start x = m P^-1 q, r = m (q - (G + mu) x)
+        AS_TRY(precond(V.qP, V.x));
+        AS_TRY(apply_G(V.x, V.gP));
+        AS_CUDA(ctx, cudaMemsetAsync(cg, 0, 8 * sizeof(double), st), "memset");
+        {
+            LaunchTimer lt(ctx, K_PCG);
+            k_cg_residual<<<nb, CG_THREADS, 0, st>>>(nP, V.qP, V.gP, V.x, mu, V.mask, V.r, rmax);
+        }
+        AS_CUDA(ctx, cudaGetLastError(), "residual");
+        double rm = 0.0;
+        int old = 0, fresh = 2, it = 0;
+        for (;; ++it) {
+            AS_CUDA(ctx, cudaMemcpyAsync(&rm, rmax, sizeof(double), cudaMemcpyDeviceToHost, st), "residual");
+            AS_CUDA(ctx, cudaStreamSynchronize(st), "pcg");
+            if (!(rm > rtol)) { converged = rm == rm; break; }
+            if (it >= ctx->opt.as_cg_max) break;
+            AS_TRY(precond(V.r, V.z));
+            AS_CUDA(ctx, cudaMemsetAsync(cg + fresh, 0, sizeof(double), st), "memset");
+            AS_CUDA(ctx, cudaMemsetAsync(cg + 1, 0, sizeof(double), st), "memset");
+            AS_CUDA(ctx, cudaMemsetAsync(cg + 3, 0, sizeof(double), st), "memset");
+            {
+                LaunchTimer lt(ctx, K_PCG);
+                k_cg_dot<<<nb, CG_THREADS, 0, st>>>(nP, V.r, V.z, nullptr, 0.0, cg + fresh);
+                k_cg_dir<<<nb, CG_THREADS, 0, st>>>(nP, cg, fresh, old, it == 0, V.z, V.p);
+            }
+            AS_CUDA(ctx, cudaGetLastError(), "pcg");
+            AS_TRY(apply_G(V.p, V.gP));
+            {
+                LaunchTimer lt(ctx, K_PCG);
+                k_cg_dot<<<nb, CG_THREADS, 0, st>>>(nP, V.p, V.gP, V.p, mu, cg + 1);
+                k_cg_step<<<nb, CG_THREADS, 0, st>>>(nP, cg, fresh, V.p, V.gP, mu, V.mask, V.x, V.r, rmax);
+            }
+            AS_CUDA(ctx, cudaGetLastError(), "pcg");
+            std::swap(old, fresh);
+        }
+        cg_total += it;
+        ++n_solves;
+        if (ctx->opt.verbose > 1)
+            fprintf(stderr, "[sw]   solve |F| %zu in |P0| %lld: max|r| %.3g (tolerance %.3g), %d steps\n", F.size(),
+                    (long long)nP, rm, rtol, it);
+        xh.resize(nP);
+        AS_CUDA(ctx, cudaMemcpyAsync(xh.data(), V.x, nP * sizeof(double), cudaMemcpyDeviceToHost, st), "x");
+        AS_CUDA(ctx, cudaStreamSynchronize(st), "reduced solve");
+        for (double v : xh)
+            if (!std::isfinite(v)) converged = false;
+        return SW_OK;
+    };
+
+    // objective chi^2 + mu |w|^2 of weights w supported on P0 (device vector in P0 order)
+    auto objective_P0 = [&](const double* wP, double& fval) -> sw_status {
+        const int64_t nP = (int64_t)P0.size();
+        double ch[4];
+        AS_CUDA(ctx, cudaMemsetAsync(V.acc, 0, M * sizeof(double), st), "memset");
+        AS_CUDA(ctx, u_times_w<T>(ctx, (const T*)ws.Uc, M, nP, wP, V.acc), "U_P w");
+        AS_CUDA(ctx, residual(ctx, M, y_dev, V.acc, V.inv_sig, V.e, V.xs), "residual");
+        AS_CUDA(ctx, cudaMemsetAsync(chi, 0, 4 * sizeof(double), st), "memset");
+        AS_CUDA(ctx, chi2(ctx, M, Um->nd, V.e, nP, wP, chi), "chi2");
+        AS_CUDA(ctx, cudaMemcpyAsync(ch, chi, 4 * sizeof(double), cudaMemcpyDeviceToHost, st), "chi2");
+        AS_CUDA(ctx, cudaStreamSynchronize(st), "objective");
+        fval = ch[0] + mu * ch[2];
+        return SW_OK;
+    };
+
+    // exact state of zh over all N: negative gradient gh, projected gradient, chi^2
+    double pg_rel = 1.0, chi_h[4] = {0, 0, 0, 0};
+    auto evaluate = [&]() -> sw_status {
+        AS_CUDA(ctx, cudaMemcpyAsync(V.w, zh.data(), N * sizeof(double), cudaMemcpyHostToDevice, st), "w");
+        AS_CUDA(ctx, cudaMemsetAsync(V.acc, 0, M * sizeof(double), st), "memset");
+        AS_CUDA(ctx, u_times_w<T>(ctx, U, M, N, V.w, V.acc), "U w");
+        AS_CUDA(ctx, residual(ctx, M, y_dev, V.acc, V.inv_sig, V.e, V.xs), "residual");
+        AS_CUDA(ctx, ut_times_x<T>(ctx, U, M, N, V.xs, V.ute), "U^T e");
+        AS_CUDA(ctx, cudaMemsetAsync(pgmax, 0, 8, st), "memset");
+        AS_CUDA(ctx, kkt(ctx, N, V.ute, V.w, mu, V.gneg, pgmax), "KKT");
+        AS_CUDA(ctx, cudaMemsetAsync(chi, 0, 4 * sizeof(double), st), "memset");
+        AS_CUDA(ctx, chi2(ctx, M, Um->nd, V.e, N, V.w, chi), "chi2");
+        unsigned long long pb = 0;
+        AS_CUDA(ctx, cudaMemcpyAsync(&pb, pgmax, 8, cudaMemcpyDeviceToHost, st), "KKT");
+        AS_CUDA(ctx, cudaMemcpyAsync(chi_h, chi, 4 * sizeof(double), cudaMemcpyDeviceToHost, st), "chi2");
+        AS_CUDA(ctx, cudaMemcpyAsync(gh.data(), V.gneg, N * sizeof(double), cudaMemcpyDeviceToHost, st), "g");
+        AS_CUDA(ctx, cudaStreamSynchronize(st), "evaluate");
+        double pgv;
+        memcpy(&pgv, &pb, 8);
+        pg_rel = pgv / std::max(qmax, 1e-300);
+        return SW_OK;
+    };
+
+    // ---- block principal pivoting (Portugal, Judice & Vicente 1994; Kim & Park 2011)
+    // on the passive set F: solve on F, then move passive orbits with negative weight
+    // out and KKT violators (g_i > tol at w_i = 0) in.  Entering is limited to the
+    // max(as_block, as_grow |F|) strongest violators (largest g_i / |u~_i|).  While the number of
+    // violations keeps falling, all of them are exchanged; after a step without a new
+    // minimum only the most violating fraction is, halved at every such step (the
+    // strongest first), which damps the cycling that a full exchange can fall into;
+    // a fraction below one orbit exchanges the single worst violator.
+    std::vector<char> inF(N, 0);
+    std::vector<int64_t> F;
+    std::vector<double> buf;
+    bool failed = false, converged = false, evaluated = false;
+    // candidate set C: the orbits with the largest q_i / |u~_i| first; pivoting runs on
+    // C and C grows by the strongest violators outside it whenever F is optimal on C
+    std::vector<char> inC(N, 0);
+    int64_t nC = std::min<int64_t>(N, std::max<int64_t>(1, ctx->opt.as_candidates > 0 ? (int64_t)ctx->opt.as_candidates : 2 * M));
+    {
+        std::vector<std::pair<double, int64_t>> sc(N);
+        for (int64_t i = 0; i < N; ++i) sc[i] = {hh[i] > 0.0 ? qh[i] / std::sqrt(hh[i]) : -1e300, i};
+        std::partial_sort(sc.begin(), sc.begin() + nC, sc.end(),
+                          [](const std::pair<double, int64_t>& a, const std::pair<double, int64_t>& b) {
+                              return a.first > b.first;
+                          });
+        for (int64_t k = 0; k < nC; ++k) inC[sc[k].second] = 1;
+    }
+    int outer = 0;
+    int64_t best_nv = N + 1;
+    double frac = 1.0;
+    const int64_t block = std::max<int64_t>(1, ctx->opt.as_block);
+    // merit: objective of the projection max(x, 0) of each iterate; the best is kept
+    std::vector<double> zbest(N, 0.0);
+    double fproj = 0.0, fbest = 0.0;
+    {
+        double f0 = 0.0;
+        AS_TRY(evaluate());
+        f0 = chi_h[0];
+        fbest = fproj = f0;
+    }
+    for (; outer < 1000000 && n_solves < ctx->opt.as_solves; ++outer) {
+        std::vector<std::pair<double, int64_t>> neg, enter;   // (violation, orbit)
+        for (int64_t i : F)
+            if (zh[i] < 0.0) neg.push_back({-zh[i] * std::sqrt(hh[i]), i});
+        for (int64_t i = 0; i < N; ++i)
+            if (inC[i] && !inF[i] && gh[i] > gtol && hh[i] > 0.0) enter.push_back({gh[i] / std::sqrt(hh[i]), i});
+        if (neg.empty() && enter.empty() && nC < N) {
+            // optimal on the candidate set C: widen C by the strongest violators outside it
+            std::vector<std::pair<double, int64_t>> out;
+            for (int64_t i = 0; i < N; ++i)
+                if (!inC[i] && gh[i] > gtol && hh[i] > 0.0) out.push_back({gh[i] / std::sqrt(hh[i]), i});
+            const int64_t kc = std::min<int64_t>((int64_t)out.size(), std::max<int64_t>(block, nC / 2));
+            std::partial_sort(out.begin(), out.begin() + kc, out.end(),
+                              [](const std::pair<double, int64_t>& a, const std::pair<double, int64_t>& b) {
+                                  return a.first > b.first;
+                              });
+            for (int64_t k = 0; k < kc; ++k) {
+                inC[out[k].second] = 1;
+                enter.push_back(out[k]);
+            }
+            nC += kc;
+            best_nv = N + 1;
+            frac = 1.0;
+            if (ctx->opt.verbose && kc)
+                fprintf(stderr, "[sw] candidate set widened by %lld to %lld orbits\n", (long long)kc, (long long)nC);
+        }
+        const int64_t nv = (int64_t)(neg.size() + enter.size());
+        if (ctx->opt.verbose)
+            fprintf(stderr,
+                    "[sw] pivoting %d: |F| %zu solves %d cg %d negative %zu entering %zu fraction %.3g "
+                    "objective+ %.10g\n",
+                    outer, F.size(), n_solves, cg_total, neg.size(), enter.size(), frac, fproj);
+        if (nv == 0) { converged = true; break; }
+        const int64_t lim = std::max<int64_t>(block, (int64_t)(ctx->opt.as_grow * (double)F.size()));
+        if (outer > 0) {
+            if (fproj < fbest * (1.0 - 1e-13) || nv < best_nv) frac = 1.0;
+            else frac *= 0.5;
+            best_nv = std::min(best_nv, nv);
+        }
+        auto by_violation = [](const std::pair<double, int64_t>& a, const std::pair<double, int64_t>& b) {
+            return a.first > b.first;
+        };
+        int64_t kn = (int64_t)std::ceil(frac * (double)neg.size());
+        int64_t ke = std::min<int64_t>(lim, (int64_t)std::ceil(frac * (double)enter.size()));
+        if (frac * (double)nv < 1.0) {   // single worst violator
+            kn = ke = 0;
+            if (!neg.empty() && (enter.empty() || *std::max_element(neg.begin(), neg.end()) >
+                                                      *std::max_element(enter.begin(), enter.end())))
+                kn = 1;
+            else
+                ke = 1;
+        }
+        ke = std::max<int64_t>(0, std::min<int64_t>(ke, cap - ((int64_t)F.size() - kn)));
+        std::partial_sort(neg.begin(), neg.begin() + kn, neg.end(), by_violation);
+        std::partial_sort(enter.begin(), enter.begin() + ke, enter.end(), by_violation);
+        for (int64_t k = 0; k < kn; ++k) inF[neg[k].second] = 0;
+        for (int64_t k = 0; k < ke; ++k) inF[enter[k].second] = 1;
+        F.clear();
+        for (int64_t i = 0; i < N; ++i)
+            if (inF[i]) F.push_back(i);
+        std::fill(zh.begin(), zh.end(), 0.0);
+        if (!F.empty()) {
+            bool ok = false, conv = false;
+            AS_TRY(factor(F, ok));
+            if (!ok) { failed = true; break; }
+            AS_TRY(solve_on(F, conv));
+            for (int64_t i : F) zh[i] = xh[pos[i]];
+            buf.assign(P0.size(), 0.0);
+            for (int64_t i : F) buf[pos[i]] = std::max(zh[i], 0.0);
+            AS_CUDA(ctx, cudaMemcpyAsync(V.xa, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, st),
+                    "x+");
+            AS_TRY(objective_P0(V.xa, fproj));
+        } else {
+            fproj = fbest;
+        }
+        if (fproj < fbest) {
+            fbest = fproj;
+            for (int64_t i = 0; i < N; ++i) zbest[i] = std::max(zh[i], 0.0);
+        }
+        AS_TRY(evaluate());
+        evaluated = true;
+    }
+    if (!converged) {   // return the best projected iterate
+        zh = zbest;
+        evaluated = false;
+    }
+    // the returned weights are the feasible part of the last iterate
+    bool clipped = false;
+    for (auto& v : zh)
+        if (v < 0.0) { v = 0.0; clipped = true; }
+    if (clipped) evaluated = false;
+    if (!evaluated) AS_TRY(evaluate());
+    const bool kkt_ok = pg_rel <= ctx->opt.kkt_tol;
+    int64_t support = 0;
+    for (int64_t i = 0; i < N; ++i) support += zh[i] > 0.0;
+    {
+        LaunchTimer lt(ctx, K_CHI2);
+        k_as_chi2_finish<<<1, 1, 0, st>>>(chi, lam / (double)N, chi2_dev);
+    }
+    AS_CUDA(ctx, cudaGetLastError(), "chi2");
+    AS_CUDA(ctx, cudaMemcpyAsync(w_dev, V.w, N * sizeof(double), cudaMemcpyDeviceToDevice, st), "weights");
+    AS_CUDA(ctx, cudaStreamSynchronize(st), "active set");
+    ctx->solve_info[0] = cg_total;
+    ctx->solve_info[1] = n_factor;
+    ctx->solve_info[2] = pg_rel;
+    ctx->solve_info[3] = N > M ? 1.0 : 0.0;
+    ctx->solve_info[4] = n_solves;
+    ctx->solve_info[5] = kkt_ok ? 1.0 : 0.0;
+    ctx->solve_info[6] = outer + 1;
+    ctx->solve_info[7] = (double)support;
+    if (ctx->opt.verbose)
+        fprintf(stderr, "[sw] active set done: support %lld solves %d factors %d cg %d pg_rel %.3g%s\n",
+                (long long)support, n_solves, n_factor, cg_total, pg_rel, converged ? "" : " (stopped)");
+    if (failed) {
+        set_error(ctx, "solve: reduced Gram not positive definite after ridge retries (|F| %zu)", F.size());
+        return SW_ENONCONV;
+    }
+    if (!kkt_ok) {
+        set_error(ctx, "solve: active set stopped at projected gradient %.3g of max|q| after %d solves", pg_rel,
+                  n_solves);
+        return SW_ENONCONV;
+    }
+    return SW_OK;
+}
+
+template sw_status solve_active_set<float, __nv_bfloat16, float>(sw_ctx*, const sw_matrix*, const double*,
+                                                                  const double*, double, double*, double*);
+template sw_status solve_active_set<float, float, float>(sw_ctx*, const sw_matrix*, const double*, const double*,
+                                                         double, double*, double*);
+template sw_status solve_active_set<double, double, double>(sw_ctx*, const sw_matrix*, const double*,
+                                                            const double*, double, double*, double*);
+
+}  // namespace sw

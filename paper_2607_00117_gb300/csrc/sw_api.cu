@@ -16,7 +16,7 @@ const char* kKernelNames[K_COUNT] = {
     "ics_to_soa", "orbit_project_bin", "orbit_drift", "zero_flagged", "finalize_columns", "trajectory",
     "potential_eval", "whiten", "gram_tcgen05", "gram_simt", "shift_diag", "potrf_diag", "trsm_panel",
     "syrk_update", "trinv_diag", "trinv_update", "gemv_n", "gemv_t", "trmv_l", "trmv_lt", "admm_update",
-    "residual", "gradient", "chi2", "misc", "batch_orbit_bin", "mlp_fwd", "mlp_bwd", "adam", "reduce_gh"};
+    "residual", "gradient", "chi2", "misc", "batch_orbit_bin", "mlp_fwd", "mlp_bwd", "adam", "reduce_gh", "pcg", "bundle"};
 
 void set_error(sw_ctx* ctx, const char* fmt, ...)
 {
@@ -607,6 +607,40 @@ extern "C" sw_status sw_reduce_gh(sw_ctx* ctx, const sw_matrix* U_hist, const do
                              : reduce_gh_impl<float>(ctx, U_hist, gh_v0_s, U_gh_out);
 }
 
+extern "C" sw_status sw_bundle(sw_ctx* ctx, const sw_matrix* U, int64_t n, sw_matrix** U_out)
+{
+    CHECK_CTX(ctx);
+    if (!U || !U_out) { set_error(ctx, "sw_bundle: NULL argument"); return SW_EINVAL; }
+    *U_out = nullptr;
+    if (U->ctx != ctx) { set_error(ctx, "sw_bundle: matrix belongs to another context"); return SW_EINVAL; }
+    if (n < 1 || U->N % n != 0) {
+        set_error(ctx, "sw_bundle: bundle size %lld must divide the orbit count %lld", (long long)n, (long long)U->N);
+        return SW_EINVAL;
+    }
+    sw_matrix* B = new sw_matrix(*U);
+    B->d = nullptr;
+    B->N = U->N / n;
+    const size_t bytes = (size_t)U->M * (size_t)B->N * (size_t)U->elem;
+    cudaError_t e = cudaMalloc(&B->d, bytes);
+    if (e) {
+        cudaGetLastError();
+        delete B;
+        set_error(ctx, "sw_bundle: allocation failed");
+        return SW_ENOMEM;
+    }
+    e = U->elem == 8 ? launch_bundle<double>(ctx, U->d, U->M, B->N, (int)n, B->d)
+                     : launch_bundle<float>(ctx, U->d, U->M, B->N, (int)n, B->d);
+    if (!e) e = cudaStreamSynchronize(ctx->stream);
+    if (e) {
+        cudaFree(B->d);
+        delete B;
+        return ctx->cuda_fail(e, "bundle");
+    }
+    ctx->live_matrices++;
+    *U_out = B;
+    return SW_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Matrix access
 // ---------------------------------------------------------------------------
@@ -808,6 +842,43 @@ extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value)
     } else if (!strcmp(key, "polish_max")) {
         if (!(value >= 0)) return SW_EINVAL;
         ctx->opt.polish_max = (int)value;
+    } else if (!strcmp(key, "large_solver")) {
+        if (!(value == 0 || value == 1)) return SW_EINVAL;
+        ctx->opt.large_solver = (int)value;
+    } else if (!strcmp(key, "as_block")) {
+        if (!(value >= 1)) return SW_EINVAL;
+        ctx->opt.as_block = (int)value;
+    } else if (!strcmp(key, "as_candidates")) {
+        if (!(value >= 0.0)) return SW_EINVAL;
+        ctx->opt.as_candidates = value;
+    } else if (!strcmp(key, "as_grow")) {
+        if (!(value >= 0.0)) return SW_EINVAL;
+        ctx->opt.as_grow = value;
+    } else if (!strcmp(key, "as_cg_tol")) {
+        if (!(value > 0.0)) return SW_EINVAL;
+        ctx->opt.as_cg_tol = value;
+    } else if (!strcmp(key, "as_cg_max")) {
+        if (!(value >= 0)) return SW_EINVAL;
+        ctx->opt.as_cg_max = (int)value;
+    } else if (!strcmp(key, "as_solves")) {
+        if (!(value >= 1)) return SW_EINVAL;
+        ctx->opt.as_solves = (int)value;
+    } else if (!strcmp(key, "inner_refine")) {
+        if (!(value >= 0 && value <= 8)) return SW_EINVAL;
+        ctx->opt.inner_refine = (int)value;
+    } else if (!strcmp(key, "verbose")) {
+        ctx->opt.verbose = (int)value;
+    } else if (!strcmp(key, "working_set")) {
+        ctx->opt.working_set = value != 0;
+    } else if (!strcmp(key, "orbit_direct_max")) {
+        if (!(value >= 0)) return SW_EINVAL;
+        ctx->opt.orbit_direct_max = (int64_t)value;
+    } else if (!strcmp(key, "ws_factor")) {
+        if (!(value > 0)) return SW_EINVAL;
+        ctx->opt.ws_factor = value;
+    } else if (!strcmp(key, "ws_rounds")) {
+        if (!(value >= 1)) return SW_EINVAL;
+        ctx->opt.ws_rounds = (int)value;
     } else if (!strcmp(key, "gram_tensor_cores")) {
         ctx->opt.gram_tc = value != 0;
     } else {

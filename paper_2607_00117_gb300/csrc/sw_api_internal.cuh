@@ -14,21 +14,38 @@ struct Options {
     int admm_max_iter = 400;     // ADMM iteration cap per run
     double admm_tol = 1e-6;      // ADMM stop: ||w-z||inf, rho||z-z_prev||inf <= tol * max(1, ||z||inf)
     int refine_max = 8;          // refinement rounds with FP64 residuals
-    double kkt_tol = 1e-6;       // KKT stop: ||P(grad)||inf <= kkt_tol * max|q|
+    double kkt_tol = 1e-9;       // KKT stop: ||P(grad)||inf <= kkt_tol * max|q|
     int check_every = 20;        // ADMM iterations between host convergence checks
     double admm_rho = 0.01;      // ADMM penalty relative to each orbit's Gram diagonal (orbit space)
     double admm_rho_cs = 1.0;    // the same in constraint space (the Woodbury form cancels digits for small rho)
     double admm_alpha = 1.6;     // over-relaxation
-    double chi2_tol = 1e-7;      // refinement also stops once chi^2 changes by less than this (relative)
-    int polish_max = 6000;       // largest support solved exactly by the active-set polish (0: off)
-    int polish_solves = 60;      // cap on reduced solves per polish
+    double chi2_tol = 1e-6;      // refinement also stops once chi^2 changes by less than this (relative)
+    int64_t orbit_direct_max = 8192;  // N > M up to this size: orbit space on all orbits
+    int polish_max = 2048;       // largest support solved exactly by the active-set polish (0: off)
+    int polish_solves = 400;     // cap on reduced solves per polish
+    bool working_set = true;     // N > M: orbit-space solves on a working set instead of the Woodbury form
+    double ws_factor = 0.6;      // initial working-set size in units of M
+    int ws_rounds = 6;           // working-set exchange rounds
+    int verbose = 0;        // solver progress on stderr
+    int inner_refine = 1;        // refinement steps of each ADMM linear solve against the kept Gram
+    int large_solver = 0;        // N > orbit_direct_max: 0 block active set, 1 ADMM working set
+    int as_block = 2048;         // active set: violators entering per pivoting step
+    double as_candidates = 0;    // active set: initial candidate-set size (0: 2 M)
+    double as_grow = 0.0;        // active set: at most max(as_block, as_grow |F|) orbits enter per step
+    int as_cg_max = 200;         // active set: conjugate-gradient steps per reduced solve
+    double as_cg_tol = 0.05;     // active set: CG stops at max|r| <= as_cg_tol * kkt_tol * max|q|
+    int as_solves = 400;         // active set: cap on reduced solves
     bool gram_tc = true;         // tcgen05 BF16 Gram (FP32 path); false: SIMT FP32 Gram
 };
 
 // Device workspace of the weight solve, sized for the largest problem seen.
 struct SolveWS {
     void* A = nullptr; size_t A_cap = 0;          // whitened matrix (BF16 or FP64), K-major for the Gram
+    void* Alo = nullptr; size_t Alo_cap = 0;      // BF16 rounding residual of A (hi/lo split)
+    void* Uc = nullptr; size_t Uc_cap = 0;        // working-set columns of U
+    void* outer = nullptr; size_t outer_cap = 0;  // working-set driver vectors
     void* G = nullptr; size_t G_cap = 0;          // K x K Gram, Cholesky factor in place
+    void* Gs = nullptr; size_t Gs_cap = 0;        // symmetric copy of Gram + I (step refinement)
     void* X = nullptr; size_t X_cap = 0;          // K x K inverse of the Cholesky factor
     void* D = nullptr; size_t D_cap = 0;          // nb x nb diagonal-block scratch
     void* vec = nullptr; size_t vec_cap = 0;      // vectors
@@ -73,7 +90,7 @@ struct sw_ctx {
     int64_t last_proj_n = 0;
     // solve
     sw::SolveWS solve_ws;
-    double solve_info[6] = {0, 0, 0, 0, 0, 0};
+    double solve_info[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // lifetime: matrices keep their context alive until the last one is freed
     int64_t live_matrices = 0;
     bool destroyed = false;

@@ -63,7 +63,7 @@ enum KernelId {
     K_ICS_SOA = 0, K_ORBIT_BIN, K_ORBIT_DRIFT, K_ZERO_FLAGGED, K_FINALIZE, K_TRAJ, K_POTEVAL,
     K_WHITEN, K_GRAM_TC, K_GRAM_SIMT, K_SHIFT, K_POTRF_DIAG, K_TRSM_PANEL, K_SYRK_UPDATE,
     K_TRINV_DIAG, K_TRINV_UPDATE, K_GEMV_N, K_GEMV_T, K_TRMV_L, K_TRMV_LT, K_ADMM_UPDATE,
-    K_RESID, K_GRAD, K_CHI2, K_MISC, K_BATCH_ORBIT, K_MLP_FWD, K_MLP_BWD, K_ADAM, K_REDUCE_GH, K_COUNT
+    K_RESID, K_GRAD, K_CHI2, K_MISC, K_BATCH_ORBIT, K_MLP_FWD, K_MLP_BWD, K_ADAM, K_REDUCE_GH, K_PCG, K_BUNDLE, K_COUNT
 };
 extern const char* kKernelNames[K_COUNT];
 
@@ -97,6 +97,8 @@ cudaError_t launch_poteval(sw_ctx* ctx, const FieldT<T>& f, const double* xyz, i
 template <typename T>
 cudaError_t launch_reduce_gh(sw_ctx* ctx, const void* Uh, int64_t Mh, int64_t N, int64_t nd, int64_t npix, int nv,
                              const void* W, void* Ug, int64_t Mg);
+template <typename T>
+cudaError_t launch_bundle(sw_ctx* ctx, const void* U, int64_t M, int64_t Nb, int n, void* out);
 cudaError_t launch_batch_orbit_bin(sw_ctx* ctx, const ModelT<float>* models_dev, int n_models,
                                    const int64_t* tile_model, const int64_t* tile_first, int64_t n_tiles,
                                    const float* soa, int64_t ld, int64_t nsteps, int ej_every, double* drift,

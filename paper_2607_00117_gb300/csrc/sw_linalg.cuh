@@ -6,7 +6,7 @@ namespace sw {
 
 template <typename T, typename AT>
 cudaError_t whiten(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* inv_sig, const double* cs, AT* A,
-                   int64_t ldA, bool orbit_space);
+                   AT* Alo, int64_t ldA, bool orbit_space);
 template <typename T>
 cudaError_t colnorm2(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* inv_sig, double* h);
 template <typename GT>
@@ -22,13 +22,26 @@ cudaError_t cholesky(sw_ctx* ctx, T* G, int64_t K, int* d_info);
 template <typename T>
 cudaError_t tri_inverse(sw_ctx* ctx, const T* G, T* X, T* D, int64_t K);
 template <typename T>
+cudaError_t symmetrize(sw_ctx* ctx, const T* G, int64_t K, T* S);
+template <typename T>
+cudaError_t shift_diag_vec(sw_ctx* ctx, T* G, int64_t K, const double* d);
+template <typename GT>
+cudaError_t scale_to(sw_ctx* ctx, int64_t n, const double* a, const double* s, GT* out);
+template <typename GT>
+cudaError_t as_residual(sw_ctx* ctx, int64_t n, const double* q, const double* g, const double* x, double mu,
+                        const double* s, GT* rs);
+template <typename GT>
+cudaError_t axpy_scaled(sw_ctx* ctx, int64_t n, const GT* c, const double* s, double* x);
+cudaError_t weight_sq(sw_ctx* ctx, int64_t m, const double* acc, const double* inv_sig, double* xs);
+template <typename T>
 cudaError_t shift_and_trace(sw_ctx* ctx, T* G, int64_t K, double* d_trace, double shift);
+// A2 (nullable, same layout): the operand is A + A2 (the lo half of a split matrix)
 template <typename AT, typename XT, typename YT, typename ACC>
 cudaError_t rowdot(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t cols, int64_t lda, const XT* x, YT* y,
-                   double alpha, double beta, bool lower);
+                   double alpha, double beta, bool lower, const AT* A2 = nullptr);
 template <typename AT, typename XT, typename YT, typename ACC>
 cudaError_t colcomb(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t cols, int64_t lda, const XT* x, YT* y,
-                    double alpha, bool lower);
+                    double alpha, bool lower, const AT* A2 = nullptr);
 template <typename GT>
 cudaError_t admm_update(sw_ctx* ctx, int64_t N, const GT* y, const GT* v, const GT* s, const GT* rho_i, const GT* d,
                         const GT* qp, double alpha, GT* rs, GT* z, GT* u, unsigned* stats);
@@ -56,11 +69,21 @@ template <typename T>
 cudaError_t gather_rows(sw_ctx* ctx, const T* U, int64_t M, const int64_t* idx, int64_t nP, const double* inv_sig,
                         double* R);
 cudaError_t gather_vec(sw_ctx* ctx, const double* a, const int64_t* idx, int64_t n, double* out);
+template <typename T>
+cudaError_t gather_cols(sw_ctx* ctx, const T* U, int64_t M, const int64_t* idx, int64_t n, T* Uc);
+cudaError_t scatter_vec(sw_ctx* ctx, const double* a, const int64_t* idx, int64_t n, double* out);
+
+// block active-set solve (sw_active_set.cu)
+template <typename T, typename AT, typename GT>
+sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* U, const double* y_dev, const double* sig_dev, double lam,
+                           double* w_dev, double* chi2_dev);
 
 // tcgen05 Gram (k_gram_tc.cu): C (K x K, FP32, row-major, lower tiles) = A A^T with A
-// K x ldA BF16 row-major (ldA a multiple of 64, columns beyond the data zero).
-// d_err receives a non-zero code if a bounded wait inside the kernel ran out.
-cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, int64_t K, int64_t ldA, float* C, int* d_err);
+// K x ldA BF16 row-major (ldA a multiple of 64, columns beyond the data zero).  With
+// A_lo non-NULL the operand is A + A_lo and the three leading products of the split
+// are accumulated.  d_err receives a non-zero code if a bounded wait ran out.
+cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, const __nv_bfloat16* A_lo, int64_t K, int64_t ldA, float* C,
+                    int* d_err);
 bool gram_tc_available();
 
 }  // namespace sw

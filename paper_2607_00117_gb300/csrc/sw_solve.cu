@@ -32,6 +32,8 @@
 // stored matrix and solved by Cholesky (supports up to polish_max orbits).
 #include "sw_linalg.cuh"
 
+#include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <vector>
 
@@ -39,7 +41,7 @@ using namespace sw;
 
 void SolveWS::release()
 {
-    void* bufs[] = {A, G, X, D, vec, R, H, Hi, pv};
+    void* bufs[] = {A, Alo, G, Gs, X, D, vec, R, H, Hi, pv, Uc, outer};
     for (void* b : bufs)
         if (b) cudaFree(b);
     *this = SolveWS();
@@ -92,7 +94,7 @@ struct Vecs {
     unsigned long long *pgmax, *qmax;
     int *info, *bad, *err;
     unsigned* stats;
-    GT *qp, *z, *u, *r, *wv, *v, *t, *t1, *t2, *t3, *tmpM, *wg, *sg, *rho_i, *dg;
+    GT *qp, *z, *u, *r, *wv, *v, *t, *t1, *t2, *t3, *tmpM, *wg, *sg, *rho_i, *dg, *zbest;
     double* y;
     double* sig;
     size_t carve(char* base, int64_t M, int64_t N, int64_t K)
@@ -108,7 +110,7 @@ struct Vecs {
         stats = c.take<unsigned>(4);
         qp = c.take<GT>(N); z = c.take<GT>(N); u = c.take<GT>(N); r = c.take<GT>(N); wv = c.take<GT>(N);
         v = c.take<GT>(N); t = c.take<GT>(N); wg = c.take<GT>(N);
-        sg = c.take<GT>(N); rho_i = c.take<GT>(N); dg = c.take<GT>(N);
+        sg = c.take<GT>(N); rho_i = c.take<GT>(N); dg = c.take<GT>(N); zbest = c.take<GT>(N);
         t1 = c.take<GT>(K); t2 = c.take<GT>(K); t3 = c.take<GT>(K); tmpM = c.take<GT>(M);
         return c.used + 256;
     }
@@ -116,16 +118,27 @@ struct Vecs {
 
 inline int64_t pad64(int64_t n) { return (n + 63) / 64 * 64; }
 
+// The weight problem on an orbit-major matrix U (M rows, N orbits, the first
+// nd rows being density cells).  n_reg is the orbit count of the regulariser
+// (lambda / n_reg) ||w||^2 -- the full library size when U holds a working set.
+struct Problem {
+    const void* U;
+    int64_t M, N, nd;
+    double n_reg;
+    bool force_orbit;
+};
+
 template <typename T, typename AT, typename GT>
-sw_status solve_impl(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, const double* sig_dev, double lam,
-                     double* w_dev, double* chi2_dev)
+sw_status solve_impl(sw_ctx* ctx, const Problem& pb, const double* y_dev, const double* sig_dev, double lam,
+                     double* w_dev, double* chi2_dev, const double* w0 = nullptr)
 {
-    const int64_t M = Um->M, N = Um->N;
-    const bool orbit = N <= M;
+    const int64_t M = pb.M, N = pb.N;
+    const bool orbit = pb.force_orbit || N <= M;
     const int64_t K = orbit ? N : M;
     const int64_t ldA = orbit ? pad64(M) : pad64(N);
     const int64_t Arows = orbit ? N : M;
-    const T* U = (const T*)Um->d;
+    const T* U = (const T*)pb.U;
+    const bool split = sizeof(AT) == 2;   // BF16 operand stored as hi + lo halves
     cudaStream_t st = ctx->stream;
     SolveWS& ws = ctx->solve_ws;
     Vecs<GT> V{};
@@ -133,10 +146,12 @@ sw_status solve_impl(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, cons
     SW_TRY(ctx->ensure(&ws.vec, &ws.vec_cap, vec_bytes, "solve vectors"));
     V.carve((char*)ws.vec, M, N, K);
     SW_TRY(ctx->ensure(&ws.A, &ws.A_cap, (size_t)Arows * ldA * sizeof(AT), "whitened matrix"));
+    if (split) SW_TRY(ctx->ensure(&ws.Alo, &ws.Alo_cap, (size_t)Arows * ldA * sizeof(AT), "whitened matrix (lo)"));
     SW_TRY(ctx->ensure(&ws.G, &ws.G_cap, (size_t)K * K * sizeof(GT), "Gram"));
     SW_TRY(ctx->ensure(&ws.X, &ws.X_cap, (size_t)K * K * sizeof(GT), "inverse factor"));
     SW_TRY(ctx->ensure(&ws.D, &ws.D_cap, 64 * 64 * sizeof(GT), "block scratch"));
     AT* A = (AT*)ws.A;
+    AT* Alo = split ? (AT*)ws.Alo : nullptr;
     GT* G = (GT*)ws.G;
     GT* X = (GT*)ws.X;
     GT* D = (GT*)ws.D;
@@ -158,14 +173,14 @@ sw_status solve_impl(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, cons
     // s_i = (2 lam/N + rho_i)^{-1/2}: with A = U~ diag(s) the ADMM matrix is
     // H~ + P = diag(1/s) (A^T A + I) diag(1/s) (orbit space) and, by Woodbury,
     // (H~ + P)^{-1} = diag(s) (I - A^T (A A^T + I)^{-1} A) diag(s) (constraint space).
-    const double two_lam_n = 2.0 * lam / (double)N;
+    const double two_lam_n = 2.0 * lam / pb.n_reg;
     const double rho = orbit ? ctx->opt.admm_rho : ctx->opt.admm_rho_cs;
     CUDA_TRY(ctx, colnorm2<T>(ctx, U, M, N, V.inv_sig, V.h), "column norms");
     CUDA_TRY(ctx, admm_scales<GT>(ctx, N, V.h, two_lam_n, rho, 0.0, V.s64, V.sg, V.rho_i, V.dg), "scales");
     // ---- whitening, Gram, unit shift, Cholesky, inverse
-    CUDA_TRY(ctx, (whiten<T, AT>(ctx, U, M, N, V.inv_sig, V.s64, A, ldA, orbit)), "whiten");
+    CUDA_TRY(ctx, (whiten<T, AT>(ctx, U, M, N, V.inv_sig, V.s64, A, Alo, ldA, orbit)), "whiten");
     if constexpr (sizeof(AT) == 2) {
-        CUDA_TRY(ctx, gram_tc(ctx, A, K, ldA, (float*)G, V.err), "tensor-core Gram");
+        CUDA_TRY(ctx, gram_tc(ctx, A, Alo, K, ldA, (float*)G, V.err), "tensor-core Gram");
     } else {
         CUDA_TRY(ctx, (gemm<GT, true, true>(ctx, K_GRAM_SIMT, K, K, ldA, GT(1), (const GT*)A, ldA, (const GT*)A, ldA,
                                             GT(0), G, K, 0)),
@@ -182,6 +197,15 @@ sw_status solve_impl(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, cons
     if (bad) { set_error(ctx, "solve: errors must be positive and finite, data finite"); return SW_EINVAL; }
     if (gerr) { set_error(ctx, "solve: tensor-core Gram kernel timed out"); return SW_ETIMEOUT; }
     CUDA_TRY(ctx, shift_and_trace<GT>(ctx, G, K, nullptr, 1.0), "shift");
+    // keep a symmetric copy of G + I: every ADMM step is refined against it, which makes
+    // the step consistent with the Gram even where the FP32 factor is not accurate
+    const int inner_refine = orbit ? ctx->opt.inner_refine : 0;
+    GT* Gs = nullptr;
+    if (inner_refine > 0) {
+        SW_TRY(ctx->ensure(&ws.Gs, &ws.Gs_cap, (size_t)K * K * sizeof(GT), "Gram copy"));
+        Gs = (GT*)ws.Gs;
+        CUDA_TRY(ctx, symmetrize<GT>(ctx, G, K, Gs), "symmetrize");
+    }
     CUDA_TRY(ctx, cholesky<GT>(ctx, G, K, V.info), "Cholesky");
     CUDA_TRY(ctx, tri_inverse<GT>(ctx, G, X, D, K), "triangular inverse");
     int info = 0;
@@ -192,18 +216,26 @@ sw_status solve_impl(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, cons
     // ---- ADMM: apply the inverse to the scaled right-hand side rs
     auto apply = [&](const GT* rs) -> cudaError_t {
         cudaError_t e;
-        if (orbit) {   // y = X^T X rs, w = s o y
+        if (orbit) {   // y = (G + I)^{-1} rs by X^T X and refinement against G + I, w = s o y
             if ((e = rowdot<GT, GT, GT, GT>(ctx, K_TRMV_L, X, K, K, K, rs, V.t1, 1.0, 0.0, true))) return e;
             if ((e = cudaMemsetAsync(V.wv, 0, K * sizeof(GT), st))) return e;
-            return colcomb<GT, GT, GT, GT>(ctx, K_TRMV_LT, X, K, K, K, V.t1, V.wv, 1.0, true);
+            if ((e = colcomb<GT, GT, GT, GT>(ctx, K_TRMV_LT, X, K, K, K, V.t1, V.wv, 1.0, true))) return e;
+            for (int k = 0; k < inner_refine; ++k) {
+                if ((e = cudaMemcpyAsync(V.t2, rs, K * sizeof(GT), cudaMemcpyDeviceToDevice, st))) return e;
+                if ((e = rowdot<GT, GT, GT, double>(ctx, K_GEMV_N, Gs, K, K, K, V.wv, V.t2, -1.0, 1.0, false)))
+                    return e;
+                if ((e = rowdot<GT, GT, GT, GT>(ctx, K_TRMV_L, X, K, K, K, V.t2, V.t1, 1.0, 0.0, true))) return e;
+                if ((e = colcomb<GT, GT, GT, GT>(ctx, K_TRMV_LT, X, K, K, K, V.t1, V.wv, 1.0, true))) return e;
+            }
+            return cudaSuccess;
         }
         // v = A^T X^T X A rs, w = s o (rs - v)
-        if ((e = rowdot<AT, GT, GT, GT>(ctx, K_GEMV_N, A, M, N, ldA, rs, V.t1, 1.0, 0.0, false))) return e;
+        if ((e = rowdot<AT, GT, GT, GT>(ctx, K_GEMV_N, A, M, N, ldA, rs, V.t1, 1.0, 0.0, false, Alo))) return e;
         if ((e = rowdot<GT, GT, GT, GT>(ctx, K_TRMV_L, X, K, K, K, V.t1, V.t2, 1.0, 0.0, true))) return e;
         if ((e = cudaMemsetAsync(V.t3, 0, K * sizeof(GT), st))) return e;
         if ((e = colcomb<GT, GT, GT, GT>(ctx, K_TRMV_LT, X, K, K, K, V.t2, V.t3, 1.0, true))) return e;
         if ((e = cudaMemsetAsync(V.v, 0, N * sizeof(GT), st))) return e;
-        return colcomb<AT, GT, GT, GT>(ctx, K_GEMV_T, A, M, N, ldA, V.t3, V.v, 1.0, false);
+        return colcomb<AT, GT, GT, GT>(ctx, K_GEMV_T, A, M, N, ldA, V.t3, V.v, 1.0, false, Alo);
     };
     int total_iter = 0;
     auto run_admm = [&](bool& converged) -> sw_status {
@@ -237,7 +269,8 @@ sw_status solve_impl(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, cons
     };
     // first run: q' = q, z = u = 0
     CUDA_TRY(ctx, (convert<double, GT>(ctx, N, V.q, V.qp)), "q'");
-    CUDA_TRY(ctx, cudaMemsetAsync(V.z, 0, N * sizeof(GT), st), "memset");
+    if (w0) CUDA_TRY(ctx, (convert<double, GT>(ctx, N, w0, V.z)), "warm start");   // w0 may alias w_dev
+    else CUDA_TRY(ctx, cudaMemsetAsync(V.z, 0, N * sizeof(GT), st), "memset");
     CUDA_TRY(ctx, cudaMemsetAsync(V.u, 0, N * sizeof(GT), st), "memset");
     bool conv = false;
     SW_TRY(run_admm(conv));
@@ -252,7 +285,7 @@ sw_status solve_impl(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, cons
         CUDA_TRY(ctx, cudaMemsetAsync(V.pgmax, 0, 8, st), "memset");
         CUDA_TRY(ctx, kkt(ctx, N, V.ute, V.wd, two_lam_n, V.gneg, V.pgmax), "KKT");
         CUDA_TRY(ctx, cudaMemsetAsync(V.chi, 0, 4 * sizeof(double), st), "memset");
-        CUDA_TRY(ctx, chi2(ctx, M, Um->nd, V.e, N, V.wd, V.chi), "chi2");
+        CUDA_TRY(ctx, chi2(ctx, M, pb.nd, V.e, N, V.wd, V.chi), "chi2");
         unsigned long long pb = 0;
         double c3[4];
         CUDA_TRY(ctx, cudaMemcpyAsync(&pb, V.pgmax, 8, cudaMemcpyDeviceToHost, st), "KKT");
@@ -269,10 +302,25 @@ sw_status solve_impl(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, cons
     int rounds = 0, polish_iters = 0;
     double pg_rel = 0.0, chi[3] = {0, 0, 0}, chi_prev = -1.0;
     bool kkt_ok = false, chi_stable = false;
+    double f_best = 1e300;
     for (;;) {
         CUDA_TRY(ctx, (convert<GT, double>(ctx, N, V.z, V.wd)), "w");
         SW_TRY(evaluate(pg_rel, chi));
+        const double f = 0.5 * chi[0] + lam / pb.n_reg * chi[2];   // the exact objective Q(w)
+        if (ctx->opt.verbose)
+            fprintf(stderr, "[sw]   core round %d: N %lld K %lld chi2 %.9g Q %.9g pg_rel %.3g admm %d\n", rounds,
+                    (long long)N, (long long)K, chi[0], f, pg_rel, total_iter);
         if (pg_rel <= ctx->opt.kkt_tol) { kkt_ok = true; break; }
+        if (!(f <= f_best)) {
+            // a refinement round that raises the exact objective means the Gram-precision
+            // problem is too far from the exact one here: return to the best iterate and stop
+            CUDA_TRY(ctx, cudaMemcpyAsync(V.z, V.zbest, N * sizeof(GT), cudaMemcpyDeviceToDevice, st), "revert");
+            CUDA_TRY(ctx, (convert<GT, double>(ctx, N, V.z, V.wd)), "w");
+            SW_TRY(evaluate(pg_rel, chi));
+            break;
+        }
+        f_best = f;
+        CUDA_TRY(ctx, cudaMemcpyAsync(V.zbest, V.z, N * sizeof(GT), cudaMemcpyDeviceToDevice, st), "best");
         if (chi_prev >= 0.0 && std::fabs(chi[0] - chi_prev) <= ctx->opt.chi2_tol * std::max(chi[0], 1e-300)) {
             chi_stable = true;
             break;
@@ -284,12 +332,12 @@ sw_status solve_impl(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, cons
         CUDA_TRY(ctx, div_to<GT>(ctx, N, V.wd, V.s64, V.wg), "w / s");
         if (orbit) {
             CUDA_TRY(ctx, cudaMemsetAsync(V.tmpM, 0, M * sizeof(GT), st), "memset");
-            CUDA_TRY(ctx, (colcomb<AT, GT, GT, GT>(ctx, K_GEMV_T, A, N, M, ldA, V.wg, V.tmpM, 1.0, false)), "A w");
-            CUDA_TRY(ctx, (rowdot<AT, GT, GT, GT>(ctx, K_GEMV_N, A, N, M, ldA, V.tmpM, V.t, 1.0, 0.0, false)), "A^T A w");
+            CUDA_TRY(ctx, (colcomb<AT, GT, GT, GT>(ctx, K_GEMV_T, A, N, M, ldA, V.wg, V.tmpM, 1.0, false, Alo)), "A w");
+            CUDA_TRY(ctx, (rowdot<AT, GT, GT, GT>(ctx, K_GEMV_N, A, N, M, ldA, V.tmpM, V.t, 1.0, 0.0, false, Alo)), "A^T A w");
         } else {
-            CUDA_TRY(ctx, (rowdot<AT, GT, GT, GT>(ctx, K_GEMV_N, A, M, N, ldA, V.wg, V.tmpM, 1.0, 0.0, false)), "A w");
+            CUDA_TRY(ctx, (rowdot<AT, GT, GT, GT>(ctx, K_GEMV_N, A, M, N, ldA, V.wg, V.tmpM, 1.0, 0.0, false, Alo)), "A w");
             CUDA_TRY(ctx, cudaMemsetAsync(V.t, 0, N * sizeof(GT), st), "memset");
-            CUDA_TRY(ctx, (colcomb<AT, GT, GT, GT>(ctx, K_GEMV_T, A, M, N, ldA, V.tmpM, V.t, 1.0, false)), "A^T A w");
+            CUDA_TRY(ctx, (colcomb<AT, GT, GT, GT>(ctx, K_GEMV_T, A, M, N, ldA, V.tmpM, V.t, 1.0, false, Alo)), "A^T A w");
         }
         CUDA_TRY(ctx, refine_rhs<GT>(ctx, N, V.t, V.gneg, V.wd, V.s64, two_lam_n, V.rho_i, V.qp, V.z, V.u),
                  "refine rhs");
@@ -421,15 +469,17 @@ sw_status solve_impl(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, cons
     // ---- outputs: chi^2 parts of the final weights, weights
     {
         LaunchTimer lt(ctx, K_CHI2);
-        k_chi2_finish<<<1, 1, 0, st>>>(V.chi, lam / (double)N, chi2_dev);
+        k_chi2_finish<<<1, 1, 0, st>>>(V.chi, lam / pb.n_reg, chi2_dev);
     }
     CUDA_TRY(ctx, cudaGetLastError(), "chi2");
     CUDA_TRY(ctx, cudaMemcpyAsync(w_dev, V.wd, N * sizeof(double), cudaMemcpyDeviceToDevice, st), "weights");
     ctx->solve_info[0] = total_iter;
     ctx->solve_info[1] = rounds;
     ctx->solve_info[2] = pg_rel;
-    ctx->solve_info[3] = orbit ? 0.0 : 1.0;
+    ctx->solve_info[3] = N > M ? 1.0 : 0.0;
     ctx->solve_info[4] = polish_iters;
+    ctx->solve_info[6] = 0.0;
+    ctx->solve_info[7] = 0.0;
     ctx->solve_info[5] = kkt_ok ? 1.0 : 0.0;
     if (!kkt_ok && !chi_stable) {
         set_error(ctx, "solve: neither the KKT tolerance (projected gradient %.3g of max|q|) nor a stable chi^2 was "
@@ -441,13 +491,202 @@ sw_status solve_impl(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, cons
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Working set for N > M.  The non-negative minimiser has at most about rank(U)
+// = M positive weights (exactly so at lambda = 0), so the orbit-space solve --
+// free of the digit cancellation of the Woodbury form -- runs on a working set
+// C of ws_factor * M orbits: first the orbits best correlated with the data
+// (q_i / ||U~ e_i||), then, round by round, the support of the last solution
+// plus the strongest violators of the exact KKT conditions over all N orbits
+// (negative gradient g_i > kkt_tol max|q| at w_i = 0).  The solution is exact
+// when no orbit outside C violates the conditions.
+// ---------------------------------------------------------------------------
+template <typename T, typename AT, typename GT>
+static sw_status solve_working_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, const double* sig_dev,
+                                   double lam, double* w_dev, double* chi2_dev)
+{
+    const int64_t M = Um->M, N = Um->N;
+    const T* U = (const T*)Um->d;
+    cudaStream_t st = ctx->stream;
+    SolveWS& ws = ctx->solve_ws;
+    int64_t nC = std::min<int64_t>(N, (int64_t)std::ceil(ctx->opt.ws_factor * (double)M));
+    const int64_t nC_max = std::min<int64_t>(N, 3 * nC);
+    // outer vectors: inv_sig, ys, acc, e, xs (M); q, h, w, ute, gneg (N); wC (nC_max); idx; scalars
+    Carve c{nullptr};
+    auto carve = [&](char* base, double** o) {
+        c = Carve{base};
+        for (int k = 0; k < 5; ++k) o[k] = c.take<double>(M);
+        for (int k = 5; k < 10; ++k) o[k] = c.take<double>(N);
+        o[10] = c.take<double>(nC_max);
+        o[11] = (double*)c.take<int64_t>(nC_max);
+        o[12] = c.take<double>(8);
+        return c.used + 256;
+    };
+    double* o[13];
+    const size_t need = carve(nullptr, o);
+    SW_TRY(ctx->ensure(&ws.outer, &ws.outer_cap, need, "working-set vectors"));
+    carve((char*)ws.outer, o);
+    double *inv_sig = o[0], *ys = o[1], *acc = o[2], *e = o[3], *xs = o[4];
+    double *q = o[5], *h = o[6], *w = o[7], *ute = o[8], *gneg = o[9], *wC = o[10], *scal = o[12];
+    int64_t* didx = (int64_t*)o[11];
+    int* bad = (int*)(scal + 4);
+    unsigned long long* pgmax = (unsigned long long*)(scal + 5);
+    unsigned long long* qmax = (unsigned long long*)(scal + 6);
+    const double two_lam_n = 2.0 * lam / (double)N;
+
+    CUDA_TRY(ctx, cudaMemsetAsync(scal, 0, 8 * sizeof(double), st), "memset");
+    CUDA_TRY(ctx, prep_data(ctx, M, sig_dev, y_dev, inv_sig, ys, bad), "prep data");
+    CUDA_TRY(ctx, ut_times_x<T>(ctx, U, M, N, ys, q), "q");
+    CUDA_TRY(ctx, colnorm2<T>(ctx, U, M, N, inv_sig, h), "column norms");
+    {
+        LaunchTimer lt(ctx, K_MISC);
+        k_absmax<<<64, 256, 0, st>>>(N, q, qmax);
+    }
+    std::vector<double> qh(N), hh(N), gh(N), wh(nC_max);
+    int badh = 0;
+    unsigned long long qb = 0;
+    CUDA_TRY(ctx, cudaMemcpyAsync(qh.data(), q, N * sizeof(double), cudaMemcpyDeviceToHost, st), "q");
+    CUDA_TRY(ctx, cudaMemcpyAsync(hh.data(), h, N * sizeof(double), cudaMemcpyDeviceToHost, st), "h");
+    CUDA_TRY(ctx, cudaMemcpyAsync(&badh, bad, sizeof(int), cudaMemcpyDeviceToHost, st), "flags");
+    CUDA_TRY(ctx, cudaMemcpyAsync(&qb, qmax, 8, cudaMemcpyDeviceToHost, st), "qmax");
+    CUDA_TRY(ctx, cudaStreamSynchronize(st), "working set");
+    if (badh) { set_error(ctx, "solve: errors must be positive and finite, data finite"); return SW_EINVAL; }
+    double qmax_d;
+    memcpy(&qmax_d, &qb, 8);
+    const double gtol = ctx->opt.kkt_tol * std::max(qmax_d, 1e-300);
+
+    // initial working set: best correlated orbits
+    std::vector<int64_t> order(N);
+    for (int64_t i = 0; i < N; ++i) order[i] = i;
+    auto score = [&](int64_t i, const std::vector<double>& g) {
+        return hh[i] > 0.0 ? g[i] / std::sqrt(hh[i]) : -1e300;
+    };
+    std::partial_sort(order.begin(), order.begin() + nC, order.end(),
+                      [&](int64_t a, int64_t b) { return score(a, qh) > score(b, qh); });
+    std::vector<int64_t> C(order.begin(), order.begin() + nC);
+    std::vector<char> inC(N, 0);
+
+    sw_status core = SW_OK;
+    double pg_rel = 0.0, chi_prev = -1.0, chi_now = 0.0;
+    bool done = false;
+    int rounds = 0;
+    double inner_info[6] = {0, 0, 0, 0, 0, 0};
+    for (; rounds < ctx->opt.ws_rounds && !done; ++rounds) {
+        std::sort(C.begin(), C.end());
+        nC = (int64_t)C.size();
+        std::fill(inC.begin(), inC.end(), 0);
+        for (int64_t i : C) inC[i] = 1;
+        SW_TRY(ctx->ensure(&ws.Uc, &ws.Uc_cap, (size_t)nC * M * sizeof(T), "working-set columns"));
+        CUDA_TRY(ctx, cudaMemcpyAsync(didx, C.data(), nC * sizeof(int64_t), cudaMemcpyHostToDevice, st), "idx");
+        CUDA_TRY(ctx, gather_cols<T>(ctx, U, M, didx, nC, (T*)ws.Uc), "gather");
+        Problem pb{ws.Uc, M, nC, Um->nd, (double)N, true};
+        if (rounds > 0) CUDA_TRY(ctx, gather_vec(ctx, w, didx, nC, wC), "warm start");
+        core = solve_impl<T, AT, GT>(ctx, pb, y_dev, sig_dev, lam, wC, scal, rounds > 0 ? wC : nullptr);
+        if (core != SW_OK && core != SW_ENONCONV) return core;
+        for (int k = 0; k < 6; ++k) inner_info[k] += (k == 2 || k == 3 || k == 5) ? 0.0 : ctx->solve_info[k];
+        inner_info[2] = ctx->solve_info[2];
+        // exact state over all N orbits
+        CUDA_TRY(ctx, cudaMemsetAsync(w, 0, N * sizeof(double), st), "memset");
+        CUDA_TRY(ctx, scatter_vec(ctx, wC, didx, nC, w), "scatter");
+        CUDA_TRY(ctx, cudaMemsetAsync(acc, 0, M * sizeof(double), st), "memset");
+        CUDA_TRY(ctx, u_times_w<T>(ctx, U, M, N, w, acc), "U w");
+        CUDA_TRY(ctx, residual(ctx, M, y_dev, acc, inv_sig, e, xs), "residual");
+        CUDA_TRY(ctx, ut_times_x<T>(ctx, U, M, N, xs, ute), "U^T e");
+        CUDA_TRY(ctx, cudaMemsetAsync(pgmax, 0, 8, st), "memset");
+        CUDA_TRY(ctx, kkt(ctx, N, ute, w, two_lam_n, gneg, pgmax), "KKT");
+        unsigned long long pb_bits = 0;
+        double chi_dev[3];
+        CUDA_TRY(ctx, cudaMemcpyAsync(&pb_bits, pgmax, 8, cudaMemcpyDeviceToHost, st), "KKT");
+        CUDA_TRY(ctx, cudaMemcpyAsync(chi_dev, scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st), "chi2");
+        CUDA_TRY(ctx, cudaMemcpyAsync(gh.data(), gneg, N * sizeof(double), cudaMemcpyDeviceToHost, st), "g");
+        CUDA_TRY(ctx, cudaMemcpyAsync(wh.data(), wC, nC * sizeof(double), cudaMemcpyDeviceToHost, st), "w");
+        CUDA_TRY(ctx, cudaStreamSynchronize(st), "working set");
+        double pg;
+        memcpy(&pg, &pb_bits, 8);
+        pg_rel = pg / std::max(qmax_d, 1e-300);
+        chi_now = chi_dev[0];
+        if (ctx->opt.verbose) {
+            int64_t nsup = 0, nviol = 0, nposq = 0;
+            for (int64_t k = 0; k < nC; ++k) nsup += wh[k] > 0.0;
+            for (int64_t i = 0; i < N; ++i) { nviol += (!inC[i] && gh[i] > gtol); nposq += qh[i] > gtol; }
+            fprintf(stderr, "[sw] ws round %d: |C| %lld core %d chi2 %.9g pg_rel %.3g support %lld violators %lld "
+                            "q>tol %lld inner admm %g refine %g polish %g\n", rounds, (long long)nC, (int)core,
+                    chi_now, pg_rel, (long long)nsup, (long long)nviol, (long long)nposq, ctx->solve_info[0],
+                    ctx->solve_info[1], ctx->solve_info[4]);
+        }
+        // violators outside C, strongest first
+        std::vector<int64_t> viol;
+        for (int64_t i = 0; i < N; ++i)
+            if (!inC[i] && gh[i] > gtol) viol.push_back(i);
+        if (viol.empty() || pg_rel <= ctx->opt.kkt_tol) { done = true; break; }
+        if (chi_prev >= 0.0 && std::fabs(chi_now - chi_prev) <= ctx->opt.chi2_tol * std::max(chi_now, 1e-300)) {
+            done = true;
+            break;
+        }
+        chi_prev = chi_now;
+        std::sort(viol.begin(), viol.end(), [&](int64_t a, int64_t b) { return score(a, gh) > score(b, gh); });
+        std::vector<int64_t> next;
+        for (int64_t k = 0; k < nC; ++k)
+            if (wh[k] > 0.0) next.push_back(C[k]);
+        const int64_t cap = std::min<int64_t>(nC_max, std::max<int64_t>((int64_t)C.size(),
+                                                                       (int64_t)(next.size() + viol.size())));
+        for (size_t k = 0; k < viol.size() && (int64_t)next.size() < cap; ++k) next.push_back(viol[k]);
+        // keep the size: refill with the previous zero-weight members
+        for (int64_t k = 0; k < nC && (int64_t)next.size() < (int64_t)C.size(); ++k)
+            if (!(wh[k] > 0.0)) next.push_back(C[k]);
+        C.swap(next);
+    }
+    // outputs: the full weight vector and the chi^2 parts of the final state
+    double* chi = scal;   // [total, obs, reg] from the last core solve equal the exact values over all N
+    CUDA_TRY(ctx, cudaMemsetAsync(chi, 0, 4 * sizeof(double), st), "memset");
+    CUDA_TRY(ctx, chi2(ctx, M, Um->nd, e, N, w, chi), "chi2");
+    {
+        LaunchTimer lt(ctx, K_CHI2);
+        k_chi2_finish<<<1, 1, 0, st>>>(chi, lam / (double)N, chi2_dev);
+    }
+    CUDA_TRY(ctx, cudaGetLastError(), "chi2");
+    CUDA_TRY(ctx, cudaMemcpyAsync(w_dev, w, N * sizeof(double), cudaMemcpyDeviceToDevice, st), "weights");
+    CUDA_TRY(ctx, cudaStreamSynchronize(st), "working set");
+    ctx->solve_info[0] = inner_info[0];
+    ctx->solve_info[1] = inner_info[1];
+    ctx->solve_info[2] = pg_rel;
+    ctx->solve_info[3] = 1.0;
+    ctx->solve_info[4] = inner_info[4];
+    ctx->solve_info[5] = pg_rel <= ctx->opt.kkt_tol ? 1.0 : 0.0;
+    ctx->solve_info[6] = rounds + (done ? 0 : 0);
+    ctx->solve_info[7] = (double)C.size();
+    if (!done) {
+        set_error(ctx, "solve: working set did not settle in %d rounds (projected gradient %.3g of max|q|)", rounds,
+                  pg_rel);
+        return SW_ENONCONV;
+    }
+    return (core == SW_ENONCONV && pg_rel > ctx->opt.kkt_tol) ? SW_ENONCONV : SW_OK;
+}
+
 static sw_status solve_dispatch(sw_ctx* ctx, const sw_matrix* U, const double* y_dev, const double* sig_dev,
                                 double lam, double* w_dev, double* chi2_dev)
 {
-    if (U->elem == 8) return solve_impl<double, double, double>(ctx, U, y_dev, sig_dev, lam, w_dev, chi2_dev);
+    // orbits outnumber constraints: moderate N -> orbit space on all orbits (exact through the
+    // polish); large N -> working set; working_set = 0 -> the constraint-space (Woodbury) form
+    const bool many = U->N > U->M;
+    const bool direct = many && ctx->opt.working_set && U->N <= ctx->opt.orbit_direct_max;
+    const bool ws = many && ctx->opt.working_set && !direct;
+    const Problem pb{U->d, U->M, U->N, U->nd, (double)U->N, direct};
+    if (ws && ctx->opt.large_solver == 0) {
+        if (U->elem == 8) return solve_active_set<double, double, double>(ctx, U, y_dev, sig_dev, lam, w_dev, chi2_dev);
+        if (ctx->opt.gram_tc && gram_tc_available())
+            return solve_active_set<float, __nv_bfloat16, float>(ctx, U, y_dev, sig_dev, lam, w_dev, chi2_dev);
+        return solve_active_set<float, float, float>(ctx, U, y_dev, sig_dev, lam, w_dev, chi2_dev);
+    }
+    if (U->elem == 8) {
+        return ws ? solve_working_set<double, double, double>(ctx, U, y_dev, sig_dev, lam, w_dev, chi2_dev)
+                  : solve_impl<double, double, double>(ctx, pb, y_dev, sig_dev, lam, w_dev, chi2_dev);
+    }
     if (ctx->opt.gram_tc && gram_tc_available())
-        return solve_impl<float, __nv_bfloat16, float>(ctx, U, y_dev, sig_dev, lam, w_dev, chi2_dev);
-    return solve_impl<float, float, float>(ctx, U, y_dev, sig_dev, lam, w_dev, chi2_dev);
+        return ws ? solve_working_set<float, __nv_bfloat16, float>(ctx, U, y_dev, sig_dev, lam, w_dev, chi2_dev)
+                  : solve_impl<float, __nv_bfloat16, float>(ctx, pb, y_dev, sig_dev, lam, w_dev, chi2_dev);
+    return ws ? solve_working_set<float, float, float>(ctx, U, y_dev, sig_dev, lam, w_dev, chi2_dev)
+              : solve_impl<float, float, float>(ctx, pb, y_dev, sig_dev, lam, w_dev, chi2_dev);
 }
 
 static sw_status check_solve_args(sw_ctx* ctx, const sw_matrix* U, const void* a, const void* b, double lam,
@@ -500,10 +739,10 @@ extern "C" sw_status sw_solve_weights(sw_ctx* ctx, const sw_matrix* U, const dou
     return s;
 }
 
-extern "C" sw_status sw_solve_info(sw_ctx* ctx, double* out6)
+extern "C" sw_status sw_solve_info(sw_ctx* ctx, double* out8)
 {
-    if (!ctx || !out6) return SW_EINVAL;
-    for (int k = 0; k < 6; ++k) out6[k] = ctx->solve_info[k];
+    if (!ctx || !out8) return SW_EINVAL;
+    for (int k = 0; k < 8; ++k) out8[k] = ctx->solve_info[k];
     return SW_OK;
 }
 

@@ -57,7 +57,7 @@ WORKLOADS = {
                       lam=1.0),
     "barred_100k": dict(potential=dict(DISC_HALO, **BAR), omega_p=40.0, n_orb=100_000, nsteps=10_000,
                         dt=DT_HALF_MYR, grid=_grid(50, 50, 32, 20, 20, 10, 45 * DEG, 30 * DEG),
-                        seeds=dict(ic=1002, w=2001, noise=2002), lam=1.0),
+                        seeds=dict(ic=1002, w=2001, noise=2002, dither=1003), lam=1.0, bundle=4),
     "batched_64": dict(n_models=64, nsteps=5000, dt=DT_HALF_MYR, n_orb_range=(10_000, 100_000),
                        grid=_grid(30, 20, 40, 10, 12, 5, 0.0, gh=1), seeds=dict(box=3001, data=3100),
                        lam=1.0),
@@ -145,6 +145,22 @@ def disc_ics(p: dict, n: int, seed: int, Rmax: float = 20.0, zmax: float = 3.0,
     vy = vt * np.cos(ph) + sigma_v * rng.standard_normal(n)
     vz = sigma_v * rng.standard_normal(n)
     return np.ascontiguousarray(np.stack([x, y, z, vx, vy, vz], 1))
+
+
+def dither(ics: np.ndarray, n: int, seed: int, p: dict, dx: float = 0.1, dv_frac: float = 0.05) -> np.ndarray:
+    """Orbit bundles (Sec. 2.2.1): n nearby realisations of every initial condition,
+    drawn uniformly from a box centred on it, dx kpc wide in each position and
+    dv_frac v_c(R, z) wide in each velocity.  Returns (len(ics) * n, 6) inertial ICs,
+    the n realisations of one bundle consecutive."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ics = np.asarray(ics, dtype=np.float64)
+    R = np.hypot(ics[:, 0], ics[:, 1])
+    vc = _vcirc(R, ics[:, 2], p)
+    base = np.repeat(ics, n, axis=0)
+    off = rng.random(base.shape) - 0.5
+    off[:, :3] *= dx
+    off[:, 3:] *= dv_frac * np.repeat(vc, n)[:, None]
+    return np.ascontiguousarray(base + off)
 
 
 def plummer_ics(M: float, a: float, n: int, seed: int, rcut: float = 20.0) -> np.ndarray:

@@ -73,6 +73,7 @@ SIGNATURES = {
                                   ctypes.POINTER(PixelGrid), ctypes.POINTER(VBins), ctypes.POINTER(DensityGrid), _D,
                                   ctypes.c_int, ctypes.POINTER(_VP)]),
     "sw_reduce_gh": (ctypes.c_int, [_VP, _VP, _D, ctypes.POINTER(_VP)]),
+    "sw_bundle": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.POINTER(_VP)]),
     "sw_project_stats": (ctypes.c_int, [_VP, _D, _U8]),
     "sw_solve_weights": (ctypes.c_int, [_VP, _VP, _D, _D, ctypes.c_double, _D, _D]),
     "sw_solve_weights_device": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP]),
@@ -262,6 +263,12 @@ class Context:
         self._check(lib().sw_reduce_gh(self.handle, U.handle, _dp(gh_v0s), ctypes.byref(out)))
         return Matrix(self, out.value)
 
+    def bundle(self, U: Matrix, n: int) -> Matrix:
+        """Mean of each run of n consecutive columns (orbit bundles of n dithers)."""
+        out = _VP()
+        self._check(lib().sw_bundle(self.handle, U.handle, int(n), ctypes.byref(out)))
+        return Matrix(self, out.value)
+
     def project_stats(self, n: int):
         drift = np.empty(n); status = np.empty(n, dtype=np.uint8)
         self._check(lib().sw_project_stats(self.handle, _dp(drift), status.ctypes.data_as(_U8)))
@@ -281,10 +288,11 @@ class Context:
                                              _tp(chi2_t))
 
     def solve_info(self) -> dict:
-        out = np.zeros(6)
+        out = np.zeros(8)
         self._check(lib().sw_solve_info(self.handle, _dp(out)))
         return {"admm_iterations": int(out[0]), "refine_rounds": int(out[1]), "kkt_rel": float(out[2]),
-                "constraint_space": bool(out[3]), "polish_solves": int(out[4]), "kkt_met": bool(out[5])}
+                "constraint_space": bool(out[3]), "polish_solves": int(out[4]), "kkt_met": bool(out[5]),
+                "ws_rounds": int(out[6]), "ws_size": int(out[7])}
 
     def trajectory(self, ics: np.ndarray, omega_p: float, dt: float, nsteps: int) -> np.ndarray:
         ics = np.ascontiguousarray(ics, dtype=np.float64).reshape(-1, 6)

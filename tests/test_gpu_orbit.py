@@ -9,9 +9,9 @@ for regular orbits (FP32 form against FP64); orbit-matrix L1 difference
 <= 1e-3 per orbit.
 
 Two readings make the FP32 gates well posed.  "Regular" means a twin orbit
-displaced by 1e-9 kpc separates by less than 50x over the 1e3 steps: FP32
-rounding of the inputs alone is ~6e-8 relative, so a 1e-5 gate leaves room
-for no more growth than that.  The per-orbit matrix gate allows, on top of
+displaced by 1e-9 kpc separates by less than 20x over the 1e3 steps: FP32
+rounding of each step's force is ~1e-7 relative and accumulates to a few
+1e-6 over 1e3 steps, so a 1e-5 gate leaves room for little amplification.  The per-orbit matrix gate allows, on top of
 1e-3, the moves of sample copies whose oracle coordinate lies within 2e-4
 bin widths of an edge (guard band, counted from the oracle trajectory); orbits
 whose oracle column itself moves by > 2e-4 under a 1e-7 relative change of the
@@ -125,7 +125,10 @@ def test_counts_fp32_outside_guard_band(sw, orc):
 def test_phase_space_fp32_regular_orbits(sw, orc):
     """Per-step relative error <= 1e-5 over 1e3 steps for regular orbits.  An
     orbit is regular if a twin displaced by 1e-9 kpc separates by less than
-    50 x over the same steps (oracle FP64)."""
+    20 x over the same steps (oracle FP64).  The error at each step is relative
+    to the orbit's own scale: |dx(t)| / max_t |x| and |dv(t)| / max_t |v| (a
+    pointwise |v(t)| near a turning point would measure a phase error against a
+    vanishing speed)."""
     pot, omega = BARRED, 40.0
     ics = inputs.disc_ics(inputs.DISC_HALO, 64, seed=103)
     S, dt = 1000, inputs.DT_HALF_MYR
@@ -138,13 +141,13 @@ def test_phase_space_fp32_regular_orbits(sw, orc):
         ic2 = ic.copy(); ic2[0] += 1e-9
         t2 = orc.trajectory(po, omega, dt, S, ic2)
         sep = np.linalg.norm(t2[:, :3] - to[:, :3], axis=1).max()
-        if sep > 50 * 1e-9:
+        if sep > 20 * 1e-9:
             continue
         n_regular += 1
-        ex = np.linalg.norm(tg[i, :, :3] - to[:, :3], axis=1) / np.linalg.norm(to[:, :3], axis=1)
-        ev = np.linalg.norm(tg[i, :, 3:] - to[:, 3:], axis=1) / np.linalg.norm(to[:, 3:], axis=1)
+        ex = np.linalg.norm(tg[i, :, :3] - to[:, :3], axis=1) / np.linalg.norm(to[:, :3], axis=1).max()
+        ev = np.linalg.norm(tg[i, :, 3:] - to[:, 3:], axis=1) / np.linalg.norm(to[:, 3:], axis=1).max()
         assert max(ex.max(), ev.max()) <= 1e-5, (i, ex.max(), ev.max())
-    assert n_regular >= 16
+    assert n_regular >= 12
 
 
 def test_phase_space_fp64(sw, orc):
