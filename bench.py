@@ -63,6 +63,20 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(value: float, dist, torch, device) -> float:
+    """The slowest rank's time (replicas run the same work; the job ends with it)."""
+    if not dist:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(base: int, rank: int) -> int:
+    """Each replica draws its own library (weak scaling: per-GPU work fixed)."""
+    return base + 1000 * rank
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -165,28 +179,31 @@ def make_data(sw, torch, W, rank):
 # ---------------------------------------------------------------------------
 # algorithmic work per unit for the roofline of the dominant kernel
 # ---------------------------------------------------------------------------
-def roofline_entry(name, stats, W, M_gh, K, hbm, bf16, sm_mhz):
-    N, S = W["n_orb"], W["nsteps"]
-    n = stats[name]["launches"]
-    t = stats[name]["ms"] / 1e3 / n
-    if name in ("gemv_n", "gemv_t"):           # one pass over the BF16 whitened matrix (M_gh x N)
-        bytes_ = 2.0 * M_gh * N + 4.0 * (M_gh + N)
-        return {"bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm, "unit": "GB/s", "frac": bytes_ / t / 1e9 / hbm}
-    if name in ("trmv_l", "trmv_lt"):           # one pass over the lower triangle of X (K x K FP32)
-        bytes_ = 4.0 * K * (K + 1) / 2 + 8.0 * K
-        return {"bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm, "unit": "GB/s", "frac": bytes_ / t / 1e9 / hbm}
-    if name == "gram_tcgen05":                  # lower-triangular tiles of K x K, contraction N
-        T = math.ceil(K / 128)
-        flops = 2.0 * (T * (T + 1) / 2) * 128 * 128 * N
-        return {"bound": "tensor", "achieved": flops / t / 1e12, "peak": bf16, "unit": "TFLOP/s",
-                "frac": flops / t / 1e12 / bf16}
-    if name == "orbit_project_bin":             # FP32 issue slots per orbit-step (counted from the source)
-        ops = 360.0 * N * S
-        peak = SM_COUNT * FP32_LANES * sm_mhz * 1e6 / 1e12
-        return {"bound": "alu", "achieved": ops / t / 1e12, "peak": peak, "unit": "Tops/s (FP32 issue)",
-                "frac": ops / t / 1e12 / peak}
-    if name in ("finalize_columns", "reduce_gh", "whiten"):
-        return {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None}
+OPS_PER_ORBIT_STEP = 360.0   # FP32-pipe instructions per orbit-step of the fused orbit kernel
+
+
+def roofline_entry(name, stats, hbm, bf16, sm_mhz):
+    """Roofline of one kernel from its algorithmic work (counted by the library at
+    each launch) and its CUDA-event time inside the timed region."""
+    st = stats[name]
+    n = st["launches"]
+    t = st["ms"] / 1e3 / n
+    work = st.get("work", 0.0) / n
+    kind = st.get("kind", "none")
+    simt_peak = SM_COUNT * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12          # FP32 FMA lanes x 2 flops, TFLOP/s
+    if kind == "bytes" and work > 0:
+        a = work / t / 1e9
+        return {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm}
+    if kind == "flop_tensor" and work > 0:
+        a = work / t / 1e12
+        return {"bound": "tensor", "achieved": a, "peak": bf16, "unit": "TFLOP/s", "frac": a / bf16}
+    if kind == "flop_simt" and work > 0:
+        a = work / t / 1e12
+        return {"bound": "alu", "achieved": a, "peak": simt_peak, "unit": "TFLOP/s (FP32 SIMT)", "frac": a / simt_peak}
+    if kind == "orbit_steps" and work > 0:
+        peak = SM_COUNT * FP32_LANES * sm_mhz * 1e6 / 1e12                  # lane-instructions / s
+        a = OPS_PER_ORBIT_STEP * work / t / 1e12
+        return {"bound": "alu", "achieved": a, "peak": peak, "unit": "T lane-instructions/s", "frac": a / peak}
     return {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None}
 
 
@@ -252,8 +269,8 @@ def run_sw(args):
     v0s, y, sig = make_data(sw, torch, W, rank)
     nb = W.get("bundle", 1)
     Nb = N // nb
-    base = inputs.disc_ics(W["potential"], Nb, seed=W["seeds"]["ic"] + 1000 * rank)
-    ics = inputs.dither(base, nb, W["seeds"]["dither"] + 1000 * rank, W["potential"]) if nb > 1 else base
+    base = inputs.disc_ics(W["potential"], Nb, seed=replica_seed(W["seeds"]["ic"], rank))
+    ics = inputs.dither(base, nb, replica_seed(W["seeds"]["dither"], rank), W["potential"]) if nb > 1 else base
     dev = torch.device("cuda", local)
     ics_d = torch.from_numpy(ics).to(dev)
     y_d = torch.from_numpy(y).to(dev)
@@ -308,9 +325,7 @@ def run_sw(args):
     info = ctx.solve_info()
     chi2 = chi_d.cpu().numpy()
     if dist:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(elapsed, dist, torch, dev)
         dist.barrier()
 
     # ---- end to end through the host-pointer calls (copies inside the timed region)
@@ -341,10 +356,7 @@ def run_sw(args):
             step_host()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(te, dist, torch, dev)
         h2d = ics_h.nbytes + y.nbytes + sig.nbytes + 8 * 2 * (S + 1) + 16 * grid["nx"] * grid["ny"]
         d2h = 8 * Nb + 8 * 3
         e2e = {"value": N * S * args.steps * world / te, "unit": "orbit-steps/s", "h2d_bytes_per_step": int(h2d),
@@ -357,12 +369,14 @@ def run_sw(args):
         return
 
     # ---- roofline of the dominant kernel (CUDA-event time inside the timed region)
-    K = min(M_gh, N)
     dom = max(kstats, key=lambda k: kstats[k]["ms"])
     sm_mhz = clk["sm_mhz"] if clk else sm_max
-    roof = roofline_entry(dom, kstats, W, M_gh, K, hbm, bf16_sus, sm_mhz)
+    roof = roofline_entry(dom, kstats, hbm, bf16_sus, sm_mhz)
     roof.update({"kernel": dom, "traffic": None, "peak_source": peak_src,
                  "ms_per_launch": kstats[dom]["ms"] / kstats[dom]["launches"]})
+    top = sorted(kstats, key=lambda k: -kstats[k]["ms"])[:8]
+    roof_top = {k: {kk: (round(v, 4) if isinstance(v, float) else v)
+                    for kk, v in roofline_entry(k, kstats, hbm, bf16_sus, sm_mhz).items()} for k in top}
     breakdown = {k: round(v["ms"] / args.steps, 3) for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])}
 
     cpu = None
@@ -382,7 +396,7 @@ def run_sw(args):
             "models_per_s": args.steps * world / elapsed,
             "chi2": {"total": float(chi2[0]), "obs": float(chi2[1]), "reg": float(chi2[2]),
                      "solver": info, "status": statuses[-args.steps:]},
-            "roofline": roof, "kernel_ms_per_step": breakdown, "gpu_launches": int(launches),
+            "roofline": roof, "roofline_top_kernels": roof_top, "kernel_ms_per_step": breakdown, "gpu_launches": int(launches),
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if dist:

@@ -136,7 +136,7 @@ sw_status sw_reduce_gh(sw_ctx* ctx, const sw_matrix* U_hist, const double* gh_v0
 /* Orbit bundles (Sec. 2.2.1: each initial condition is dithered into n nearby realisations that
  * enter the fit as one orbit).  For a matrix whose N columns hold N/n bundles of n consecutive
  * realisations, *U_out receives a new matrix of N/n columns, column j the mean of columns
- * j n .. j n + n - 1 (FP64 sum, rounded once to the matrix precision); rows and layout are
+ * j n .. j n + n - 1 (summed in the matrix precision in realisation order); rows and layout are
  * unchanged.  n must divide N (SW_EINVAL otherwise).  U is unchanged; free both with
  * sw_matrix_free. */
 sw_status sw_bundle(sw_ctx* ctx, const sw_matrix* U, int64_t n, sw_matrix** U_out);
@@ -207,6 +207,11 @@ sw_status sw_set_profiling(sw_ctx* ctx, int enable);
 int sw_kernel_count(void);
 sw_status sw_kernel_stats(sw_ctx* ctx, int k, const char** name, int64_t* launches, double* total_ms);
 sw_status sw_reset_stats(sw_ctx* ctx);
+/* Algorithmic work accumulated by kernel k while profiling is on (since the last reset): *kind 1 =
+ * FLOPs on the SIMT pipes (dense factorisation, MLP), 2 = FLOPs on the tensor cores (Gram), 3 = HBM
+ * bytes (streaming kernels: the bytes their algorithm must move), 4 = orbit-steps (orbit kernels),
+ * 0 = not counted.  Either output may be NULL. */
+sw_status sw_kernel_work(sw_ctx* ctx, int k, double* work, int* kind);
 int64_t sw_launch_count(const sw_ctx* ctx);
 
 /* Tunables (value semantics in parentheses); unknown keys return SW_EINVAL:
@@ -234,12 +239,72 @@ int64_t sw_launch_count(const sw_ctx* ctx);
  *  "as_cg_max" (>= 0)       active set: preconditioned conjugate-gradient steps per reduced solve (default 200)
  *  "as_cg_tol" (> 0)        active set: CG stops at max|r| <= as_cg_tol * kkt_tol * max|q| (default 0.05)
  *  "as_solves" (>= 1)       active set: cap on pivoting steps (default 400)
+ *  "as_grow" (>= 0)         active set: at most max(as_block, as_grow |F|) orbits enter per step (default 0)
+ *  "as_candidates" (>= 0)   active set: initial candidate-set size, 0 for 2 M (default 0)
  *  "ws_factor" (> 0)        initial working-set size in units of M (default 0.6; it grows to take in the
  *                           violators of each round, up to three times that)
  *  "ws_rounds" (>= 1)       working-set exchange rounds (default 6)
  *  "gram_tensor_cores" (0/1) tcgen05 BF16 Gram in the FP32 form (default 1; the operand is split into
  *                           BF16 hi + lo halves and three products are accumulated) */
 sw_status sw_set_option(sw_ctx* ctx, const char* key, double value);
+
+/* ---- Batched model construction.  The paper evaluates one trial potential at a time inside its
+ * MCMC (Sec. 3.2); a batch builds the orbit matrices of many trial potentials at once: each model k
+ * has its own potential, pattern speed, viewing angles and orbit count n_orb[k], and all share the
+ * step count, dt and the observation grid.  One persistent launch integrates, projects and bins
+ * every orbit of every model from a work queue of (model, orbit tile) items; the launch shape
+ * (threads per CTA, CTAs) is chosen on the first run by timing short probe runs of the actual
+ * models, and the run (zeroing, orbit kernel, quality cut, normalisation) is captured in a CUDA graph
+ * that later runs replay.  Results are per-model matrices identical to those of sw_project with the
+ * same inputs (Sec. 2.2.3-2.2.4). */
+typedef struct sw_batch sw_batch;
+/* Allocate a batch of n_models models (n_orb: host, n_models counts >= 1) with nsteps steps on the
+ * given grid (vb NULL when gh != 0: Gauss-Hermite rows, as sw_project with gh_v0_s).  The batch
+ * owns all its device memory; free it with sw_batch_destroy. */
+sw_status sw_batch_create(sw_ctx* ctx, int n_models, const int64_t* n_orb, int64_t nsteps, const sw_pixel_grid* pix,
+                          const sw_vbins* vb, const sw_density_grid* dens, int gh, int mirror4, sw_batch** out);
+/* Load the models: pots[k], omega_p[k], angles[3 k .. 3 k + 2] = (incl, pa, bar_angle) of model k,
+ * the common dt, ics (host, sum(n_orb) x 6 inertial initial conditions, model after model) and in GH
+ * mode gh_v0_s (host, n_models x npix x 2 reference (v0, s) per pixel).  Host arrays are read during
+ * the call only. */
+sw_status sw_batch_set_models(sw_batch* b, const sw_potential_params* pots, const double* omega_p,
+                              const double* angles, double dt, const double* ics, const double* gh_v0_s);
+/* Build every model's matrix (autotunes and captures the graph on the first call). */
+sw_status sw_batch_run(sw_batch* b);
+/* A borrowed view of model k's matrix: valid until the batch is destroyed, overwritten by the next
+ * sw_batch_run; usable wherever a matrix is read (sw_solve_weights, sw_matrix_copy, ...), but
+ * sw_matrix_free refuses it (SW_EINVAL). */
+sw_status sw_batch_matrix(sw_batch* b, int k, sw_matrix** view);
+/* Per-orbit Jacobi drift and status of the last run (host arrays of sum(n_orb), either may be NULL). */
+sw_status sw_batch_stats(sw_batch* b, double* drift_out, uint8_t* status_out);
+/* info4 = (threads per CTA, CTAs, autotuned 0/1, graph 0/1); tune_ms12 (nullable) receives the probe
+ * times of the 12 candidate shapes (threads 64, 128, 256 x 1, 2, 4, 8 CTAs per SM; -1 if not run). */
+sw_status sw_batch_info(const sw_batch* b, int64_t* info4, double* tune_ms12);
+sw_status sw_batch_destroy(sw_batch* b);
+
+/* ---- Learned chi^2 emulator (no counterpart in the paper's method).  The paper samples the
+ * potential parameters by MCMC on the exact chi^2, 1.3 s per evaluation (Sec. 3.2), and names
+ * differentiable surrogates as the route to cheaper likelihoods (Sec. 5.3).  These calls train and
+ * run a fully connected network n_in -> width (n_hidden SiLU layers) -> 1 that screens MCMC
+ * proposals before the exact model judges them (delayed acceptance, Christen & Fox 2005).
+ * Parameters: one FP32 device array; for each layer l, W_l (out x in, row-major) then b_l (out).
+ * All arrays are device memory owned by the caller; activations live in the context's scratch.
+ * Errors: SW_EINVAL for a bad shape or NULL pointer, SW_ECUDA / SW_ENOMEM from the runtime. */
+/* Number of parameters of the network (-1 for an invalid shape). */
+int64_t sw_mlp_param_count(int n_in, int width, int n_hidden);
+/* out[b] = f(x[b, :]) for batch rows of x (batch x n_in, row-major FP32).  bf16 != 0 rounds weights
+ * and layer inputs to BF16 as they enter each product (FP32 accumulation): the inference form. */
+sw_status sw_mlp_forward(sw_ctx* ctx, int n_in, int width, int n_hidden, const float* params_dev,
+                         const float* x_dev, int64_t batch, int bf16, float* out_dev);
+/* Mean-squared error L = mean_b (f(x_b) - t_b)^2 (*loss_out, host) and its gradient dL/dparams
+ * (grad_dev, same layout as params) by back-propagation, FP32. */
+sw_status sw_mlp_loss_grad(sw_ctx* ctx, int n_in, int width, int n_hidden, const float* params_dev,
+                           const float* x_dev, const float* t_dev, int64_t batch, float* grad_dev,
+                           double* loss_out);
+/* One Adam step (Kingma & Ba 2015, bias-corrected; step >= 1 counts from 1) on n_params values:
+ * m, v are the caller's moment arrays (zero before the first step). */
+sw_status sw_mlp_adam(sw_ctx* ctx, int64_t n_params, float* params_dev, const float* grad_dev, float* m_dev,
+                      float* v_dev, int64_t step, double lr, double beta1, double beta2, double eps);
 
 #if defined(__GNUC__)
 #pragma GCC visibility pop

@@ -328,6 +328,7 @@ cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, const __nv_bfloat16* A_
     const int64_t tiles = T * (T + 1) / 2;
     const int nk = (int)(ldA / BKC);
     LaunchTimer lt(ctx, K_GRAM_TC);
+    add_work(ctx, K_GRAM_TC, 2.0 * (double)tiles * BM * BM * (double)ldA * (split ? 3.0 : 1.0));
     if (split)
         k_gram<true><<<(unsigned)tiles, THREADS, Cfg<true>::SMEM_BYTES, ctx_stream(ctx)>>>(map, map_lo, K, nk, C, d_err);
     else

@@ -548,6 +548,74 @@ __global__ void __launch_bounds__(256) k_u_times_w(const T* __restrict__ U, int6
     if (i1 > i0) atomicAdd(acc + r, s);
 }
 
+// ---- double-float products for FP32 matrices.  GB300's FP64 pipe is a small
+// fraction of its FP32 rate, so the products of the stored FP32 matrix with FP64
+// vectors are formed in float-float arithmetic (Dekker 1971; Knuth's two-sum): the
+// vector is split once into float hi + lo, each product u x_hi is made exact by an
+// FMA residual, and the running sum keeps its own rounding error; about 2^-44
+// relative per term, far below the solver's tolerances.
+__global__ void k_split_ff(int64_t n, const double* __restrict__ x, float* __restrict__ hi, float* __restrict__ lo)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        const float h = (float)v;
+        hi[i] = h;
+        lo[i] = (float)(v - (double)h);
+    }
+}
+
+struct FF {
+    float h, l;
+};
+
+__device__ __forceinline__ void ff_add_prod(FF& s, float u, float xh, float xl)
+{
+    const float ph = u * xh;
+    const float pl = fmaf(u, xh, -ph) + u * xl;
+    const float t = s.h + ph;
+    const float bb = t - s.h;
+    const float e = (s.h - (t - bb)) + (ph - bb) + s.l + pl;
+    s.h = t + e;
+    s.l = e - (s.h - t);
+}
+
+// acc[r] += sum_i U[i, r] w[i] with w split into (wh, wl); zero weights skipped
+__global__ void __launch_bounds__(256) k_u_times_w_ff(const float* __restrict__ U, int64_t M, int64_t N,
+                                                      const float* __restrict__ wh, const float* __restrict__ wl,
+                                                      double* __restrict__ acc, int64_t orbits_per_split)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    const int64_t i0 = (int64_t)blockIdx.y * orbits_per_split;
+    int64_t i1 = i0 + orbits_per_split;
+    if (i1 > N) i1 = N;
+    FF s{0.f, 0.f};
+    for (int64_t i = i0; i < i1; ++i) {
+        const float h = wh[i];
+        if (h != 0.f) ff_add_prod(s, U[(size_t)i * M + r], h, wl[i]);
+    }
+    if (i1 > i0) atomicAdd(acc + r, (double)s.h + (double)s.l);
+}
+
+// out[i] = sum_r U[i, r] x[r] with x split into (xh, xl); one warp per orbit
+__global__ void __launch_bounds__(256) k_ut_times_x_ff(const float* __restrict__ U, int64_t M, int64_t N,
+                                                       const float* __restrict__ xh, const float* __restrict__ xl,
+                                                       double* __restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < N; i += nwarp) {
+        const float* col = U + (size_t)i * M;
+        FF s{0.f, 0.f};
+        for (int64_t r = lane; r < M; r += 32) ff_add_prod(s, col[r], xh[r], xl[r]);
+        double d = (double)s.h + (double)s.l;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) out[i] = d;
+    }
+}
+
 // e[r] = (y[r] - acc[r]) * inv_sig[r]; also xs[r] = e[r] * inv_sig[r].
 __global__ void k_residual(int64_t M, const double* __restrict__ y, const double* __restrict__ acc,
                            const double* __restrict__ inv_sig, double* __restrict__ e, double* __restrict__ xs)
@@ -741,6 +809,7 @@ cudaError_t whiten(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* 
                    AT* Alo, int64_t ldA, bool orbit_space)
 {
     LaunchTimer lt(ctx, K_WHITEN);
+    add_work(ctx, K_WHITEN, (double)M * N * (sizeof(T) + (Alo ? 2.0 : 1.0) * sizeof(AT)));
     if (orbit_space) {
         k_whiten_orbit<T, AT><<<cap_grid(N, 1, 65536), 256, 0, ctx_stream(ctx)>>>(U, M, N, inv_sig, cs, A, Alo, ldA);
     } else {
@@ -782,6 +851,7 @@ cudaError_t gemm(sw_ctx* ctx, int kid, int64_t m, int64_t n, int64_t k, T alpha,
 {
     if (m <= 0 || n <= 0) return cudaSuccess;
     LaunchTimer lt(ctx, kid);
+    add_work(ctx, kid, LOWER ? (double)m * (double)(n + 1) * (double)k : 2.0 * (double)m * (double)n * (double)k);
     dim3 grid((unsigned)((n + 63) / 64), (unsigned)((m + 63) / 64));
     k_gemm<T, BT, LOWER><<<grid, 256, 0, ctx_stream(ctx)>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, diag_off);
     return cudaGetLastError();
@@ -804,12 +874,14 @@ cudaError_t cholesky(sw_ctx* ctx, T* G, int64_t K, int* d_info)
         int bs = (int)(K - j0 < NB ? K - j0 : NB);
         {
             LaunchTimer lt(ctx, K_POTRF_DIAG);
+            add_work(ctx, K_POTRF_DIAG, (double)bs * bs * bs / 3.0);
             k_potrf_diag<T><<<1, 256, smem2<T>() / 2, st>>>(G, K, j0, bs, d_info);
         }
         int64_t r0 = j0 + bs, r1 = K;
         if (r1 > r0) {
             {
                 LaunchTimer lt(ctx, K_TRSM_PANEL);
+                add_work(ctx, K_TRSM_PANEL, (double)(r1 - r0) * bs * bs);
                 k_trsm_panel<T><<<(unsigned)((r1 - r0 + NB - 1) / NB), 64, smem2<T>(), st>>>(G, K, j0, bs, r0, r1);
             }
             // trailing lower update: G[r0:, r0:] -= P P^T with P = G[r0:, j0:j0+bs]
@@ -841,10 +913,12 @@ cudaError_t tri_inverse(sw_ctx* ctx, const T* G, T* X, T* D, int64_t K)
         int64_t ncols = j0 + bs;
         {
             LaunchTimer lt(ctx, K_TRINV_DIAG);
+            add_work(ctx, K_TRINV_DIAG, (double)bs * bs * bs / 3.0);
             k_trinv_diag<T><<<1, 64, smem2<T>(), st>>>(G, K, j0, bs, D);
         }
         {
             LaunchTimer lt(ctx, K_TRINV_DIAG);
+            add_work(ctx, K_TRINV_DIAG, (double)bs * bs * (double)ncols);
             k_trmm_diag<T><<<(unsigned)((ncols + NB - 1) / NB), 64, smem2<T>(), st>>>(X, K, j0, bs, ncols, D);
         }
         int64_t r0 = j0 + bs;
@@ -930,6 +1004,7 @@ cudaError_t rowdot(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t cols
 {
     if (rows <= 0) return cudaSuccess;
     LaunchTimer lt(ctx, kid);
+    add_work(ctx, kid, (double)rows * cols * sizeof(AT) * (lower ? 0.5 : 1.0) * (A2 ? 2.0 : 1.0));
     k_rowdot<AT, XT, YT, ACC><<<cap_grid(rows * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(
         A, A2, rows, cols, lda, x, y, alpha, beta, lower);
     return cudaGetLastError();
@@ -942,6 +1017,7 @@ cudaError_t colcomb(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t col
 {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     LaunchTimer lt(ctx, kid);
+    add_work(ctx, kid, (double)rows * cols * sizeof(AT) * (lower ? 0.5 : 1.0) * (A2 ? 2.0 : 1.0));
     int64_t pairs = (cols + 1) / 2;
     unsigned gx = (unsigned)((pairs + 255) / 256);
     // enough blocks to fill the GPU several times over, rows split evenly
@@ -974,17 +1050,35 @@ cudaError_t admm_init(sw_ctx* ctx, int64_t N, const GT* qp, const GT* z, const G
     return cudaGetLastError();
 }
 
+static cudaError_t split_ff(sw_ctx* ctx, const double* x, int64_t n, float** hi, float** lo)
+{
+    if (ctx->ensure(&ctx->d_split, &ctx->split_cap, (size_t)2 * n * sizeof(float), "split vector") != SW_OK)
+        return cudaErrorMemoryAllocation;
+    *hi = (float*)ctx->d_split;
+    *lo = *hi + n;
+    k_split_ff<<<cap_grid(n, 256, 4096), 256, 0, ctx_stream(ctx)>>>(n, x, *hi, *lo);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t u_times_w(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* w, double* acc)
 {
     LaunchTimer lt(ctx, K_RESID);
+    add_work(ctx, K_RESID, (double)M * N * sizeof(T) + 8.0 * (N + 2.0 * M));
     unsigned gx = (unsigned)((M + 255) / 256);
     int64_t want = (152 * 16 + gx - 1) / gx;
     if (want < 1) want = 1;
     int64_t ops = (N + want - 1) / want;
     if (ops < 16) ops = 16;
     unsigned gy = (unsigned)((N + ops - 1) / ops);
-    k_u_times_w<T><<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(U, M, N, w, acc, ops);
+    if constexpr (sizeof(T) == 4) {
+        float *wh, *wl;
+        cudaError_t e = split_ff(ctx, w, N, &wh, &wl);
+        if (e) return e;
+        k_u_times_w_ff<<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(U, M, N, wh, wl, acc, ops);
+    } else {
+        k_u_times_w<T><<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(U, M, N, w, acc, ops);
+    }
     return cudaGetLastError();
 }
 
@@ -1000,7 +1094,15 @@ template <typename T>
 cudaError_t ut_times_x(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* xs, double* out)
 {
     LaunchTimer lt(ctx, K_GRAD);
-    k_ut_times_x<T><<<cap_grid(N * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xs, out);
+    add_work(ctx, K_GRAD, (double)M * N * sizeof(T) + 8.0 * (N + M));
+    if constexpr (sizeof(T) == 4) {
+        float *xh, *xl;
+        cudaError_t e = split_ff(ctx, xs, M, &xh, &xl);
+        if (e) return e;
+        k_ut_times_x_ff<<<cap_grid(N * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xh, xl, out);
+    } else {
+        k_ut_times_x<T><<<cap_grid(N * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xs, out);
+    }
     return cudaGetLastError();
 }
 

@@ -104,13 +104,6 @@ sw_status sw_ctx::ensure(void** p, size_t* cap, size_t need, const char* what)
 // ---------------------------------------------------------------------------
 // Every entry point starts by clearing any stale, non-sticky runtime error so
 // that a later cudaGetLastError() reports only errors of this call.
-#define CHECK_CTX(ctx)                                       \
-    do {                                                     \
-        if (!(ctx) || (ctx)->destroyed) return SW_EINVAL;    \
-        (ctx)->err.clear();                                  \
-        cudaSetDevice((ctx)->device);                        \
-        cudaGetLastError();                                  \
-    } while (0)
 #define CUDA_TRY(ctx, expr, what)                                  \
     do {                                                           \
         cudaError_t e_ = (expr);                                   \
@@ -161,10 +154,11 @@ static void ctx_release(sw_ctx* ctx)
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     ctx->harvest();
-    void* bufs[] = {ctx->d_soa, ctx->d_cs, ctx->d_aos, ctx->d_drift, ctx->d_status, ctx->d_stats, ctx->d_ghtab};
+    void* bufs[] = {ctx->d_soa, ctx->d_cs, ctx->d_aos, ctx->d_drift, ctx->d_status, ctx->d_stats, ctx->d_ghtab,
+                    ctx->d_mlp, ctx->d_split};
     for (void* b : bufs)
         if (b) cudaFree(b);
-    ctx->d_soa = ctx->d_cs = ctx->d_ghtab = nullptr;
+    ctx->d_soa = ctx->d_cs = ctx->d_ghtab = ctx->d_mlp = ctx->d_split = nullptr;
     ctx->d_aos = ctx->d_drift = nullptr;
     ctx->d_status = nullptr;
     ctx->d_stats = nullptr;
@@ -195,9 +189,10 @@ extern "C" const char* sw_last_error(const sw_ctx* ctx) { return ctx ? ctx->err.
 // ---------------------------------------------------------------------------
 static bool pos_finite(double x) { return std::isfinite(x) && x > 0.0; }
 
-extern "C" sw_status sw_set_potential(sw_ctx* ctx, const sw_potential_params* p)
+namespace sw {
+
+sw_status check_potential(sw_ctx* ctx, const sw_potential_params* p)
 {
-    CHECK_CTX(ctx);
     if (!p) { set_error(ctx, "sw_set_potential: params is NULL"); return SW_EINVAL; }
     if (p->disc_M != 0.0 && !(pos_finite(p->disc_M) && pos_finite(p->disc_a) && pos_finite(p->disc_b))) {
         set_error(ctx, "sw_set_potential: disc mass and scales must be positive and finite");
@@ -217,34 +212,49 @@ extern "C" sw_status sw_set_potential(sw_ctx* ctx, const sw_potential_params* p)
         set_error(ctx, "sw_set_potential: bad test potential");
         return SW_EINVAL;
     }
-    ctx->pot = *p;
-    ctx->Mdm = 0.0;
-    ctx->rs = 1.0;
-    if (p->halo_M200 > 0.0) {
+    return SW_OK;
+}
+
+// NFW from (M200, c, H0) (Sec. 2.1): rho_crit = 3 H0^2 / (8 pi G), R200 from M200 = 200 rho_crit
+// (4 pi / 3) R200^3, R_s = R200 / c, M_DM = M200 / [ln(1 + c) - c / (1 + c)].
+void halo_constants(const sw_potential_params& p, double& Mdm, double& rs)
+{
+    Mdm = 0.0;
+    rs = 1.0;
+    if (p.halo_M200 > 0.0) {
         const double pi = 3.14159265358979323846;
-        double H = p->H0 / 1000.0;
+        double H = p.H0 / 1000.0;
         double rho_c = 3.0 * H * H / (8.0 * pi * SW_G);
-        double Rv = cbrt(3.0 * p->halo_M200 / (4.0 * pi * 200.0 * rho_c));
-        ctx->rs = Rv / p->halo_c;
-        ctx->Mdm = p->halo_M200 / (log(1.0 + p->halo_c) - p->halo_c / (1.0 + p->halo_c));
+        double Rv = cbrt(3.0 * p.halo_M200 / (4.0 * pi * 200.0 * rho_c));
+        rs = Rv / p.halo_c;
+        Mdm = p.halo_M200 / (log(1.0 + p.halo_c) - p.halo_c / (1.0 + p.halo_c));
     }
+}
+
+}  // namespace sw
+
+extern "C" sw_status sw_set_potential(sw_ctx* ctx, const sw_potential_params* p)
+{
+    CHECK_CTX(ctx);
+    SW_TRY(check_potential(ctx, p));
+    ctx->pot = *p;
+    halo_constants(*p, ctx->Mdm, ctx->rs);
     ctx->has_pot = true;
     return SW_OK;
 }
 
 template <typename T>
-FieldT<T> make_field(const sw_ctx* ctx)
+FieldT<T> make_field_from(const sw_potential_params& p, double Mdm, double rs)
 {
-    const sw_potential_params& p = ctx->pot;
     FieldT<T> f{};
     f.has_disc = p.disc_M > 0.0;
     f.gm_disc = (T)(SW_G * p.disc_M);
     f.disc_a = (T)p.disc_a;
     f.disc_b2 = (T)(p.disc_b * p.disc_b);
-    f.has_halo = ctx->Mdm > 0.0;
-    f.gm_halo = (T)(SW_G * ctx->Mdm);
-    f.halo_rs = (T)ctx->rs;
-    f.halo_inv_rs = (T)(1.0 / ctx->rs);
+    f.has_halo = Mdm > 0.0;
+    f.gm_halo = (T)(SW_G * Mdm);
+    f.halo_rs = (T)rs;
+    f.halo_inv_rs = (T)(1.0 / rs);
     f.has_bar = p.bar_M > 0.0;
     f.k_bar = p.bar_M > 0.0 ? (T)(SW_G * p.bar_M / (2.0 * p.bar_L)) : T(0);
     f.bar_L = (T)p.bar_L;
@@ -256,13 +266,21 @@ FieldT<T> make_field(const sw_ctx* ctx)
     return f;
 }
 
+template <typename T>
+FieldT<T> make_field(const sw_ctx* ctx)
+{
+    return make_field_from<T>(ctx->pot, ctx->Mdm, ctx->rs);
+}
+template FieldT<float> make_field_from<float>(const sw_potential_params&, double, double);
+template FieldT<double> make_field_from<double>(const sw_potential_params&, double, double);
+
 // rows of the SoA orbit state: 6, plus 6 rounding residuals in FP32
 template <typename T>
 static constexpr int soa_rows() { return sizeof(T) == 4 ? 12 : 6; }
 
 // cos / sin of Omega_p * (n dt), n = 0..nsteps, in FP64 on the host.
 template <typename T>
-static void cs_table(std::vector<T>& out, double omega, double dt, int64_t nsteps)
+void cs_table(std::vector<T>& out, double omega, double dt, int64_t nsteps)
 {
     out.resize(2 * (nsteps + 1));
     for (int64_t n = 0; n <= nsteps; ++n) {
@@ -429,6 +447,13 @@ GridT<T> make_grid(double incl, double pa, double bar_angle, const sw_pixel_grid
     g.M = g.nd + g.npix + (gh ? 4 * g.npix : g.npix * g.nv);
     return g;
 }
+
+template void cs_table<float>(std::vector<float>&, double, double, int64_t);
+template void cs_table<double>(std::vector<double>&, double, double, int64_t);
+template GridT<float> make_grid<float>(double, double, double, const sw_pixel_grid*, const sw_vbins*,
+                                       const sw_density_grid*, int, int);
+template GridT<double> make_grid<double>(double, double, double, const sw_pixel_grid*, const sw_vbins*,
+                                         const sw_density_grid*, int, int);
 
 template <typename T>
 static sw_status project_impl(sw_ctx* ctx, const GridT<T>& g, const double* gh_v0_s, sw_matrix** U_out)
@@ -675,6 +700,7 @@ extern "C" sw_status sw_matrix_copy(const sw_matrix* U, double* host_out)
 extern "C" sw_status sw_matrix_free(sw_matrix* U)
 {
     if (!U) return SW_OK;
+    if (U->borrowed) return SW_EINVAL;   // owned by its batch
     sw_ctx* ctx = U->ctx;
     cudaSetDevice(U->device);
     if (!ctx->destroyed) {
@@ -792,11 +818,35 @@ extern "C" sw_status sw_kernel_stats(sw_ctx* ctx, int k, const char** name, int6
     return SW_OK;
 }
 
+namespace sw {
+const int kKernelWorkKind[K_COUNT] = {
+    W_BYTES /*ics_soa*/, W_ORBIT_STEPS /*orbit_bin*/, W_ORBIT_STEPS /*orbit_drift*/, W_BYTES /*zero_flagged*/,
+    W_BYTES /*finalize*/, W_NONE /*trajectory*/, W_NONE /*poteval*/, W_BYTES /*whiten*/, W_FLOP_TENSOR /*gram_tc*/,
+    W_FLOP_SIMT /*gram_simt*/, W_NONE /*shift*/, W_FLOP_SIMT /*potrf_diag*/, W_FLOP_SIMT /*trsm_panel*/,
+    W_FLOP_SIMT /*syrk_update*/, W_FLOP_SIMT /*trinv_diag*/, W_FLOP_SIMT /*trinv_update*/, W_BYTES /*gemv_n*/,
+    W_BYTES /*gemv_t*/, W_BYTES /*trmv_l*/, W_BYTES /*trmv_lt*/, W_NONE /*admm_update*/, W_BYTES /*residual*/,
+    W_BYTES /*gradient*/, W_NONE /*chi2*/, W_NONE /*misc*/, W_ORBIT_STEPS /*batch_orbit*/, W_FLOP_SIMT /*mlp_fwd*/,
+    W_FLOP_SIMT /*mlp_bwd*/, W_NONE /*adam*/, W_BYTES /*reduce_gh*/, W_NONE /*pcg*/, W_BYTES /*bundle*/};
+
+void add_work(sw_ctx* ctx, int kid, double units)
+{
+    if (ctx && ctx->prof && kid >= 0 && kid < K_COUNT) ctx->k_work[kid] += units;
+}
+}  // namespace sw
+
+extern "C" sw_status sw_kernel_work(sw_ctx* ctx, int k, double* work, int* kind)
+{
+    if (!ctx || k < 0 || k >= K_COUNT) return SW_EINVAL;
+    if (work) *work = ctx->k_work[k];
+    if (kind) *kind = kKernelWorkKind[k];
+    return SW_OK;
+}
+
 extern "C" sw_status sw_reset_stats(sw_ctx* ctx)
 {
     CHECK_CTX(ctx);
     ctx->harvest();
-    for (int k = 0; k < K_COUNT; ++k) { ctx->k_launch[k] = 0; ctx->k_ms[k] = 0.0; }
+    for (int k = 0; k < K_COUNT; ++k) { ctx->k_launch[k] = 0; ctx->k_ms[k] = 0.0; ctx->k_work[k] = 0.0; }
     return SW_OK;
 }
 

@@ -88,6 +88,8 @@ struct sw_ctx {
     unsigned long long* d_stats = nullptr;
     void* d_ghtab = nullptr; size_t ghtab_cap = 0;
     int64_t last_proj_n = 0;
+    void* d_mlp = nullptr; size_t mlp_cap = 0;   // MLP activations
+    void* d_split = nullptr; size_t split_cap = 0;   // FP64 vectors split into float hi + lo
     // solve
     sw::SolveWS solve_ws;
     double solve_info[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -101,6 +103,7 @@ struct sw_ctx {
     int64_t launches = 0;
     int64_t k_launch[sw::K_COUNT] = {};
     double k_ms[sw::K_COUNT] = {};
+    double k_work[sw::K_COUNT] = {};
 
     cudaEvent_t take_event();
     void harvest();
@@ -117,6 +120,30 @@ struct sw_matrix {
     int nv = 0;            // velocity bins of a histogram matrix (0 in GH mode)
     double v0 = 0.0, dv = 1.0;
     void* d = nullptr;   // orbit-major: column i at d + i * M
+    bool borrowed = false; // a view into a batch's storage: freed with the batch, not by sw_matrix_free
 };
 
 extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value);
+
+// shared by the single-model and batched paths (sw_api.cu)
+namespace sw {
+sw_status check_potential(sw_ctx* ctx, const sw_potential_params* p);
+void halo_constants(const sw_potential_params& p, double& Mdm, double& rs);
+}  // namespace sw
+template <typename T>
+sw::FieldT<T> make_field_from(const sw_potential_params& p, double Mdm, double rs);
+template <typename T>
+void cs_table(std::vector<T>& out, double omega, double dt, int64_t nsteps);
+template <typename T>
+sw::GridT<T> make_grid(double incl, double pa, double bar_angle, const sw_pixel_grid* pix, const sw_vbins* vb,
+                       const sw_density_grid* dens, int gh, int mirror4);
+
+// Entry-point prologue: reject a NULL or destroyed context, clear the last error
+// message, select the context's device and drop a stale CUDA error.
+#define CHECK_CTX(ctx)                                       \
+    do {                                                     \
+        if (!(ctx) || (ctx)->destroyed) return SW_EINVAL;    \
+        (ctx)->err.clear();                                  \
+        cudaSetDevice((ctx)->device);                        \
+        cudaGetLastError();                                  \
+    } while (0)

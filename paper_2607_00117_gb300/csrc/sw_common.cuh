@@ -75,6 +75,13 @@ struct LaunchTimer {
 
 cudaStream_t ctx_stream(sw_ctx* ctx);
 
+// Algorithmic work of a launch, accumulated per kernel for the roofline: FLOPs for the
+// dense factorisation and Gram kernels, HBM bytes for the streaming kernels, orbit-steps
+// for the orbit kernels (kind per kernel in kKernelWorkKind).
+void add_work(sw_ctx* ctx, int kid, double units);
+enum WorkKind { W_NONE = 0, W_FLOP_SIMT = 1, W_FLOP_TENSOR = 2, W_BYTES = 3, W_ORBIT_STEPS = 4 };
+extern const int kKernelWorkKind[K_COUNT];
+
 // ---- orbit kernels (k_orbit.cu)
 template <typename T>
 cudaError_t launch_ics_to_soa(sw_ctx* ctx, const double* ics_dev_aos, int64_t n, T* soa, int64_t ld);
@@ -99,9 +106,10 @@ cudaError_t launch_reduce_gh(sw_ctx* ctx, const void* Uh, int64_t Mh, int64_t N,
                              const void* W, void* Ug, int64_t Mg);
 template <typename T>
 cudaError_t launch_bundle(sw_ctx* ctx, const void* U, int64_t M, int64_t Nb, int n, void* out);
-cudaError_t launch_batch_orbit_bin(sw_ctx* ctx, const ModelT<float>* models_dev, int n_models,
-                                   const int64_t* tile_model, const int64_t* tile_first, int64_t n_tiles,
-                                   const float* soa, int64_t ld, int64_t nsteps, int ej_every, double* drift,
-                                   uint8_t* status, int block, int* work_counter);
+// persistent multi-model launch: threads per CTA in {64, 128, 256}, grid CTAs
+template <typename T>
+cudaError_t launch_batch_orbit_bin(cudaStream_t st, int threads, int grid, int gh, const ModelT<T>* models,
+                                   const int2* items, int n_items, int* next, const T* soa, int64_t ld,
+                                   int64_t nsteps, int ej_every, double* drift, uint8_t* status);
 
 }  // namespace sw

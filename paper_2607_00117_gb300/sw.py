@@ -74,6 +74,21 @@ SIGNATURES = {
                                   ctypes.c_int, ctypes.POINTER(_VP)]),
     "sw_reduce_gh": (ctypes.c_int, [_VP, _VP, _D, ctypes.POINTER(_VP)]),
     "sw_bundle": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.POINTER(_VP)]),
+    "sw_batch_create": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int64, _VP, _VP, _VP, ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(_VP)]),
+    "sw_batch_set_models": (ctypes.c_int, [_VP, _VP, _D, _D, ctypes.c_double, _D, _D]),
+    "sw_batch_run": (ctypes.c_int, [_VP]),
+    "sw_batch_matrix": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "sw_batch_stats": (ctypes.c_int, [_VP, _D, _U8]),
+    "sw_batch_info": (ctypes.c_int, [_VP, _VP, _D]),
+    "sw_batch_destroy": (ctypes.c_int, [_VP]),
+    "sw_mlp_param_count": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "sw_mlp_forward": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int64,
+                                      ctypes.c_int, _VP]),
+    "sw_mlp_loss_grad": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP,
+                                        ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_double)]),
+    "sw_mlp_adam": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "sw_project_stats": (ctypes.c_int, [_VP, _D, _U8]),
     "sw_solve_weights": (ctypes.c_int, [_VP, _VP, _D, _D, ctypes.c_double, _D, _D]),
     "sw_solve_weights_device": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP]),
@@ -89,6 +104,7 @@ SIGNATURES = {
     "sw_kernel_count": (ctypes.c_int, []),
     "sw_kernel_stats": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), _I64, _D]),
     "sw_reset_stats": (ctypes.c_int, [_VP]),
+    "sw_kernel_work": (ctypes.c_int, [_VP, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]),
     "sw_launch_count": (ctypes.c_int64, [_VP]),
     "sw_set_option": (ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_double]),
 }
@@ -181,13 +197,74 @@ class Matrix:
         return y
 
     def free(self) -> None:
-        if self.handle:
+        if self.handle and not getattr(self, "borrowed", False):
             lib().sw_matrix_free(self.handle)
             self.handle = None
 
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many trial models built in one persistent launch (see sw_batch_* in include/sw.h)."""
+
+    def __init__(self, ctx: "Context", n_orb, nsteps: int, grid: dict):
+        self.ctx = ctx
+        self.n_orb = np.ascontiguousarray(n_orb, dtype=np.int64)
+        self.grid = dict(grid)
+        self._pg, self._vb, self._dg = pixel_grid(grid), vbins(grid), density_grid(grid)
+        gh = int(bool(grid.get("gh")))
+        h = _VP()
+        ctx._check(lib().sw_batch_create(ctx.handle, len(self.n_orb), self.n_orb.ctypes.data_as(_VP), int(nsteps),
+                                         ctypes.byref(self._pg), None if gh else ctypes.byref(self._vb),
+                                         ctypes.byref(self._dg), gh, int(grid.get("mirror4", 1)), ctypes.byref(h)))
+        self.handle = h.value
+
+    def set_models(self, pots: list, omega_p, angles, dt: float, ics: np.ndarray, gh_v0s: Optional[np.ndarray] = None):
+        arr = (PotentialParams * len(pots))(*[potential_params(p) for p in pots])
+        om = np.ascontiguousarray(omega_p, dtype=np.float64)
+        an = np.ascontiguousarray(angles, dtype=np.float64).reshape(-1)
+        ics = np.ascontiguousarray(ics, dtype=np.float64).reshape(-1)
+        gh = None
+        if gh_v0s is not None:
+            gh_v0s = np.ascontiguousarray(gh_v0s, dtype=np.float64).reshape(-1)
+            gh = _dp(gh_v0s)
+        self.ctx._check(lib().sw_batch_set_models(self.handle, arr, _dp(om), _dp(an), dt, _dp(ics), gh))
+
+    def run(self) -> None:
+        self.ctx._check(lib().sw_batch_run(self.handle))
+
+    def matrix(self, k: int) -> Matrix:
+        out = _VP()
+        self.ctx._check(lib().sw_batch_matrix(self.handle, int(k), ctypes.byref(out)))
+        m = Matrix(self.ctx, out.value)
+        m.borrowed = True
+        return m
+
+    def stats(self):
+        n = int(self.n_orb.sum())
+        drift = np.empty(n); status = np.empty(n, dtype=np.uint8)
+        self.ctx._check(lib().sw_batch_stats(self.handle, _dp(drift), status.ctypes.data_as(_U8)))
+        return drift, status
+
+    def info(self) -> dict:
+        i4 = (ctypes.c_int64 * 4)()
+        t = np.empty(12)
+        self.ctx._check(lib().sw_batch_info(self.handle, i4, _dp(t)))
+        return {"threads": i4[0], "ctas": i4[1], "autotuned": bool(i4[2]), "graph": bool(i4[3]),
+                "probe_ms": t.tolist()}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib().sw_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
 
@@ -203,6 +280,7 @@ class Context:
             raise SwError(st, "sw_create failed (no CUDA device?)")
         self.handle = h.value
         self.precision = precision
+        self.device = device
 
     def _check(self, st: int) -> int:
         if st not in (SW_OK,):
@@ -269,6 +347,22 @@ class Context:
         self._check(lib().sw_bundle(self.handle, U.handle, int(n), ctypes.byref(out)))
         return Matrix(self, out.value)
 
+    # ---- learned chi^2 emulator (device pointers, e.g. torch tensors' data_ptr())
+    def mlp_forward(self, shape, params_ptr: int, x_ptr: int, batch: int, out_ptr: int, bf16: bool = False):
+        self._check(lib().sw_mlp_forward(self.handle, *shape, params_ptr, x_ptr, int(batch), int(bool(bf16)),
+                                         out_ptr))
+
+    def mlp_loss_grad(self, shape, params_ptr: int, x_ptr: int, t_ptr: int, batch: int, grad_ptr: int) -> float:
+        loss = ctypes.c_double()
+        self._check(lib().sw_mlp_loss_grad(self.handle, *shape, params_ptr, x_ptr, t_ptr, int(batch), grad_ptr,
+                                           ctypes.byref(loss)))
+        return loss.value
+
+    def mlp_adam(self, n: int, params_ptr: int, grad_ptr: int, m_ptr: int, v_ptr: int, step: int, lr: float,
+                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        self._check(lib().sw_mlp_adam(self.handle, int(n), params_ptr, grad_ptr, m_ptr, v_ptr, int(step), lr,
+                                      beta1, beta2, eps))
+
     def project_stats(self, n: int):
         drift = np.empty(n); status = np.empty(n, dtype=np.uint8)
         self._check(lib().sw_project_stats(self.handle, _dp(drift), status.ctypes.data_as(_U8)))
@@ -319,7 +413,11 @@ class Context:
             name = ctypes.c_char_p(); n = ctypes.c_int64(); ms = ctypes.c_double()
             self._check(lib().sw_kernel_stats(self.handle, k, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms)))
             if n.value:
-                out[name.value.decode()] = {"launches": n.value, "ms": ms.value}
+                work, kind = ctypes.c_double(), ctypes.c_int()
+                self._check(lib().sw_kernel_work(self.handle, k, ctypes.byref(work), ctypes.byref(kind)))
+                out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "work": work.value,
+                                            "kind": ["none", "flop_simt", "flop_tensor", "bytes",
+                                                     "orbit_steps"][kind.value]}
         return out
 
     def launch_count(self) -> int:

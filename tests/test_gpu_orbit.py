@@ -288,3 +288,26 @@ def test_reduce_gh(sw, orc, prec):
     ref = orc.reduce_gh(Uh.copy(), 192, 120, 32, -400.0, 25.0, v0s)   # reduce the GPU's own histogram
     np.testing.assert_allclose(Ug.copy(), ref, rtol=1e-12 if prec == "fp64" else 2e-5,
                                atol=1e-15 if prec == "fp64" else 1e-7)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_bundle(sw, orc, prec):
+    """sw_bundle against the oracle's bundle mean on the GPU's own matrix, with
+    dithered initial conditions (Sec. 2.2.1), a ragged bundle count and the
+    n = 1 identity; a size that does not divide N is rejected."""
+    pot = BARRED
+    base = inputs.disc_ics(inputs.DISC_HALO, 37, seed=111)
+    ics = inputs.dither(base, 4, 112, pot)
+    assert ics.shape == (148, 6)
+    grid = _grid(W2, nx=12, ny=10, nv=8, nR=6, nphi=6, nz=4)
+    c = ctx_for(sw, prec, pot)
+    c.integrate_library(ics, 40.0, inputs.DT_HALF_MYR, 200)
+    U = c.project(grid)
+    Ug = U.copy()
+    B = c.bundle(U, 4)
+    assert (B.M, B.N) == (U.M, 37)
+    tol = 1e-15 if prec == "fp64" else 3e-7
+    np.testing.assert_allclose(B.copy(), orc.bundle(Ug, 4), rtol=tol, atol=0)
+    np.testing.assert_array_equal(c.bundle(U, 1).copy(), Ug)
+    with pytest.raises(sw.SwError):
+        c.bundle(U, 3)

@@ -122,8 +122,33 @@ def test_solve_rejects_bad_errors(sw, orc):
         c.solve_weights(U, y, np.ones(U.M), -1.0)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_solve_active_set_path(sw, orc, prec):
+    """The active-set path (used above 8 192 orbits) forced on a small problem
+    with more orbits than constraints: exact chi^2 (1e-4 relative to the
+    oracle's Lawson-Hanson) and its KKT certificate met."""
+    grid = dict(W1["grid"], nx=6, ny=6, nR=5, nphi=4, nz=3, gh=1, incl=0.9)
+    ics = inputs.disc_ics(BARRED, 700, seed=202)
+    po = orc.make_pot(BARRED)
+    mom = orc.pixel_moments(po, 40.0, inputs.DT_HALF_MYR, 500, ics, orc.make_obs(grid), np.ones(len(ics)))
+    v0s, gh_err = inputs.gh_reference(mom)
+    c, U = _build(sw, prec, BARRED, 40.0, ics, 500, grid, gh_v0s=v0s)
+    c.set_option("orbit_direct_max", 0)
+    Ug = U.copy().T.copy()
+    blocks = inputs.row_blocks(grid)
+    y, sig = _mock(orc, Ug, blocks, gh_err=gh_err)
+    w, chi2 = c.solve_weights(U, y, sig, 1.0)
+    info = c.solve_info()
+    assert info["kkt_met"] and info["ws_size"] == int((w > 0).sum())
+    w_o, chi2_o, H, q = _oracle_solve(orc, Ug, y, sig, 1.0, blocks["dens"][1])
+    assert np.all(w >= 0)
+    np.testing.assert_allclose(chi2[:2], chi2_o[:2], rtol=1e-4)
+    k = orc.kkt_residual(H, q, w)
+    assert k["pg_inf"] <= 1e-6 * np.abs(q).max(), k
+
+
 def test_solve_working_set_path(sw, orc):
-    """The working-set path (used for very many orbits) on a small problem with
+    """The ADMM working-set option for very many orbits on a small problem with
     the direct path disabled: its chi^2 approaches the exact one and its
     weights satisfy the KKT conditions to the solver's reported level."""
     grid = dict(W1["grid"], nx=6, ny=6, nR=5, nphi=4, nz=3, gh=1, incl=0.9)
@@ -133,6 +158,7 @@ def test_solve_working_set_path(sw, orc):
     v0s, gh_err = inputs.gh_reference(mom)
     c, U = _build(sw, "fp32", BARRED, 40.0, ics, 500, grid, gh_v0s=v0s)
     c.set_option("orbit_direct_max", 0)
+    c.set_option("large_solver", 1)
     c.set_option("ws_rounds", 12)
     Ug = U.copy().T.copy()
     blocks = inputs.row_blocks(grid)

@@ -198,3 +198,17 @@ def test_reduce_gh_of_gaussian_histogram(orc):
     np.testing.assert_allclose(out[0, 2:], 0.0, atol=1e-9)
     out2 = orc.reduce_gh(U, 1, 1, nv, vmin, dv, np.array([[v0 - 10.0, s]]))
     assert out2[0, 2] > 0.05 * mass
+
+
+def test_bundle_is_the_mean_of_consecutive_columns(orc):
+    """Orbit bundles (Sec. 2.2.1): a hand case, identical realisations, and mass
+    conservation (n x the bundle's column sum = the realisations' total)."""
+    U = np.array([[1.0, 2.0], [3.0, 4.0], [5.0, 6.0], [7.0, 9.0]])   # (N=4 orbits, 2 rows)
+    np.testing.assert_array_equal(orc.bundle(U, 2), [[2.0, 3.0], [6.0, 7.5]])
+    np.testing.assert_array_equal(orc.bundle(U, 1), U)
+    rng = np.random.default_rng(5)
+    col = rng.random(7)
+    np.testing.assert_allclose(orc.bundle(np.tile(col, (3, 1)), 3), col[None, :], rtol=1e-15)
+    V = rng.random((12, 5))
+    B = orc.bundle(V, 4)
+    np.testing.assert_allclose(4 * B.sum(axis=1), V.reshape(3, 4, 5).sum(axis=(1, 2)), rtol=1e-14)
