@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--impl", default="sw", choices=["sw", "reference"])
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched_64"],
+                    help="batched_64: 64 trial potentials built in one persistent launch, then solved")
     return ap.parse_args()
 
 
@@ -403,9 +405,104 @@ def run_sw(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """64 trial potentials of the 12-D box with orbit counts U(10k, 100k), 5 000
+    steps, built in one persistent launch (autotuned, replayed from a CUDA graph),
+    each bundled 4 -> 1 and solved against mock data from its own library."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2607_00117_gb300 import sw
+    sw.lib()
+    W = inputs.WORKLOADS["batched_64"]
+    grid, S, dt = W["grid"], W["nsteps"], W["dt"]
+    K = W["n_models"]
+    hbm, bf16, bf16_sus, sm_max, peak_src = peaks()
+    th = inputs.draw_box(K, replica_seed(W["seeds"]["box"], rank))
+    models = [inputs.box_model(t) for t in th]
+    counts = inputs.batched_orbit_counts(K, *W["n_orb_range"], seed=replica_seed(W["seeds"]["box"] + 1, rank))
+    counts = (counts // 4) * 4                                    # whole bundles of 4 dithers
+    ics = np.concatenate([inputs.dither(inputs.disc_ics(m["potential"], int(n) // 4, seed=W["seeds"]["data"] + k),
+                                        4, W["seeds"]["data"] + 500 + k, m["potential"])
+                          for k, (m, n) in enumerate(zip(models, counts))])
+    npix = grid["nx"] * grid["ny"]
+    v0s = np.tile(np.array([0.0, 150.0]), (K, npix, 1))
+    stream = torch.cuda.current_stream()
+    ctx = sw.Context(local, "fp32", stream.cuda_stream)
+    b = sw.Batch(ctx, counts, S, grid)
+    b.set_models([m["potential"] for m in models], [m["omega_p"] for m in models],
+                 [[m["incl"], 0.0, m["bar_angle"]] for m in models], dt, ics, v0s)
+    blocks = None
+    data = []
+
+    def step(make_data=False):
+        b.run()
+        chis = []
+        for k in range(K):
+            Ub = ctx.bundle(b.matrix(k), 4)
+            if make_data:
+                y0 = Ub.apply(inputs.true_weights(Ub.N, W["seeds"]["data"] + 100 + k))
+                bl = {"dens": (0, Ub.blocks[0]), "pix": (Ub.blocks[0], Ub.blocks[0] + Ub.blocks[1]),
+                      "kin": (Ub.blocks[0] + Ub.blocks[1], Ub.M)}
+                sig = inputs.mock_sigma(y0, bl, gh_err=np.tile([0.02, 0.02, 0.03, 0.03], (npix, 1)))
+                data.append((y0 + sig * inputs.noise(len(y0), W["seeds"]["data"] + 200 + k), sig))
+            y, sig = data[k]
+            _, chi = ctx.solve_weights(Ub, y, sig, W["lam"], allow_nonconv=True)
+            chis.append(float(chi[1]))
+            Ub.free()
+        return chis
+
+    step(make_data=True)
+    for _ in range(max(0, args.warmup - 1)):
+        step()
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    ctx.reset_stats()
+    clocks = Clocks(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        chis = step()
+    torch.cuda.synchronize()                # every step ends synchronised with the context stream
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    clk = clocks.stop()
+    kstats = ctx.kernel_stats()
+    ctx.set_profiling(False)
+    info = b.info()
+    if rank != 0:
+        return
+    ntot = int(counts.sum())
+    sm_mhz = clk["sm_mhz"] if clk else sm_max
+    dom = max(kstats, key=lambda k: kstats[k]["ms"])
+    roof = roofline_entry(dom, kstats, hbm, bf16_sus, sm_mhz)
+    roof.update({"kernel": dom, "traffic": None, "peak_source": peak_src})
+    bo = kstats.get("batch_orbit_bin", {"ms": float("nan")})
+    line = {"metric": "orbit-steps/s (whole model evaluations, FP32 batched vs FP64 plain at matched chi^2)",
+            "value": ntot * S * args.steps / elapsed, "unit": "orbit-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched_64", "n_models": K, "orbits": ntot, "nsteps": S,
+                       "bundles_per_model": [int(n) // 4 for n in counts], "rows": int(inputs.rows_of(grid)),
+                       "launch": info, "l2": "orbit matrices (1.6 GB+) far larger than L2"},
+            "models_per_s": K * args.steps / elapsed,
+            "construction_orbit_steps_per_s": ntot * S / (bo["ms"] / 1e3 / args.steps) if bo["ms"] == bo["ms"] else None,
+            "chi2_obs_median": float(np.median(chis)), "roofline": roof,
+            "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in
+                                   sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])},
+            "clocks": clk, "e2e": None, "cpu_baseline": None, "gpu_launches": int(ctx.launch_count())}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batched_64":
+        run_batched(a)
     else:
         run_sw(a)

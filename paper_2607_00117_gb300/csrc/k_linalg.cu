@@ -148,40 +148,39 @@ __global__ void __launch_bounds__(256) k_gemm(int64_t m, int64_t n, int64_t k, T
 // ---------------------------------------------------------------------------
 constexpr int NB = 64;
 
-// In-place Cholesky of the bs x bs diagonal block at (j0, j0).  A pivot that
-// is not positive records its global index + 1 in *info and is replaced by a
-// tiny positive value so the factorisation can finish.
+// In-place Cholesky of the bs x bs diagonal block at (j0, j0): thread t owns row t
+// (two warps; the row updates of a column step need no index arithmetic and every
+// thread computes the pivot itself, so a column costs two barriers).  A pivot that
+// is not positive records its global index + 1 in *info and is replaced by a tiny
+// positive value so the factorisation can finish.
 template <typename T>
-__global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t ld, int64_t j0, int bs, int* info)
+__global__ void __launch_bounds__(NB) k_potrf_diag(T* __restrict__ G, int64_t ld, int64_t j0, int bs, int* info)
 {
     extern __shared__ unsigned char smraw[];
     T (*a)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);
     const int t = threadIdx.x;
-    for (int e = t; e < NB * NB; e += blockDim.x) {
+    for (int e = t; e < NB * NB; e += NB) {
         int i = e / NB, j = e % NB;
         a[i][j] = (i < bs && j <= i) ? G[(size_t)(j0 + i) * ld + j0 + j] : T(0);
     }
     __syncthreads();
     for (int j = 0; j < bs; ++j) {
-        if (t == 0) {
-            T d = a[j][j];
-            if (!(d > T(0))) {
-                if (info) atomicCAS(info, 0, (int)(j0 + j + 1));
-                d = T(1e-30);
-            }
-            a[j][j] = sqrt(d);
+        T d = a[j][j];
+        if (!(d > T(0))) {
+            if (t == j && info) atomicCAS(info, 0, (int)(j0 + j + 1));
+            d = T(1e-30);
         }
+        d = sqrt(d);
+        if (t > j && t < bs) a[t][j] /= d;
         __syncthreads();
-        for (int i = j + 1 + t; i < bs; i += blockDim.x) a[i][j] /= a[j][j];
-        __syncthreads();
-        const int rem = bs - j - 1;
-        for (int e = t; e < rem * rem; e += blockDim.x) {
-            int i = j + 1 + e / rem, l = j + 1 + e % rem;
-            if (l <= i) a[i][l] -= a[i][j] * a[l][j];
+        if (t == j) a[j][j] = d;
+        if (t > j && t < bs) {
+            const T aij = a[t][j];
+            for (int l = j + 1; l <= t; ++l) a[t][l] -= aij * a[l][j];
         }
         __syncthreads();
     }
-    for (int e = t; e < NB * NB; e += blockDim.x) {
+    for (int e = t; e < NB * NB; e += NB) {
         int i = e / NB, j = e % NB;
         if (i < bs && j <= i) G[(size_t)(j0 + i) * ld + j0 + j] = a[i][j];
     }
@@ -204,12 +203,20 @@ __global__ void __launch_bounds__(64) k_trsm_panel(T* __restrict__ G, int64_t ld
         X[i][j] = (gr < r1 && j < bs) ? G[(size_t)gr * ld + j0 + j] : T(0);
     }
     __syncthreads();
-    // thread t solves row t: x_c = (a_c - sum_{l<c} x_l L[c][l]) / L[c][c]
-    for (int c = 0; c < bs; ++c) {
-        T s = X[t][c];
-        for (int l = 0; l < c; ++l) s -= X[t][l] * L[c][l];
-        X[t][c] = s / L[c][c];
+    // thread t solves row t: x_c = (a_c - sum_{l<c} x_l L[c][l]) / L[c][c], with the row
+    // held in registers (fully unrolled; columns at or beyond bs are never stored)
+    T x[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) x[c] = X[t][c];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+        T s = x[c];
+#pragma unroll
+        for (int l = 0; l < c; ++l) s -= x[l] * L[c][l];
+        x[c] = c < bs ? s / L[c][c] : T(0);
     }
+#pragma unroll
+    for (int c = 0; c < NB; ++c) X[t][c] = x[c];
     __syncthreads();
     for (int e = t; e < NB * NB; e += blockDim.x) {
         int i = e / NB, j = e % NB;
@@ -234,14 +241,19 @@ __global__ void __launch_bounds__(64) k_trinv_diag(const T* __restrict__ G, int6
         X[i][j] = T(0);
     }
     __syncthreads();
-    // thread t computes column t of the inverse by forward substitution
+    // thread t computes column t of the inverse by forward substitution, the column
+    // in registers (fully unrolled; entries above the diagonal are zero)
     if (t < bs) {
-        X[t][t] = T(1) / L[t][t];
-        for (int i = t + 1; i < bs; ++i) {
+        T x[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
             T s = T(0);
-            for (int l = t; l < i; ++l) s += L[i][l] * X[l][t];
-            X[i][t] = -s / L[i][i];
+#pragma unroll
+            for (int l = 0; l < i; ++l) s += L[i][l] * x[l];
+            x[i] = i < t || i >= bs ? T(0) : (i == t ? T(1) / L[i][i] : -s / L[i][i]);
         }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) X[i][t] = x[i];
     }
     __syncthreads();
     for (int e = t; e < NB * NB; e += blockDim.x) D[e] = X[e / NB][e % NB];
@@ -267,9 +279,15 @@ __global__ void __launch_bounds__(64) k_trmm_diag(T* __restrict__ X, int64_t ld,
     // thread t owns column t of the slab (S is a private copy, so writing X is safe)
     const int64_t gc = c0 + t;
     if (gc >= ncols) return;
-    for (int i = 0; i < bs; ++i) {
+    T col[NB];
+#pragma unroll
+    for (int l = 0; l < NB; ++l) col[l] = S[l][t];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        if (i >= bs) break;
         T s = T(0);
-        for (int l = 0; l <= i; ++l) s += Dm[i][l] * S[l][t];
+#pragma unroll
+        for (int l = 0; l <= i; ++l) s += Dm[i][l] * col[l];
         X[(size_t)(j0 + i) * ld + gc] = s;
     }
 }
@@ -875,7 +893,7 @@ cudaError_t cholesky(sw_ctx* ctx, T* G, int64_t K, int* d_info)
         {
             LaunchTimer lt(ctx, K_POTRF_DIAG);
             add_work(ctx, K_POTRF_DIAG, (double)bs * bs * bs / 3.0);
-            k_potrf_diag<T><<<1, 256, smem2<T>() / 2, st>>>(G, K, j0, bs, d_info);
+            k_potrf_diag<T><<<1, NB, smem2<T>() / 2, st>>>(G, K, j0, bs, d_info);
         }
         int64_t r0 = j0 + bs, r1 = K;
         if (r1 > r0) {
@@ -929,6 +947,16 @@ cudaError_t tri_inverse(sw_ctx* ctx, const T* G, T* X, T* D, int64_t K)
         }
     }
     return cudaGetLastError();
+}
+
+// Cholesky factor L of G (in place, lower) and X = L^{-1}: the factorisation, then the
+// inverse by block rows, on the context stream.
+template <typename T>
+cudaError_t cholesky_inverse(sw_ctx* ctx, T* G, T* X, T* D, int64_t K, int* d_info)
+{
+    cudaError_t e = cholesky<T>(ctx, G, K, d_info);
+    if (e) return e;
+    return tri_inverse<T>(ctx, G, X, D, K);
 }
 
 template <typename T>
@@ -1204,6 +1232,8 @@ template cudaError_t cholesky<float>(sw_ctx*, float*, int64_t, int*);
 template cudaError_t cholesky<double>(sw_ctx*, double*, int64_t, int*);
 template cudaError_t tri_inverse<float>(sw_ctx*, const float*, float*, float*, int64_t);
 template cudaError_t tri_inverse<double>(sw_ctx*, const double*, double*, double*, int64_t);
+template cudaError_t cholesky_inverse<float>(sw_ctx*, float*, float*, float*, int64_t, int*);
+template cudaError_t cholesky_inverse<double>(sw_ctx*, double*, double*, double*, int64_t, int*);
 template cudaError_t shift_and_trace<float>(sw_ctx*, float*, int64_t, double*, double);
 template cudaError_t shift_and_trace<double>(sw_ctx*, double*, int64_t, double*, double);
 template cudaError_t rowdot<__nv_bfloat16, float, float, float>(sw_ctx*, int, const __nv_bfloat16*, int64_t, int64_t,

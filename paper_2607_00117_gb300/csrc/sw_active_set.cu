@@ -269,7 +269,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
                         "reduced Gram");
             }
             AS_CUDA(ctx, shift_diag_vec<GT>(ctx, G, nP, V.ridge), "ridge");
-            AS_CUDA(ctx, cholesky<GT>(ctx, G, nP, info), "reduced Cholesky");
+            AS_CUDA(ctx, cholesky_inverse<GT>(ctx, G, (GT*)ws.X, (GT*)ws.D, nP, info), "reduced Cholesky");
             AS_CUDA(ctx, cudaMemcpyAsync(&infoh, info, sizeof(int), cudaMemcpyDeviceToHost, st), "info");
             AS_CUDA(ctx, cudaMemcpyAsync(&gerrh, gerr, sizeof(int), cudaMemcpyDeviceToHost, st), "flags");
             AS_CUDA(ctx, cudaStreamSynchronize(st), "reduced factor");
@@ -277,7 +277,6 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         }
         ++n_factor;
         if (infoh != 0) return SW_OK;   // ok = false
-        AS_CUDA(ctx, tri_inverse<GT>(ctx, G, (GT*)ws.X, (GT*)ws.D, nP), "reduced inverse");
         ok = true;
         return SW_OK;
     };

@@ -21,6 +21,9 @@ template <typename T>
 cudaError_t cholesky(sw_ctx* ctx, T* G, int64_t K, int* d_info);
 template <typename T>
 cudaError_t tri_inverse(sw_ctx* ctx, const T* G, T* X, T* D, int64_t K);
+// Cholesky (in place) and the explicit inverse X = L^{-1}, the inverse overlapped on a second stream
+template <typename T>
+cudaError_t cholesky_inverse(sw_ctx* ctx, T* G, T* X, T* D, int64_t K, int* d_info);
 template <typename T>
 cudaError_t symmetrize(sw_ctx* ctx, const T* G, int64_t K, T* S);
 template <typename T>

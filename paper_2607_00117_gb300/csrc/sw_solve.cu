@@ -206,8 +206,7 @@ sw_status solve_impl(sw_ctx* ctx, const Problem& pb, const double* y_dev, const 
         Gs = (GT*)ws.Gs;
         CUDA_TRY(ctx, symmetrize<GT>(ctx, G, K, Gs), "symmetrize");
     }
-    CUDA_TRY(ctx, cholesky<GT>(ctx, G, K, V.info), "Cholesky");
-    CUDA_TRY(ctx, tri_inverse<GT>(ctx, G, X, D, K), "triangular inverse");
+    CUDA_TRY(ctx, cholesky_inverse<GT>(ctx, G, X, D, K, V.info), "Cholesky and inverse");
     int info = 0;
     CUDA_TRY(ctx, cudaMemcpyAsync(&info, V.info, sizeof(int), cudaMemcpyDeviceToHost, st), "info");
     CUDA_TRY(ctx, cudaStreamSynchronize(st), "factorisation");
@@ -391,8 +390,7 @@ sw_status solve_impl(sw_ctx* ctx, const Problem& pb, const double* y_dev, const 
                 CUDA_TRY(ctx, cudaStreamSynchronize(st), "trace");
                 const double ridge = std::max(two_lam_n, 1e-11 * trH / (double)nP);
                 CUDA_TRY(ctx, shift_and_trace<double>(ctx, Hm, nP, nullptr, ridge), "shift");
-                CUDA_TRY(ctx, cholesky<double>(ctx, Hm, nP, V.info), "reduced Cholesky");
-                CUDA_TRY(ctx, tri_inverse<double>(ctx, Hm, Hi, Dd, nP), "reduced inverse");
+                CUDA_TRY(ctx, cholesky_inverse<double>(ctx, Hm, Hi, Dd, nP, V.info), "reduced Cholesky");
                 CUDA_TRY(ctx, gather_vec(ctx, V.q, didx, nP, qP), "q_P");
                 CUDA_TRY(ctx, (rowdot<double, double, double, double>(ctx, K_TRMV_L, Hi, nP, nP, nP, qP, tP, 1.0, 0.0,
                                                                       true)), "solve");

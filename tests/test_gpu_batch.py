@@ -54,7 +54,14 @@ def test_batch_matches_single_model_path(sw, prec, gh):
         c1.set_potential(m["potential"])
         c1.integrate_library(ics[k], m["omega_p"], dt, S)
         U = c1.project(dict(grid, incl=m["incl"], bar_angle=m["bar_angle"]), gh_v0s=v0s[k] if gh else None)
-        np.testing.assert_array_equal(first[k], U.copy())
+        Us = U.copy()
+        nc = U.blocks[0] + U.blocks[1]              # count rows (density, pixel mass): exact
+        np.testing.assert_array_equal(first[k][:, :nc], Us[:, :nc])
+        if gh:   # GH sums: the two kernels may contract the FP32 GH arithmetic differently
+            np.testing.assert_allclose(first[k][:, nc:], Us[:, nc:], rtol=0,
+                                       atol=(1e-6 if prec == "fp32" else 1e-14) * np.abs(Us).max())
+        else:
+            np.testing.assert_array_equal(first[k], Us)
         d1, s1 = c1.project_stats(counts[k])
         np.testing.assert_array_equal(status_b[off[k]:off[k + 1]], s1)
         np.testing.assert_allclose(drift_b[off[k]:off[k + 1]], d1, rtol=0, atol=0)
