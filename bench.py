@@ -53,7 +53,9 @@ def parse():
     ap.add_argument("--impl", default="sw", choices=["sw", "reference"])
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched_64"],
+    ap.add_argument("--n-orb", type=int, default=0, help="override the orbit count (small cases for ncu captures)")
+    ap.add_argument("--nsteps", type=int, default=0, help="override the step count (small cases for ncu captures)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched_64", "surrogate"],
                     help="batched_64: 64 trial potentials built in one persistent launch, then solved")
     return ap.parse_args()
 
@@ -181,7 +183,10 @@ def make_data(sw, torch, W, rank):
 # ---------------------------------------------------------------------------
 # algorithmic work per unit for the roofline of the dominant kernel
 # ---------------------------------------------------------------------------
-OPS_PER_ORBIT_STEP = 360.0   # FP32-pipe instructions per orbit-step of the fused orbit kernel
+# lane-instructions executed per orbit-step by the fused orbit kernel (FP32 form, barred potential,
+# histogram rows, four mirror copies): smsp__inst_executed x threads per instruction / orbit-steps from
+# the ncu capture in profiles/orbit_kernel_fp32_barred.md
+OPS_PER_ORBIT_STEP = 891.0
 
 
 def roofline_entry(name, stats, hbm, bf16, sm_mhz):
@@ -207,6 +212,45 @@ def roofline_entry(name, stats, hbm, bf16, sm_mhz):
         a = OPS_PER_ORBIT_STEP * work / t / 1e12
         return {"bound": "alu", "achieved": a, "peak": peak, "unit": "T lane-instructions/s", "frac": a / peak}
     return {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None}
+
+
+def matched_leg(sw, torch, reps=3):
+    """FP32 (Kahan, tensor-core Gram) against plain FP64 on the small axisymmetric
+    workload (2 000 orbits x 2 000 steps, 7 300 rows): models/s of each form and the
+    relative difference of their chi^2 on the same initial conditions and data."""
+    W = inputs.WORKLOADS["axisym_2k"]
+    ics = inputs.disc_ics(W["potential"], W["n_orb"], seed=W["seeds"]["ic"])
+    out = {"workload": "axisym_2k"}
+    data = None
+    for prec in ("fp64", "fp32"):
+        c = sw.Context(0, prec)
+        c.set_potential(W["potential"])
+
+        def model():
+            c.integrate_library(ics, W["omega_p"], W["dt"], W["nsteps"])
+            U = c.project(W["grid"])
+            return U
+        U = model()
+        if data is None:                      # data from the FP64 library (the plain form)
+            y0 = U.apply(inputs.true_weights(U.N, W["seeds"]["w"]))
+            sig = inputs.mock_sigma(y0, inputs.row_blocks(W["grid"]))
+            data = (y0 + sig * inputs.noise(len(y0), W["seeds"]["noise"]), sig)
+        _, chi = c.solve_weights(U, data[0], data[1], W["lam"], allow_nonconv=True)
+        U.free()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            U = model()
+            _, chi = c.solve_weights(U, data[0], data[1], W["lam"], allow_nonconv=True)
+            U.free()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        out[prec] = {"models_per_s": 1.0 / dt, "orbit_steps_per_s": W["n_orb"] * W["nsteps"] / dt,
+                     "chi2": float(chi[0])}
+        c.close()
+    out["chi2_rel_diff"] = abs(out["fp32"]["chi2"] - out["fp64"]["chi2"]) / out["fp64"]["chi2"]
+    out["fp32_over_fp64_models_per_s"] = out["fp32"]["models_per_s"] / out["fp64"]["models_per_s"]
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -264,7 +308,11 @@ def run_sw(args):
     from paper_2607_00117_gb300 import sw
     sw.lib()
 
-    W = inputs.WORKLOADS[WORKLOAD]
+    W = dict(inputs.WORKLOADS[WORKLOAD])
+    if args.n_orb:
+        W["n_orb"] = args.n_orb - args.n_orb % W.get("bundle", 1)
+    if args.nsteps:
+        W["nsteps"] = args.nsteps
     grid, N, S = W["grid"], W["n_orb"], W["nsteps"]
     hbm, bf16, bf16_sus, sm_max, peak_src = peaks()
 
@@ -314,10 +362,12 @@ def run_sw(args):
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed_region")
     ev0.record(stream)
     for _ in range(args.steps):
         step()
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     clk = clocks.stop()
@@ -381,6 +431,8 @@ def run_sw(args):
                     for kk, v in roofline_entry(k, kstats, hbm, bf16_sus, sm_mhz).items()} for k in top}
     breakdown = {k: round(v["ms"] / args.steps, 3) for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])}
 
+    matched = matched_leg(sw, torch) if not args.no_e2e else None
+
     cpu = None
     if not args.no_cpu:
         v, cores, sample, _ = cpu_sample(W)
@@ -398,6 +450,7 @@ def run_sw(args):
             "models_per_s": args.steps * world / elapsed,
             "chi2": {"total": float(chi2[0]), "obs": float(chi2[1]), "reg": float(chi2[2]),
                      "solver": info, "status": statuses[-args.steps:]},
+            "matched_chi2_fp32_vs_fp64": matched,
             "roofline": roof, "roofline_top_kernels": roof_top, "kernel_ms_per_step": breakdown, "gpu_launches": int(launches),
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
@@ -432,7 +485,6 @@ def run_batched(args):
     b = sw.Batch(ctx, counts, S, grid)
     b.set_models([m["potential"] for m in models], [m["omega_p"] for m in models],
                  [[m["incl"], 0.0, m["bar_angle"]] for m in models], dt, ics, v0s)
-    blocks = None
     data = []
 
     def step(make_data=False):
@@ -498,11 +550,99 @@ def run_batched(args):
     b.close()
 
 
+def run_surrogate(args):
+    """The learned chi^2 emulator at reduced fidelity (the survey's fallback for the
+    20k-model training set): 12-D box models of 2 000 orbits x 1 000 steps on a
+    16 x 12 pixel GH grid, their exact chi^2_obs computed in batches of 64 models
+    (one persistent launch each), the emulator trained by the library's kernels,
+    its held-out error, and delayed-acceptance MCMC against plain Metropolis on the
+    exact model (exact models per step, accepted models per second)."""
+    import torch
+    from paper_2607_00117_gb300 import sw, surrogate
+    sw.lib()
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    grid = dict(inputs.WORKLOADS["batched_64"]["grid"], nx=16, ny=12, nR=6, nphi=8, nz=4, gh=1)
+    n_orb, S, dt = 2000, 1000, 2 * inputs.DT_HALF_MYR
+    c = sw.Context(local, "fp32")
+    truth = surrogate.box_point(np.full(12, 0.5))[0]
+    mt = inputs.box_model(truth)
+    ics = inputs.disc_ics(mt["potential"], n_orb, seed=4001)
+    # data: the true model's own library with weights U(0, 2) and noise
+    npix = grid["nx"] * grid["ny"]
+    v0s = np.tile(np.array([0.0, 150.0]), (npix, 1))
+    c.set_potential(mt["potential"])
+    c.integrate_library(ics, mt["omega_p"], dt, S)
+    Ud = c.project(dict(grid, incl=mt["incl"], bar_angle=mt["bar_angle"]), gh_v0s=v0s)
+    y0 = Ud.apply(inputs.true_weights(n_orb, 4999))
+    bl = {"dens": (0, Ud.blocks[0]), "pix": (Ud.blocks[0], Ud.blocks[0] + Ud.blocks[1]),
+          "kin": (Ud.blocks[0] + Ud.blocks[1], Ud.M)}
+    sig = inputs.mock_sigma(y0, bl, gh_err=np.tile([0.02, 0.02, 0.03, 0.03], (npix, 1)))
+    y = y0 + sig * inputs.noise(len(y0), 4998)
+    Ud.free()
+    exact = surrogate.ModelChi2(c, grid, ics, S, dt, y, sig, v0s)
+    # training set: batches of 64 box points built in one persistent launch each
+    rng = np.random.default_rng(4002)
+    n_train, K = 512, 64
+    u_all = np.clip(0.5 + 0.2 * rng.standard_normal((n_train + 128, 12)), 0, 1)
+    chi = np.empty(len(u_all))
+    t0 = time.perf_counter()
+    b = sw.Batch(c, np.full(K, n_orb), S, grid)
+    for s0 in range(0, len(u_all), K):
+        th = surrogate.box_point(u_all[s0:s0 + K])
+        ms = [inputs.box_model(t) for t in th]
+        b.set_models([m["potential"] for m in ms], [m["omega_p"] for m in ms],
+                     [[m["incl"], 0.0, m["bar_angle"]] for m in ms], dt, np.tile(ics, (K, 1)), np.tile(v0s, (K, 1, 1)))
+        b.run()
+        for k in range(K):
+            _, cc = c.solve_weights(b.matrix(k), y, sig, 1.0, allow_nonconv=True)
+            chi[s0 + k] = cc[1]
+    t_train_data = time.perf_counter() - t0
+    models_per_s_exact = len(u_all) / t_train_data
+    emu = surrogate.Emulator(c, torch, seed=4003)
+    t0 = time.perf_counter()
+    losses = emu.fit(u_all[:n_train], chi[:n_train], epochs=200, batch=128, lr=2e-3)
+    t_fit = time.perf_counter() - t0
+    pred = emu.predict(u_all[n_train:], bf16=True)
+    err = np.abs(np.log(pred) - np.log(chi[n_train:]))
+    temp = float(np.sqrt(2 * len(y)))
+    n_steps = 150
+    t0 = time.perf_counter()
+    exact.calls = 0
+    mh = surrogate.mh_chain(exact, np.full(12, 0.5), n_steps, 0.05, temp, seed=4004)
+    t_mh = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    da = surrogate.da_chain(exact, emu, np.full(12, 0.5), n_steps, 0.05, temp, seed=4004)
+    t_da = time.perf_counter() - t0
+    line = {"metric": "accepted models/s of delayed-acceptance MCMC (emulator screen, exact judge)",
+            "value": da["n_accept"] / t_da, "unit": "accepted models/s", "n_gpus": 1, "steps": n_steps,
+            "warmup": 0, "ms_per_step": 1e3 * t_da / n_steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 train / bf16 inference", "data": "synthetic",
+            "config": {"workload": "surrogate", "network": "12-256-256-256-1 SiLU", "train_models": n_train,
+                       "orbits_per_model": n_orb, "nsteps": S, "rows": int(inputs.rows_of(grid)),
+                       "fidelity": "reduced (2 000 orbits x 1 000 steps per model)"},
+            "emulator": {"heldout_median_abs_dlog_chi2": float(np.median(err)),
+                         "heldout_p90_abs_dlog_chi2": float(np.percentile(err, 90)),
+                         "final_train_loss": losses[-1], "fit_s": t_fit},
+            "exact_models_per_s_batched": models_per_s_exact,
+            "plain_mh": {"exact_models": mh["n_exact"], "accepted": mh["n_accept"],
+                         "accepted_per_s": mh["n_accept"] / t_mh},
+            "delayed_acceptance": {"exact_models": da["n_exact"], "stage1_passed": da["n_stage1"],
+                                   "accepted": da["n_accept"], "accepted_per_s": da["n_accept"] / t_da},
+            "e2e": None, "cpu_baseline": None, "roofline": None, "gpu_launches": int(c.launch_count())}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "batched_64":
         run_batched(a)
+    elif a.workload == "surrogate":
+        run_surrogate(a)
     else:
         run_sw(a)

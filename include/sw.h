@@ -239,6 +239,10 @@ int64_t sw_launch_count(const sw_ctx* ctx);
  *  "as_cg_max" (>= 0)       active set: preconditioned conjugate-gradient steps per reduced solve (default 200)
  *  "as_cg_tol" (> 0)        active set: CG stops at max|r| <= as_cg_tol * kkt_tol * max|q| (default 0.05)
  *  "as_solves" (>= 1)       active set: cap on pivoting steps (default 400)
+ *  "solver" (0/1/2)         0 (default): the active set when lambda > 0, when N <= M, or for libraries above
+ *                           orbit_direct_max orbits, ADMM otherwise; 1: always the active set; 2: always ADMM
+ *                           (the paper's solver, Sec. 2.3, with FP64 refinement and the exact polish)
+ *  "chol_coop" (0/1)        active set: Cholesky and its inverse in one cooperative launch (default 0)
  *  "as_grow" (>= 0)         active set: at most max(as_block, as_grow |F|) orbits enter per step (default 0)
  *  "as_candidates" (>= 0)   active set: initial candidate-set size, 0 for 2 M (default 0)
  *  "ws_factor" (> 0)        initial working-set size in units of M (default 0.6; it grows to take in the

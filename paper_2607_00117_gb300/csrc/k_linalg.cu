@@ -607,12 +607,27 @@ __global__ void __launch_bounds__(256) k_u_times_w_ff(const float* __restrict__ 
     const int64_t i0 = (int64_t)blockIdx.y * orbits_per_split;
     int64_t i1 = i0 + orbits_per_split;
     if (i1 > N) i1 = N;
-    FF s{0.f, 0.f};
-    for (int64_t i = i0; i < i1; ++i) {
-        const float h = wh[i];
-        if (h != 0.f) ff_add_prod(s, U[(size_t)i * M + r], h, wl[i]);
+    // four independent double-float sums keep four loads in flight per thread
+    FF s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    int64_t i = i0;
+    for (; i + 4 <= i1; i += 4) {
+        float u[4], h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h[q] = wh[i + q];
+            l[q] = wl[i + q];
+            u[q] = h[q] != 0.f ? U[(size_t)(i + q) * M + r] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ff_add_prod(s[q], u[q], h[q], l[q]);
     }
-    if (i1 > i0) atomicAdd(acc + r, (double)s.h + (double)s.l);
+    for (; i < i1; ++i) {
+        const float h = wh[i];
+        if (h != 0.f) ff_add_prod(s[0], U[(size_t)i * M + r], h, wl[i]);
+    }
+    if (i1 > i0)
+        atomicAdd(acc + r, (((double)s[0].h + (double)s[0].l) + ((double)s[1].h + (double)s[1].l)) +
+                               (((double)s[2].h + (double)s[2].l) + ((double)s[3].h + (double)s[3].l)));
 }
 
 // out[i] = sum_r U[i, r] x[r] with x split into (xh, xl); one warp per orbit
@@ -625,9 +640,22 @@ __global__ void __launch_bounds__(256) k_ut_times_x_ff(const float* __restrict__
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < N; i += nwarp) {
         const float* col = U + (size_t)i * M;
-        FF s{0.f, 0.f};
-        for (int64_t r = lane; r < M; r += 32) ff_add_prod(s, col[r], xh[r], xl[r]);
-        double d = (double)s.h + (double)s.l;
+        FF s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        int64_t r = lane;
+        for (; r + 96 < M; r += 128) {
+            float u[4], h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                u[q] = col[r + 32 * q];
+                h[q] = xh[r + 32 * q];
+                l[q] = xl[r + 32 * q];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ff_add_prod(s[q], u[q], h[q], l[q]);
+        }
+        for (; r < M; r += 32) ff_add_prod(s[0], col[r], xh[r], xl[r]);
+        double d = (((double)s[0].h + (double)s[0].l) + ((double)s[1].h + (double)s[1].l)) +
+                   (((double)s[2].h + (double)s[2].l) + ((double)s[3].h + (double)s[3].l));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
         if (lane == 0) out[i] = d;

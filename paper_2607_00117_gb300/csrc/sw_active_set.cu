@@ -269,11 +269,22 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
                         "reduced Gram");
             }
             AS_CUDA(ctx, shift_diag_vec<GT>(ctx, G, nP, V.ridge), "ridge");
-            AS_CUDA(ctx, cholesky_inverse<GT>(ctx, G, (GT*)ws.X, (GT*)ws.D, nP, info), "reduced Cholesky");
+            int* cerr = (int*)(V.scal + 12);
+            AS_CUDA(ctx, cudaMemsetAsync(cerr, 0, sizeof(int), st), "memset");
+            cudaError_t ce = ctx->opt.chol_coop ? cholesky_inverse_coop<GT>(ctx, G, (GT*)ws.X, nP, info, cerr)
+                                                : cudaErrorNotSupported;
+            if (ce == cudaErrorNotSupported) {
+                cudaGetLastError();
+                ce = cholesky_inverse<GT>(ctx, G, (GT*)ws.X, (GT*)ws.D, nP, info);
+            }
+            AS_CUDA(ctx, ce, "reduced Cholesky");
+            int cerrh = 0;
             AS_CUDA(ctx, cudaMemcpyAsync(&infoh, info, sizeof(int), cudaMemcpyDeviceToHost, st), "info");
             AS_CUDA(ctx, cudaMemcpyAsync(&gerrh, gerr, sizeof(int), cudaMemcpyDeviceToHost, st), "flags");
+            AS_CUDA(ctx, cudaMemcpyAsync(&cerrh, cerr, sizeof(int), cudaMemcpyDeviceToHost, st), "flags");
             AS_CUDA(ctx, cudaStreamSynchronize(st), "reduced factor");
             if (gerrh) { set_error(ctx, "solve: tensor-core Gram kernel timed out"); return SW_ETIMEOUT; }
+            if (cerrh) { set_error(ctx, "solve: a grid barrier of the Cholesky kernel timed out"); return SW_ETIMEOUT; }
         }
         ++n_factor;
         if (infoh != 0) return SW_OK;   // ok = false

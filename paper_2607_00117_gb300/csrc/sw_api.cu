@@ -16,7 +16,7 @@ const char* kKernelNames[K_COUNT] = {
     "ics_to_soa", "orbit_project_bin", "orbit_drift", "zero_flagged", "finalize_columns", "trajectory",
     "potential_eval", "whiten", "gram_tcgen05", "gram_simt", "shift_diag", "potrf_diag", "trsm_panel",
     "syrk_update", "trinv_diag", "trinv_update", "gemv_n", "gemv_t", "trmv_l", "trmv_lt", "admm_update",
-    "residual", "gradient", "chi2", "misc", "batch_orbit_bin", "mlp_fwd", "mlp_bwd", "adam", "reduce_gh", "pcg", "bundle"};
+    "residual", "gradient", "chi2", "misc", "batch_orbit_bin", "mlp_fwd", "mlp_bwd", "adam", "reduce_gh", "pcg", "bundle", "cholesky_inverse"};
 
 void set_error(sw_ctx* ctx, const char* fmt, ...)
 {
@@ -155,10 +155,10 @@ static void ctx_release(sw_ctx* ctx)
     cudaStreamSynchronize(ctx->stream);
     ctx->harvest();
     void* bufs[] = {ctx->d_soa, ctx->d_cs, ctx->d_aos, ctx->d_drift, ctx->d_status, ctx->d_stats, ctx->d_ghtab,
-                    ctx->d_mlp, ctx->d_split};
+                    ctx->d_mlp, ctx->d_split, ctx->d_chol};
     for (void* b : bufs)
         if (b) cudaFree(b);
-    ctx->d_soa = ctx->d_cs = ctx->d_ghtab = ctx->d_mlp = ctx->d_split = nullptr;
+    ctx->d_soa = ctx->d_cs = ctx->d_ghtab = ctx->d_mlp = ctx->d_split = ctx->d_chol = nullptr;
     ctx->d_aos = ctx->d_drift = nullptr;
     ctx->d_status = nullptr;
     ctx->d_stats = nullptr;
@@ -830,7 +830,8 @@ const int kKernelWorkKind[K_COUNT] = {
     W_FLOP_SIMT /*syrk_update*/, W_FLOP_SIMT /*trinv_diag*/, W_FLOP_SIMT /*trinv_update*/, W_BYTES /*gemv_n*/,
     W_BYTES /*gemv_t*/, W_BYTES /*trmv_l*/, W_BYTES /*trmv_lt*/, W_NONE /*admm_update*/, W_BYTES /*residual*/,
     W_BYTES /*gradient*/, W_NONE /*chi2*/, W_NONE /*misc*/, W_ORBIT_STEPS /*batch_orbit*/, W_FLOP_SIMT /*mlp_fwd*/,
-    W_FLOP_SIMT /*mlp_bwd*/, W_NONE /*adam*/, W_BYTES /*reduce_gh*/, W_NONE /*pcg*/, W_BYTES /*bundle*/};
+    W_FLOP_SIMT /*mlp_bwd*/, W_NONE /*adam*/, W_BYTES /*reduce_gh*/, W_NONE /*pcg*/, W_BYTES /*bundle*/,
+    W_FLOP_SIMT /*cholesky_inverse*/};
 
 void add_work(sw_ctx* ctx, int kid, double units)
 {
@@ -905,6 +906,12 @@ extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value)
     } else if (!strcmp(key, "as_candidates")) {
         if (!(value >= 0.0)) return SW_EINVAL;
         ctx->opt.as_candidates = value;
+    } else if (!strcmp(key, "solver")) {
+        if (!(value == 0 || value == 1 || value == 2)) return SW_EINVAL;
+        ctx->opt.solver = (int)value;
+    } else if (!strcmp(key, "chol_coop")) {
+        if (!(value == 0 || value == 1)) return SW_EINVAL;
+        ctx->opt.chol_coop = (int)value;
     } else if (!strcmp(key, "as_grow")) {
         if (!(value >= 0.0)) return SW_EINVAL;
         ctx->opt.as_grow = value;

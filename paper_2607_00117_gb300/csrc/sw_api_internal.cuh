@@ -32,6 +32,8 @@ struct Options {
     int as_block = 2048;         // active set: violators entering per pivoting step
     double as_candidates = 0;    // active set: initial candidate-set size (0: 2 M)
     double as_grow = 0.0;        // active set: at most max(as_block, as_grow |F|) orbits enter per step
+    int solver = 0;              // 0 auto, 1 active set, 2 ADMM (see solve_dispatch)
+    int chol_coop = 0;           // Cholesky + inverse in one cooperative launch (0: per-step launches)
     int as_cg_max = 200;         // active set: conjugate-gradient steps per reduced solve
     double as_cg_tol = 0.05;     // active set: CG stops at max|r| <= as_cg_tol * kkt_tol * max|q|
     int as_solves = 400;         // active set: cap on reduced solves
@@ -92,6 +94,7 @@ struct sw_ctx {
     int64_t last_proj_n = 0;
     void* d_mlp = nullptr; size_t mlp_cap = 0;   // MLP activations
     void* d_split = nullptr; size_t split_cap = 0;   // FP64 vectors split into float hi + lo
+    void* d_chol = nullptr; size_t chol_cap = 0;     // cooperative Cholesky: diagonal inverses, barrier
     // solve
     sw::SolveWS solve_ws;
     double solve_info[8] = {0, 0, 0, 0, 0, 0, 0, 0};

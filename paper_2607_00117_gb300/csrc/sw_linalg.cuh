@@ -21,7 +21,11 @@ template <typename T>
 cudaError_t cholesky(sw_ctx* ctx, T* G, int64_t K, int* d_info);
 template <typename T>
 cudaError_t tri_inverse(sw_ctx* ctx, const T* G, T* X, T* D, int64_t K);
-// Cholesky (in place) and the explicit inverse X = L^{-1}, the inverse overlapped on a second stream
+// Cholesky (in place) and the explicit inverse X = L^{-1} in one cooperative launch (k_chol.cu);
+// cudaErrorNotSupported when the device cannot launch it; *d_err != 0 if a barrier wait ran out
+template <typename T>
+cudaError_t cholesky_inverse_coop(sw_ctx* ctx, T* G, T* X, int64_t K, int* d_info, int* d_err);
+// Cholesky (in place) and the explicit inverse X = L^{-1} by per-step launches
 template <typename T>
 cudaError_t cholesky_inverse(sw_ctx* ctx, T* G, T* X, T* D, int64_t K, int* d_info);
 template <typename T>

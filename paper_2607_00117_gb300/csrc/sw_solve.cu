@@ -670,7 +670,12 @@ static sw_status solve_dispatch(sw_ctx* ctx, const sw_matrix* U, const double* y
     const bool direct = many && ctx->opt.working_set && U->N <= ctx->opt.orbit_direct_max;
     const bool ws = many && ctx->opt.working_set && !direct;
     const Problem pb{U->d, U->M, U->N, U->nd, (double)U->N, direct};
-    if (ws && ctx->opt.large_solver == 0) {
+    // solver: 1 active set, 2 ADMM (the paper's, with refinement and polish), 0 (auto) the active
+    // set whenever its reduced systems stay definite (lambda > 0, or no more orbits than rows) and for
+    // large libraries, ADMM otherwise
+    const bool active = ctx->opt.solver == 1 ||
+                        (ctx->opt.solver == 0 && (lam > 0.0 || !many || (ws && ctx->opt.large_solver == 0)));
+    if (active) {
         if (U->elem == 8) return solve_active_set<double, double, double>(ctx, U, y_dev, sig_dev, lam, w_dev, chi2_dev);
         if (ctx->opt.gram_tc && gram_tc_available())
             return solve_active_set<float, __nv_bfloat16, float>(ctx, U, y_dev, sig_dev, lam, w_dev, chi2_dev);

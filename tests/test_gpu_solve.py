@@ -51,11 +51,14 @@ def _build(sw, prec, pot, omega, ics, S, grid, gh_v0s=None):
     return c, U
 
 
+@pytest.mark.parametrize("solver", [0, 2])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("lam", [1.0, 0.0])
-def test_solve_orbit_space(sw, orc, prec, lam):
+def test_solve_orbit_space(sw, orc, prec, lam, solver):
+    """solver 0: the default choice (active set here); 2: the paper's ADMM with refinement and polish."""
     ics = inputs.disc_ics(W1["potential"], 500, seed=201)
     c, U = _build(sw, prec, W1["potential"], 0.0, ics, 1000, W1["grid"])
+    c.set_option("solver", solver)
     Ug = U.copy().T.copy()                       # (M, N)
     blocks = inputs.row_blocks(W1["grid"])
     y, sig = _mock(orc, Ug, blocks)
@@ -68,10 +71,12 @@ def test_solve_orbit_space(sw, orc, prec, lam):
     np.testing.assert_allclose(chi2[2], chi2_o[2], rtol=1e-3, atol=1e-9 * max(1.0, chi2_o[0]))
 
 
+@pytest.mark.parametrize("solver", [0, 2])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("lam", [1.0, 0.0])
-def test_solve_constraint_space_gh(sw, orc, prec, lam):
-    """M < N: the Woodbury form on the constraint-space Gram; GH rows."""
+def test_solve_constraint_space_gh(sw, orc, prec, lam, solver):
+    """M < N with GH rows: the default choice (active set for lambda > 0, ADMM for lambda = 0) and
+    the paper's ADMM throughout."""
     grid = dict(W1["grid"], nx=6, ny=6, nR=5, nphi=4, nz=3, gh=1, incl=0.9)
     npix = 36
     ics = inputs.disc_ics(BARRED, 700, seed=202)
@@ -79,6 +84,7 @@ def test_solve_constraint_space_gh(sw, orc, prec, lam):
     mom = orc.pixel_moments(po, 40.0, inputs.DT_HALF_MYR, 500, ics, orc.make_obs(grid), np.ones(len(ics)))
     v0s, gh_err = inputs.gh_reference(mom)
     c, U = _build(sw, prec, BARRED, 40.0, ics, 500, grid, gh_v0s=v0s)
+    c.set_option("solver", solver)
     assert U.M == 60 + 36 + 144 and U.N == 700
     Ug = U.copy().T.copy()
     blocks = inputs.row_blocks(grid)
@@ -145,6 +151,28 @@ def test_solve_active_set_path(sw, orc, prec):
     np.testing.assert_allclose(chi2[:2], chi2_o[:2], rtol=1e-4)
     k = orc.kkt_residual(H, q, w)
     assert k["pg_inf"] <= 1e-6 * np.abs(q).max(), k
+
+
+def test_cooperative_factorisation_matches_per_step_launches(sw, orc):
+    """The one-launch Cholesky + inverse (cooperative grid) and the per-step
+    launches give the same active-set solution."""
+    grid = dict(W1["grid"], nx=8, ny=8, nR=5, nphi=4, nz=3, gh=1, incl=0.9)
+    ics = inputs.disc_ics(BARRED, 1500, seed=205)
+    po = orc.make_pot(BARRED)
+    mom = orc.pixel_moments(po, 40.0, inputs.DT_HALF_MYR, 300, ics, orc.make_obs(grid), np.ones(len(ics)))
+    v0s, gh_err = inputs.gh_reference(mom)
+    out = []
+    for coop in (0, 1):
+        c, U = _build(sw, "fp32", BARRED, 40.0, ics, 300, grid, gh_v0s=v0s)
+        c.set_option("orbit_direct_max", 0)
+        c.set_option("chol_coop", coop)
+        Ug = U.copy().T.copy()
+        y, sig = _mock(orc, Ug, inputs.row_blocks(grid), gh_err=gh_err)
+        w, chi2 = c.solve_weights(U, y, sig, 1.0)
+        assert c.solve_info()["kkt_met"]
+        out.append((w, chi2))
+    np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-7)
+    np.testing.assert_allclose(out[0][0], out[1][0], rtol=1e-4, atol=1e-6 * out[0][0].max())
 
 
 def test_solve_working_set_path(sw, orc):
