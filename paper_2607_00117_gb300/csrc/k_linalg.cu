@@ -148,18 +148,18 @@ __global__ void __launch_bounds__(256) k_gemm(int64_t m, int64_t n, int64_t k, T
 // ---------------------------------------------------------------------------
 constexpr int NB = 64;
 
-// In-place Cholesky of the bs x bs diagonal block at (j0, j0): thread t owns row t
-// (two warps; the row updates of a column step need no index arithmetic and every
-// thread computes the pivot itself, so a column costs two barriers).  A pivot that
+// In-place Cholesky of the bs x bs diagonal block at (j0, j0).  256 threads: four per
+// row, each row's update split over the four by column (no index division), and every
+// thread computes the pivot itself, so a column step costs two barriers.  A pivot that
 // is not positive records its global index + 1 in *info and is replaced by a tiny
 // positive value so the factorisation can finish.
 template <typename T>
-__global__ void __launch_bounds__(NB) k_potrf_diag(T* __restrict__ G, int64_t ld, int64_t j0, int bs, int* info)
+__global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t ld, int64_t j0, int bs, int* info)
 {
     extern __shared__ unsigned char smraw[];
     T (*a)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);
-    const int t = threadIdx.x;
-    for (int e = t; e < NB * NB; e += NB) {
+    const int t = threadIdx.x, row = t & (NB - 1), q = t >> 6;
+    for (int e = t; e < NB * NB; e += 256) {
         int i = e / NB, j = e % NB;
         a[i][j] = (i < bs && j <= i) ? G[(size_t)(j0 + i) * ld + j0 + j] : T(0);
     }
@@ -167,23 +167,97 @@ __global__ void __launch_bounds__(NB) k_potrf_diag(T* __restrict__ G, int64_t ld
     for (int j = 0; j < bs; ++j) {
         T d = a[j][j];
         if (!(d > T(0))) {
-            if (t == j && info) atomicCAS(info, 0, (int)(j0 + j + 1));
+            if (t == 0 && info) atomicCAS(info, 0, (int)(j0 + j + 1));
             d = T(1e-30);
         }
         d = sqrt(d);
-        if (t > j && t < bs) a[t][j] /= d;
+        if (q == 0 && row > j && row < bs) a[row][j] /= d;
         __syncthreads();
-        if (t == j) a[j][j] = d;
-        if (t > j && t < bs) {
-            const T aij = a[t][j];
-            for (int l = j + 1; l <= t; ++l) a[t][l] -= aij * a[l][j];
+        if (row > j && row < bs) {
+            const T aij = a[row][j];
+            for (int l = j + 1 + q; l <= row; l += 4) a[row][l] -= aij * a[l][j];
         }
+        if (t == 0) a[j][j] = d;
         __syncthreads();
     }
-    for (int e = t; e < NB * NB; e += NB) {
+    for (int e = t; e < NB * NB; e += 256) {
         int i = e / NB, j = e % NB;
         if (i < bs && j <= i) G[(size_t)(j0 + i) * ld + j0 + j] = a[i][j];
     }
+}
+
+// The diagonal block's factor and its inverse in one CTA of 64 threads, rows and columns
+// held in registers (every loop fully unrolled, so register indices are static):
+//   Cholesky: thread i owns row i; at step j the pivot owner takes the square root, every
+//   row scales its column-j entry and publishes it, and each row applies the rank-1
+//   update to its own entries -- independent FMAs, two barriers per step;
+//   inverse:  thread t owns column t of D = L_kk^{-1} and substitutes down the rows of L,
+//   read by broadcast from shared memory.
+// L_kk goes back to G, D (NB x NB row-major, zero outside bs) to D.  A pivot that is not
+// positive records its global index + 1 in *info and is replaced by a tiny positive value.
+template <typename T>
+__global__ void __launch_bounds__(NB) k_diag_factor_inv(T* __restrict__ G, int64_t ld, int64_t j0, int bs,
+                                                        T* __restrict__ D, int* info)
+{
+    extern __shared__ unsigned char smraw[];
+    T (*Ls)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);
+    __shared__ T col[NB];
+    __shared__ T piv;
+    const int i = threadIdx.x;
+    T r[NB];
+#pragma unroll
+    for (int l = 0; l < NB; ++l) r[l] = (i < bs && l <= i) ? G[(size_t)(j0 + i) * ld + j0 + l] : T(0);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j < bs) {
+            if (i == j) {
+                T d = r[j];
+                if (!(d > T(0))) {
+                    if (info) atomicCAS(info, 0, (int)(j0 + j + 1));
+                    d = T(1e-30);
+                }
+                d = sqrt(d);
+                r[j] = d;
+                piv = d;
+            }
+            __syncthreads();
+            if (i > j) r[j] = r[j] / piv;
+            col[i] = r[j];
+            __syncthreads();
+            if (i > j) {
+                const T aij = r[j];
+#pragma unroll
+                for (int l = j + 1; l < NB; ++l)
+                    if (l <= i) r[l] -= aij * col[l];
+            }
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < NB; ++l) {
+        Ls[i][l] = r[l];
+        if (i < bs && l <= i) G[(size_t)(j0 + i) * ld + j0 + l] = r[l];
+    }
+    __syncthreads();
+    // column t = i of the inverse
+    T x[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        T v = T(0);
+        if (k < bs && k >= i) {
+            if (k == i) {
+                v = T(1) / Ls[k][k];
+            } else {
+                T s = T(0);
+#pragma unroll
+                for (int l = 0; l < k; ++l)
+                    if (l >= i) s += Ls[k][l] * x[l];
+                v = -s / Ls[k][k];
+            }
+        }
+        x[k] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k) D[k * NB + i] = x[k];
 }
 
 // Rows below the diagonal block: A[i, j0:j0+bs] <- A[i, j0:j0+bs] L_kk^{-T}.
@@ -921,7 +995,7 @@ cudaError_t cholesky(sw_ctx* ctx, T* G, int64_t K, int* d_info)
         {
             LaunchTimer lt(ctx, K_POTRF_DIAG);
             add_work(ctx, K_POTRF_DIAG, (double)bs * bs * bs / 3.0);
-            k_potrf_diag<T><<<1, NB, smem2<T>() / 2, st>>>(G, K, j0, bs, d_info);
+            k_potrf_diag<T><<<1, 256, smem2<T>() / 2, st>>>(G, K, j0, bs, d_info);
         }
         int64_t r0 = j0 + bs, r1 = K;
         if (r1 > r0) {
@@ -977,14 +1051,73 @@ cudaError_t tri_inverse(sw_ctx* ctx, const T* G, T* X, T* D, int64_t K)
     return cudaGetLastError();
 }
 
-// Cholesky factor L of G (in place, lower) and X = L^{-1}: the factorisation, then the
-// inverse by block rows, on the context stream.
+// Cholesky factor L of G (in place, lower) and X = L^{-1}.  Per 64-wide step: one CTA
+// factors the diagonal block and inverts it (D_k = L_kk^{-1}); the panel below becomes
+// P = A D_k^T, a plain GEMM over all rows instead of a row-by-row substitution; then the
+// trailing update.  The inverse X is then built by block rows from the kept D_k.
 template <typename T>
 cudaError_t cholesky_inverse(sw_ctx* ctx, T* G, T* X, T* D, int64_t K, int* d_info)
 {
-    cudaError_t e = cholesky<T>(ctx, G, K, d_info);
-    if (e) return e;
-    return tri_inverse<T>(ctx, G, X, D, K);
+    (void)D;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_diag_factor_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<T>());
+        cudaFuncSetAttribute(k_trmm_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<T>());
+        attr_set = true;
+    }
+    if (K <= 0) return cudaSuccess;
+    cudaStream_t st = ctx_stream(ctx);
+    const int64_t nb = (K + NB - 1) / NB;
+    const size_t dbytes = (size_t)nb * NB * NB * sizeof(T), pbytes = (size_t)K * NB * sizeof(T);
+    if (ctx->ensure(&ctx->d_chol, &ctx->chol_cap, dbytes + pbytes + 256, "factor scratch") != SW_OK)
+        return cudaErrorMemoryAllocation;
+    T* Dall = (T*)ctx->d_chol;
+    T* P = (T*)((char*)ctx->d_chol + ((dbytes + 255) & ~(size_t)255));
+    cudaError_t e;
+    for (int64_t jb = 0; jb < nb; ++jb) {
+        const int64_t j0 = jb * NB;
+        const int bs = (int)(K - j0 < NB ? K - j0 : NB);
+        T* Dk = Dall + (size_t)jb * NB * NB;
+        {
+            LaunchTimer lt(ctx, K_POTRF_DIAG);
+            add_work(ctx, K_POTRF_DIAG, 2.0 * (double)bs * bs * bs / 3.0);
+            k_diag_factor_inv<T><<<1, NB, smem2<T>() / 2, st>>>(G, K, j0, bs, Dk, d_info);
+        }
+        if ((e = cudaGetLastError())) return e;
+        const int64_t r0 = j0 + bs;
+        if (r0 < K) {
+            e = gemm<T, true, false>(ctx, K_TRSM_PANEL, K - r0, bs, bs, T(1), G + (size_t)r0 * K + j0, K, Dk, NB, T(0),
+                                     P, NB, 0);
+            if (!e) e = cudaMemcpy2DAsync(G + (size_t)r0 * K + j0, K * sizeof(T), P, NB * sizeof(T), bs * sizeof(T),
+                                          K - r0, cudaMemcpyDeviceToDevice, st);
+            if (!e)
+                e = gemm<T, true, true>(ctx, K_SYRK_UPDATE, K - r0, K - r0, bs, T(-1), G + (size_t)r0 * K + j0, K,
+                                        G + (size_t)r0 * K + j0, K, T(1), G + (size_t)r0 * K + r0, K, 0);
+            if (e) return e;
+        }
+    }
+    {
+        LaunchTimer lt(ctx, K_MISC);
+        k_set_identity<T><<<cap_grid(K * K, 256, 65536), 256, 0, st>>>(X, K);
+    }
+    for (int64_t jb = 0; jb < nb; ++jb) {
+        const int64_t j0 = jb * NB;
+        const int bs = (int)(K - j0 < NB ? K - j0 : NB);
+        const int64_t ncols = j0 + bs;
+        {
+            LaunchTimer lt(ctx, K_TRINV_DIAG);
+            add_work(ctx, K_TRINV_DIAG, 2.0 * (double)bs * bs * (double)ncols);
+            k_trmm_diag<T><<<(unsigned)((ncols + NB - 1) / NB), 64, smem2<T>(), st>>>(X, K, j0, bs, ncols,
+                                                                                    Dall + (size_t)jb * NB * NB);
+        }
+        const int64_t r0 = j0 + bs;
+        if (r0 < K) {
+            e = gemm<T, false, false>(ctx, K_TRINV_UPDATE, K - r0, ncols, bs, T(-1), G + (size_t)r0 * K + j0, K,
+                                      X + (size_t)j0 * K, K, T(1), X + (size_t)r0 * K, K, 0);
+            if (e) return e;
+        }
+    }
+    return cudaGetLastError();
 }
 
 template <typename T>

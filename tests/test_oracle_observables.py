@@ -212,3 +212,36 @@ def test_bundle_is_the_mean_of_consecutive_columns(orc):
     V = rng.random((12, 5))
     B = orc.bundle(V, 4)
     np.testing.assert_allclose(4 * B.sum(axis=1), V.reshape(3, 4, 5).sum(axis=(1, 2)), rtol=1e-14)
+
+
+def test_mirror_copies_follow_table1(orc):
+    """Golden fixture: the sign patterns of Table 1 (Sec. 2.2.2).  A nearly free
+    particle sampled once, viewed face-on (incl = 0, so X = x, Y = y, V = v_z
+    of each copy), must land in the pixel, velocity and cylindrical bins that the
+    table's signs give, each copy carrying 1/4 of the sample."""
+    import os
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "table1_mirrors.txt"))
+    assert rows.shape == (4, 7)
+    g = dict(nx=20, ny=20, pix=0.5, nv=16, vmax=400.0, nR=10, nphi=10, nz=5, Rmax=10.0, zmin=-3.0, zmax=3.0,
+             incl=0.0, bar_angle=0.0, pa=0.0, gh=0, mirror4=1)
+    pot = orc.make_pot(dict(test_kind=1, test_M=1e-6))
+    ic = np.array([[1.3, 0.7, 0.8, 12.0, 30.0, 120.0]])
+    U, _, status = orc.build_matrix(pot, 0.0, inputs.DT_HALF_MYR, 1, ic, orc.make_obs(g))
+    assert status[0] == 0
+    pos = ic[0, :3] + inputs.DT_HALF_MYR * ic[0, 3:]          # one drift step; the force is negligible
+    vel = ic[0, 3:]
+    nd, npix = 10 * 10 * 5, 20 * 20
+    expected = {}
+    for r in rows:
+        sp, sv = r[1:4], r[4:7]
+        x, y, z = sp * pos
+        vz = (sv * vel)[2]
+        ix, iy = int(math.floor((x + 5.0) / 0.5)), int(math.floor((y + 5.0) / 0.5))
+        iv = int(math.floor((vz + 400.0) / 50.0))
+        R, ph = math.hypot(x, y), math.atan2(y, x) % (2 * math.pi)
+        iR, ip, iz = int(R / 1.0), int(ph / (2 * math.pi / 10)), int(math.floor((z + 3.0) / 1.2))
+        p = iy * 20 + ix
+        for row in ((iR * 10 + ip) * 5 + iz, nd + p, nd + npix + p * 16 + iv):
+            expected[row] = expected.get(row, 0.0) + 0.25
+    got = {int(k): float(U[0, k]) for k in np.flatnonzero(U[0])}
+    assert got == expected
