@@ -186,78 +186,61 @@ __global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t l
     }
 }
 
-// The diagonal block's factor and its inverse in one CTA of 64 threads, rows and columns
-// held in registers (every loop fully unrolled, so register indices are static):
-//   Cholesky: thread i owns row i; at step j the pivot owner takes the square root, every
-//   row scales its column-j entry and publishes it, and each row applies the rank-1
-//   update to its own entries -- independent FMAs, two barriers per step;
-//   inverse:  thread t owns column t of D = L_kk^{-1} and substitutes down the rows of L,
-//   read by broadcast from shared memory.
-// L_kk goes back to G, D (NB x NB row-major, zero outside bs) to D.  A pivot that is not
-// positive records its global index + 1 in *info and is replaced by a tiny positive value.
+// The diagonal block's factor and its inverse in one CTA: the Cholesky of k_potrf_diag,
+// then D = L_kk^{-1} by forward substitution with four lanes of one warp per column (the
+// columns are independent; each column's dot products are split over its four lanes and
+// combined by shuffles).  L_kk goes back to G, D (NB x NB, zero outside bs) to D.  (A
+// register-resident variant with fully unrolled loops measured slower: its code no longer
+// fits the instruction cache.)
 template <typename T>
-__global__ void __launch_bounds__(NB) k_diag_factor_inv(T* __restrict__ G, int64_t ld, int64_t j0, int bs,
-                                                        T* __restrict__ D, int* info)
+__global__ void __launch_bounds__(256) k_diag_factor_inv(T* __restrict__ G, int64_t ld, int64_t j0, int bs,
+                                                         T* __restrict__ D, int* info)
 {
     extern __shared__ unsigned char smraw[];
-    T (*Ls)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);
-    __shared__ T col[NB];
-    __shared__ T piv;
-    const int i = threadIdx.x;
-    T r[NB];
-#pragma unroll
-    for (int l = 0; l < NB; ++l) r[l] = (i < bs && l <= i) ? G[(size_t)(j0 + i) * ld + j0 + l] : T(0);
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        if (j < bs) {
-            if (i == j) {
-                T d = r[j];
-                if (!(d > T(0))) {
-                    if (info) atomicCAS(info, 0, (int)(j0 + j + 1));
-                    d = T(1e-30);
-                }
-                d = sqrt(d);
-                r[j] = d;
-                piv = d;
-            }
-            __syncthreads();
-            if (i > j) r[j] = r[j] / piv;
-            col[i] = r[j];
-            __syncthreads();
-            if (i > j) {
-                const T aij = r[j];
-#pragma unroll
-                for (int l = j + 1; l < NB; ++l)
-                    if (l <= i) r[l] -= aij * col[l];
-            }
-        }
-    }
-#pragma unroll
-    for (int l = 0; l < NB; ++l) {
-        Ls[i][l] = r[l];
-        if (i < bs && l <= i) G[(size_t)(j0 + i) * ld + j0 + l] = r[l];
+    T (*a)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);
+    T (*x)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw + sizeof(T) * NB * (NB + 1));
+    const int t = threadIdx.x, row = t & (NB - 1), q = t >> 6;
+    for (int e = t; e < NB * NB; e += 256) {
+        int i = e / NB, j = e % NB;
+        a[i][j] = (i < bs && j <= i) ? G[(size_t)(j0 + i) * ld + j0 + j] : T(0);
+        x[i][j] = T(0);
     }
     __syncthreads();
-    // column t = i of the inverse
-    T x[NB];
-#pragma unroll
-    for (int k = 0; k < NB; ++k) {
-        T v = T(0);
-        if (k < bs && k >= i) {
-            if (k == i) {
-                v = T(1) / Ls[k][k];
-            } else {
-                T s = T(0);
-#pragma unroll
-                for (int l = 0; l < k; ++l)
-                    if (l >= i) s += Ls[k][l] * x[l];
-                v = -s / Ls[k][k];
-            }
+    for (int j = 0; j < bs; ++j) {
+        T d = a[j][j];
+        if (!(d > T(0))) {
+            if (t == 0 && info) atomicCAS(info, 0, (int)(j0 + j + 1));
+            d = T(1e-30);
         }
-        x[k] = v;
+        d = sqrt(d);
+        if (q == 0 && row > j && row < bs) a[row][j] /= d;
+        __syncthreads();
+        if (row > j && row < bs) {
+            const T aij = a[row][j];
+            for (int l = j + 1 + q; l <= row; l += 4) a[row][l] -= aij * a[l][j];
+        }
+        if (t == 0) a[j][j] = d;
+        __syncthreads();
     }
-#pragma unroll
-    for (int k = 0; k < NB; ++k) D[k * NB + i] = x[k];
+    // inverse: lanes 4c .. 4c + 3 own column c
+    const int col = t >> 2, part = t & 3;
+    if (part == 0 && col < bs) x[col][col] = T(1) / a[col][col];
+    __syncwarp();
+    for (int i = 1; i < bs; ++i) {
+        T s = T(0);
+        if (i > col)
+            for (int l = col + part; l < i; l += 4) s += a[i][l] * x[l][col];
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        if (part == 0 && i > col && col < bs) x[i][col] = -s / a[i][i];
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int e = t; e < NB * NB; e += 256) {
+        int i = e / NB, j = e % NB;
+        if (i < bs && j <= i) G[(size_t)(j0 + i) * ld + j0 + j] = a[i][j];
+        D[e] = x[i][j];
+    }
 }
 
 // Rows below the diagonal block: A[i, j0:j0+bs] <- A[i, j0:j0+bs] L_kk^{-T}.
@@ -1081,7 +1064,7 @@ cudaError_t cholesky_inverse(sw_ctx* ctx, T* G, T* X, T* D, int64_t K, int* d_in
         {
             LaunchTimer lt(ctx, K_POTRF_DIAG);
             add_work(ctx, K_POTRF_DIAG, 2.0 * (double)bs * bs * bs / 3.0);
-            k_diag_factor_inv<T><<<1, NB, smem2<T>() / 2, st>>>(G, K, j0, bs, Dk, d_info);
+            k_diag_factor_inv<T><<<1, 256, smem2<T>(), st>>>(G, K, j0, bs, Dk, d_info);
         }
         if ((e = cudaGetLastError())) return e;
         const int64_t r0 = j0 + bs;
