@@ -148,46 +148,10 @@ __global__ void __launch_bounds__(256) k_gemm(int64_t m, int64_t n, int64_t k, T
 // ---------------------------------------------------------------------------
 constexpr int NB = 64;
 
-// In-place Cholesky of the bs x bs diagonal block at (j0, j0).  256 threads: four per
-// row, each row's update split over the four by column (no index division), and every
-// thread computes the pivot itself, so a column step costs two barriers.  A pivot that
-// is not positive records its global index + 1 in *info and is replaced by a tiny
-// positive value so the factorisation can finish.
-template <typename T>
-__global__ void __launch_bounds__(256) k_potrf_diag(T* __restrict__ G, int64_t ld, int64_t j0, int bs, int* info)
-{
-    extern __shared__ unsigned char smraw[];
-    T (*a)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);
-    const int t = threadIdx.x, row = t & (NB - 1), q = t >> 6;
-    for (int e = t; e < NB * NB; e += 256) {
-        int i = e / NB, j = e % NB;
-        a[i][j] = (i < bs && j <= i) ? G[(size_t)(j0 + i) * ld + j0 + j] : T(0);
-    }
-    __syncthreads();
-    for (int j = 0; j < bs; ++j) {
-        T d = a[j][j];
-        if (!(d > T(0))) {
-            if (t == 0 && info) atomicCAS(info, 0, (int)(j0 + j + 1));
-            d = T(1e-30);
-        }
-        d = sqrt(d);
-        if (q == 0 && row > j && row < bs) a[row][j] /= d;
-        __syncthreads();
-        if (row > j && row < bs) {
-            const T aij = a[row][j];
-            for (int l = j + 1 + q; l <= row; l += 4) a[row][l] -= aij * a[l][j];
-        }
-        if (t == 0) a[j][j] = d;
-        __syncthreads();
-    }
-    for (int e = t; e < NB * NB; e += 256) {
-        int i = e / NB, j = e % NB;
-        if (i < bs && j <= i) G[(size_t)(j0 + i) * ld + j0 + j] = a[i][j];
-    }
-}
-
-// The diagonal block's factor and its inverse in one CTA: the Cholesky of k_potrf_diag,
-// then D = L_kk^{-1} by forward substitution with four lanes of one warp per column (the
+// The diagonal block's factor and its inverse in one CTA of 256 threads.  Cholesky: four
+// threads per row, each row's update split over the four by column, every thread computing
+// the pivot itself, two barriers per column step.  Then D = L_kk^{-1} by forward
+// substitution with four lanes of one warp per column (the
 // columns are independent; each column's dot products are split over its four lanes and
 // combined by shuffles).  L_kk goes back to G, D (NB x NB, zero outside bs) to D.  (A
 // register-resident variant with fully unrolled loops measured slower: its code no longer
@@ -241,79 +205,6 @@ __global__ void __launch_bounds__(256) k_diag_factor_inv(T* __restrict__ G, int6
         if (i < bs && j <= i) G[(size_t)(j0 + i) * ld + j0 + j] = a[i][j];
         D[e] = x[i][j];
     }
-}
-
-// Rows below the diagonal block: A[i, j0:j0+bs] <- A[i, j0:j0+bs] L_kk^{-T}.
-template <typename T>
-__global__ void __launch_bounds__(64) k_trsm_panel(T* __restrict__ G, int64_t ld, int64_t j0, int bs, int64_t r0,
-                                                   int64_t r1)
-{
-    extern __shared__ unsigned char smraw[];
-    T (*L)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);
-    T (*X)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw + sizeof(T) * NB * (NB + 1));
-    const int t = threadIdx.x;
-    const int64_t rb = r0 + (int64_t)blockIdx.x * NB;
-    for (int e = t; e < NB * NB; e += blockDim.x) {
-        int i = e / NB, j = e % NB;
-        L[i][j] = (i < bs && j <= i) ? G[(size_t)(j0 + i) * ld + j0 + j] : T(0);
-        int64_t gr = rb + i;
-        X[i][j] = (gr < r1 && j < bs) ? G[(size_t)gr * ld + j0 + j] : T(0);
-    }
-    __syncthreads();
-    // thread t solves row t: x_c = (a_c - sum_{l<c} x_l L[c][l]) / L[c][c], with the row
-    // held in registers (fully unrolled; columns at or beyond bs are never stored)
-    T x[NB];
-#pragma unroll
-    for (int c = 0; c < NB; ++c) x[c] = X[t][c];
-#pragma unroll
-    for (int c = 0; c < NB; ++c) {
-        T s = x[c];
-#pragma unroll
-        for (int l = 0; l < c; ++l) s -= x[l] * L[c][l];
-        x[c] = c < bs ? s / L[c][c] : T(0);
-    }
-#pragma unroll
-    for (int c = 0; c < NB; ++c) X[t][c] = x[c];
-    __syncthreads();
-    for (int e = t; e < NB * NB; e += blockDim.x) {
-        int i = e / NB, j = e % NB;
-        int64_t gr = rb + i;
-        if (gr < r1 && j < bs) G[(size_t)gr * ld + j0 + j] = X[i][j];
-    }
-}
-
-// Inverse of the lower-triangular bs x bs diagonal block: D = L_kk^{-1}
-// (full NB x NB storage, zeros above the diagonal and outside bs).
-template <typename T>
-__global__ void __launch_bounds__(64) k_trinv_diag(const T* __restrict__ G, int64_t ld, int64_t j0, int bs,
-                                                   T* __restrict__ D)
-{
-    extern __shared__ unsigned char smraw[];
-    T (*L)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);
-    T (*X)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw + sizeof(T) * NB * (NB + 1));
-    const int t = threadIdx.x;
-    for (int e = t; e < NB * NB; e += blockDim.x) {
-        int i = e / NB, j = e % NB;
-        L[i][j] = (i < bs && j <= i) ? G[(size_t)(j0 + i) * ld + j0 + j] : T(0);
-        X[i][j] = T(0);
-    }
-    __syncthreads();
-    // thread t computes column t of the inverse by forward substitution, the column
-    // in registers (fully unrolled; entries above the diagonal are zero)
-    if (t < bs) {
-        T x[NB];
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-            T s = T(0);
-#pragma unroll
-            for (int l = 0; l < i; ++l) s += L[i][l] * x[l];
-            x[i] = i < t || i >= bs ? T(0) : (i == t ? T(1) / L[i][i] : -s / L[i][i]);
-        }
-#pragma unroll
-        for (int i = 0; i < NB; ++i) X[i][t] = x[i];
-    }
-    __syncthreads();
-    for (int e = t; e < NB * NB; e += blockDim.x) D[e] = X[e / NB][e % NB];
 }
 
 // Block row k of X (rows j0..j0+bs, columns 0..ncols): X_k <- D X_k.
@@ -963,77 +854,6 @@ cudaError_t gemm(sw_ctx* ctx, int kid, int64_t m, int64_t n, int64_t k, T alpha,
 template <typename T>
 static size_t smem2() { return 2 * sizeof(T) * NB * (NB + 1); }
 
-template <typename T>
-cudaError_t cholesky(sw_ctx* ctx, T* G, int64_t K, int* d_info)
-{
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<T>());
-        cudaFuncSetAttribute(k_trsm_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<T>());
-        attr_set = true;
-    }
-    cudaStream_t st = ctx_stream(ctx);
-    for (int64_t j0 = 0; j0 < K; j0 += NB) {
-        int bs = (int)(K - j0 < NB ? K - j0 : NB);
-        {
-            LaunchTimer lt(ctx, K_POTRF_DIAG);
-            add_work(ctx, K_POTRF_DIAG, (double)bs * bs * bs / 3.0);
-            k_potrf_diag<T><<<1, 256, smem2<T>() / 2, st>>>(G, K, j0, bs, d_info);
-        }
-        int64_t r0 = j0 + bs, r1 = K;
-        if (r1 > r0) {
-            {
-                LaunchTimer lt(ctx, K_TRSM_PANEL);
-                add_work(ctx, K_TRSM_PANEL, (double)(r1 - r0) * bs * bs);
-                k_trsm_panel<T><<<(unsigned)((r1 - r0 + NB - 1) / NB), 64, smem2<T>(), st>>>(G, K, j0, bs, r0, r1);
-            }
-            // trailing lower update: G[r0:, r0:] -= P P^T with P = G[r0:, j0:j0+bs]
-            cudaError_t e = gemm<T, true, true>(ctx, K_SYRK_UPDATE, r1 - r0, r1 - r0, bs, T(-1), G + (size_t)r0 * K + j0,
-                                                K, G + (size_t)r0 * K + j0, K, T(1), G + (size_t)r0 * K + r0, K, 0);
-            if (e != cudaSuccess) return e;
-        }
-    }
-    return cudaGetLastError();
-}
-
-// X = L^{-1} for the lower-triangular Cholesky factor L stored in G.
-template <typename T>
-cudaError_t tri_inverse(sw_ctx* ctx, const T* G, T* X, T* D, int64_t K)
-{
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_trinv_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<T>());
-        cudaFuncSetAttribute(k_trmm_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2<T>());
-        attr_set = true;
-    }
-    cudaStream_t st = ctx_stream(ctx);
-    {
-        LaunchTimer lt(ctx, K_MISC);
-        k_set_identity<T><<<cap_grid(K * K, 256, 65536), 256, 0, st>>>(X, K);
-    }
-    for (int64_t j0 = 0; j0 < K; j0 += NB) {
-        int bs = (int)(K - j0 < NB ? K - j0 : NB);
-        int64_t ncols = j0 + bs;
-        {
-            LaunchTimer lt(ctx, K_TRINV_DIAG);
-            add_work(ctx, K_TRINV_DIAG, (double)bs * bs * bs / 3.0);
-            k_trinv_diag<T><<<1, 64, smem2<T>(), st>>>(G, K, j0, bs, D);
-        }
-        {
-            LaunchTimer lt(ctx, K_TRINV_DIAG);
-            add_work(ctx, K_TRINV_DIAG, (double)bs * bs * (double)ncols);
-            k_trmm_diag<T><<<(unsigned)((ncols + NB - 1) / NB), 64, smem2<T>(), st>>>(X, K, j0, bs, ncols, D);
-        }
-        int64_t r0 = j0 + bs;
-        if (r0 < K) {
-            cudaError_t e = gemm<T, false, false>(ctx, K_TRINV_UPDATE, K - r0, ncols, bs, T(-1), G + (size_t)r0 * K + j0,
-                                                  K, X + (size_t)j0 * K, K, T(1), X + (size_t)r0 * K, K, 0);
-            if (e != cudaSuccess) return e;
-        }
-    }
-    return cudaGetLastError();
-}
-
 // Cholesky factor L of G (in place, lower) and X = L^{-1}.  Per 64-wide step: one CTA
 // factors the diagonal block and inverts it (D_k = L_kk^{-1}); the panel below becomes
 // P = A D_k^T, a plain GEMM over all rows instead of a row-by-row substitution; then the
@@ -1372,10 +1192,6 @@ template cudaError_t gemm<float, true, true>(sw_ctx*, int, int64_t, int64_t, int
                                              const float*, int64_t, float, float*, int64_t, int64_t);
 template cudaError_t gemm<double, true, true>(sw_ctx*, int, int64_t, int64_t, int64_t, double, const double*,
                                               int64_t, const double*, int64_t, double, double*, int64_t, int64_t);
-template cudaError_t cholesky<float>(sw_ctx*, float*, int64_t, int*);
-template cudaError_t cholesky<double>(sw_ctx*, double*, int64_t, int*);
-template cudaError_t tri_inverse<float>(sw_ctx*, const float*, float*, float*, int64_t);
-template cudaError_t tri_inverse<double>(sw_ctx*, const double*, double*, double*, int64_t);
 template cudaError_t cholesky_inverse<float>(sw_ctx*, float*, float*, float*, int64_t, int*);
 template cudaError_t cholesky_inverse<double>(sw_ctx*, double*, double*, double*, int64_t, int*);
 template cudaError_t shift_and_trace<float>(sw_ctx*, float*, int64_t, double*, double);

@@ -14,8 +14,8 @@ namespace sw {
 
 const char* kKernelNames[K_COUNT] = {
     "ics_to_soa", "orbit_project_bin", "orbit_drift", "zero_flagged", "finalize_columns", "trajectory",
-    "potential_eval", "whiten", "gram_tcgen05", "gram_simt", "shift_diag", "potrf_diag", "trsm_panel",
-    "syrk_update", "trinv_diag", "trinv_update", "gemv_n", "gemv_t", "trmv_l", "trmv_lt", "admm_update",
+    "potential_eval", "whiten", "gram_tcgen05", "gram_simt", "shift_diag", "diag_factor_inverse", "panel_gemm",
+    "syrk_update", "inverse_block_row", "trinv_update", "gemv_n", "gemv_t", "trmv_l", "trmv_lt", "admm_update",
     "residual", "gradient", "chi2", "misc", "batch_orbit_bin", "mlp_fwd", "mlp_bwd", "adam", "reduce_gh", "pcg", "bundle", "cholesky_inverse"};
 
 void set_error(sw_ctx* ctx, const char* fmt, ...)

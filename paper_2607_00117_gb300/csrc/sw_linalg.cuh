@@ -17,15 +17,11 @@ cudaError_t div_to(sw_ctx* ctx, int64_t n, const double* a, const double* b, GT*
 template <typename T, bool BT, bool LOWER>
 cudaError_t gemm(sw_ctx* ctx, int kid, int64_t m, int64_t n, int64_t k, T alpha, const T* A, int64_t lda, const T* B,
                  int64_t ldb, T beta, T* C, int64_t ldc, int64_t diag_off);
-template <typename T>
-cudaError_t cholesky(sw_ctx* ctx, T* G, int64_t K, int* d_info);
-template <typename T>
-cudaError_t tri_inverse(sw_ctx* ctx, const T* G, T* X, T* D, int64_t K);
 // Cholesky (in place) and the explicit inverse X = L^{-1} in one cooperative launch (k_chol.cu);
 // cudaErrorNotSupported when the device cannot launch it; *d_err != 0 if a barrier wait ran out
 template <typename T>
 cudaError_t cholesky_inverse_coop(sw_ctx* ctx, T* G, T* X, int64_t K, int* d_info, int* d_err);
-// Cholesky (in place) and the explicit inverse X = L^{-1} by per-step launches
+// Cholesky (in place) and the explicit inverse X = L^{-1} by per-step launches (D unused)
 template <typename T>
 cudaError_t cholesky_inverse(sw_ctx* ctx, T* G, T* X, T* D, int64_t K, int* d_info);
 template <typename T>
