@@ -214,7 +214,8 @@ sw_status sw_reset_stats(sw_ctx* ctx);
 sw_status sw_kernel_work(sw_ctx* ctx, int k, double* work, int* kind);
 int64_t sw_launch_count(const sw_ctx* ctx);
 
-/* Tunables (value semantics in parentheses); unknown keys return SW_EINVAL:
+/* Tunables (value semantics in parentheses); unknown keys return SW_EINVAL.  The ADMM keys apply to the
+ * paper's solver (Sec. 2.3), the "as_" keys to the active-set solver; "solver" chooses between them: */
  *  "ej_every" (>= 1)        steps between Jacobi-energy checks in sw_project (default 1 in FP64, 8 in FP32)
  *  "admm_max_iter" (>= 1)   ADMM iteration cap per run (default 400; a run also stops when its residual
  *                           has not halved over five checks)
@@ -230,11 +231,12 @@ int64_t sw_launch_count(const sw_ctx* ctx);
  *  "polish_max" (>= 0)      largest support the exact active-set polish handles (default 2048; 0 = off)
  *  "polish_solves" (>= 0)   cap on reduced solves of one polish (default 400)
  *  "inner_refine" (0..8)    refinement steps of each ADMM linear solve against the Gram (default 1)
- *  "verbose" (0/1)          print solver progress to stderr (default 0; the only output the library makes)
- *  "working_set" (0/1)      N > M: orbit-space solves on a working set of orbits (default 1); 0 uses the
- *                           constraint-space (Woodbury) form of the ADMM step
- *  "orbit_direct_max" (>= 0) N > M up to this many orbits: orbit-space solve on all orbits (default 8192)
- *  "large_solver" (0/1)     above orbit_direct_max orbits: 0 block active set (default), 1 ADMM working set
+ *  "verbose" (0, 1, 2)      print solver progress to stderr (default 0; the only output the library makes)
+ *  "working_set" (0/1)      ADMM path, N > M: orbit-space solves (default 1); 0 uses the constraint-space
+ *                           (Woodbury) form of the ADMM step
+ *  "orbit_direct_max" (>= 0) ADMM path, N > M up to this many orbits: orbit-space solve on all orbits
+ *                           (default 8192); above it the large-library solver below
+ *  "large_solver" (0/1)     above orbit_direct_max orbits: 0 active set (default), 1 ADMM on a working set
  *  "as_block" (>= 1)        active set: KKT violators entering per pivoting step (default 2048)
  *  "as_cg_max" (>= 0)       active set: preconditioned conjugate-gradient steps per reduced solve (default 200)
  *  "as_cg_tol" (> 0)        active set: CG stops at max|r| <= as_cg_tol * kkt_tol * max|q| (default 0.05)

@@ -165,10 +165,6 @@ static void ctx_release(sw_ctx* ctx)
     ctx->solve_ws.release();
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
     ctx->pool.clear();
-    if (ctx->side) cudaStreamDestroy(ctx->side);
-    for (cudaEvent_t& e : ctx->side_ev)
-        if (e) { cudaEventDestroy(e); e = nullptr; }
-    ctx->side = nullptr;
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     ctx->stream = nullptr;
     cudaGetLastError();

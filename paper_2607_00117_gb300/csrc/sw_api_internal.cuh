@@ -71,8 +71,6 @@ struct sw_ctx {
     int device = 0;
     sw_precision prec = SW_FP32_KAHAN;
     cudaStream_t stream = nullptr;
-    cudaStream_t side = nullptr;          // second stream for work overlapped with the main one
-    cudaEvent_t side_ev[2] = {nullptr, nullptr};
     bool own_stream = false;
     std::string err;
     sw::Options opt;
