@@ -215,7 +215,7 @@ sw_status sw_kernel_work(sw_ctx* ctx, int k, double* work, int* kind);
 int64_t sw_launch_count(const sw_ctx* ctx);
 
 /* Tunables (value semantics in parentheses); unknown keys return SW_EINVAL.  The ADMM keys apply to the
- * paper's solver (Sec. 2.3), the "as_" keys to the active-set solver; "solver" chooses between them: */
+ * paper's solver (Sec. 2.3), the "as_" keys to the active-set solver; "solver" chooses between them.
  *  "ej_every" (>= 1)        steps between Jacobi-energy checks in sw_project (default 1 in FP64, 8 in FP32)
  *  "admm_max_iter" (>= 1)   ADMM iteration cap per run (default 400; a run also stops when its residual
  *                           has not halved over five checks)
