@@ -16,12 +16,12 @@
 // Each reduced problem (U~_F^T U~_F + 2 lambda/N I) x = q_F is solved on the
 // GPU by preconditioned conjugate gradients whose products use the stored
 // matrix with FP64 accumulation.  The preconditioner is the Cholesky factor of
-// the Jacobi-scaled Gram of a superset P0 of F, formed on the tensor cores
+// the Jacobi-scaled Gram of the factored set P0, formed on the tensor cores
 // (BF16 hi + lo split, FP32 accumulation), factored in FP32 with its triangular
-// inverse kept explicitly; while F stays inside P0 (orbits leaving) the factor
-// is reused, its F block differing from the exact inverse by a term of the rank
-// of P0 \ F.  The gradient over all N orbits is recomputed in FP64 whenever the
-// iterate settles on the optimum of its passive set.
+// inverse kept explicitly.  The solve accepts any F inside P0 (the orbits of
+// P0 outside F masked); every pivoting step refactors on its own passive set,
+// so P0 = F as the loop stands.  The gradient over all N orbits is recomputed
+// in FP64 after every step.
 #include "sw_linalg.cuh"
 
 #include <algorithm>
@@ -226,9 +226,9 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     const double gtol = ctx->opt.kkt_tol * std::max(qmax, 1e-300);
     const double rtol = ctx->opt.as_cg_tol * gtol;
 
-    // ---- factor of the passive Gram on a set P0 of orbits (kept while the passive
-    // set stays inside P0): gathered columns Uc, scales s = h^-1/2, explicit inverse X
-    // of the Cholesky factor of S G~ S + R (tensor-core Gram of the scaled columns)
+    // ---- factor of the passive Gram on a set P0 of orbits: gathered columns Uc,
+    // scales s = h^-1/2, explicit inverse X of the Cholesky factor of S G~ S + R
+    // (tensor-core Gram of the scaled columns)
     std::vector<int64_t> P0;
     std::vector<int64_t> pos(N, -1);
     int n_factor = 0, n_solves = 0, cg_total = 0;
