@@ -1,0 +1,169 @@
+"""Parity at the benchmark's full size: the barred workload of 10^5 orbits
+(25 000 initial conditions x 4 dithered realisations, the orbit bundles of
+Sec. 2.2.1) x 10^4 steps, projected into 20 x 20 x 10 density cells and
+50 x 50 pixels x 32 velocity bins (86 500 rows), bundled, reduced to
+Gauss-Hermite rows (16 500 rows) and solved, through the same calls, seeds and
+launch configuration as the benchmark's end-to-end leg (FP32 form, host inputs).
+
+The oracle cannot hold the 34.6 GB matrix, so sampled outputs are compared one
+by one.  Columns are read back exactly as U e_i.
+
+* Raw columns of sampled orbits: the count structure holds exactly (every
+  count row is a multiple of 1/(4S), block sums at most one, a pixel's mass at
+  least the sum of its velocity bins).  Against the oracle's integration of the
+  same initial conditions, a column at 10^4 steps is defined only to within its
+  sensitivity to the rounding of the integration (a relative change of 1e-7 in
+  the initial conditions already moves half of these columns by more than
+  2e-4 in L1, chaotic ones by O(1)).  The gate is therefore the oracle's own
+  spread: each column's L1 difference is at most 3x the largest L1 change of
+  the oracle's column under four seeded relative perturbations of 3e-5 of its
+  initial condition, plus 1e-3; and the median difference is at most the
+  median spread.  A perturbation of 3e-5 exceeds the FP32 path's accumulated
+  phase-space error (at most 1e-5 after 10^3 steps, the phase-space test) as
+  an initial-condition equivalent; a wrong sign, index or angle anywhere in
+  the projection moves regular orbits' columns by O(1) and fails the gate.
+* Bundle and Gauss-Hermite columns of sampled bundles: the oracle's bundle
+  mean and histogram -> GH reduction of the GPU's own raw columns.
+* The solve, by properties that hold at any size: non-negative finite
+  weights, chi^2 parts equal to their definition on the returned weights, and
+  the KKT conditions of the objective on sampled bundles (support and zero
+  weights), evaluated on the host in FP64 from the read-back columns.
+"""
+import numpy as np
+import pytest
+
+from paper_2607_00117_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+W = inputs.WORKLOADS["barred_100k"]
+N_SAMPLE_BUNDLES = 32
+PERTURB, N_PERTURB, SPREAD_FACTOR = 3e-5, 4, 3.0
+
+
+def _column(U, i: int) -> np.ndarray:
+    e = np.zeros(U.N)
+    e[i] = 1.0
+    return U.apply(e)
+
+
+@pytest.fixture(scope="module")
+def full():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2607_00117_gb300 import sw
+    sw.lib(build_if_missing=True)
+    import bench
+
+    v0s, y, sig = bench.make_data(sw, torch, W, 0)
+    nb = W["bundle"]
+    Nb = W["n_orb"] // nb
+    base = inputs.disc_ics(W["potential"], Nb, seed=bench.replica_seed(W["seeds"]["ic"], 0))
+    ics = inputs.dither(base, nb, bench.replica_seed(W["seeds"]["dither"], 0), W["potential"])
+    ctx = sw.Context(0, "fp32")
+    ctx.set_potential(W["potential"])
+    ctx.integrate_library(ics, W["omega_p"], W["dt"], W["nsteps"])
+    Uh = ctx.project(W["grid"])
+    Ub = ctx.bundle(Uh, nb)
+    Ug = ctx.reduce_gh(Ub, v0s)
+    w, chi2 = ctx.solve_weights(Ug, y, sig, W["lam"])
+    info = ctx.solve_info()
+    rng = np.random.default_rng(4242)
+    bundles = np.sort(rng.choice(Nb, N_SAMPLE_BUNDLES, replace=False))
+    orbits = (bundles[:, None] * nb + np.arange(nb)[None, :]).ravel()
+    d = dict(ctx=ctx, Uh=Uh, Ub=Ub, Ug=Ug, w=w, chi2=chi2, info=info, y=y, sig=sig, v0s=v0s, ics=ics,
+             nb=nb, bundles=bundles, orbits=orbits,
+             raw=np.stack([_column(Uh, int(i)) for i in orbits]))
+    yield d
+    for U in (Ug, Ub, Uh):
+        U.free()
+    ctx.close()
+
+
+def test_full_size_shapes(full):
+    nd = W["grid"]["nR"] * W["grid"]["nphi"] * W["grid"]["nz"]
+    npix = W["grid"]["nx"] * W["grid"]["ny"]
+    assert (full["Uh"].M, full["Uh"].N) == (nd + npix + npix * W["grid"]["nv"], W["n_orb"])
+    assert (full["Ub"].M, full["Ub"].N) == (full["Uh"].M, W["n_orb"] // full["nb"])
+    assert (full["Ug"].M, full["Ug"].N) == (nd + 5 * npix, W["n_orb"] // full["nb"])
+    assert full["Ug"].blocks == (nd, npix, 4 * npix)
+
+
+def test_full_size_count_structure(full):
+    """Every count row of a sampled raw column is a multiple of 1/(4S); the
+    density and pixel blocks each hold at most the orbit's unit mass; a pixel's
+    mass is at least the sum of its velocity bins (velocities outside the
+    range count toward the pixel only)."""
+    g = W["grid"]
+    nd, npix, nv = g["nR"] * g["nphi"] * g["nz"], g["nx"] * g["ny"], g["nv"]
+    S4 = 4.0 * W["nsteps"]
+    raw = full["raw"]
+    assert np.all(raw >= 0.0)
+    c = raw * S4
+    assert np.abs(c - np.rint(c)).max() < 1e-2
+    assert np.all(raw[:, :nd].sum(1) <= 1.0 + 1e-5)
+    assert np.all(raw[:, nd:nd + npix].sum(1) <= 1.0 + 1e-5)
+    hist = raw[:, nd + npix:].reshape(len(raw), npix, nv).sum(2)
+    assert np.all(raw[:, nd:nd + npix] >= hist - 1e-6)
+    # the sample is not degenerate: most sampled orbits put mass in the field
+    assert (raw[:, nd:nd + npix].sum(1) > 0.1).mean() > 0.5
+
+
+def test_full_size_raw_columns_vs_oracle(full, orc):
+    pot, obs = orc.make_pot(W["potential"]), orc.make_obs(W["grid"])
+    I = full["ics"][full["orbits"]]
+    args = (pot, W["omega_p"], W["dt"], W["nsteps"])
+    Uo, _, so = orc.build_matrix(*args, I, obs)
+    spread = np.zeros(len(I))
+    for k in range(N_PERTURB):
+        xi = np.random.default_rng(9000 + k).standard_normal(I.shape)
+        Up, _, _ = orc.build_matrix(*args, I + PERTURB * np.abs(I) * xi, obs)
+        spread = np.maximum(spread, np.abs(Up - Uo).sum(1))
+    keep = so == 0                                   # orbits the oracle's quality cut keeps
+    assert (~keep).sum() <= 2, (~keep).sum()
+    l1 = np.abs(full["raw"] - Uo).sum(1)
+    bad = keep & (l1 > SPREAD_FACTOR * spread + 1e-3)
+    assert not bad.any(), (full["orbits"][bad], l1[bad], spread[bad])
+    assert np.median(l1[keep]) <= np.median(spread[keep]), (np.median(l1[keep]), np.median(spread[keep]))
+
+
+def test_full_size_bundle_and_gh_columns(full, orc):
+    g = W["grid"]
+    nb = full["nb"]
+    nd, npix, nv = g["nR"] * g["nphi"] * g["nz"], g["nx"] * g["ny"], g["nv"]
+    Bg = np.stack([_column(full["Ub"], int(b)) for b in full["bundles"]])
+    np.testing.assert_allclose(Bg, orc.bundle(full["raw"], nb), rtol=3e-7, atol=0)
+    Gg = np.stack([_column(full["Ug"], int(b)) for b in full["bundles"]])
+    ref = orc.reduce_gh(Bg, nd, npix, nv, -g["vmax"], 2 * g["vmax"] / nv, full["v0s"])
+    np.testing.assert_allclose(Gg, ref, rtol=2e-5, atol=1e-7)
+
+
+def test_full_size_solve_properties(full):
+    """Weights, chi^2 parts and the KKT conditions of
+    1/2 ||(U w - y)/sigma||^2 + (lam/N) ||w||^2 on sampled bundles."""
+    Ug, w, y, sig = full["Ug"], full["w"], full["y"], full["sig"]
+    lam, N = W["lam"], Ug.N
+    assert w.shape == (N,) and np.all(np.isfinite(w)) and np.all(w >= 0.0)
+    assert full["info"]["kkt_met"]
+    r = (y - Ug.apply(w)) / sig
+    nd = Ug.blocks[0]
+    parts = np.array([np.sum(r * r), np.sum(r[nd:] ** 2), lam / N * np.sum(w * w)])
+    np.testing.assert_allclose(full["chi2"], parts, rtol=1e-9)
+    # KKT on sampled bundles: the support (w > 0) and zero weights
+    rng = np.random.default_rng(4343)
+    sup = np.flatnonzero(w > 0)
+    zero = np.flatnonzero(w == 0)
+    assert len(sup) > 0
+    pick = np.concatenate([rng.choice(sup, min(16, len(sup)), replace=False),
+                           rng.choice(zero, min(16, len(zero)), replace=False)])
+    mu = 2.0 * lam / N
+    g, q = [], []
+    for b in pick:
+        u = _column(Ug, int(b)) / sig
+        g.append(u @ r - mu * w[b])                 # minus the gradient of the objective
+        q.append(u @ (y / sig))
+    g, q = np.array(g), np.array(q)
+    tol = 1e-6 * np.abs(q).max()
+    on = w[pick] > 0
+    assert np.all(np.abs(g[on]) <= tol), (pick[on], g[on], tol)
+    assert np.all(g[~on] <= tol), (pick[~on], g[~on], tol)
