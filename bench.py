@@ -189,6 +189,12 @@ def make_data(sw, torch, W, rank):
 OPS_PER_ORBIT_STEP = 891.0
 
 
+# kernels launched as a single CTA (a chain of dependent launches): their roofline also
+# states the fraction of one SM's FP32 peak, the most one launch can reach
+ONE_CTA_KERNELS = {"diag_factor_inverse": "one 256-thread CTA per launch: the 64 x 64 diagonal blocks of the "
+                                          "blocked factorisation, a chain of dependent launches (latency-bound)"}
+
+
 def roofline_entry(name, stats, hbm, bf16, sm_mhz):
     """Roofline of one kernel from its algorithmic work (counted by the library at
     each launch) and its CUDA-event time inside the timed region."""
@@ -206,7 +212,11 @@ def roofline_entry(name, stats, hbm, bf16, sm_mhz):
         return {"bound": "tensor", "achieved": a, "peak": bf16, "unit": "TFLOP/s", "frac": a / bf16}
     if kind == "flop_simt" and work > 0:
         a = work / t / 1e12
-        return {"bound": "alu", "achieved": a, "peak": simt_peak, "unit": "TFLOP/s (FP32 SIMT)", "frac": a / simt_peak}
+        r = {"bound": "alu", "achieved": a, "peak": simt_peak, "unit": "TFLOP/s (FP32 SIMT)", "frac": a / simt_peak}
+        if name in ONE_CTA_KERNELS:
+            r["one_sm_frac"] = a / (simt_peak / SM_COUNT)
+            r["note"] = ONE_CTA_KERNELS[name]
+        return r
     if kind == "orbit_steps" and work > 0:
         peak = SM_COUNT * FP32_LANES * sm_mhz * 1e6 / 1e12                  # lane-instructions / s
         a = OPS_PER_ORBIT_STEP * work / t / 1e12

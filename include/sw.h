@@ -237,7 +237,7 @@ int64_t sw_launch_count(const sw_ctx* ctx);
  *  "orbit_direct_max" (>= 0) ADMM path, N > M up to this many orbits: orbit-space solve on all orbits
  *                           (default 8192); above it the large-library solver below
  *  "large_solver" (0/1)     above orbit_direct_max orbits: 0 active set (default), 1 ADMM on a working set
- *  "as_block" (>= 1)        active set: KKT violators entering per pivoting step (default 2048)
+ *  "as_block" (>= 1)        active set: KKT violators entering per pivoting step (default 1024)
  *  "as_cg_max" (>= 0)       active set: preconditioned conjugate-gradient steps per reduced solve (default 200)
  *  "as_cg_tol" (> 0)        active set: CG stops at max|r| <= as_cg_tol * kkt_tol * max|q| (default 0.05)
  *  "as_solves" (>= 1)       active set: cap on pivoting steps (default 400)

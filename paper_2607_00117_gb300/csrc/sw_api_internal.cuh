@@ -29,7 +29,7 @@ struct Options {
     int verbose = 0;        // solver progress on stderr
     int inner_refine = 1;        // refinement steps of each ADMM linear solve against the kept Gram
     int large_solver = 0;        // N > orbit_direct_max: 0 block active set, 1 ADMM working set
-    int as_block = 2048;         // active set: violators entering per pivoting step
+    int as_block = 1024;         // active set: violators entering per pivoting step
     double as_candidates = 0;    // active set: initial candidate-set size (0: 2 M)
     double as_grow = 0.0;        // active set: at most max(as_block, as_grow |F|) orbits enter per step
     int solver = 0;              // 0 auto, 1 active set, 2 ADMM (see solve_dispatch)

@@ -40,6 +40,10 @@ def test_roofline_entry_arithmetic():
     r = bench.roofline_entry("k_simt", stats, 6000.0, 1700.0, 2070.0)
     peak = 152 * 128 * 2 * 2070e6 / 1e12
     assert r["bound"] == "alu" and math.isclose(r["achieved"], 20.0) and math.isclose(r["peak"], peak)
+    assert "one_sm_frac" not in r
+    one = {"diag_factor_inverse": {"launches": 10, "ms": 0.5, "work": 10 * 1.0e5, "kind": "flop_simt"}}
+    r = bench.roofline_entry("diag_factor_inverse", one, 6000.0, 1700.0, 2070.0)
+    assert math.isclose(r["achieved"], 2e-3) and math.isclose(r["one_sm_frac"], r["frac"] * 152)
     r = bench.roofline_entry("k_orbit", stats, 6000.0, 1700.0, 2070.0)
     assert math.isclose(r["achieved"], bench.OPS_PER_ORBIT_STEP * 1e9 / 0.1 / 1e12)
     assert math.isclose(r["peak"], 152 * 128 * 2070e6 / 1e12)
