@@ -189,6 +189,12 @@ def make_data(sw, torch, W, rank):
 OPS_PER_ORBIT_STEP = 891.0
 
 
+# DRAM bytes (read + write) per launch from an ncu capture of the kernel as it stands (two
+# launches of the factorisation kernels' capture on the small barred case: 24 576 and 23 040
+# bytes read, 0 written); a launch factors one 64 x 64 block whatever the problem size, so the
+# figure holds at full size
+NCU_TRAFFIC_PER_LAUNCH = {"diag_factor_inverse": 23808.0}
+
 # kernels launched as a single CTA (a chain of dependent launches): their roofline also
 # states the fraction of one SM's FP32 peak, the most one launch can reach
 ONE_CTA_KERNELS = {"diag_factor_inverse": "one 256-thread CTA per launch: the 64 x 64 diagonal blocks of the "
@@ -434,7 +440,7 @@ def run_sw(args):
     dom = max(kstats, key=lambda k: kstats[k]["ms"])
     sm_mhz = clk["sm_mhz"] if clk else sm_max
     roof = roofline_entry(dom, kstats, hbm, bf16_sus, sm_mhz)
-    roof.update({"kernel": dom, "traffic": None, "peak_source": peak_src,
+    roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(dom), "peak_source": peak_src,
                  "ms_per_launch": kstats[dom]["ms"] / kstats[dom]["launches"]})
     top = sorted(kstats, key=lambda k: -kstats[k]["ms"])[:8]
     roof_top = {k: {kk: (round(v, 4) if isinstance(v, float) else v)
@@ -541,7 +547,7 @@ def run_batched(args):
     sm_mhz = clk["sm_mhz"] if clk else sm_max
     dom = max(kstats, key=lambda k: kstats[k]["ms"])
     roof = roofline_entry(dom, kstats, hbm, bf16_sus, sm_mhz)
-    roof.update({"kernel": dom, "traffic": None, "peak_source": peak_src})
+    roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(dom), "peak_source": peak_src})
     bo = kstats.get("batch_orbit_bin", {"ms": float("nan")})
     line = {"metric": "orbit-steps/s (whole model evaluations, FP32 batched vs FP64 plain at matched chi^2)",
             "value": ntot * S * args.steps / elapsed, "unit": "orbit-steps/s", "n_gpus": world, "steps": args.steps,
