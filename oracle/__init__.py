@@ -62,6 +62,14 @@ class Obs(ctypes.Structure):
                 ("gh", ctypes.c_int32), ("mirror4", ctypes.c_int32)]
 
 
+class BS3Opts(ctypes.Structure):
+    """Adaptive Bogacki-Shampine 3(2) controls (Sec. 2.2.2): relative tolerance,
+    first trial step, step-size controller, fixed-step switch, rejection cap."""
+    _fields_ = [("rtol", ctypes.c_double), ("h0", ctypes.c_double), ("safety", ctypes.c_double),
+                ("fac_min", ctypes.c_double), ("fac_max", ctypes.c_double), ("fixed", ctypes.c_int32),
+                ("max_reject", ctypes.c_int32)]
+
+
 DISC, HALO, BAR, TEST = 1, 2, 4, 8
 _D = ctypes.POINTER(ctypes.c_double)
 _I32 = ctypes.POINTER(ctypes.c_int32)
@@ -88,6 +96,10 @@ def lib():
             "orc_apply_matrix": (None, [P, dbl, dbl, i64, i64, _D, O, _D, _D, _D]),
             "orc_pixel_moments": (None, [P, dbl, dbl, i64, i64, _D, O, _D, _D]),
             "orc_gh_weights": (None, [dbl, _D]),
+            "orc_bs3_trajectory": (i64, [P, dbl, ctypes.POINTER(BS3Opts), i64, _D, _D, _D]),
+            "orc_build_matrix_bs3": (None, [P, dbl, ctypes.POINTER(BS3Opts), i64, i64, _D, O, _D, _D, _D, _I32]),
+            "orc_bs3_single_step": (None, [P, dbl, dbl, _D, _D, _D]),
+            "orc_jacobi_rot": (dbl, [P, dbl, _D]),
             "orc_max_threads": (i32, []),
             "orc_set_threads": (None, [i32]),
         }
@@ -166,6 +178,67 @@ def drift(pot: Pot, omega: float, dt: float, nsteps: int, ics: np.ndarray) -> np
     out = np.zeros(len(ics))
     lib().orc_drift(ctypes.byref(pot), omega, dt, nsteps, len(ics), _dp(ics), _dp(out))
     return out
+
+
+# ---------------------------------------------------------------------------
+# The paper's adaptive integrator (Sec. 2.2.2): Bogacki-Shampine 3(2) in the
+# bar frame, a fixed number of accepted steps, samples weighted by their step
+# ---------------------------------------------------------------------------
+def bs3_opts(rtol: float = 1e-4, h0: float = 5.11356e-4, safety: float = 0.9, fac_min: float = 0.2,
+             fac_max: float = 5.0, fixed: bool = False, max_reject: int = 50) -> BS3Opts:
+    """Controller readings (the paper gives only rtol = 1e-4 and the step count):
+    error ratio max(|e_x| / (rtol max|x|), |e_v| / (rtol max|v|)) over the step,
+    next step h (safety r^(-1/3)) clipped to [fac_min, fac_max] h, first trial
+    step 0.5 Myr."""
+    return BS3Opts(rtol=rtol, h0=h0, safety=safety, fac_min=fac_min, fac_max=fac_max, fixed=int(fixed),
+                   max_reject=max_reject)
+
+
+def bs3_trajectory(pot: Pot, omega: float, opts: BS3Opts, nsteps: int, ic):
+    """(times (nsteps+1,), rotating-frame states (nsteps+1, 6), rejected trial
+    steps; -1 when the orbit was abandoned) from an inertial initial condition."""
+    ic = np.ascontiguousarray(ic, dtype=np.float64).reshape(6)
+    ts = np.zeros(nsteps + 1)
+    ys = np.zeros((nsteps + 1, 6))
+    rej = lib().orc_bs3_trajectory(ctypes.byref(pot), omega, ctypes.byref(opts), nsteps, _dp(ic), _dp(ts), _dp(ys))
+    return ts, ys, int(rej)
+
+
+def rotating_to_inertial(omega: float, t: np.ndarray, ys: np.ndarray) -> np.ndarray:
+    """Rotating-frame states at times t -> inertial (x, v): rotate the position and
+    v_rot + Omega z^ x x by R_z(Omega t)."""
+    t = np.asarray(t, dtype=np.float64)
+    c, s = np.cos(omega * t), np.sin(omega * t)
+    x, y, z = ys[:, 0], ys[:, 1], ys[:, 2]
+    vx, vy, vz = ys[:, 3] - omega * y, ys[:, 4] + omega * x, ys[:, 5]
+    return np.stack([c * x - s * y, s * x + c * y, z, c * vx - s * vy, s * vx + c * vy, vz], 1)
+
+
+def bs3_single_step(pot: Pot, omega: float, h: float, y):
+    """One step from a rotating-frame state: (third-order y_new, y_new - embedded second order)."""
+    y = np.ascontiguousarray(y, dtype=np.float64).reshape(6)
+    yn, err = np.zeros(6), np.zeros(6)
+    lib().orc_bs3_single_step(ctypes.byref(pot), omega, h, _dp(y), _dp(yn), _dp(err))
+    return yn, err
+
+
+def jacobi_rot(pot: Pot, omega: float, y) -> float:
+    y = np.ascontiguousarray(y, dtype=np.float64).reshape(6)
+    return lib().orc_jacobi_rot(ctypes.byref(pot), omega, _dp(y))
+
+
+def build_matrix_bs3(pot: Pot, omega: float, opts: BS3Opts, nsteps: int, ics: np.ndarray, obs: "Obs",
+                     gh_v0s: Optional[np.ndarray] = None):
+    """Orbit matrix (N, M) from the adaptive integrator: sample weights h_n / t_total
+    (Sec. 2.2.4), shared by the mirror copies."""
+    ics = np.ascontiguousarray(ics, dtype=np.float64).reshape(-1, 6)
+    M = n_rows(obs)
+    U = np.zeros((len(ics), M))
+    drift = np.zeros(len(ics)); status = np.zeros(len(ics), dtype=np.int32)
+    lib().orc_build_matrix_bs3(ctypes.byref(pot), omega, ctypes.byref(opts), nsteps, len(ics), _dp(ics),
+                               ctypes.byref(obs), _gh_arg(obs, gh_v0s), _dp(U), _dp(drift),
+                               status.ctypes.data_as(_I32))
+    return U, drift, status
 
 
 # ---------------------------------------------------------------------------

@@ -389,12 +389,13 @@ static double hermite(int m, double w)
 
 /* Contribution of one sample (bar-frame position xb and inertial velocity in
  * bar axes vb) to an orbit's column, for each of the four mirror copies of
- * Table 1.  `col` is indexed by row; mass rows get +1 per copy (integer
- * counts held exactly in double), GH rows get 2 sqrt(pi) alpha(w) H_m(w)
- * (mass-weighted linearisation of the GH moments, Eq. GH and the Rix et al.
- * 1997 estimator the paper cites).  gh_v0s: per pixel (v0, s). */
+ * Table 1.  `col` is indexed by row; mass rows get +wt per copy (wt = 1 for
+ * the fixed-step integrator: integer counts held exactly in double), GH rows
+ * get wt 2 sqrt(pi) alpha(w) H_m(w) (mass-weighted linearisation of the GH
+ * moments, Eq. GH and the Rix et al. 1997 estimator the paper cites).
+ * gh_v0s: per pixel (v0, s). */
 static void bin_sample(const orc_obs* o, const double R[9], const double* gh_v0s,
-                       const double xb[3], const double vb[3], double* col)
+                       const double xb[3], const double vb[3], double wt, double* col)
 {
     static const double sx[4] = {1, 1, -1, -1}, sz[4] = {1, -1, 1, -1};
     int64_t nd = (int64_t)o->nR * o->nphi * o->nz;
@@ -411,7 +412,7 @@ static void bin_sample(const orc_obs* o, const double R[9], const double* gh_v0s
         int iphi = bin_index(ph, 0.0, 2.0 * ORC_PI / o->nphi, o->nphi + 1);
         if (iphi == o->nphi) iphi = 0;   /* phi rounded up to exactly 2 pi */
         int iz = bin_index(p[2], o->zmin, (o->zmax - o->zmin) / o->nz, o->nz);
-        if (iR >= 0 && iphi >= 0 && iz >= 0) col[((int64_t)iR * o->nphi + iphi) * o->nz + iz] += 1.0;
+        if (iR >= 0 && iphi >= 0 && iz >= 0) col[((int64_t)iR * o->nphi + iphi) * o->nz + iz] += wt;
         /* sky projection (Eq. Euler): X = x', Y = y', v_los = v'_z */
         double X = R[0] * p[0] + R[1] * p[1] + R[2] * p[2];
         double Y = R[3] * p[0] + R[4] * p[1] + R[5] * p[2];
@@ -420,15 +421,15 @@ static void bin_sample(const orc_obs* o, const double R[9], const double* gh_v0s
         int iy = bin_index(Y, o->y0, o->dy, o->ny);
         if (ix < 0 || iy < 0) continue;
         int64_t pix = (int64_t)iy * o->nx + ix;
-        col[nd + pix] += 1.0;
+        col[nd + pix] += wt;
         if (o->gh) {
             double v0 = gh_v0s[2 * pix], s = gh_v0s[2 * pix + 1];
             double w = (V - v0) / s;
             double al = exp(-0.5 * w * w) / sqrt(2.0 * ORC_PI);
-            for (int m = 1; m <= 4; ++m) col[nd + np + 4 * pix + (m - 1)] += 2.0 * sqrt(ORC_PI) * al * hermite(m, w);
+            for (int m = 1; m <= 4; ++m) col[nd + np + 4 * pix + (m - 1)] += wt * 2.0 * sqrt(ORC_PI) * al * hermite(m, w);
         } else {
             int iv = bin_index(V, o->v0, o->dv, o->nv);
-            if (iv >= 0) col[nd + np + pix * o->nv + iv] += 1.0;
+            if (iv >= 0) col[nd + np + pix * o->nv + iv] += wt;
         }
     }
 }
@@ -456,7 +457,7 @@ static int orbit_column(const orc_pot* p, double omega, double dt, int64_t nstep
         double xb[3] = {c * x[0] + s * x[1], -s * x[0] + c * x[1], x[2]};
         double vb[3] = {c * v[0] + s * v[1], -s * v[0] + c * v[1], v[2]};
         if (!isfinite(xb[0] + xb[1] + xb[2] + vb[0] + vb[1] + vb[2])) { worst = NAN; break; }
-        bin_sample(o, R, gh_v0s, xb, vb, col);
+        bin_sample(o, R, gh_v0s, xb, vb, 1.0, col);
     }
     if (drift_out) *drift_out = worst;
     int status = isnan(worst) ? 2 : (worst > 0.1 ? 1 : 0);
@@ -558,6 +559,203 @@ void orc_pixel_moments(const orc_pot* p, double omega, double dt, int64_t nsteps
         free(acc);
         free(mine);
     }
+}
+
+/* ---------------------------------------------------------------------- */
+/* The paper's own integrator (Sec. 2.2.2): the third-order adaptive        */
+/* Runge-Kutta pair of Bogacki & Shampine (1989) with a relative tolerance  */
+/* (1e-4 in the paper), run for a fixed number of accepted steps in the     */
+/* frame that rotates with the bar (the bar at rest along x); the total     */
+/* time then differs from orbit to orbit.  Each sample is weighted by the   */
+/* step that produced it over the orbit's total time (Sec. 2.2.4).          */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    double rtol;              /* relative tolerance on |x| and on |v| */
+    double h0;                /* first trial step */
+    double safety, fac_min, fac_max;   /* step-size controller */
+    int32_t fixed;            /* 1: every step accepted with h = h0 (no control) */
+    int32_t max_reject;       /* consecutive rejected steps that end the orbit */
+} orc_bs3_opts;
+
+/* Equations of motion in the frame rotating at omega about z (bar static):
+ * dx/dt = v, dv/dt = -grad Phi(x) - 2 Omega x v - Omega x (Omega x x)
+ *                  = a(x) + 2 omega (v_y, -v_x, 0) + omega^2 (x, y, 0). */
+static void rot_rhs(const orc_pot* p, double omega, const double y[6], double f[6])
+{
+    double phi, a[3];
+    pot_static(p, ORC_DISC | ORC_HALO | ORC_BAR | ORC_TEST, y, &phi, a);
+    f[0] = y[3];
+    f[1] = y[4];
+    f[2] = y[5];
+    f[3] = a[0] + 2.0 * omega * y[4] + omega * omega * y[0];
+    f[4] = a[1] - 2.0 * omega * y[3] + omega * omega * y[1];
+    f[5] = a[2];
+}
+
+/* One Bogacki-Shampine step of size h from y, where k1 = f(y).  Stages at
+ * h/2 and 3h/4; third-order solution y_new = y + h (2 k1 + 3 k2 + 4 k3)/9;
+ * k4 = f(y_new) (reused as the next step's k1); the embedded second-order
+ * solution z = y + h (7 k1/24 + k2/4 + k3/3 + k4/8); err = y_new - z. */
+static void bs3_step(const orc_pot* p, double omega, double h, const double y[6], const double k1[6],
+                     double y_new[6], double k4[6], double err[6])
+{
+    double k2[6], k3[6], t[6];
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + 0.5 * h * k1[i];
+    rot_rhs(p, omega, t, k2);
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + 0.75 * h * k2[i];
+    rot_rhs(p, omega, t, k3);
+    for (int i = 0; i < 6; ++i) y_new[i] = y[i] + h * (2.0 * k1[i] + 3.0 * k2[i] + 4.0 * k3[i]) / 9.0;
+    rot_rhs(p, omega, y_new, k4);
+    for (int i = 0; i < 6; ++i) {
+        double z = y[i] + h * (7.0 * k1[i] / 24.0 + k2[i] / 4.0 + k3[i] / 3.0 + k4[i] / 8.0);
+        err[i] = y_new[i] - z;
+    }
+}
+
+static double norm3(const double* a) { return sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]); }
+
+/* Error ratio of a step: the position and velocity parts of err each against
+ * rtol times the larger of their magnitudes before and after the step. */
+static double bs3_ratio(double rtol, const double y[6], const double yn[6], const double err[6])
+{
+    double sx = rtol * fmax(norm3(y), norm3(yn)), sv = rtol * fmax(norm3(y + 3), norm3(yn + 3));
+    return fmax(norm3(err) / fmax(sx, 1e-300), norm3(err + 3) / fmax(sv, 1e-300));
+}
+
+/* Inertial initial condition at t = 0 (bar frame = inertial frame then) ->
+ * rotating-frame state: v_rot = v - Omega z^ x x. */
+static void to_rotating(double omega, const double* ic, double y[6])
+{
+    y[0] = ic[0]; y[1] = ic[1]; y[2] = ic[2];
+    y[3] = ic[3] + omega * ic[1];
+    y[4] = ic[4] - omega * ic[0];
+    y[5] = ic[5];
+}
+
+/* Jacobi energy in the rotating frame: |v_rot|^2/2 + Phi(x) - omega^2 (x^2 + y^2)/2
+ * (equal to the inertial-frame form |v|^2/2 + Phi - omega (x v_y - y v_x)). */
+static double jacobi_rot(const orc_pot* p, double omega, const double y[6])
+{
+    double phi, a[3];
+    pot_static(p, ORC_DISC | ORC_HALO | ORC_BAR | ORC_TEST, y, &phi, a);
+    return 0.5 * (y[3] * y[3] + y[4] * y[4] + y[5] * y[5]) + phi - 0.5 * omega * omega * (y[0] * y[0] + y[1] * y[1]);
+}
+
+/* Advance one accepted step: on entry y, k1 = f(y) and *h the trial step; on
+ * exit y, k1 for the new state, *h_used the step taken and *h the next trial
+ * step.  Returns the rejected trials, or -1 after max_reject of them in a row
+ * or a non-finite state. */
+static int bs3_advance(const orc_pot* p, double omega, const orc_bs3_opts* o, double y[6], double k1[6], double* h,
+                       double* h_used)
+{
+    double yn[6], k4[6], err[6];
+    int rejected = 0;
+    for (;;) {
+        double hh = o->fixed ? o->h0 : *h;
+        bs3_step(p, omega, hh, y, k1, yn, k4, err);
+        double r = o->fixed ? 0.0 : bs3_ratio(o->rtol, y, yn, err);
+        int finite = 1;
+        for (int i = 0; i < 6; ++i) finite &= isfinite(yn[i]);
+        if (!finite || isnan(r)) return -1;
+        double grow = r > 0.0 ? o->safety * pow(r, -1.0 / 3.0) : o->fac_max;
+        grow = fmin(o->fac_max, fmax(o->fac_min, grow));
+        if (r <= 1.0) {
+            memcpy(y, yn, sizeof yn);
+            memcpy(k1, k4, sizeof k4);
+            *h_used = hh;
+            *h = hh * grow;
+            return rejected;
+        }
+        *h = hh * grow;
+        if (++rejected >= o->max_reject) return -1;
+    }
+}
+
+/* nsteps accepted steps from an inertial initial condition.  ts[n] (n = 0..nsteps)
+ * the times and ys[6 n + k] the rotating-frame states (both nullable).  Returns the
+ * total number of rejected trial steps, or -1 if the orbit had to be abandoned. */
+int64_t orc_bs3_trajectory(const orc_pot* p, double omega, const orc_bs3_opts* o, int64_t nsteps, const double* ic,
+                           double* ts, double* ys)
+{
+    double y[6], k1[6], h = o->h0, t = 0.0;
+    int64_t rej = 0;
+    to_rotating(omega, ic, y);
+    rot_rhs(p, omega, y, k1);
+    if (ts) ts[0] = 0.0;
+    if (ys) memcpy(ys, y, sizeof y);
+    for (int64_t n = 0; n < nsteps; ++n) {
+        double hu;
+        int r = bs3_advance(p, omega, o, y, k1, &h, &hu);
+        if (r < 0) return -1;
+        rej += r;
+        t += hu;
+        if (ts) ts[n + 1] = t;
+        if (ys) memcpy(ys + 6 * (n + 1), y, sizeof y);
+    }
+    return rej;
+}
+
+/* One orbit's column from the adaptive integrator: the sample after accepted
+ * step n (n = 1..nsteps) has weight h_n / t_total (Sec. 2.2.4) shared by its
+ * mirror copies; its bar-frame position is the state's x and its velocity the
+ * inertial one in bar axes, v_rot + Omega z^ x x (Sec. 2.2.2: velocities are
+ * taken back to the inertial frame for the comparison with data).  Status as
+ * in orbit_column; 2 also when the step control gave up. */
+static int orbit_column_bs3(const orc_pot* p, double omega, const orc_bs3_opts* opt, int64_t nsteps,
+                            const double* ic, const orc_obs* o, const double R[9], const double* gh_v0s, double* col,
+                            double* drift_out)
+{
+    int64_t M = orc_n_rows(o);
+    memset(col, 0, M * sizeof(double));
+    double y[6], k1[6], h = opt->h0, total = 0.0;
+    to_rotating(omega, ic, y);
+    rot_rhs(p, omega, y, k1);
+    double e0 = jacobi_rot(p, omega, y), worst = 0.0;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        double hu;
+        if (bs3_advance(p, omega, opt, y, k1, &h, &hu) < 0) { worst = NAN; break; }
+        total += hu;
+        double d = fabs(jacobi_rot(p, omega, y) - e0) / fabs(e0);
+        if (isnan(d) || d > worst) worst = d;
+        double vb[3] = {y[3] - omega * y[1], y[4] + omega * y[0], y[5]};
+        bin_sample(o, R, gh_v0s, y, vb, hu, col);
+    }
+    if (drift_out) *drift_out = worst;
+    int status = isnan(worst) ? 2 : (worst > 0.1 ? 1 : 0);
+    double norm = 1.0 / ((double)(o->mirror4 ? 4 : 1) * total);
+    for (int64_t r = 0; r < M; ++r) col[r] = status ? 0.0 : col[r] * norm;
+    return status;
+}
+
+/* Orbit matrix from the adaptive integrator, orbit-major as orc_build_matrix. */
+void orc_build_matrix_bs3(const orc_pot* p, double omega, const orc_bs3_opts* opt, int64_t nsteps, int64_t n_orb,
+                          const double* ics, const orc_obs* o, const double* gh_v0s, double* U, double* drift,
+                          int32_t* status)
+{
+    double R[9];
+    orc_euler_matrix(o->alpha, o->beta, o->gamma, R);
+    int64_t M = orc_n_rows(o);
+#pragma omp parallel for schedule(dynamic, 2)
+    for (int64_t i = 0; i < n_orb; ++i) {
+        double d;
+        int st = orbit_column_bs3(p, omega, opt, nsteps, ics + 6 * i, o, R, gh_v0s, U + i * M, &d);
+        if (drift) drift[i] = d;
+        if (status) status[i] = st;
+    }
+}
+
+/* One step from a rotating-frame state (for the order pins): y_new and err. */
+void orc_bs3_single_step(const orc_pot* p, double omega, double h, const double* y, double* y_new, double* err)
+{
+    double k1[6], k4[6];
+    rot_rhs(p, omega, y, k1);
+    bs3_step(p, omega, h, y, k1, y_new, k4, err);
+}
+
+/* Jacobi energy of a rotating-frame state. */
+double orc_jacobi_rot(const orc_pot* p, double omega, const double* y)
+{
+    return jacobi_rot(p, omega, y);
 }
 
 /* Per-sample Gauss-Hermite row weights 2 sqrt(pi) alpha(w) H_m(w), m = 0..4. */
