@@ -287,6 +287,22 @@ def cpu_sample(W, n_orb=N_CPU_SAMPLE):
     return value, cores, sample, dt
 
 
+def cpu_single_thread(W, n_orb=64):
+    """The same oracle work on one host thread (orbit-steps/s), beside the all-core figure."""
+    import oracle
+    pot = oracle.make_pot(W["potential"])
+    obs = oracle.make_obs(W["grid"])
+    ics = inputs.disc_ics(W["potential"], n_orb, seed=W["seeds"]["ic"])
+    cores = oracle.max_threads()
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.build_matrix(pot, W["omega_p"], W["dt"], W["nsteps"], ics, obs)
+        return n_orb * W["nsteps"] / (time.perf_counter() - t0)
+    finally:
+        oracle.set_threads(cores)
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -305,7 +321,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample_orbits": 512, "nsteps": W["nsteps"]}, "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "orbit-steps/s", "cores": cores, "kind": "oracle",
-                             "sample": sample.replace(str(N_CPU_SAMPLE), "512")},
+                             "sample": sample.replace(str(N_CPU_SAMPLE), "512"),
+                             "single_thread_value": cpu_single_thread(W)},
             "e2e": {"value": value, "unit": "orbit-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -452,7 +469,8 @@ def run_sw(args):
     cpu = None
     if not args.no_cpu:
         v, cores, sample, _ = cpu_sample(W)
-        cpu = {"value": v, "unit": "orbit-steps/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": "orbit-steps/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread_value": cpu_single_thread(W)}
 
     value = N * S * args.steps * world / elapsed
     line = {"metric": "orbit-steps/s (whole model evaluations, FP32 batched vs FP64 plain at matched chi^2)",
