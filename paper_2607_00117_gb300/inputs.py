@@ -163,6 +163,120 @@ def dither(ics: np.ndarray, n: int, seed: int, p: dict, dx: float = 0.1, dv_frac
     return np.ascontiguousarray(base + off)
 
 
+# ---------------------------------------------------------------------------
+# The paper's initial conditions (Sec. 2.2.1, with h_R = 3.5 and h_z = 1.2 kpc
+# from Sec. 3.2): positions from p(R, z) ~ R exp(-R/h_R) exp(-|z|/h_z),
+# velocities from the Jeans equations of that tracer in the azimuthally
+# averaged potential (disc + halo + bar), drawn as Gaussians.
+# ---------------------------------------------------------------------------
+def _mn_phi(M, a, b, R, z):
+    return -G * M / np.sqrt(R * R + (a + np.sqrt(z * z + b * b)) ** 2)
+
+
+def _nfw_consts(p):
+    H = p.get("H0", 70.0) / 1000.0
+    rho_c = 3 * H * H / (8 * math.pi * G)
+    Rv = (3 * p["halo_M200"] / (4 * math.pi * 200 * rho_c)) ** (1.0 / 3.0)
+    c = p["halo_c"]
+    return p["halo_M200"] / (math.log(1 + c) - c / (1 + c)), Rv / c
+
+
+def _bar_phi(M, L, b, c, x, y, z):
+    """Needle-convolved Miyamoto-Nagai bar (half-length L), with each log argument
+    rationalised where its two terms would cancel."""
+    Z = b + np.sqrt(z * z + c * c)
+    q2 = y * y + Z * Z
+    Tm = np.sqrt((L - x) ** 2 + q2)
+    Tp = np.sqrt((L + x) ** 2 + q2)
+    um, up = x - L, x + L
+    num = np.where(um >= 0, um + Tm, q2 / np.maximum(Tm - um, 1e-300))
+    den = np.where(up >= 0, up + Tp, q2 / np.maximum(Tp - up, 1e-300))
+    return G * M / (2 * L) * np.log(num / den)
+
+
+def axisym_potential(p: dict, R, z, n_phi: int = 32):
+    """Disc + halo + the bar averaged over azimuth (trapezoid rule, exact for the
+    bar's low azimuthal harmonics) at cylindrical (R, z)."""
+    R = np.asarray(R, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    out = _mn_phi(p["disc_M"], p["disc_a"], p["disc_b"], R, z)
+    if p.get("halo_M200", 0.0) > 0:
+        Mdm, rs = _nfw_consts(p)
+        r = np.maximum(np.sqrt(R * R + z * z), 1e-12)
+        out = out - G * Mdm * np.log1p(r / rs) / r
+    if p.get("bar_M", 0.0) > 0:
+        ph = 2 * math.pi * (np.arange(n_phi) + 0.5) / n_phi
+        xs = R[..., None] * np.cos(ph)
+        ys = R[..., None] * np.sin(ph)
+        out = out + _bar_phi(p["bar_M"], p["bar_L"], p["bar_b"], p["bar_c"], xs, ys, z[..., None]).mean(-1)
+    return out
+
+
+def jeans_moments(phi_fn, R, z, h_R: float, h_z: float, beta_z: float = 0.2, n_quad: int = 40):
+    """Second moments of a tracer nu ~ exp(-R/h_R - |z|/h_z) in an axisymmetric
+    potential phi_fn(R, z), with a velocity ellipsoid aligned with the cylinder and
+    sigma_R^2 = sigma_z^2 / (1 - beta_z):
+      nu sigma_z^2 = int_|z|^inf nu dPhi/dz' dz'   (vertical equation; Gauss-Laguerre
+                                                    in s = (z' - |z|)/h_z, exact weight),
+      <v_phi^2> = b (sigma_z^2 + R d(nu sigma_z^2)/dR / nu) + R dPhi/dR,  b = 1/(1-beta_z).
+    Returns (sigma_R^2, sigma_z^2, <v_phi^2>, v_c^2 = R dPhi/dR)."""
+    R = np.asarray(R, dtype=np.float64)
+    az = np.abs(np.asarray(z, dtype=np.float64))
+    s, w = np.polynomial.laguerre.laggauss(n_quad)
+
+    def sig2(RR):
+        zq = az[..., None] + h_z * s
+        d = 1e-4 * (1.0 + zq)
+        fz = (phi_fn(RR[..., None], zq + d) - phi_fn(RR[..., None], zq - d)) / (2 * d)
+        return h_z * (fz * w).sum(-1)
+
+    dR = 1e-3 * (1.0 + R)
+    s0 = sig2(R)
+    ds = (sig2(R + dR) - sig2(np.maximum(R - dR, 0.0))) / (R + dR - np.maximum(R - dR, 0.0))
+    fR = (phi_fn(R + dR, az) - phi_fn(np.maximum(R - dR, 0.0), az)) / (R + dR - np.maximum(R - dR, 0.0))
+    vc2 = R * fR
+    b = 1.0 / (1.0 - beta_z)
+    vphi2 = b * (s0 + R * (ds - s0 / h_R)) + vc2
+    return b * s0, s0, vphi2, vc2
+
+
+def paper_ics(p: dict, n: int, seed: int, h_R: float = 3.5, h_z: float = 1.2, beta_z: float = 0.2,
+              n_grid: int = 48) -> np.ndarray:
+    """(n, 6) inertial initial conditions after Sec. 2.2.1: R ~ Gamma(2, h_R) and
+    |z| ~ Exp(h_z) (the density p(R, z) ~ R exp(-R/h_R) exp(-|z|/h_z)), phi uniform;
+    v_R, v_z ~ N(0, sigma_R), N(0, sigma_z); v_phi ~ N(vbar_phi, sigma_phi) with
+    sigma_phi = sigma_R and vbar_phi = sqrt(<v_phi^2> - sigma_phi^2), the mean
+    streaming the Jeans equations give (jeans_moments), tabulated on an
+    n_grid x n_grid (R, |z|) grid and interpolated bilinearly."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    R = rng.gamma(2.0, h_R, n)
+    z = rng.exponential(h_z, n) * np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    ph = 2 * math.pi * rng.random(n)
+    gR = np.concatenate([[0.0], np.geomspace(0.02, max(R.max(), 0.03) * 1.001, n_grid - 1)])
+    gz = np.concatenate([[0.0], np.geomspace(0.01, max(np.abs(z).max(), 0.02) * 1.001, n_grid - 1)])
+    RR, ZZ = np.meshgrid(gR, gz, indexing="ij")
+    sR2, sz2, vp2, _ = jeans_moments(lambda a, b: axisym_potential(p, a, b), RR, ZZ, h_R, h_z, beta_z)
+    sR2, sz2 = np.maximum(sR2, 0.0), np.maximum(sz2, 0.0)
+    vbar2 = np.maximum(vp2 - sR2, 0.0)
+
+    def interp(tab, x, y):
+        i = np.clip(np.searchsorted(gR, x) - 1, 0, n_grid - 2)
+        j = np.clip(np.searchsorted(gz, y) - 1, 0, n_grid - 2)
+        tx = (x - gR[i]) / (gR[i + 1] - gR[i])
+        ty = (y - gz[j]) / (gz[j + 1] - gz[j])
+        return ((1 - tx) * (1 - ty) * tab[i, j] + tx * (1 - ty) * tab[i + 1, j] + (1 - tx) * ty * tab[i, j + 1]
+                + tx * ty * tab[i + 1, j + 1])
+
+    az = np.abs(z)
+    sr, szz = np.sqrt(interp(sR2, R, az)), np.sqrt(interp(sz2, R, az))
+    vbar = np.sqrt(interp(vbar2, R, az))
+    vR = sr * rng.standard_normal(n)
+    vz = szz * rng.standard_normal(n)
+    vph = vbar + sr * rng.standard_normal(n)
+    c, sn = np.cos(ph), np.sin(ph)
+    return np.ascontiguousarray(np.stack([R * c, R * sn, z, vR * c - vph * sn, vR * sn + vph * c, vz], 1))
+
+
 def plummer_ics(M: float, a: float, n: int, seed: int, rcut: float = 20.0) -> np.ndarray:
     """Plummer sphere from its isotropic distribution function f(E) ~ (-E)^(7/2)
     by the Aarseth, Henon & Wielen (1974) recipe (radii beyond rcut * a
