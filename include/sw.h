@@ -245,6 +245,11 @@ int64_t sw_launch_count(const sw_ctx* ctx);
  *                           orbit_direct_max orbits, ADMM otherwise; 1: always the active set; 2: always ADMM
  *                           (the paper's solver, Sec. 2.3, with FP64 refinement and the exact polish)
  *  "chol_coop" (0/1)        active set: Cholesky and its inverse in one cooperative launch (default 0)
+ *  "integrator" (0/1)       sw_project's integrator: 0 (default) kick-drift-kick at the fixed dt in the inertial
+ *                           frame; 1 the paper's adaptive Bogacki-Shampine 3(2) pair (Sec. 2.2.2) in the frame
+ *                           rotating with the bar, nsteps accepted steps from a first trial step dt, each sample
+ *                           weighted by its step over the orbit's total time (Sec. 2.2.4)
+ *  "bs3_rtol" (0, 1)        relative tolerance of the adaptive integrator on |x| and |v| per step (default 1e-4)
  *  "as_grow" (>= 0)         active set: at most max(as_block, as_grow |F|) orbits enter per step (default 0)
  *  "as_candidates" (>= 0)   active set: initial candidate-set size, 0 for 2 M (default 0)
  *  "ws_factor" (> 0)        initial working-set size in units of M (default 0.6; it grows to take in the

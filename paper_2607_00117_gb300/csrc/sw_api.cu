@@ -155,10 +155,11 @@ static void ctx_release(sw_ctx* ctx)
     cudaStreamSynchronize(ctx->stream);
     ctx->harvest();
     void* bufs[] = {ctx->d_soa, ctx->d_cs, ctx->d_aos, ctx->d_drift, ctx->d_status, ctx->d_stats, ctx->d_ghtab,
-                    ctx->d_mlp, ctx->d_split, ctx->d_chol};
+                    ctx->d_mlp, ctx->d_split, ctx->d_chol, ctx->d_ttotal};
     for (void* b : bufs)
         if (b) cudaFree(b);
     ctx->d_soa = ctx->d_cs = ctx->d_ghtab = ctx->d_mlp = ctx->d_split = ctx->d_chol = nullptr;
+    ctx->d_ttotal = nullptr;
     ctx->d_aos = ctx->d_drift = nullptr;
     ctx->d_status = nullptr;
     ctx->d_stats = nullptr;
@@ -503,15 +504,29 @@ static sw_status project_impl(sw_ctx* ctx, const GridT<T>& g, const double* gh_v
     if (s != SW_OK) return fail(s);
     if ((e = cudaMemsetAsync(ctx->d_stats, 0, 4 * sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
         return fail(ctx->cuda_fail(e, "memset"));
-    if ((e = launch_orbit_bin<T>(ctx, m, (const T*)ctx->d_soa, N, ctx->nsteps, ctx->opt.ej_every, ctx->d_drift,
-                                 ctx->d_status, ctx->d_stats)) != cudaSuccess)
-        return fail(ctx->cuda_fail(e, "orbit kernel"));
-    if ((e = launch_zero_flagged<T>(ctx, U->d, M, N, ctx->d_status)) != cudaSuccess)
-        return fail(ctx->cuda_fail(e, "zero flagged"));
-    const int64_t count_rows = g.gh ? g.nd + g.npix : M;
-    const double norm = 1.0 / ((double)g.ncopy * (double)ctx->nsteps);
-    if ((e = launch_finalize<T>(ctx, U->d, M, N, count_rows, norm)) != cudaSuccess)
-        return fail(ctx->cuda_fail(e, "finalize"));
+    if (ctx->opt.integrator == 1) {
+        // the paper's adaptive Bogacki-Shampine integrator in the bar frame, step-weighted samples
+        s = ctx->ensure(&ctx->d_ttotal, &ctx->ttotal_cap, (size_t)N * sizeof(double), "integration times");
+        if (s != SW_OK) return fail(s);
+        if ((e = launch_orbit_bin_bs3<T>(ctx, m, (const T*)ctx->d_soa, N, ctx->nsteps, ctx->opt.ej_every,
+                                         ctx->opt.bs3_rtol, ctx->d_drift, ctx->d_status, (double*)ctx->d_ttotal,
+                                         ctx->d_stats)) != cudaSuccess)
+            return fail(ctx->cuda_fail(e, "orbit kernel (adaptive)"));
+        if ((e = launch_zero_flagged<T>(ctx, U->d, M, N, ctx->d_status)) != cudaSuccess)
+            return fail(ctx->cuda_fail(e, "zero flagged"));
+        if ((e = launch_finalize_w<T>(ctx, U->d, M, N, (const double*)ctx->d_ttotal, g.ncopy)) != cudaSuccess)
+            return fail(ctx->cuda_fail(e, "finalize"));
+    } else {
+        if ((e = launch_orbit_bin<T>(ctx, m, (const T*)ctx->d_soa, N, ctx->nsteps, ctx->opt.ej_every, ctx->d_drift,
+                                     ctx->d_status, ctx->d_stats)) != cudaSuccess)
+            return fail(ctx->cuda_fail(e, "orbit kernel"));
+        if ((e = launch_zero_flagged<T>(ctx, U->d, M, N, ctx->d_status)) != cudaSuccess)
+            return fail(ctx->cuda_fail(e, "zero flagged"));
+        const int64_t count_rows = g.gh ? g.nd + g.npix : M;
+        const double norm = 1.0 / ((double)g.ncopy * (double)ctx->nsteps);
+        if ((e = launch_finalize<T>(ctx, U->d, M, N, count_rows, norm)) != cudaSuccess)
+            return fail(ctx->cuda_fail(e, "finalize"));
+    }
     ctx->last_proj_n = N;
     ctx->live_matrices++;
     *U_out = U;
@@ -908,6 +923,12 @@ extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value)
     } else if (!strcmp(key, "chol_coop")) {
         if (!(value == 0 || value == 1)) return SW_EINVAL;
         ctx->opt.chol_coop = (int)value;
+    } else if (!strcmp(key, "integrator")) {
+        if (!(value == 0 || value == 1)) return SW_EINVAL;
+        ctx->opt.integrator = (int)value;
+    } else if (!strcmp(key, "bs3_rtol")) {
+        if (!(value > 0.0 && value < 1.0)) return SW_EINVAL;
+        ctx->opt.bs3_rtol = value;
     } else if (!strcmp(key, "as_grow")) {
         if (!(value >= 0.0)) return SW_EINVAL;
         ctx->opt.as_grow = value;

@@ -34,6 +34,8 @@ struct Options {
     double as_grow = 0.0;        // active set: at most max(as_block, as_grow |F|) orbits enter per step
     int solver = 0;              // 0 auto, 1 active set, 2 ADMM (see solve_dispatch)
     int chol_coop = 0;           // Cholesky + inverse in one cooperative launch (0: per-step launches)
+    int integrator = 0;          // 0: kick-drift-kick at fixed dt; 1: adaptive Bogacki-Shampine 3(2) in the bar frame
+    double bs3_rtol = 1e-4;      // relative tolerance of the adaptive integrator
     int as_cg_max = 200;         // active set: conjugate-gradient steps per reduced solve
     double as_cg_tol = 0.05;     // active set: CG stops at max|r| <= as_cg_tol * kkt_tol * max|q|
     int as_solves = 400;         // active set: cap on reduced solves
@@ -93,6 +95,7 @@ struct sw_ctx {
     void* d_mlp = nullptr; size_t mlp_cap = 0;   // MLP activations
     void* d_split = nullptr; size_t split_cap = 0;   // FP64 vectors split into float hi + lo
     void* d_chol = nullptr; size_t chol_cap = 0;     // cooperative Cholesky: diagonal inverses, barrier
+    void* d_ttotal = nullptr; size_t ttotal_cap = 0;   // per-orbit integration time (adaptive integrator)
     // solve
     sw::SolveWS solve_ws;
     double solve_info[8] = {0, 0, 0, 0, 0, 0, 0, 0};

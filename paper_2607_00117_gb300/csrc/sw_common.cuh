@@ -95,6 +95,13 @@ template <typename T>
 cudaError_t launch_zero_flagged(sw_ctx* ctx, void* U, int64_t M, int64_t N, const uint8_t* status);
 template <typename T>
 cudaError_t launch_finalize(sw_ctx* ctx, void* U, int64_t M, int64_t N, int64_t count_rows, double norm);
+// the paper's adaptive integrator: step-weighted columns and the per-orbit integration time
+template <typename T>
+cudaError_t launch_orbit_bin_bs3(sw_ctx* ctx, const ModelT<T>& m, const T* soa, int64_t ld, int64_t nsteps,
+                                 int ej_every, double rtol, double* drift, uint8_t* status, double* t_total,
+                                 unsigned long long* stats);
+template <typename T>
+cudaError_t launch_finalize_w(sw_ctx* ctx, void* U, int64_t M, int64_t N, const double* t_total, int ncopy);
 template <typename T>
 cudaError_t launch_trajectory(sw_ctx* ctx, const ModelT<T>& m, const T* soa, int64_t ld, int64_t n,
                               int64_t nsteps, double* out);
