@@ -585,8 +585,8 @@ def run_batched(args):
 
 
 def run_surrogate(args):
-    """The learned chi^2 emulator at reduced fidelity (the survey's fallback for the
-    20k-model training set): 12-D box models of 2 000 orbits x 1 000 steps on a
+    """The learned chi^2 emulator at reduced fidelity (a 20k-model training set of
+    full-size models would take hours): 12-D box models of 2 000 orbits x 1 000 steps on a
     16 x 12 pixel GH grid, their exact chi^2_obs computed in batches of 64 models
     (one persistent launch each), the emulator trained by the library's kernels,
     its held-out error, and delayed-acceptance MCMC against plain Metropolis on the
