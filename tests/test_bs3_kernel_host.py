@@ -59,17 +59,19 @@ def harness(tmp_path_factory):
     return exe, d
 
 
-def _run(harness, p, Mdm, rs, omega, grid, ics, S, rtol):
+def _run(harness, p, Mdm, rs, omega, grid, ics, S, rtol, gh_v0s=None):
     exe, d = harness
     P = [p["disc_M"], p["disc_a"], p["disc_b"], Mdm, rs, p.get("bar_M", 0.0), p.get("bar_L", 1.0),
          p.get("bar_b", 1.0), p.get("bar_c", 1.0), omega, grid["incl"], grid.get("bar_angle", 0.0),
          inputs.DT_HALF_MYR, rtol, S, len(ics)]
     G = [grid["nx"], grid["ny"], grid["pix"], grid["nv"], grid["vmax"], grid["nR"], grid["nphi"], grid["nz"],
-         grid.get("Rmax", 10.0), grid.get("zmin", -3.0), grid.get("zmax", 3.0)]
+         grid.get("Rmax", 10.0), grid.get("zmin", -3.0), grid.get("zmax", 3.0), 1.0 if gh_v0s is not None else 0.0]
     fin, fout = d / "in.bin", d / "out.bin"
     with open(fin, "wb") as f:
         np.array(P + G, dtype=np.float64).tofile(f)
         np.ascontiguousarray(ics, dtype=np.float64).tofile(f)
+        if gh_v0s is not None:
+            np.ascontiguousarray(gh_v0s, dtype=np.float64).tofile(f)
     subprocess.run([str(exe), str(fin), str(fout)], check=True)
     return np.fromfile(fout, dtype=np.float64)
 
@@ -94,3 +96,24 @@ def test_bs3_device_functions_match_oracle(orc, harness, barred):
     np.testing.assert_allclose(th, t_o, rtol=1e-10)
     assert np.abs(Uh - Uo).sum(1).max() < 1e-9
     np.testing.assert_allclose(Uh[:, :500].sum(1), Uo[:, :500].sum(1), rtol=1e-10)
+
+
+def test_bs3_device_functions_gauss_hermite_rows(orc, harness):
+    """The same check with Gauss-Hermite rows: each copy in pixel p adds its step weight
+    times 2 sqrt(pi) alpha(w) H_m(w), w = (V - v0_p) / s_p."""
+    p = dict(inputs.DISC_HALO, **inputs.BAR)
+    Mdm, rs = orc.nfw_from_m200(p["halo_M200"], p["halo_c"], p.get("H0", 70.0))
+    grid = dict(inputs.WORKLOADS["barred_100k"]["grid"])
+    grid.update(nx=12, ny=10, nv=1, nR=6, nphi=8, nz=4, gh=1)
+    rng = np.random.default_rng(6)
+    v0s = np.stack([rng.normal(0, 40, 120), rng.uniform(60, 160, 120)], 1)
+    S = 400
+    ics = inputs.disc_ics(inputs.DISC_HALO, 30, seed=107)
+    raw = _run(harness, p, Mdm, rs, 40.0, grid, ics, S, 1e-4, gh_v0s=v0s)
+    obs = orc.make_obs(grid)
+    M = orc.n_rows(obs)
+    Uh = raw[:M * len(ics)].reshape(len(ics), M)
+    Uo, _, so = orc.build_matrix_bs3(orc.make_pot(p), 40.0, orc.bs3_opts(rtol=1e-4, h0=inputs.DT_HALF_MYR), S, ics,
+                                     obs, gh_v0s=v0s)
+    assert np.all(so == 0)
+    np.testing.assert_allclose(Uh, Uo, rtol=1e-9, atol=1e-12)
