@@ -474,6 +474,43 @@ def kkt_residual(H: np.ndarray, q: np.ndarray, w: np.ndarray) -> dict:
             "pg_norm2": float(pg @ pg)}
 
 
+def bootstrap_data(y: np.ndarray, sigma: np.ndarray, n_dens: int, xi: np.ndarray) -> np.ndarray:
+    """Bootstrap realisations of the data (Sec. 2.4): every observed row (surface density
+    and kinematics) perturbed by its error times a standard normal draw xi[b]; the
+    3-D density rows (the first n_dens) are not bootstrapped.  Returns (B, M)."""
+    Y = np.repeat(np.asarray(y, dtype=np.float64)[None, :], len(xi), axis=0)
+    Y[:, n_dens:] += sigma[None, n_dens:] * xi[:, n_dens:]
+    return Y
+
+
+def chi2_model(chi2_b: np.ndarray) -> float:
+    """Marginalised chi^2 over the bootstrap weight sets (Sec. 2.5): -2 ln of the
+    bootstrap-averaged likelihood exp(-chi2_b / 2), evaluated relative to the smallest
+    chi2_b so that no exponential over- or underflows:
+    chi2_min - 2 ln[(1/B) sum_b exp(-(chi2_b - chi2_min) / 2)]."""
+    c = np.asarray(chi2_b, dtype=np.float64)
+    cmin = c.min()
+    return float(cmin - 2.0 * np.log(np.mean(np.exp(-0.5 * (c - cmin)))))
+
+
+def bootstrap_solve(U_rows: np.ndarray, y: np.ndarray, sigma: np.ndarray, lam: float, n_dens: int,
+                    xi: np.ndarray):
+    """One NNLS per bootstrap realisation with the same matrix (Lawson-Hanson on the
+    normal equations, whose H is shared), and each weight set's observational chi^2
+    against the observed data (density rows left out, Sec. 2.5).  Returns the weights
+    (B, N), the chi2_b and the marginalised chi^2."""
+    Yb = bootstrap_data(y, sigma, n_dens, xi)
+    Ut = U_rows / sigma[:, None]
+    H = Ut.T @ Ut + (2.0 * lam / U_rows.shape[1]) * np.eye(U_rows.shape[1])
+    W = np.zeros((len(Yb), U_rows.shape[1]))
+    chi = np.zeros(len(Yb))
+    for b, yb in enumerate(Yb):
+        W[b] = nnls_lh_normal(H, Ut.T @ (yb / sigma))
+        r = (U_rows @ W[b] - y) / sigma
+        chi[b] = float(r[n_dens:] @ r[n_dens:])
+    return W, chi, chi2_model(chi)
+
+
 def admm_nnls(H: np.ndarray, q: np.ndarray, rho: Optional[float] = None, tol: float = 1e-12,
               max_iter: int = 200000) -> tuple:
     """The paper's solver (Sec. 2.3): ADMM splitting into an unconstrained

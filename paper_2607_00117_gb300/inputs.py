@@ -328,6 +328,12 @@ def noise(m: int, seed: int) -> np.ndarray:
     return np.random.Generator(np.random.PCG64(seed)).standard_normal(m)
 
 
+def bootstrap_noise(m: int, n_boot: int, seed: int) -> np.ndarray:
+    """(n_boot, m) standard normal draws for the bootstrap realisations of the data
+    (Sec. 2.4: 100 realisations of the observed maps perturbed by their errors)."""
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal((n_boot, m))
+
+
 def mock_sigma(y0: np.ndarray, blocks: dict, frac: float = 0.02, gh_err: Optional[np.ndarray] = None) -> np.ndarray:
     """Errors per row.  Mass rows: frac * max(y0, 0.01 * block mean).  GH rows
     (when gh_err = per-pixel (dh1, dh2, dh3, dh4) is given): dh_m * Sigma_p with
