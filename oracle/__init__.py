@@ -18,6 +18,7 @@ Contents
 from __future__ import annotations
 
 import ctypes
+import math
 import itertools
 import os
 import subprocess
@@ -156,6 +157,86 @@ def density(pot: Pot, xyz: np.ndarray, mask: int = DISC | HALO | BAR | TEST, bar
     rho = np.zeros(len(xyz))
     lib().orc_density_eval(ctypes.byref(pot), mask, len(xyz), _dp(xyz), _dp(rho), bar_nodes)
     return rho
+
+
+# ---------------------------------------------------------------------------
+# The paper's bar (Sec. 2.1.2, App. A): Dehnen & Aly (2023) T3 and V4 parent pairs
+# convolved with a needle along x, R^-n -> I_n (Eq. Rn_to_In)
+# ---------------------------------------------------------------------------
+_GL_X, _GL_W = np.polynomial.legendre.leggauss(48)
+
+
+def needle_In(x, y, Z, n: int, L: float, eta: float) -> np.ndarray:
+    """I_n(x, y, Z) = int_{x-L}^{x+L} f(x - x') [x'^2 + y^2 + Z^2]^(-n/2) dx' with
+    f(u) = [1 + eta (1 - 2|u|/L)] / (2L) (Eq. Rn_to_In), by 48-point Gauss-Legendre
+    quadrature on the pieces between x - L, 0, x and x + L (the integrand's peak at
+    x' = 0 and the needle's kink at x' = x)."""
+    x, y, Z = (np.asarray(v, dtype=np.float64) for v in np.broadcast_arrays(x, y, Z))
+    q2 = y * y + Z * Z
+    lo, hi = x - L, x + L
+    c1 = np.clip(0.0, lo, x)
+    c2 = np.clip(0.0, x, hi)
+    out = np.zeros_like(x)
+    for a, b in ((lo, c1), (c1, x), (x, c2), (c2, hi)):
+        half = 0.5 * (b - a)
+        xp = (0.5 * (a + b))[..., None] + half[..., None] * _GL_X
+        u = np.abs(x[..., None] - xp)
+        f = (1.0 + eta * (1.0 - 2.0 * u / L)) / (2.0 * L)
+        out += half * (f * (xp * xp + q2[..., None]) ** (-0.5 * n) * _GL_W).sum(-1)
+    return out
+
+
+def _da_terms(family: str, a: float, b: float, z):
+    """Coefficients c_n(z) of the parent pair, Phi = -G M sum_n c_n R^-n and
+    rho = M sum_n d_n R^-n (App. A), as functions of Z = a + zeta, zeta = sqrt(z^2 + b^2)."""
+    zeta = np.sqrt(np.asarray(z, dtype=np.float64) ** 2 + b * b)
+    Z = a + zeta
+    if family == "T3":
+        phi = {1: np.ones_like(Z), 3: a * (Z - a / 3.0), 5: a * a * Z * Z}
+        k = b * b / (4.0 * math.pi)
+        rho = {5: 3.0 * k * np.ones_like(Z),
+               7: k * 5.0 * a * Z * Z * (3.0 * zeta ** 2 - 2.0 * a * zeta + a * a) / zeta ** 3,
+               9: k * 35.0 * a * a * Z ** 4 / zeta ** 2}
+    elif family == "V4":
+        phi = {1: np.ones_like(Z), 3: a * (Z - 2.0 * a / 5.0) + b * b / 2.0,
+               5: 3.0 * a * (a * Z * (2.0 * Z - a) / 5.0 + b * b / 2.0 * (Z - a / 5.0)),
+               7: a * a * Z * Z * (a * Z + 3.0 * b * b), 9: 7.0 * a ** 3 * b * b * Z ** 4 / (2.0 * zeta)}
+        k = 3.0 * b ** 4 / (8.0 * math.pi)
+        rho = {7: 5.0 * k * np.ones_like(Z),
+               9: k * 7.0 * a * Z * Z * (5 * zeta ** 4 - 4 * a * zeta ** 3 + 3 * a * a * zeta ** 2 - 2 * a ** 3 * zeta
+                                         + a ** 4) / zeta ** 5,
+               11: k * 63.0 * a * a * Z ** 4 * (2 * zeta ** 2 - 2 * a * zeta + a * a) / zeta ** 4,
+               13: k * 231.0 * a ** 3 * Z ** 6 / zeta ** 3}
+    else:
+        raise ValueError(family)
+    return Z, phi, rho
+
+
+def dehnen_aly(family: str, M: float, a: float, b: float, L: float, eta: float, xyz: np.ndarray):
+    """Potential and density of a Dehnen-Aly barred component (family 'T3' or 'V4';
+    mass M, parent scales a, b, needle half-length L, slope eta) at bar-frame points
+    (n, 3).  L = 0 gives the axisymmetric parent."""
+    xyz = np.atleast_2d(np.asarray(xyz, dtype=np.float64))
+    x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+    Z, cphi, crho = _da_terms(family, a, b, z)
+
+    def In(n):
+        if L == 0.0:
+            return (x * x + y * y + Z * Z) ** (-0.5 * n)
+        return needle_In(x, y, Z, n, L, eta)
+
+    phi = -G * M * sum(c * In(n) for n, c in cphi.items())
+    rho = M * sum(c * In(n) for n, c in crho.items())
+    return phi, rho
+
+
+def paper_bar(M_b: float, L_b: float, b_d: float, xyz: np.ndarray, split_mass: float = 0.5):
+    """The paper's composite bar (Sec. 2.1.2): a T3 long bar (eta = 1, a = L_b/5, b = b_d,
+    L = L_b) plus a V4 boxy/peanut bulge (eta = 0, a = b = 0.5 kpc, L = 0.1 kpc) with tied
+    masses; split_mass is the T3 share of M_b (0.5: equal masses summing to M_b)."""
+    p1, r1 = dehnen_aly("T3", split_mass * M_b, L_b / 5.0, b_d, L_b, 1.0, xyz)
+    p2, r2 = dehnen_aly("V4", (1.0 - split_mass) * M_b, 0.5, 0.5, 0.1, 0.0, xyz)
+    return p1 + p2, r1 + r2
 
 
 # ---------------------------------------------------------------------------
