@@ -186,6 +186,36 @@ def needle_In(x, y, Z, n: int, L: float, eta: float) -> np.ndarray:
     return out
 
 
+def needle_In_closed(x, y, Z, n: int, L: float, eta: float) -> np.ndarray:
+    """The same I_n (odd n) in closed form, as a kernel would evaluate it: with
+    S(t) = sqrt(t^2 + q^2), q^2 = y^2 + Z^2, the antiderivatives
+      J_1 = asinh(t/q),  J_{n+2} = [t S^-n + (n - 1) J_n] / (n q^2),
+      K_n = int t S^-n dt = S^(2-n) / (2 - n)   (K_1 = S),
+    and f(u) = [(1 + eta) - 2 eta |u| / L] / (2L) split at t = x."""
+    x, y, Z = (np.asarray(v, dtype=np.float64) for v in np.broadcast_arrays(x, y, Z))
+    q2 = y * y + Z * Z
+    q = np.sqrt(q2)
+
+    def J(t):
+        S = np.sqrt(t * t + q2)
+        j = np.arcsinh(t / q)
+        for m in range(1, n, 2):
+            j = (t * S ** (-m) + (m - 1) * j) / (m * q2)
+        return j
+
+    def K(t):
+        S = np.sqrt(t * t + q2)
+        return S ** (2 - n) / (2 - n)
+
+    lo, hi = x - L, x + L
+    Jlo, Jx, Jhi = J(lo), J(x), J(hi)
+    Klo, Kx, Khi = K(lo), K(x), K(hi)
+    flat = (Jhi - Jlo) / (2 * L)
+    left = x * (Jx - Jlo) - (Kx - Klo)          # int_{x-L}^{x} (x - t) S^-n dt
+    right = (Khi - Kx) - x * (Jhi - Jx)         # int_{x}^{x+L} (t - x) S^-n dt
+    return (1 + eta) * flat - eta / (L * L) * (left + right)
+
+
 def _da_terms(family: str, a: float, b: float, z):
     """Coefficients c_n(z) of the parent pair, Phi = -G M sum_n c_n R^-n and
     rho = M sum_n d_n R^-n (App. A), as functions of Z = a + zeta, zeta = sqrt(z^2 + b^2)."""

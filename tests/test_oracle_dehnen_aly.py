@@ -93,3 +93,17 @@ def test_bar_symmetries_and_paper_composite(orc):
     # the bar is elongated along x: deeper potential at (2, 0, 0) than at (0, 2, 0)
     a, _ = orc.paper_bar(1e10, 4.0, 0.3, np.array([[2.0, 0, 0], [0, 2.0, 0]]))
     assert a[0] < a[1]
+
+
+@pytest.mark.parametrize("n", [1, 3, 5, 7, 9, 11, 13])
+def test_closed_form_needle_integrals_match_quadrature(orc, n):
+    """The antiderivative recurrences against the quadrature; for the 0.1 kpc needle of
+    the V4 bulge the closed form loses digits to cancellation (differences of nearly equal
+    antiderivatives), which the looser bound records."""
+    rng = np.random.default_rng(1)
+    x, y, Z = rng.uniform(-6, 6, 30), rng.uniform(-4, 4, 30), 0.6 + rng.uniform(0, 2, 30)
+    for eta in (-0.5, 0.0, 1.0):
+        np.testing.assert_allclose(orc.needle_In_closed(x, y, Z, n, 4.0, eta), orc.needle_In(x, y, Z, n, 4.0, eta),
+                                   rtol=1e-10)
+        np.testing.assert_allclose(orc.needle_In_closed(x, y, Z, n, 0.1, eta), orc.needle_In(x, y, Z, n, 0.1, eta),
+                                   rtol=1e-7)
