@@ -49,7 +49,7 @@ class Pot(ctypes.Structure):
     _fields_ = [("disc_M", ctypes.c_double), ("disc_a", ctypes.c_double), ("disc_b", ctypes.c_double),
                 ("halo_Mdm", ctypes.c_double), ("halo_rs", ctypes.c_double),
                 ("bar_M", ctypes.c_double), ("bar_L", ctypes.c_double), ("bar_a", ctypes.c_double),
-                ("bar_b", ctypes.c_double), ("test_kind", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("bar_b", ctypes.c_double), ("test_kind", ctypes.c_int32), ("bar_kind", ctypes.c_int32),
                 ("test_M", ctypes.c_double), ("test_a", ctypes.c_double)]
 
 
@@ -141,7 +141,7 @@ def make_pot(p: dict) -> Pot:
     return Pot(disc_M=p.get("disc_M", 0.0), disc_a=p.get("disc_a", 1.0), disc_b=p.get("disc_b", 1.0),
                halo_Mdm=Mdm, halo_rs=rs,
                bar_M=p.get("bar_M", 0.0), bar_L=p.get("bar_L", 1.0), bar_a=p.get("bar_b", 1.0),
-               bar_b=p.get("bar_c", 1.0), test_kind=int(p.get("test_kind", 0)),
+               bar_b=p.get("bar_c", 1.0), test_kind=int(p.get("test_kind", 0)), bar_kind=int(p.get("bar_kind", 0)),
                test_M=p.get("test_M", 0.0), test_a=p.get("test_a", 1.0))
 
 

@@ -32,7 +32,7 @@ typedef struct {
     double halo_Mdm, halo_rs;           /* NFW characteristic mass M_DM and R_s (Sec. 3.2.1) */
     double bar_M, bar_L, bar_a, bar_b;  /* needle-convolved MN: mass, half-length L, a, b (Eq. Rn_to_In) */
     int32_t test_kind;                  /* 0 none, 1 point mass, 2 Plummer sphere */
-    int32_t pad_;
+    int32_t bar_kind;                   /* 0 needle-convolved MN (Long-Murali); 1 the paper's T3 + V4 bar */
     double test_M, test_a;
 } orc_pot;
 
@@ -196,6 +196,150 @@ static double plummer_rho(double M, double a, const double x[3])
 
 /* Static potential and acceleration of the selected components at a
  * bar-frame position. */
+/* ---- The paper's bar (Sec. 2.1.2, App. A): Dehnen & Aly (2023) T3 long bar
+ * (eta = 1, a = L_b/5, b = the disc's height b_d, L = L_b) plus V4 bulge (eta = 0,
+ * a = b = 0.5, L = 0.1 kpc), each of mass M_b/2, every R^-n of the parent pair
+ * replaced by the needle integral I_n (Eq. Rn_to_In).  The integrals and their x
+ * derivatives, d I_n/dx = -n int f(x - x') x' S^-(n+2) dx', are taken by 48-point
+ * Gauss-Legendre quadrature on the pieces between x - L, 0, x and x + L; y and Z
+ * derivatives use d I_n/dy = -n y I_(n+2) and d I_n/dZ = -n Z I_(n+2). */
+#define DA_NQ 48
+#define DA_NMAX 13
+static double da_gx[DA_NQ], da_gw[DA_NQ];
+static int da_ready = 0;
+
+static void da_nodes(void)
+{
+    /* Gauss-Legendre nodes by Newton's method on P_48 (Golub-Welsch-free textbook form) */
+    for (int i = 0; i < DA_NQ; ++i) {
+        double t = cos(ORC_PI * (i + 0.75) / (DA_NQ + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= DA_NQ; ++k) {
+                double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = DA_NQ * (t * p1 - p0) / (t * t - 1.0);
+            double dt = p1 / dp;
+            t -= dt;
+            if (fabs(dt) < 1e-16) break;
+        }
+        da_gx[i] = t;
+        da_gw[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+    da_ready = 1;
+}
+
+/* I[n] = I_n and Ix[n] = d I_n / dx for odd n = 1..nmax at (x, q^2 = y^2 + Z^2) */
+static void da_integrals(double x, double q2, double L, double eta, int nmax, double* I, double* Ix)
+{
+    for (int n = 0; n <= nmax + 2; ++n) { I[n] = 0.0; Ix[n] = 0.0; }
+    double lo = x - L, hi = x + L;
+    double c1 = 0.0 < lo ? lo : (0.0 > x ? x : 0.0);
+    double c2 = 0.0 < x ? x : (0.0 > hi ? hi : 0.0);
+    double ends[5] = {lo, c1, x, c2, hi};
+    for (int pc = 0; pc < 4; ++pc) {
+        double a = ends[pc], b = ends[pc + 1], half = 0.5 * (b - a), mid = 0.5 * (a + b);
+        if (half <= 0.0) continue;
+        for (int k = 0; k < DA_NQ; ++k) {
+            double t = mid + half * da_gx[k];
+            double u = fabs(x - t);
+            double f = (1.0 + eta * (1.0 - 2.0 * u / L)) / (2.0 * L);
+            double s2 = t * t + q2, inv_s = 1.0 / sqrt(s2), inv_s2 = 1.0 / s2;
+            double w = half * da_gw[k] * f, pw = inv_s;       /* S^-n, n = 1, 3, ... */
+            for (int n = 1; n <= nmax + 2; n += 2) {
+                I[n] += w * pw;
+                Ix[n] += -n * w * t * pw * inv_s2;
+                pw *= inv_s2;
+            }
+        }
+    }
+}
+
+/* one barred component: family 0 = T3, 1 = V4 */
+static void da_component(int family, double M, double a, double b, double L, double eta, const double x[3],
+                         double* phi, double acc[3])
+{
+    if (!da_ready) da_nodes();
+    double z = x[2], zeta = sqrt(z * z + b * b), Z = a + zeta, dzeta = z / zeta;
+    double c[DA_NMAX + 1] = {0}, dc[DA_NMAX + 1] = {0};   /* c_n and dc_n/dzeta (Z = a + zeta) */
+    int nmax;
+    if (family == 0) {
+        nmax = 5;
+        c[1] = 1.0;
+        c[3] = a * (Z - a / 3.0);             dc[3] = a;
+        c[5] = a * a * Z * Z;                 dc[5] = 2.0 * a * a * Z;
+    } else {
+        nmax = 9;
+        c[1] = 1.0;
+        c[3] = a * (Z - 2.0 * a / 5.0) + b * b / 2.0;                      dc[3] = a;
+        c[5] = 3.0 * a * (a * Z * (2.0 * Z - a) / 5.0 + b * b / 2.0 * (Z - a / 5.0));
+        dc[5] = 3.0 * a * (a * (4.0 * Z - a) / 5.0 + b * b / 2.0);
+        c[7] = a * a * Z * Z * (a * Z + 3.0 * b * b);                       dc[7] = a * a * (3.0 * a * Z * Z + 6.0 * b * b * Z);
+        c[9] = 7.0 * a * a * a * b * b * Z * Z * Z * Z / (2.0 * zeta);
+        dc[9] = 3.5 * a * a * a * b * b * (4.0 * Z * Z * Z / zeta - Z * Z * Z * Z / (zeta * zeta));
+    }
+    double I[DA_NMAX + 3], Ix[DA_NMAX + 3];
+    da_integrals(x[0], x[1] * x[1] + Z * Z, L, eta, nmax, I, Ix);
+    double ph = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int n = 1; n <= nmax; n += 2) {
+        ph += c[n] * I[n];
+        gx += c[n] * Ix[n];
+        gy += c[n] * (-n * x[1] * I[n + 2]);
+        gz += (dc[n] * I[n] + c[n] * (-n * Z * I[n + 2])) * dzeta;
+    }
+    *phi = -ORC_G * M * ph;
+    acc[0] = ORC_G * M * gx;                 /* a = -grad Phi = G M grad(sum c_n I_n) */
+    acc[1] = ORC_G * M * gy;
+    acc[2] = ORC_G * M * gz;
+}
+
+/* density of one barred component: M sum_n d_n I_n with the parent's density coefficients */
+static double da_component_rho(int family, double M, double a, double b, double L, double eta, const double x[3])
+{
+    if (!da_ready) da_nodes();
+    double z = x[2], zeta = sqrt(z * z + b * b), Z = a + zeta;
+    double d[DA_NMAX + 1] = {0};
+    int nmax;
+    if (family == 0) {
+        double k = b * b / (4.0 * ORC_PI);
+        nmax = 9;
+        d[5] = 3.0 * k;
+        d[7] = k * 5.0 * a * Z * Z * (3.0 * zeta * zeta - 2.0 * a * zeta + a * a) / (zeta * zeta * zeta);
+        d[9] = k * 35.0 * a * a * Z * Z * Z * Z / (zeta * zeta);
+    } else {
+        double k = 3.0 * b * b * b * b / (8.0 * ORC_PI), z2 = zeta * zeta;
+        nmax = 13;
+        d[7] = 5.0 * k;
+        d[9] = k * 7.0 * a * Z * Z *
+               (5.0 * z2 * z2 - 4.0 * a * z2 * zeta + 3.0 * a * a * z2 - 2.0 * a * a * a * zeta + a * a * a * a) /
+               (z2 * z2 * zeta);
+        d[11] = k * 63.0 * a * a * Z * Z * Z * Z * (2.0 * z2 - 2.0 * a * zeta + a * a) / (z2 * z2);
+        d[13] = k * 231.0 * a * a * a * Z * Z * Z * Z * Z * Z / (z2 * zeta);
+    }
+    double I[DA_NMAX + 3], Ix[DA_NMAX + 3];
+    da_integrals(x[0], x[1] * x[1] + Z * Z, L, eta, nmax, I, Ix);
+    double r = 0.0;
+    for (int n = 5; n <= nmax; n += 2) r += d[n] * I[n];
+    return M * r;
+}
+
+static double paper_bar_rho(const orc_pot* p, const double x[3])
+{
+    return da_component_rho(0, 0.5 * p->bar_M, p->bar_L / 5.0, p->disc_b, p->bar_L, 1.0, x) +
+           da_component_rho(1, 0.5 * p->bar_M, 0.5, 0.5, 0.1, 0.0, x);
+}
+
+static void paper_bar_phi_acc(const orc_pot* p, const double x[3], double* phi, double acc[3])
+{
+    double ph1, a1[3], ph2, a2[3];
+    da_component(0, 0.5 * p->bar_M, p->bar_L / 5.0, p->disc_b, p->bar_L, 1.0, x, &ph1, a1);
+    da_component(1, 0.5 * p->bar_M, 0.5, 0.5, 0.1, 0.0, x, &ph2, a2);
+    *phi = ph1 + ph2;
+    for (int k = 0; k < 3; ++k) acc[k] = a1[k] + a2[k];
+}
+
 static void pot_static(const orc_pot* p, int mask, const double x[3], double* phi, double acc[3])
 {
     double ph, ac[3];
@@ -209,7 +353,8 @@ static void pot_static(const orc_pot* p, int mask, const double x[3], double* ph
         *phi += ph; acc[0] += ac[0]; acc[1] += ac[1]; acc[2] += ac[2];
     }
     if ((mask & ORC_BAR) && p->bar_M != 0.0) {
-        bar_phi_acc(p->bar_M, p->bar_L, p->bar_a, p->bar_b, x, &ph, ac);
+        if (p->bar_kind == 1) paper_bar_phi_acc(p, x, &ph, ac);
+        else bar_phi_acc(p->bar_M, p->bar_L, p->bar_a, p->bar_b, x, &ph, ac);
         *phi += ph; acc[0] += ac[0]; acc[1] += ac[1]; acc[2] += ac[2];
     }
     if ((mask & ORC_TEST) && p->test_kind == 1) {
@@ -235,7 +380,8 @@ void orc_density_eval(const orc_pot* p, int mask, int64_t n, const double* xyz, 
         double r = 0.0;
         if ((mask & ORC_DISC) && p->disc_M != 0.0) r += mn_rho(p->disc_M, p->disc_a, p->disc_b, x);
         if ((mask & ORC_HALO) && p->halo_Mdm != 0.0) r += nfw_rho(p->halo_Mdm, p->halo_rs, x);
-        if ((mask & ORC_BAR) && p->bar_M != 0.0) r += bar_rho(p->bar_M, p->bar_L, p->bar_a, p->bar_b, x, bar_nodes);
+        if ((mask & ORC_BAR) && p->bar_M != 0.0)
+            r += p->bar_kind == 1 ? paper_bar_rho(p, x) : bar_rho(p->bar_M, p->bar_L, p->bar_a, p->bar_b, x, bar_nodes);
         if ((mask & ORC_TEST) && p->test_kind == 2) r += plummer_rho(p->test_M, p->test_a, x);
         rho[i] = r;
     }

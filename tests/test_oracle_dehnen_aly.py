@@ -107,3 +107,39 @@ def test_closed_form_needle_integrals_match_quadrature(orc, n):
                                    rtol=1e-10)
         np.testing.assert_allclose(orc.needle_In_closed(x, y, Z, n, 0.1, eta), orc.needle_In(x, y, Z, n, 0.1, eta),
                                    rtol=1e-5)
+
+
+PAPER_BAR_POT = dict(inputs.DISC_HALO, bar_M=1e10, bar_L=4.0, bar_kind=1)
+
+
+def test_c_oracle_paper_bar_matches_and_is_consistent(orc):
+    """oracle.c's paper bar (bar_kind = 1, used by its integrator) against the Python
+    implementation, its acceleration against -grad Phi, and Poisson's equation."""
+    pot = orc.make_pot(PAPER_BAR_POT)
+    pts = _pts(seed=31, n=10)
+    phi_c, acc_c = orc.potential(pot, pts, orc.BAR)
+    rho_c = orc.density(pot, pts, orc.BAR)
+    phi_p, rho_p = orc.paper_bar(1e10, 4.0, inputs.DISC_HALO["disc_b"], pts)
+    np.testing.assert_allclose(phi_c, phi_p, rtol=1e-12)
+    np.testing.assert_allclose(rho_c, rho_p, rtol=1e-12)
+    h = 1e-4
+    for k in range(3):
+        e = np.zeros(3); e[k] = h
+        fd = -(orc.potential(pot, pts + e, orc.BAR)[0] - orc.potential(pot, pts - e, orc.BAR)[0]) / (2 * h)
+        np.testing.assert_allclose(acc_c[:, k], fd, rtol=1e-6, atol=1e-7 * np.abs(acc_c).max())
+    lap = _laplacian(lambda q: orc.potential(pot, q, orc.BAR)[0], pts)
+    np.testing.assert_allclose(lap, 4 * math.pi * G * rho_c, rtol=1e-4)
+
+
+def test_jacobi_energy_in_the_rotating_paper_bar(orc):
+    """Disc + halo + the paper's bar rotating at 40 km/s/kpc: the fixed-step KDK keeps the
+    Jacobi energy bounded with no secular drift, as for the Long-Murali bar."""
+    pot = orc.make_pot(PAPER_BAR_POT)
+    omega, dt, S = 40.0, inputs.DT_HALF_MYR, 20_000
+    ic = inputs.disc_ics(inputs.DISC_HALO, 1, seed=21, vfrac=(1.0, 1.0), sigma_v=5.0)[0]
+    tr = orc.trajectory(pot, omega, dt, S, ic)
+    ej = np.array([orc.jacobi(pot, omega, n * dt, tr[n]) for n in range(0, S + 1, 20)])
+    dev = np.abs(ej / ej[0] - 1)
+    assert dev.max() < 1e-4, dev.max()
+    half = len(dev) // 2
+    assert dev[half:].max() < 3 * max(dev[:half].max(), 1e-12)
