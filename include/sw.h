@@ -144,9 +144,17 @@ sw_status sw_bundle(sw_ctx* ctx, const sw_matrix* U, int64_t n, sw_matrix** U_ou
 sw_status sw_project_stats(sw_ctx* ctx, double* drift_out, uint8_t* status_out);
 
 /* Solve min_w 1/2 ||(U w - data) / errors||^2 + (lambda / N) ||w||^2 subject to w >= 0
- * (Sec. 2.3, Eq. objective_function in its compact NNLS form) by ADMM on the Gram of the
- * whitened matrix, followed by refinement with FP64 residuals against the stored U until the
- * KKT conditions hold.  data, errors: M host values (errors > 0); weights_out: N host values;
+ * (Sec. 2.3, Eq. objective_function in its compact NNLS form) to its exact minimiser (KKT
+ * conditions to the option kkt_tol).  Two solvers reach it (option "solver"):
+ *  - the default (solver = 0) is an active-set method (block principal pivoting) whenever its
+ *    reduced systems stay definite -- lambda > 0, no more orbits than rows, or libraries above
+ *    orbit_direct_max orbits -- which covers every solve with the default lambda = 1: each
+ *    reduced problem on the passive set is solved by conjugate gradients with FP64 products of
+ *    the stored U, preconditioned by the Cholesky factor of the passive set's tensor-core Gram;
+ *  - the paper's ADMM (Sec. 2.3) runs when lambda = 0 with more orbits than rows (up to
+ *    orbit_direct_max) and on request (solver = 2): ADMM on the Gram of the whitened matrix,
+ *    then refinement with FP64 residuals against the stored U and an exact active-set polish.
+ * data, errors: M host values (errors > 0); weights_out: N host values;
  * chi2_out: host [chi2_total, chi2_obs, reg] with chi2_total = ||(U w - data)/errors||^2,
  * chi2_obs the same without the density rows (Sec. 2.4) and reg = (lambda/N)||w||^2.
  * Returns SW_ENONCONV (with the best iterate) when the iteration caps are reached. */
@@ -176,9 +184,11 @@ sw_status sw_matrix_apply(const sw_matrix* U, const double* w, double* y_out);
 /* No counterpart in the paper: a variant of sw_matrix_apply for callers that cannot allocate
  * device memory when they call (e.g. a process whose device memory belongs to another allocator's
  * pool, or a pipeline that must not allocate once running).  Same arguments and result as
- * sw_matrix_apply, but its scratch (the staged w and the FP64 accumulator of U w) lives in a fixed
- * static device array of 2^21 doubles (16 MiB), held by every device that loads the library until
- * the process exits; N + M above 2^21 returns SW_EINVAL.  It calls no cudaMalloc/cudaFree.  The
+ * sw_matrix_apply, but its scratch (the staged w, the FP64 accumulator of U w and, for an FP32
+ * matrix, the float hi + lo halves of w) lives in a fixed static device array of 2^21 doubles
+ * (16 MiB), held by every device that loads the library until the process exits; a call needing
+ * more than 2^21 doubles (N + M for an FP64 matrix, 2 N + M for an FP32 one) returns SW_EINVAL.
+ * It calls no cudaMalloc/cudaFree and touches none of the context's workspace.  The
  * first call on a device looks up the array's device address (once per device, with that device
  * current); make that first call before any stream capture.  All calls share the array, so calls
  * that overlap on the GPU race: serialise them. */
@@ -213,6 +223,9 @@ sw_status sw_reset_stats(sw_ctx* ctx);
  * 0 = not counted.  Either output may be NULL. */
 sw_status sw_kernel_work(sw_ctx* ctx, int k, double* work, int* kind);
 int64_t sw_launch_count(const sw_ctx* ctx);
+/* Number of device allocations (cudaMalloc of a workspace buffer) the context has made since its
+ * creation; -1 for a NULL context.  Lets a caller check that a call allocated nothing. */
+int64_t sw_alloc_count(const sw_ctx* ctx);
 
 /* Tunables (value semantics in parentheses); unknown keys return SW_EINVAL.  The ADMM keys apply to the
  * paper's solver (Sec. 2.3), the "as_" keys to the active-set solver; "solver" chooses between them.

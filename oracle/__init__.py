@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
         cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-               "-fno-fast-math", src, "-o", _LIB_PATH + ".tmp", "-lm"]
+               "-fno-fast-math", src, "-o", _LIB_PATH + ".tmp", "-lm", "-lpthread"]
         subprocess.run(cmd, check=True)
         os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
     return _LIB_PATH

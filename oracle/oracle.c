@@ -14,6 +14,7 @@
  * galactic-dynamics choice).  One time unit is kpc/(km/s) = 977.79 Myr.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -206,7 +207,8 @@ static double plummer_rho(double M, double a, const double x[3])
 #define DA_NQ 48
 #define DA_NMAX 13
 static double da_gx[DA_NQ], da_gw[DA_NQ];
-static int da_ready = 0;
+/* built once, before first use, by pthread_once (callers run inside OpenMP loops) */
+static pthread_once_t da_once = PTHREAD_ONCE_INIT;
 
 static void da_nodes(void)
 {
@@ -228,7 +230,6 @@ static void da_nodes(void)
         da_gx[i] = t;
         da_gw[i] = 2.0 / ((1.0 - t * t) * dp * dp);
     }
-    da_ready = 1;
 }
 
 /* I[n] = I_n and Ix[n] = d I_n / dx for odd n = 1..nmax at (x, q^2 = y^2 + Z^2) */
@@ -261,7 +262,7 @@ static void da_integrals(double x, double q2, double L, double eta, int nmax, do
 static void da_component(int family, double M, double a, double b, double L, double eta, const double x[3],
                          double* phi, double acc[3])
 {
-    if (!da_ready) da_nodes();
+    pthread_once(&da_once, da_nodes);
     double z = x[2], zeta = sqrt(z * z + b * b), Z = a + zeta, dzeta = z / zeta;
     double c[DA_NMAX + 1] = {0}, dc[DA_NMAX + 1] = {0};   /* c_n and dc_n/dzeta (Z = a + zeta) */
     int nmax;
@@ -298,7 +299,7 @@ static void da_component(int family, double M, double a, double b, double L, dou
 /* density of one barred component: M sum_n d_n I_n with the parent's density coefficients */
 static double da_component_rho(int family, double M, double a, double b, double L, double eta, const double x[3])
 {
-    if (!da_ready) da_nodes();
+    pthread_once(&da_once, da_nodes);
     double z = x[2], zeta = sqrt(z * z + b * b), Z = a + zeta;
     double d[DA_NMAX + 1] = {0};
     int nmax;

@@ -817,7 +817,7 @@ template <typename T>
 cudaError_t colnorm2(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* inv_sig, double* h)
 {
     LaunchTimer lt(ctx, K_MISC);
-    k_colnorm2<T><<<cap_grid(N * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, inv_sig, h);
+    k_colnorm2<T><<<cap_grid(N * 32, 256, ctx_sms(ctx) * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, inv_sig, h);
     return cudaGetLastError();
 }
 
@@ -997,7 +997,7 @@ cudaError_t rowdot(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t cols
     if (rows <= 0) return cudaSuccess;
     LaunchTimer lt(ctx, kid);
     add_work(ctx, kid, (double)rows * cols * sizeof(AT) * (lower ? 0.5 : 1.0) * (A2 ? 2.0 : 1.0));
-    k_rowdot<AT, XT, YT, ACC><<<cap_grid(rows * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(
+    k_rowdot<AT, XT, YT, ACC><<<cap_grid(rows * 32, 256, ctx_sms(ctx) * 64), 256, 0, ctx_stream(ctx)>>>(
         A, A2, rows, cols, lda, x, y, alpha, beta, lower);
     return cudaGetLastError();
 }
@@ -1013,7 +1013,7 @@ cudaError_t colcomb(sw_ctx* ctx, int kid, const AT* A, int64_t rows, int64_t col
     int64_t pairs = (cols + 1) / 2;
     unsigned gx = (unsigned)((pairs + 255) / 256);
     // enough blocks to fill the GPU several times over, rows split evenly
-    int64_t want = (152 * 16 + gx - 1) / gx;
+    int64_t want = (ctx_sms(ctx) * 16 + gx - 1) / gx;
     if (want < 1) want = 1;
     int64_t rps = (rows + want - 1) / want;
     if (rps < 32) rps = 32;
@@ -1028,7 +1028,7 @@ cudaError_t admm_update(sw_ctx* ctx, int64_t N, const GT* y, const GT* v, const 
                         const GT* qp, double alpha, GT* rs, GT* z, GT* u, unsigned* stats)
 {
     LaunchTimer lt(ctx, K_ADMM_UPDATE);
-    k_admm_update<GT><<<cap_grid(N, 256, 152 * 8), 256, 0, ctx_stream(ctx)>>>(N, y, v, s, rho_i, d, qp, (GT)alpha,
+    k_admm_update<GT><<<cap_grid(N, 256, ctx_sms(ctx) * 8), 256, 0, ctx_stream(ctx)>>>(N, y, v, s, rho_i, d, qp, (GT)alpha,
                                                                               rs, z, u, stats);
     return cudaGetLastError();
 }
@@ -1038,7 +1038,7 @@ cudaError_t admm_init(sw_ctx* ctx, int64_t N, const GT* qp, const GT* z, const G
                       GT* rs)
 {
     LaunchTimer lt(ctx, K_MISC);
-    k_admm_init<GT><<<cap_grid(N, 256, 152 * 8), 256, 0, ctx_stream(ctx)>>>(N, qp, z, u, s, rho_i, rs);
+    k_admm_init<GT><<<cap_grid(N, 256, ctx_sms(ctx) * 8), 256, 0, ctx_stream(ctx)>>>(N, qp, z, u, s, rho_i, rs);
     return cudaGetLastError();
 }
 
@@ -1058,7 +1058,7 @@ cudaError_t u_times_w(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const doubl
     LaunchTimer lt(ctx, K_RESID);
     add_work(ctx, K_RESID, (double)M * N * sizeof(T) + 8.0 * (N + 2.0 * M));
     unsigned gx = (unsigned)((M + 255) / 256);
-    int64_t want = (152 * 16 + gx - 1) / gx;
+    int64_t want = (ctx_sms(ctx) * 16 + gx - 1) / gx;
     if (want < 1) want = 1;
     int64_t ops = (N + want - 1) / want;
     if (ops < 16) ops = 16;
@@ -1071,6 +1071,22 @@ cudaError_t u_times_w(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const doubl
     } else {
         k_u_times_w<T><<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(U, M, N, w, acc, ops);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t u_times_w_presplit(sw_ctx* ctx, const float* U, int64_t M, int64_t N, const double* w, float* wh,
+                               float* wl, double* acc)
+{
+    LaunchTimer lt(ctx, K_RESID);
+    add_work(ctx, K_RESID, (double)M * N * sizeof(float) + 8.0 * (N + 2.0 * M));
+    unsigned gx = (unsigned)((M + 255) / 256);
+    int64_t want = (ctx_sms(ctx) * 16 + gx - 1) / gx;
+    if (want < 1) want = 1;
+    int64_t ops = (N + want - 1) / want;
+    if (ops < 16) ops = 16;
+    unsigned gy = (unsigned)((N + ops - 1) / ops);
+    k_split_ff<<<cap_grid(N, 256, 4096), 256, 0, ctx_stream(ctx)>>>(N, w, wh, wl);
+    k_u_times_w_ff<<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(U, M, N, wh, wl, acc, ops);
     return cudaGetLastError();
 }
 
@@ -1091,9 +1107,9 @@ cudaError_t ut_times_x(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const doub
         float *xh, *xl;
         cudaError_t e = split_ff(ctx, xs, M, &xh, &xl);
         if (e) return e;
-        k_ut_times_x_ff<<<cap_grid(N * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xh, xl, out);
+        k_ut_times_x_ff<<<cap_grid(N * 32, 256, ctx_sms(ctx) * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xh, xl, out);
     } else {
-        k_ut_times_x<T><<<cap_grid(N * 32, 256, 152 * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xs, out);
+        k_ut_times_x<T><<<cap_grid(N * 32, 256, ctx_sms(ctx) * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xs, out);
     }
     return cudaGetLastError();
 }

@@ -143,7 +143,10 @@ __global__ void k_adam(int64_t n, float* __restrict__ p, const float* __restrict
     }
 }
 
-inline int grid_for(int64_t n, int threads = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 8)); }
+inline int grid_for(const sw_ctx* ctx, int64_t n, int threads = 256)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, (int64_t)ctx_sms(ctx) * 8));
+}
 
 struct Net {
     int n_in, width, n_hidden;
@@ -188,7 +191,7 @@ cudaError_t forward(sw_ctx* ctx, const Net& n, const float* P, const float* X, i
             LaunchTimer lt(ctx, K_MLP_FWD);
             e = gemm(st, (int)Bn, o, in, h, in, 1, W, 1, in, Z, o, false, bf16);
             if (!e) {
-                k_mlp_bias_act<<<grid_for(Bn * o), 256, 0, st>>>(Bn, o, b, Z, H, l < n.n_hidden);
+                k_mlp_bias_act<<<grid_for(ctx, Bn * o), 256, 0, st>>>(Bn, o, b, Z, H, l < n.n_hidden);
                 e = cudaGetLastError();
             }
         }
@@ -257,7 +260,7 @@ extern "C" sw_status sw_mlp_loss_grad(sw_ctx* ctx, int n_in, int width, int n_hi
     if (!e) e = cudaMemsetAsync(dloss, 0, sizeof(double), st);
     if (!e) {
         LaunchTimer lt(ctx, K_MLP_BWD);
-        k_mlp_mse<<<grid_for(batch), 256, 0, st>>>(batch, out, t_dev, D, dloss);
+        k_mlp_mse<<<grid_for(ctx, batch), 256, 0, st>>>(batch, out, t_dev, D, dloss);
         e = cudaGetLastError();
     }
     for (int l = n.layers() - 1; l >= 0 && !e; --l) {
@@ -277,7 +280,7 @@ extern "C" sw_status sw_mlp_loss_grad(sw_ctx* ctx, int n_in, int width, int n_hi
             const float* Zin = ws + (size_t)(l - 1) * 2 * batch * n.width;
             e = gemm(st, (int)batch, in, o, D, o, 1, W, in, 1, D2, in, false, false);
             if (!e) {
-                k_mlp_silu_bwd<<<grid_for(batch * in), 256, 0, st>>>(batch * in, Zin, D2);
+                k_mlp_silu_bwd<<<grid_for(ctx, batch * in), 256, 0, st>>>(batch * in, Zin, D2);
                 e = cudaGetLastError();
             }
             std::swap(D, D2);
@@ -304,7 +307,7 @@ extern "C" sw_status sw_mlp_adam(sw_ctx* ctx, int64_t n_params, float* params_de
     const float c1 = (float)(1.0 - std::pow(beta1, (double)step)), c2 = (float)(1.0 - std::pow(beta2, (double)step));
     {
         LaunchTimer lt(ctx, K_ADAM);
-        k_adam<<<grid_for(n_params), 256, 0, ctx->stream>>>(n_params, params_dev, grad_dev, m_dev, v_dev, (float)lr,
+        k_adam<<<grid_for(ctx, n_params), 256, 0, ctx->stream>>>(n_params, params_dev, grad_dev, m_dev, v_dev, (float)lr,
                                                             (float)beta1, (float)beta2, (float)eps, c1, c2);
     }
     cudaError_t e = cudaGetLastError();

@@ -142,7 +142,10 @@ __global__ void k_cg_mask(int64_t n, const double* __restrict__ m, double* __res
         z[i] *= m[i];
 }
 
-inline int cg_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + CG_THREADS - 1) / CG_THREADS, 152 * 8)); }
+inline int cg_blocks(const sw_ctx* ctx, int64_t n)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + CG_THREADS - 1) / CG_THREADS, (int64_t)ctx_sms(ctx) * 8));
+}
 
 struct Span {
     char* p;
@@ -305,7 +308,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         std::vector<double> mh(nP, 0.0);
         for (int64_t i : F) mh[pos[i]] = 1.0;
         AS_CUDA(ctx, cudaMemcpyAsync(V.mask, mh.data(), nP * sizeof(double), cudaMemcpyHostToDevice, st), "mask");
-        const int nb = cg_blocks(nP);
+        const int nb = cg_blocks(ctx, nP);
         auto precond = [&](const double* r, double* z) -> sw_status {   // z = m S X^T X S r
             AS_CUDA(ctx, scale_to<GT>(ctx, nP, r, V.sP, V.rs), "precondition");
             AS_CUDA(ctx, (rowdot<GT, GT, GT, GT>(ctx, K_TRMV_L, X, nP, nP, nP, V.rs, V.t1, 1.0, 0.0, true)),

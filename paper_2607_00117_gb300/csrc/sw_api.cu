@@ -30,6 +30,7 @@ void set_error(sw_ctx* ctx, const char* fmt, ...)
 }
 
 cudaStream_t ctx_stream(sw_ctx* ctx) { return ctx->stream; }
+int ctx_sms(const sw_ctx* ctx) { return ctx->n_sm; }
 
 LaunchTimer::LaunchTimer(sw_ctx* c, int kid) : ctx(c), id(kid), on(c && c->prof)
 {
@@ -97,6 +98,7 @@ sw_status sw_ctx::ensure(void** p, size_t* cap, size_t need, const char* what)
         set_error(this, "cudaMalloc(%zu bytes) for %s failed: %s", need, what, cudaGetErrorString(e));
         return SW_ENOMEM;
     }
+    ++n_alloc;
     *cap = need;
     return SW_OK;
 }
@@ -129,6 +131,10 @@ extern "C" sw_status sw_create(sw_ctx** out, int device, sw_precision prec, void
     sw_ctx* c = new sw_ctx();
     c->device = device;
     c->prec = prec;
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || c->n_sm < 1) {
+        cudaGetLastError();
+        c->n_sm = 1;
+    }
     if (cuda_stream) {
         c->stream = (cudaStream_t)cuda_stream;
         c->own_stream = false;
@@ -867,6 +873,7 @@ extern "C" sw_status sw_reset_stats(sw_ctx* ctx)
 }
 
 extern "C" int64_t sw_launch_count(const sw_ctx* ctx) { return ctx ? ctx->launches : 0; }
+extern "C" int64_t sw_alloc_count(const sw_ctx* ctx) { return ctx ? ctx->n_alloc : -1; }
 
 extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value)
 {

@@ -71,6 +71,8 @@ struct LaunchRec {
 
 struct sw_ctx {
     int device = 0;
+    int n_sm = 1;                  // streaming multiprocessors of the device (queried at creation)
+    int64_t n_alloc = 0;           // device allocations made by ensure() since creation
     sw_precision prec = SW_FP32_KAHAN;
     cudaStream_t stream = nullptr;
     bool own_stream = false;

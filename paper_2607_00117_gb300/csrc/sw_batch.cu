@@ -37,7 +37,7 @@ struct sw_batch {
     int n_items = 0;
     std::vector<sw_matrix> views;
     bool models_set = false, tuned = false, have_graph = false;
-    int threads = 128, grid = 152 * 4, ej_every = 8;
+    int threads = 128, grid = 0, ej_every = 8;   // grid: set from the device's SM count at creation
     std::vector<double> tune_ms;   // per candidate, in candidate order
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -47,7 +47,6 @@ namespace {
 
 constexpr int kThreads[3] = {64, 128, 256};
 constexpr int kCtasPerSm[4] = {1, 2, 4, 8};
-constexpr int kSMs = 152;
 
 void free_batch(sw_batch* b)
 {
@@ -104,14 +103,15 @@ sw_status autotune(sw_batch* b)
     const bool prof = ctx->prof;
     ctx->prof = false;
     double best = 1e300;
-    int best_t = 128, best_g = kSMs * 2;
+    const int sms = ctx_sms(ctx);
+    int best_t = 128, best_g = sms * 2;
     b->tune_ms.clear();
     sw_status s = SW_OK;
     for (int t : kThreads) {
         if ((s = build_items(b, t)) != SW_OK) break;
         for (int c : kCtasPerSm) {
             b->threads = t;
-            b->grid = kSMs * c * (128 / t > 0 ? 128 / t : 1);
+            b->grid = sms * c * (128 / t > 0 ? 128 / t : 1);
             if (b->grid < 1) b->grid = 1;
             cudaEventRecord(e0, ctx->stream);
             cudaError_t e = enqueue<T>(b, probe);
@@ -261,6 +261,10 @@ extern "C" sw_status sw_batch_create(sw_ctx* ctx, int n_models, const int64_t* n
         return SW_EINVAL;
     }
     *out = nullptr;
+    if (ctx->opt.integrator != 0) {
+        set_error(ctx, "sw_batch_create: the batched launch integrates with kick-drift-kick only (option integrator = 0)");
+        return SW_EINVAL;
+    }
     if (pix->nx <= 0 || pix->ny <= 0 || !(pix->dx > 0) || !(pix->dy > 0) || dens->nR <= 0 || dens->nphi <= 0 ||
         dens->nz <= 0 || !(dens->Rmax > 0) || !(dens->zmax > dens->zmin) ||
         (!gh && (vb->nv <= 0 || !(vb->dv > 0)))) {
@@ -269,6 +273,7 @@ extern "C" sw_status sw_batch_create(sw_ctx* ctx, int n_models, const int64_t* n
     }
     sw_batch* b = new sw_batch();
     b->ctx = ctx;
+    b->grid = ctx_sms(ctx) * 4;
     b->n_models = n_models;
     b->nsteps = nsteps;
     b->gh = gh != 0;
@@ -344,6 +349,10 @@ extern "C" sw_status sw_batch_run(sw_batch* b)
     sw_ctx* ctx = b->ctx;
     CHECK_CTX(ctx);
     if (!b->models_set) { set_error(ctx, "sw_batch_run: set the models first"); return SW_ESTATE; }
+    if (ctx->opt.integrator != 0) {
+        set_error(ctx, "sw_batch_run: the batched launch integrates with kick-drift-kick only (option integrator = 0)");
+        return SW_EINVAL;
+    }
     for (auto& v : b->views) ctx->solve_ws.forget_matrix(&v);
     return b->elem == 8 ? run_impl<double>(b) : run_impl<float>(b);
 }

@@ -74,6 +74,8 @@ struct LaunchTimer {
 };
 
 cudaStream_t ctx_stream(sw_ctx* ctx);
+// streaming multiprocessors of the context's device
+int ctx_sms(const sw_ctx* ctx);
 
 // Algorithmic work of a launch, accumulated per kernel for the roofline: FLOPs for the
 // dense factorisation and Gram kernels, HBM bytes for the streaming kernels, orbit-steps

@@ -53,6 +53,10 @@ cudaError_t admm_init(sw_ctx* ctx, int64_t N, const GT* qp, const GT* z, const G
                       GT* rs);
 template <typename T>
 cudaError_t u_times_w(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* w, double* acc);
+// U w for an FP32 matrix with the float hi + lo halves of w staged in caller-provided buffers
+// (N floats each): no workspace of the context is touched or allocated
+cudaError_t u_times_w_presplit(sw_ctx* ctx, const float* U, int64_t M, int64_t N, const double* w, float* wh,
+                               float* wl, double* acc);
 cudaError_t residual(sw_ctx* ctx, int64_t M, const double* y, const double* acc, const double* inv_sig, double* e,
                      double* xs);
 template <typename T>

@@ -9,11 +9,14 @@
 // device array of fixed size instead of cudaMalloc'ed buffers.
 //
 // The array holds SW_APPLY_STATIC_MAX doubles (16 MiB); every device that
-// loads the library keeps it until the process exits.  All calls share it, so
-// calls that overlap on the GPU race (serialise them, e.g. on one stream).
+// loads the library keeps it until the process exits.  One call uses N
+// doubles for w, M for the accumulator and, for an FP32 matrix, N more
+// (2 N floats) for the float hi + lo halves of w that the FP32 product reads.
+// All calls share it, so calls that overlap on the GPU race (serialise them,
+// e.g. on one stream).
 #include "sw_linalg.cuh"
 
-#define SW_APPLY_STATIC_MAX (1 << 21)  // doubles: N + M of one call must not exceed this
+#define SW_APPLY_STATIC_MAX (1 << 21)  // doubles: N + M (2 N + M for FP32 matrices) of one call
 
 namespace {
 
@@ -47,9 +50,12 @@ extern "C" sw_status sw_matrix_apply_static(const sw_matrix* U, const double* w,
     ctx->err.clear();
     cudaSetDevice(ctx->device);
     cudaGetLastError();
-    if (U->N + U->M > (int64_t)SW_APPLY_STATIC_MAX) {
-        sw::set_error(ctx, "sw_matrix_apply_static: N + M = %lld exceeds the static scratch of %d values",
-                      (long long)(U->N + U->M), SW_APPLY_STATIC_MAX);
+    const int64_t need = (U->elem == 8 ? 1 : 2) * U->N + U->M;
+    if (need > (int64_t)SW_APPLY_STATIC_MAX) {
+        sw::set_error(ctx,
+                      "sw_matrix_apply_static: the call needs %lld values of scratch (N + M, 2 N + M for an FP32 "
+                      "matrix), more than the static array's %d",
+                      (long long)need, SW_APPLY_STATIC_MAX);
         return SW_EINVAL;
     }
     double* scratch = nullptr;
@@ -57,10 +63,12 @@ extern "C" sw_status sw_matrix_apply_static(const sw_matrix* U, const double* w,
     if (e != cudaSuccess) return ctx->cuda_fail(e, "static scratch address");
     double* d_w = scratch;           // N staged weights
     double* d_y = scratch + U->N;    // M accumulators, zeroed below (the array keeps the last call's contents)
+    float* d_wh = reinterpret_cast<float*>(d_y + U->M);   // FP32 matrices: float hi + lo halves of w
+    float* d_wl = d_wh + U->N;
     if ((e = cudaMemcpyAsync(d_w, w, U->N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream)) ||
         (e = cudaMemsetAsync(d_y, 0, U->M * sizeof(double), ctx->stream)) ||
         (e = (U->elem == 8 ? sw::u_times_w<double>(ctx, (const double*)U->d, U->M, U->N, d_w, d_y)
-                           : sw::u_times_w<float>(ctx, (const float*)U->d, U->M, U->N, d_w, d_y))) ||
+                           : sw::u_times_w_presplit(ctx, (const float*)U->d, U->M, U->N, d_w, d_wh, d_wl, d_y))) ||
         (e = cudaMemcpyAsync(y_out, d_y, U->M * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream)) ||
         (e = cudaStreamSynchronize(ctx->stream)))
         return ctx->cuda_fail(e, "static matrix apply");

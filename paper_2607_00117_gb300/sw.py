@@ -106,6 +106,7 @@ SIGNATURES = {
     "sw_reset_stats": (ctypes.c_int, [_VP]),
     "sw_kernel_work": (ctypes.c_int, [_VP, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]),
     "sw_launch_count": (ctypes.c_int64, [_VP]),
+    "sw_alloc_count": (ctypes.c_int64, [_VP]),
     "sw_set_option": (ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_double]),
 }
 
@@ -422,3 +423,6 @@ class Context:
 
     def launch_count(self) -> int:
         return lib().sw_launch_count(self.handle)
+
+    def alloc_count(self) -> int:
+        return lib().sw_alloc_count(self.handle)

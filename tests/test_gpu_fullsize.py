@@ -167,3 +167,28 @@ def test_full_size_solve_properties(full):
     on = w[pick] > 0
     assert np.all(np.abs(g[on]) <= tol), (pick[on], g[on], tol)
     assert np.all(g[~on] <= tol), (pick[~on], g[~on], tol)
+
+
+def test_full_size_kkt_certificate_all_bundles(full):
+    """FP64 KKT certificate over every bundle of the benchmark's solve, computed on the host
+    from the read-back Gauss-Hermite matrix (stored FP32 values, exact in FP64):
+    g = U~^T (U~ w - y~) + (2 lam/N) w is the objective's gradient and P(g) its projection
+    (g_i on the support, min(g_i, 0) at w_i = 0).  Strong convexity (modulus mu = 2 lam/N)
+    bounds the objective gap, f(w) - f* <= ||P(g)||^2 / (2 mu); the bound must be below
+    1e-4 of chi^2, so the returned chi^2 is within 1e-4 of the optimum's."""
+    Ug, w, y, sig = full["Ug"], full["w"], full["y"], full["sig"]
+    lam, N = W["lam"], Ug.N
+    rows = Ug.copy()                                  # (N, M) FP64
+    assert rows.shape == (N, Ug.M)
+    e = (rows.T @ w - y) / sig                        # whitened residual (M)
+    mu = 2.0 * lam / N
+    g = rows @ (e / sig) + mu * w
+    q = rows @ (y / (sig * sig))
+    pg = np.where(w > 0, g, np.minimum(g, 0.0))
+    chi2 = float(e @ e)
+    np.testing.assert_allclose(full["chi2"][0], chi2, rtol=1e-9)
+    bound = float(pg @ pg) / (2.0 * mu)
+    print(f"all {N} bundles: max|P(g)| {np.abs(pg).max():.3g} = {np.abs(pg).max() / np.abs(q).max():.3g} of "
+          f"max|q|; gap bound {bound:.3g} = {bound / chi2:.3g} of chi^2 {chi2:.6g}; support {int((w > 0).sum())}")
+    assert np.abs(pg).max() <= 1e-6 * np.abs(q).max()
+    assert bound <= 1e-4 * chi2

@@ -133,3 +133,26 @@ def test_mlp_shapes_and_adam(orc):
         orc.adam_step(params, g, m, v, it, lr=1e-3)
     loss1, _ = orc.mlp_loss_grad(params, X, t)
     assert loss1 < 0.5 * loss0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_whiten_pins_the_objective(orc, seed):
+    """whiten (with normal_equations) against the objective's definition: at any w,
+    1/2 w^T H w - q^T w + 1/2 |y~|^2 equals 1/2 ||(U w - y)/sigma||^2 + (lam/N) |w|^2,
+    with chi^2 and the regulariser taken from chi2_parts.  Errors far from 1 make a
+    division by sigma^2 (or by sqrt(sigma)) fail; a hand case fixes the scaling."""
+    rng = np.random.default_rng(40 + seed)
+    M, N, lam = 30, 12, 0.7
+    U = rng.random((M, N))
+    y = rng.random(M) * 3.0
+    sigma = rng.uniform(0.05, 9.0, M)
+    Ut, yt = orc.whiten(U, y, sigma)
+    H, q = orc.normal_equations(Ut, yt, lam)
+    for _ in range(3):
+        w = rng.uniform(0, 2, N)
+        f = orc.objective(H, q, w) + 0.5 * yt @ yt
+        c = orc.chi2_parts(U, y, sigma, w, lam, 5)
+        assert abs(f - (0.5 * c[0] + c[2])) <= 1e-12 * max(1.0, f)
+    Ut2, yt2 = orc.whiten(np.array([[2.0, 4.0], [3.0, 9.0]]), np.array([6.0, 12.0]), np.array([2.0, 3.0]))
+    np.testing.assert_array_equal(Ut2, [[1.0, 2.0], [1.0, 3.0]])
+    np.testing.assert_array_equal(yt2, [3.0, 4.0])

@@ -30,12 +30,21 @@ def test_static_apply_matches_allocating_apply(sw, prec):
     ctx.integrate_library(ics, 40.0, inputs.DT_HALF_MYR, 300)
     U = ctx.project(W["grid"])
     rng = np.random.default_rng(7)
+    ws = [rng.uniform(0, 2, U.N) for _ in range(2)]
+    # the static calls come first on this context, before any allocating apply has sized its
+    # workspace: they must allocate nothing
+    n0 = ctx.alloc_count()
+    got = [U.apply_static(w) for w in ws]
+    assert ctx.alloc_count() == n0, "sw_matrix_apply_static allocated device memory"
+    ref = [U.apply(w) for w in ws]
+    if prec == "fp32":
+        assert ctx.alloc_count() > n0   # control: the allocating form does size a workspace here
     for call in range(2):
-        w = rng.uniform(0, 2, U.N)
-        ref = U.apply(w)
-        got = U.apply_static(w)
-        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
-        assert np.abs(ref).max() > 0
+        np.testing.assert_allclose(got[call], ref[call], rtol=1e-12, atol=1e-12 * np.abs(ref[call]).max())
+        assert np.abs(ref[call]).max() > 0
+    # and again after the allocating calls (the shared array keeps the previous call's contents)
+    for w, r in zip(ws, ref):
+        np.testing.assert_allclose(U.apply_static(w), r, rtol=1e-12, atol=1e-12 * np.abs(r).max())
 
 
 def test_static_apply_rejects_oversize(sw):
@@ -43,8 +52,8 @@ def test_static_apply_rejects_oversize(sw):
     ctx.set_potential(inputs.DISC_HALO)
     ics = inputs.disc_ics(inputs.DISC_HALO, 300, seed=32)
     ctx.integrate_library(ics, 0.0, inputs.DT_HALF_MYR, 2)
-    grid = dict(inputs.WORKLOADS["barred_100k"]["grid"], nv=1000)   # M = 4000 + 2500 * 1001 > 2^21 - N
+    grid = dict(inputs.WORKLOADS["barred_100k"]["grid"], nv=1000)   # M = 4000 + 2500 * 1001 > 2^21 - 2 N
     U = ctx.project(grid)
-    assert U.N + U.M > (1 << 21)
+    assert 2 * U.N + U.M > (1 << 21)
     with pytest.raises(sw.SwError):
         U.apply_static(np.ones(U.N))
