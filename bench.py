@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--n-orb", type=int, default=0, help="override the orbit count (small cases for ncu captures)")
     ap.add_argument("--nsteps", type=int, default=0, help="override the step count (small cases for ncu captures)")
+    ap.add_argument("--n-mock", type=int, default=N_MOCK,
+                    help="orbits of the mock library that makes the data (smaller for small ncu captures)")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched_64", "surrogate"],
                     help="batched_64: 64 trial potentials built in one persistent launch, then solved")
     return ap.parse_args()
@@ -156,7 +158,7 @@ def pixel_moments_from_hist(y_hist, grid):
     return np.stack([m0, h @ vc, h @ (vc * vc)], 1)
 
 
-def make_data(sw, torch, W, rank):
+def make_data(sw, torch, W, rank, n_mock=N_MOCK):
     """Mock observation: an independent library of N_MOCK orbits with weights
     U(0, 2) (scaled to the library size), its pixels' reference Gaussians, and
     2% mass errors / Sec. 3.1 GH errors with Gaussian noise.  Built with the
@@ -164,10 +166,10 @@ def make_data(sw, torch, W, rank):
     grid = W["grid"]
     ctx = sw.Context(0, "fp32")
     ctx.set_potential(W["potential"])
-    ics = inputs.disc_ics(W["potential"], N_MOCK, seed=W["seeds"]["ic"] + 500 + rank)
+    ics = inputs.disc_ics(W["potential"], n_mock, seed=W["seeds"]["ic"] + 500 + rank)
     ctx.integrate_library(ics, W["omega_p"], W["dt"], W["nsteps"])
     Uh = ctx.project(grid)
-    wt = inputs.true_weights(N_MOCK, W["seeds"]["w"]) * (W["n_orb"] / N_MOCK)
+    wt = inputs.true_weights(n_mock, W["seeds"]["w"]) * (W["n_orb"] / n_mock)
     y_hist = Uh.apply(wt)
     v0s, gh_err = inputs.gh_reference(pixel_moments_from_hist(y_hist, grid))
     Ug = ctx.reduce_gh(Uh, v0s)
@@ -349,7 +351,7 @@ def run_sw(args):
     grid, N, S = W["grid"], W["n_orb"], W["nsteps"]
     hbm, bf16, bf16_sus, sm_max, peak_src = peaks()
 
-    v0s, y, sig = make_data(sw, torch, W, rank)
+    v0s, y, sig = make_data(sw, torch, W, rank, args.n_mock)
     nb = W.get("bundle", 1)
     Nb = N // nb
     base = inputs.disc_ics(W["potential"], Nb, seed=replica_seed(W["seeds"]["ic"], rank))

@@ -61,17 +61,22 @@ enum { SW_ORBIT_OK = 0, SW_ORBIT_DRIFT = 1, SW_ORBIT_NONFINITE = 2 };
 
 /* Potential (Sec. 3.2).  Disc: Miyamoto-Nagai Phi = -G M_d / sqrt(R^2 + (R_d + sqrt(z^2 + H_d^2))^2)
  * with (disc_M, disc_a, disc_b) = (M_d, R_d, H_d).  Halo: NFW from (halo_M200, halo_c) with
- * Delta = 200 and rho_crit = 3 H0^2 / (8 pi G), H0 in km/s/Mpc (Sec. 3.2.1).  Bar: the n = 1,
- * eta = 0 needle convolution of Eq. (Rn_to_In) (the Long-Murali bar) with half-length bar_L,
- * parent MN radial scale bar_b and height bar_c; bar_M = 0 disables it.  The bar's major axis
- * is the rotating x axis.  test_kind 1 adds a point mass test_M, 2 a Plummer sphere
- * (test_M, test_a); 0 none.  Components with zero mass are skipped. */
+ * Delta = 200 and rho_crit = 3 H0^2 / (8 pi G), H0 in km/s/Mpc (Sec. 3.2.1).  Bar (bar_M = 0
+ * disables it; its major axis is the rotating x axis), by bar_kind:
+ *   0: the n = 1, eta = 0 needle convolution of Eq. (Rn_to_In) (the Long-Murali bar) with
+ *      half-length bar_L, parent MN radial scale bar_b and height bar_c;
+ *   1: the paper's bar (Sec. 2.1.2, App. A): a Dehnen-Aly T3 long bar (eta = 1, a = bar_L / 5,
+ *      b = disc_b, needle half-length bar_L) plus a V4 boxy/peanut bulge (eta = 0, a = b = 0.5 kpc,
+ *      half-length 0.1 kpc), each of mass bar_M / 2, every R^-n of the parent potentials replaced
+ *      by the needle integral I_n of Eq. (Rn_to_In); bar_b and bar_c are not used.
+ * test_kind 1 adds a point mass test_M, 2 a Plummer sphere (test_M, test_a); 0 none.  Components
+ * with zero mass are skipped.  Other bar_kind values return SW_EINVAL. */
 typedef struct {
     double disc_M, disc_a, disc_b;
     double halo_M200, halo_c, H0;
     double bar_M, bar_L, bar_b, bar_c;
     int32_t test_kind;
-    int32_t reserved;
+    int32_t bar_kind;
     double test_M, test_a;
 } sw_potential_params;
 
@@ -164,6 +169,22 @@ sw_status sw_solve_weights(sw_ctx* ctx, const sw_matrix* U, const double* data, 
 sw_status sw_solve_weights_device(sw_ctx* ctx, const sw_matrix* U, const double* data_dev,
                                   const double* errors_dev, double lambda, double* weights_dev,
                                   double* chi2_dev);
+
+/* Bootstrap solves and the marginalised chi^2 (Sec. 2.4 and the model-likelihood passage after it).
+ * For b = 0 .. n_boot-1 the observed rows of the data (every row after the 3-D density cells) are
+ * perturbed by their errors, y_b = data + errors * xi[b] (the density rows unchanged); the weight
+ * problem of sw_solve_weights is solved for y_b with the same matrix and lambda; chi2_b_out[b] is the
+ * observational chi^2 of those weights against the unperturbed data (density rows excluded), and
+ * *chi2_model_out = min_b chi2_b - 2 ln[(1/n_boot) sum_b exp(-(chi2_b - min_b chi2_b) / 2)], -2 ln of
+ * the bootstrap-averaged likelihood.  The solves run the active-set method warm-started from the
+ * solve on the unperturbed data, sharing the factor of its passive set (plus the orbits nearest to
+ * entering) for every realisation whose passive set stays inside it.  xi: host n_boot x M standard
+ * normal draws (the caller's random numbers); weights_out: host n_boot x N or NULL; chi2_b_out: host
+ * n_boot; chi2_model_out: host, one value.  Needs lambda > 0 or N <= M (SW_EINVAL otherwise);
+ * SW_ENONCONV if a realisation stopped at an iteration cap (its best iterate is used). */
+sw_status sw_solve_bootstrap(sw_ctx* ctx, const sw_matrix* U, const double* data, const double* errors, double lambda,
+                             int64_t n_boot, const double* xi, double* weights_out, double* chi2_b_out,
+                             double* chi2_model_out);
 
 /* Solver diagnostics of the last solve: out[0] ADMM iterations, out[1] refinement rounds,
  * out[2] final KKT projected-gradient infinity norm (scaled by max |U~^T y~|), out[3] 1 if the
@@ -258,6 +279,8 @@ int64_t sw_alloc_count(const sw_ctx* ctx);
  *                           orbit_direct_max orbits, ADMM otherwise; 1: always the active set; 2: always ADMM
  *                           (the paper's solver, Sec. 2.3, with FP64 refinement and the exact polish)
  *  "chol_coop" (0/1)        active set: Cholesky and its inverse in one cooperative launch (default 0)
+ *  "chol_tc" (0/1)          active set, FP32 form: Cholesky and its inverse in 128-wide steps with the trailing and
+ *                           inverse updates on the tensor cores (BF16 hi + lo split, default 1); 0: FP32 SIMT updates
  *  "integrator" (0/1)       sw_project's integrator: 0 (default) kick-drift-kick at the fixed dt in the inertial
  *                           frame; 1 the paper's adaptive Bogacki-Shampine 3(2) pair (Sec. 2.2.2) in the frame
  *                           rotating with the bar, nsteps accepted steps from a first trial step dt, each sample

@@ -1,0 +1,683 @@
+// Cholesky factor L of the shifted passive Gram (in place, lower) and the explicit
+// inverse X = L^{-1}: the preconditioner of the weight solve's reduced systems
+// (Sec. 2.3).  Blocked right-looking in 128-wide steps; at step k
+//
+//   1. k_diag128 (one CTA): L_kk = chol(A_kk) and D_k = L_kk^{-1}.  A chain of
+//      128 column steps for the factor and 128 row steps for the inverse, each
+//      thread holding a fixed 4 x 8 set of the block's elements in registers
+//      and one CTA barrier per step (column j, or row k of the inverse, is
+//      passed through shared memory by the threads that own it);
+//   2. k_panel128: the panel below, L_ik = A_ik D_k^T (FP32, in place), also
+//      written as BF16 hi + lo halves (the split operand of step 3);
+//   3. k_tc_sub<lower>: the trailing update A_ij -= L_ik L_jk^T on the 5th-
+//      generation tensor cores: the tile is accumulated in TMEM from the three
+//      leading products of the split (hi hi, hi lo, lo hi; ~2^-16 relative)
+//      and subtracted from the FP32 trailing matrix in the epilogue;
+//   4. k_trmm128: block row k of the inverse, X_k <- D_k X_k (FP32), also
+//      written transposed as BF16 hi + lo halves;
+//   5. k_tc_sub<full>: the rows below, X_i -= L_ik X_k (tensor cores).
+//
+// Steps 1, 2 and 4 are FP32 SIMT; 3 and 5 hold the O(K^3) work.  The split
+// products make the factor a preconditioner accurate to ~1e-4 relative, which
+// the conjugate-gradient solve that uses it absorbs in one or two extra steps.
+#include "sw_linalg.cuh"
+#include "sw_tc.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+namespace sw {
+
+namespace ctc {
+
+using namespace sw::tc;
+
+constexpr int DB = 128;  // block width
+constexpr int LP = DB + 1;
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo)
+{
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// ---------------------------------------------------------------------------
+// 1. Diagonal block: Cholesky and triangular inverse.  512 threads; thread
+// (ty, tx) = (t / 16, t % 16) owns rows i = ty + 32 r (r < 4) and columns
+// l = tx + 16 c (c < 8) of the 128 x 128 block.  Cholesky in the unscaled
+// form a_il -= a_ij a_lj / a_jj (column j of the result is a_ij / sqrt(a_jj)).
+// The update runs unconditionally over every owned element of the row and
+// column blocks that can still change: the column values of finished rows and
+// columns enter as zeros, and the upper-triangle elements it also touches are
+// never read.  The loops over the column block cb (factor) and the row block
+// rb (inverse) are unrolled so that every register index is a compile-time
+// constant (a selection by a runtime block index would put the arrays in local
+// memory).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512, 1) k_diag128(float* __restrict__ G, int64_t ld, int64_t j0, int bs,
+                                                    float* __restrict__ D, int* info)
+{
+    extern __shared__ float sm[];
+    float* Ls = sm;                 // DB x LP: the factor
+    float* col = Ls + DB * LP;      // 2 x DB: column j of the working matrix (ping-pong)
+    float* rowx = col + 2 * DB;     // 2 x DB: row k of the inverse (ping-pong)
+    float* rdiag = rowx + 2 * DB;   // DB: 1 / L_jj
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+    float a[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int i = ty + 32 * r, l = tx + 16 * c;
+            a[r][c] = (i < bs && l <= i) ? G[(size_t)(j0 + i) * ld + j0 + l] : 0.f;
+        }
+    if (tx == 0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) col[ty + 32 * r] = a[r][0];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int cb = 0; cb < 8; ++cb) {
+#pragma unroll 1
+        for (int jj = 0; jj < 16; ++jj) {
+            const int j = 16 * cb + jj;
+            if (j >= bs) break;
+            const int b = j & 1;
+            float d = col[b * DB + j];
+            if (!(d > 0.f)) {
+                if (t == 0 && info) atomicCAS(info, 0, (int)(j0 + j + 1));
+                d = 1e-30f;
+            }
+            const float rd = 1.0f / d, rs = rsqrtf(d);
+            if (t == 0) rdiag[j] = 1.0f / (d * rs);   // d rs = sqrt(d) = L_jj
+            // column j is final: L_ij = a_ij / sqrt(d) for i >= j
+            if (tx == jj) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int i = ty + 32 * r;
+                    if (i >= j && i < bs) Ls[i * LP + j] = a[r][cb] * rs;
+                }
+            }
+            // rows i > j and columns l > j change; rows below 16 cb - 31 are finished
+            float ci[4], lj[8];
+#pragma unroll
+            for (int r = cb / 2; r < 4; ++r) {
+                const int i = ty + 32 * r;
+                ci[r] = (i > j) ? col[b * DB + i] * rd : 0.f;
+            }
+#pragma unroll
+            for (int c = cb; c < 8; ++c) {
+                const int l = tx + 16 * c;
+                lj[c] = (l > j) ? col[b * DB + l] : 0.f;
+            }
+#pragma unroll
+            for (int r = cb / 2; r < 4; ++r)
+#pragma unroll
+                for (int c = cb; c < 8; ++c) a[r][c] -= ci[r] * lj[c];
+            // the owners of column j + 1 pass it on (block cb, or cb + 1 after its last column)
+            if (j + 1 < bs) {
+                if (jj < 15) {
+                    if (tx == jj + 1) {
+#pragma unroll
+                        for (int r = cb / 2; r < 4; ++r) {
+                            const int i = ty + 32 * r;
+                            if (i > j) col[(b ^ 1) * DB + i] = a[r][cb];
+                        }
+                    }
+                } else if (cb < 7) {
+                    if (tx == 0) {
+#pragma unroll
+                        for (int r = cb / 2; r < 4; ++r) {
+                            const int i = ty + 32 * r;
+                            if (i > j) col[(b ^ 1) * DB + i] = a[r][cb < 7 ? cb + 1 : 7];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ---- inverse X = L^{-1}, right-looking by rows: row k final = row k / L_kk, then
+    // rows i > k lose L_ik * row k (whose entries beyond column k are zero).  Thread
+    // ownership as above, x starts as I.
+    float x[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int i = ty + 32 * r, l = tx + 16 * c;
+            x[r][c] = (i == l && i < bs) ? 1.f : 0.f;
+        }
+    if (ty == 0) {   // row 0 (r = 0)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            x[0][c] *= rdiag[0];
+            rowx[tx + 16 * c] = x[0][c];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rb = 0; rb < 4; ++rb) {
+#pragma unroll 1
+        for (int kk = 0; kk < 32; ++kk) {
+            const int k = 32 * rb + kk;
+            if (k + 1 >= bs) break;
+            const int b = k & 1;
+            // row k of X is zero beyond column k < 32 rb + 32: column blocks c <= 2 rb + 1 only
+            float xk[8], lik[4];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c <= 2 * rb + 1) xk[c] = rowx[b * DB + tx + 16 * c];
+#pragma unroll
+            for (int r = rb; r < 4; ++r) {
+                const int i = ty + 32 * r;
+                lik[r] = (i > k && i < bs) ? Ls[i * LP + k] : 0.f;
+            }
+#pragma unroll
+            for (int r = rb; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c <= 2 * rb + 1) x[r][c] -= lik[r] * xk[c];
+            // row k + 1 is now final up to its scaling: block rb, or rb + 1 after its last row
+            const float s = rdiag[k + 1];
+            if (kk < 31) {
+                if (ty == kk + 1) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        x[rb][c] *= s;
+                        rowx[(b ^ 1) * DB + tx + 16 * c] = x[rb][c];
+                    }
+                }
+            } else if (rb < 3) {
+                if (ty == 0) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        x[rb < 3 ? rb + 1 : 3][c] *= s;
+                        rowx[(b ^ 1) * DB + tx + 16 * c] = x[rb < 3 ? rb + 1 : 3][c];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int i = ty + 32 * r, l = tx + 16 * c;
+            D[i * DB + l] = (i < bs && l <= i) ? x[r][c] : 0.f;
+            if (i < bs && l <= i) G[(size_t)(j0 + i) * ld + j0 + l] = Ls[i * LP + l];
+        }
+}
+
+constexpr size_t DIAG_SMEM = sizeof(float) * (DB * LP + 5 * DB);
+
+// ---------------------------------------------------------------------------
+// 2. Panel: P = A D^T for m rows below the diagonal block (A = G[r0 + i][j0 ..
+// j0 + 127]), in place in G, and its BF16 hi + lo halves (m x 128 row-major).
+// 64 rows per CTA of 256 threads; thread (tr, tc) = (t / 16, t % 16) computes
+// rows 4 tr .. 4 tr + 3 and columns tc + 16 q (q < 8).
+// ---------------------------------------------------------------------------
+constexpr int PR = 64;
+__global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t ld, int64_t j0, int64_t r0,
+                                                  int64_t m, const float* __restrict__ D,
+                                                  __nv_bfloat16* __restrict__ Ph, __nv_bfloat16* __restrict__ Pl)
+{
+    extern __shared__ float sm[];
+    float* As = sm;              // PR x LP
+    float* Ds = As + PR * LP;    // DB x LP
+    const int t = threadIdx.x;
+    const int64_t row0 = (int64_t)blockIdx.x * PR;
+    for (int e = t; e < PR * DB; e += 256) {
+        const int i = e >> 7, l = e & (DB - 1);
+        const int64_t gi = row0 + i;
+        As[i * LP + l] = gi < m ? G[(size_t)(r0 + gi) * ld + j0 + l] : 0.f;
+    }
+    for (int e = t; e < DB * DB; e += 256) {
+        const int i = e >> 7, l = e & (DB - 1);
+        Ds[i * LP + l] = D[e];
+    }
+    __syncthreads();
+    const int tr = t >> 4, tc = t & 15;
+    float acc[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
+    const int lmax = tc + 16 * 7;   // D[c][l] = 0 for l > c
+#pragma unroll 4
+    for (int l = 0; l <= lmax; ++l) {
+        float av[4], dv[8];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) av[r] = As[(4 * tr + r) * LP + l];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dv[q] = Ds[(tc + 16 * q) * LP + l];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[r][q] += av[r] * dv[q];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t gi = row0 + 4 * tr + r;
+        if (gi >= m) continue;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = tc + 16 * q;
+            G[(size_t)(r0 + gi) * ld + j0 + c] = acc[r][q];
+            __nv_bfloat16 h, lo;
+            split_bf16(acc[r][q], h, lo);
+            Ph[(size_t)gi * DB + c] = h;
+            Pl[(size_t)gi * DB + c] = lo;
+        }
+    }
+}
+
+constexpr size_t PANEL_SMEM = sizeof(float) * (PR + DB) * LP;
+
+// ---------------------------------------------------------------------------
+// 4. Block row of the inverse: X[j0 + i][c] <- sum_l D[i][l] X[j0 + l][c] for
+// the ncols leading columns (in place), and its transpose as BF16 hi + lo
+// halves: XT[c][i] (ncols x 128 row-major).  64 columns per CTA of 256 threads;
+// thread (trow, tcol) = (t / 16, t % 16) computes rows trow + 16 k (k < 8),
+// columns 4 tcol .. 4 tcol + 3.
+// ---------------------------------------------------------------------------
+constexpr int TC = 64;
+__global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t ld, int64_t j0, int bs,
+                                                 int64_t ncols, const float* __restrict__ D,
+                                                 __nv_bfloat16* __restrict__ XTh, __nv_bfloat16* __restrict__ XTl)
+{
+    extern __shared__ float sm[];
+    float* Ss = sm;                 // DB x (TC + 4)
+    float* Ds = Ss + DB * (TC + 4); // DB x LP
+    __nv_bfloat16* Th = reinterpret_cast<__nv_bfloat16*>(Ds + DB * LP);   // TC x (DB + 8)
+    __nv_bfloat16* Tl = Th + TC * (DB + 8);
+    const int t = threadIdx.x;
+    const int64_t c0 = (int64_t)blockIdx.x * TC;
+    for (int e = t; e < DB * TC; e += 256) {
+        const int i = e / TC, cc = e % TC;
+        const int64_t gc = c0 + cc;
+        Ss[i * (TC + 4) + cc] = (i < bs && gc < ncols) ? X[(size_t)(j0 + i) * ld + gc] : 0.f;
+    }
+    for (int e = t; e < DB * DB; e += 256) {
+        const int i = e >> 7, l = e & (DB - 1);
+        Ds[i * LP + l] = D[e];
+    }
+    __syncthreads();
+    const int trow = t >> 4, tcol = t & 15;
+    float acc[8][4];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[k][j] = 0.f;
+    const int lmax = trow + 16 * 7;   // D[i][l] = 0 for l > i
+#pragma unroll 4
+    for (int l = 0; l <= lmax; ++l) {
+        const float4 s = *reinterpret_cast<const float4*>(&Ss[l * (TC + 4) + 4 * tcol]);
+        float dv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dv[k] = Ds[(trow + 16 * k) * LP + l];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            acc[k][0] += dv[k] * s.x;
+            acc[k][1] += dv[k] * s.y;
+            acc[k][2] += dv[k] * s.z;
+            acc[k][3] += dv[k] * s.w;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int i = trow + 16 * k;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int cc = 4 * tcol + j;
+            const int64_t gc = c0 + cc;
+            if (i < bs && gc < ncols) X[(size_t)(j0 + i) * ld + gc] = acc[k][j];
+            __nv_bfloat16 h, lo;
+            split_bf16(i < bs ? acc[k][j] : 0.f, h, lo);
+            Th[cc * (DB + 8) + i] = h;
+            Tl[cc * (DB + 8) + i] = lo;
+        }
+    }
+    __syncthreads();
+    // coalesced rows of XT: 64 columns x 128 BF16 = 16 chunks of 16 bytes per row and half
+    for (int e = t; e < TC * 16; e += 256) {
+        const int cc = e >> 4, ch = e & 15;
+        const int64_t gc = c0 + cc;
+        if (gc >= ncols) continue;
+        *reinterpret_cast<uint4*>(XTh + (size_t)gc * DB + ch * 8) =
+            *reinterpret_cast<const uint4*>(Th + cc * (DB + 8) + ch * 8);
+        *reinterpret_cast<uint4*>(XTl + (size_t)gc * DB + ch * 8) =
+            *reinterpret_cast<const uint4*>(Tl + cc * (DB + 8) + ch * 8);
+    }
+}
+
+constexpr size_t TRMM_SMEM = sizeof(float) * (DB * (TC + 4) + DB * LP) + 2 * sizeof(__nv_bfloat16) * TC * (DB + 8);
+
+// ---------------------------------------------------------------------------
+// 3, 5. C[m x n] (FP32, row-major, ldc) -= (A_hi + A_lo)(B_hi + B_lo)^T over a
+// contraction of 64 nk, the A and B operands K-major BF16 (rows of the maps),
+// in 128 x 128 tiles (LOWER: only tiles with tj <= ti).  Persistent: each CTA
+// (one per SM) walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0
+// issues TMA loads (128-byte swizzle) through a 3-stage ring, one thread of
+// warp 1 issues tcgen05.mma into one of two 128-column TMEM accumulators, and
+// warps 2-5 drain the other one (tcgen05.ld) and subtract it from C, so that a
+// tile's loads and products overlap the previous tile's epilogue.  Every wait
+// is bounded: on expiry the CTA records an error, stops issuing, waits for its
+// own copies and products in flight, frees TMEM and returns.
+// ---------------------------------------------------------------------------
+constexpr int BM = 128, BN = 128, BKC = 64;
+constexpr int OP_BYTES = BM * BKC * 2;                 // one 128 x 64 BF16 operand box
+constexpr int STAGES = 3, STAGE_BYTES = 4 * OP_BYTES;  // A_hi, B_hi, A_lo, B_lo
+constexpr int SUB_SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int SUB_THREADS = 192;
+constexpr uint32_t TMEM_COLS = 256;                    // two 128-column accumulators
+
+template <bool LOWER>
+__device__ __forceinline__ void tile_of(int64_t t, int64_t tiles_n, int64_t& ti, int64_t& tj)
+{
+    if (LOWER) {
+        ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+        while (ti * (ti + 1) / 2 > t) --ti;
+        tj = t - ti * (ti + 1) / 2;
+    } else {
+        ti = t / tiles_n;
+        tj = t % tiles_n;
+    }
+}
+
+template <bool LOWER>
+__global__ void __launch_bounds__(SUB_THREADS, 1)
+    k_tc_sub(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap ma_lo,
+             const __grid_constant__ CUtensorMap mb, const __grid_constant__ CUtensorMap mb_lo, int64_t m, int64_t n,
+             int64_t n_tiles, int64_t tiles_n, int nk, float* __restrict__ C, int64_t ldc, int* err)
+{
+    extern __shared__ unsigned char smraw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* acc_full = empty + STAGES;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        int64_t it = 0;
+        for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
+            int64_t ti, tj;
+            tile_of<LOWER>(t, tiles_n, ti, tj);
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+                const int s = (int)(it % STAGES);
+                const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1u)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                unsigned char* sa = base + s * STAGE_BYTES;
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                tma_load_2d(sa, &ma, kc * BKC, (int)(ti * BM), &full[s]);
+                tma_load_2d(sa + OP_BYTES, &mb, kc * BKC, (int)(tj * BN), &full[s]);
+                tma_load_2d(sa + 2 * OP_BYTES, &ma_lo, kc * BKC, (int)(ti * BM), &full[s]);
+                tma_load_2d(sa + 3 * OP_BYTES, &mb_lo, kc * BKC, (int)(tj * BN), &full[s]);
+            }
+        }
+        if (*abort_flag) {
+            // wait for this CTA's copies still in flight (the last STAGES issued)
+            for (int64_t k = it - STAGES < 0 ? 0 : it - STAGES; k < it; ++k)
+                mbar_wait(&full[k % STAGES], (uint32_t)(k / STAGES) & 1u);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        const uint32_t idesc = idesc_bf16(BM, BN);
+        int64_t it = 0, tc = 0;
+        for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x, ++tc) {
+            const int b = (int)(tc & 1);
+            const uint32_t use = (uint32_t)(tc >> 1) & 1u;
+            if (!mbar_wait(&acc_empty[b], use ^ 1u)) {
+                *abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dt = tmem + (uint32_t)(b * BN);
+            bool ok = true;
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+                const int s = (int)(it % STAGES);
+                const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                if (*abort_flag || !mbar_wait(&full[s], ph)) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = su32(base + s * STAGE_BYTES);
+                const uint64_t da = smem_desc(sa), db = smem_desc(sa + OP_BYTES);
+                const uint64_t dal = smem_desc(sa + 2 * OP_BYTES), dbl = smem_desc(sa + 3 * OP_BYTES);
+#pragma unroll
+                for (int k = 0; k < BKC / 16; ++k) {
+                    umma(dt, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (kc | k) != 0);
+                    umma(dt, da + (uint64_t)(2 * k), dbl + (uint64_t)(2 * k), idesc, 1u);
+                    umma(dt, dal + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, 1u);
+                }
+                umma_commit(&empty[s]);
+            }
+            if (!ok) break;
+            umma_commit(&acc_full[b]);
+        }
+        // every product this thread issued completes before TMEM is freed
+        umma_commit(drain);
+        mbar_wait(drain, 0);
+    } else if (warp >= 2) {
+        // ---- epilogue: C -= accumulator.  A thread owns one row of the tile (its TMEM lane) and
+        // loads that row's 128 values of C before the accumulator is ready, so that the global
+        // latency overlaps the tile's loads and products.
+        const int q = warp & 3;   // TMEM lane quarter this warp may access
+        const bool vec = (((uintptr_t)C & 15) == 0) && ((ldc & 3) == 0);
+        int64_t tc = 0;
+        for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x, ++tc) {
+            int64_t ti, tj;
+            tile_of<LOWER>(t, tiles_n, ti, tj);
+            const int b = (int)(tc & 1);
+            const uint32_t use = (uint32_t)(tc >> 1) & 1u;
+            const int64_t gi = ti * BM + q * 32 + lane, gj = tj * BN;
+            float* dst = C + (size_t)gi * ldc + gj;
+            const bool full_row = vec && gi < m && gj + BN <= n;
+            float4 cv[BN / 4];
+            if (full_row) {
+#pragma unroll
+                for (int k = 0; k < BN / 4; ++k) cv[k] = *reinterpret_cast<const float4*>(dst + 4 * k);
+            }
+            if (!mbar_wait(&acc_full[b], use)) {
+                *abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0), v);
+                if (full_row) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        float4& o = cv[(c0 + j) / 4];
+                        o.x -= __uint_as_float(v[j]);
+                        o.y -= __uint_as_float(v[j + 1]);
+                        o.z -= __uint_as_float(v[j + 2]);
+                        o.w -= __uint_as_float(v[j + 3]);
+                    }
+                } else if (gi < m) {
+                    for (int j = 0; j < 32; ++j)
+                        if (gj + c0 + j < n) dst[c0 + j] -= __uint_as_float(v[j]);
+                }
+            }
+            // the accumulator is in registers: hand the TMEM buffer back before storing
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+            if (full_row) {
+#pragma unroll
+                for (int k = 0; k < BN / 4; ++k) *reinterpret_cast<float4*>(dst + 4 * k) = cv[k];
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) atomicExch(err, 1);
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+__global__ void k_unit_diag(float* __restrict__ X, int64_t K)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < K) X[(size_t)i * K + i] = 1.f;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static bool encoder()
+{
+    if (g_encode) return true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return false;
+    }
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return true;
+}
+
+// rows x 128 BF16, row-major (256-byte rows): boxes of 64 x 128 with the 128-byte swizzle
+static bool make_map(CUtensorMap* map, const __nv_bfloat16* A, int64_t rows)
+{
+    cuuint64_t dims[2] = {(cuuint64_t)DB, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)DB * 2};
+    cuuint32_t box[2] = {BKC, BM};
+    cuuint32_t estr[2] = {1, 1};
+    return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)A, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace ctc
+
+bool chol_tc_available() { return ctc::encoder(); }
+
+cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int* d_info, int* d_err)
+{
+    using namespace ctc;
+    if (K <= 0) return cudaSuccess;
+    if (!encoder() || K > 0x7fffff00LL) return cudaErrorNotSupported;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e;
+        if ((e = cudaFuncSetAttribute(k_diag128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DIAG_SMEM)) ||
+            (e = cudaFuncSetAttribute(k_panel128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM)) ||
+            (e = cudaFuncSetAttribute(k_trmm128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TRMM_SMEM)) ||
+            (e = cudaFuncSetAttribute(k_tc_sub<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SUB_SMEM)) ||
+            (e = cudaFuncSetAttribute(k_tc_sub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SUB_SMEM)))
+            return e;
+        attr = true;
+    }
+    cudaStream_t st = ctx_stream(ctx);
+    // scratch: D_k (128 x 128 FP32), the panel's and the inverse block row's BF16 halves (K x 128 each)
+    const size_t dbytes = (size_t)DB * DB * sizeof(float);
+    const size_t hbytes = ((size_t)K * DB * sizeof(__nv_bfloat16) + 255) & ~(size_t)255;
+    if (ctx->ensure(&ctx->d_chol_tc, &ctx->chol_tc_cap, dbytes + 4 * hbytes + 256, "factor scratch") != SW_OK)
+        return cudaErrorMemoryAllocation;
+    float* Dk = (float*)ctx->d_chol_tc;
+    __nv_bfloat16* Ph = (__nv_bfloat16*)((char*)ctx->d_chol_tc + dbytes);
+    __nv_bfloat16* Pl = (__nv_bfloat16*)((char*)Ph + hbytes);
+    __nv_bfloat16* XTh = (__nv_bfloat16*)((char*)Pl + hbytes);
+    __nv_bfloat16* XTl = (__nv_bfloat16*)((char*)XTh + hbytes);
+    CUtensorMap mph, mpl, mxh, mxl;
+    if (!make_map(&mph, Ph, K) || !make_map(&mpl, Pl, K) || !make_map(&mxh, XTh, K) || !make_map(&mxl, XTl, K))
+        return cudaErrorInvalidValue;
+    cudaError_t e;
+    // X = I
+    if ((e = cudaMemsetAsync(X, 0, (size_t)K * K * sizeof(float), st))) return e;
+    {
+        LaunchTimer lt(ctx, K_MISC);
+        k_unit_diag<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(X, K);
+    }
+    const int64_t nb = (K + DB - 1) / DB;
+    for (int64_t kb = 0; kb < nb; ++kb) {
+        const int64_t j0 = kb * DB;
+        const int bs = (int)(K - j0 < DB ? K - j0 : DB);
+        const int64_t r0 = j0 + bs, m = K - r0;
+        {
+            LaunchTimer lt(ctx, K_POTRF_DIAG);
+            add_work(ctx, K_POTRF_DIAG, 2.0 * (double)bs * bs * bs / 3.0);
+            k_diag128<<<1, 512, DIAG_SMEM, st>>>(G, K, j0, bs, Dk, d_info);
+        }
+        if ((e = cudaGetLastError())) return e;
+        if (m > 0) {
+            {
+                LaunchTimer lt(ctx, K_TRSM_PANEL);
+                add_work(ctx, K_TRSM_PANEL, (double)m * DB * DB);
+                k_panel128<<<(unsigned)((m + PR - 1) / PR), 256, PANEL_SMEM, st>>>(G, K, j0, r0, m, Dk, Ph, Pl);
+            }
+            if ((e = cudaGetLastError())) return e;
+            const int64_t T = (m + BM - 1) / BM, tiles = T * (T + 1) / 2;
+            {
+                LaunchTimer lt(ctx, K_SYRK_TC);
+                add_work(ctx, K_SYRK_TC, (double)m * (double)(m + 1) * DB);
+                k_tc_sub<true><<<(unsigned)std::min<int64_t>(tiles, ctx_sms(ctx)), SUB_THREADS, SUB_SMEM, st>>>(
+                    mph, mpl, mph, mpl, m, m, tiles, T, DB / BKC, G + (size_t)r0 * K + r0, K, d_err);
+            }
+            if ((e = cudaGetLastError())) return e;
+        }
+        {
+            LaunchTimer lt(ctx, K_TRINV_DIAG);
+            add_work(ctx, K_TRINV_DIAG, (double)bs * bs * (double)r0);
+            k_trmm128<<<(unsigned)((r0 + TC - 1) / TC), 256, TRMM_SMEM, st>>>(X, K, j0, bs, r0, Dk, XTh, XTl);
+        }
+        if ((e = cudaGetLastError())) return e;
+        if (m > 0) {
+            const int64_t Tm = (m + BM - 1) / BM, Tn = (r0 + BN - 1) / BN, tiles = Tm * Tn;
+            LaunchTimer lt(ctx, K_TRINV_TC);
+            add_work(ctx, K_TRINV_TC, 2.0 * (double)m * (double)r0 * DB);
+            k_tc_sub<false><<<(unsigned)std::min<int64_t>(tiles, ctx_sms(ctx)), SUB_THREADS, SUB_SMEM, st>>>(
+                mph, mpl, mxh, mxl, m, r0, tiles, Tn, DB / BKC, X + (size_t)r0 * K, K, d_err);
+        }
+        if ((e = cudaGetLastError())) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace sw

@@ -190,7 +190,7 @@ struct AsVecs {
 
 template <typename T, typename AT, typename GT>
 sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, const double* sig_dev, double lam,
-                           double* w_dev, double* chi2_dev)
+                           double* w_dev, double* chi2_dev, AsWarm* warm)
 {
     const int64_t M = Um->M, N = Um->N;
     const T* U = (const T*)Um->d;
@@ -256,7 +256,6 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         AS_CUDA(ctx, cudaMemcpyAsync(V.idx, S.data(), nP * sizeof(int64_t), cudaMemcpyHostToDevice, st), "idx");
         AS_CUDA(ctx, cudaMemcpyAsync(V.sP, sh.data(), nP * sizeof(double), cudaMemcpyHostToDevice, st), "scales");
         AS_CUDA(ctx, gather_cols<T>(ctx, U, M, V.idx, nP, Uc), "gather");
-        AS_CUDA(ctx, gather_vec(ctx, V.q, V.idx, nP, V.qP), "q_P");
         AS_CUDA(ctx, (whiten<T, AT>(ctx, Uc, M, nP, V.inv_sig, V.sP, A, Alo, ldA, true)), "whiten");
         double fl = floor_ridge;
         int infoh = 1, gerrh = 0;
@@ -276,6 +275,10 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             AS_CUDA(ctx, cudaMemsetAsync(cerr, 0, sizeof(int), st), "memset");
             cudaError_t ce = ctx->opt.chol_coop ? cholesky_inverse_coop<GT>(ctx, G, (GT*)ws.X, nP, info, cerr)
                                                 : cudaErrorNotSupported;
+            if constexpr (sizeof(GT) == 4) {
+                if (ce == cudaErrorNotSupported && !ctx->opt.chol_coop && ctx->opt.chol_tc)
+                    ce = cholesky_inverse_tc(ctx, (float*)G, (float*)ws.X, nP, info, gerr);
+            }
             if (ce == cudaErrorNotSupported) {
                 cudaGetLastError();
                 ce = cholesky_inverse<GT>(ctx, G, (GT*)ws.X, (GT*)ws.D, nP, info);
@@ -286,10 +289,11 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             AS_CUDA(ctx, cudaMemcpyAsync(&gerrh, gerr, sizeof(int), cudaMemcpyDeviceToHost, st), "flags");
             AS_CUDA(ctx, cudaMemcpyAsync(&cerrh, cerr, sizeof(int), cudaMemcpyDeviceToHost, st), "flags");
             AS_CUDA(ctx, cudaStreamSynchronize(st), "reduced factor");
-            if (gerrh) { set_error(ctx, "solve: tensor-core Gram kernel timed out"); return SW_ETIMEOUT; }
+            if (gerrh) { set_error(ctx, "solve: a tensor-core kernel (Gram or factor update) timed out"); return SW_ETIMEOUT; }
             if (cerrh) { set_error(ctx, "solve: a grid barrier of the Cholesky kernel timed out"); return SW_ETIMEOUT; }
         }
         ++n_factor;
+        if (warm) ++warm->factorisations;
         if (infoh != 0) return SW_OK;   // ok = false
         ok = true;
         return SW_OK;
@@ -308,6 +312,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         std::vector<double> mh(nP, 0.0);
         for (int64_t i : F) mh[pos[i]] = 1.0;
         AS_CUDA(ctx, cudaMemcpyAsync(V.mask, mh.data(), nP * sizeof(double), cudaMemcpyHostToDevice, st), "mask");
+        AS_CUDA(ctx, gather_vec(ctx, V.q, V.idx, nP, V.qP), "q_P");
         const int nb = cg_blocks(ctx, nP);
         auto precond = [&](const double* r, double* z) -> sw_status {   // z = m S X^T X S r
             AS_CUDA(ctx, scale_to<GT>(ctx, nP, r, V.sP, V.rs), "precondition");
@@ -434,6 +439,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     // C and C grows by the strongest violators outside it whenever F is optimal on C
     std::vector<char> inC(N, 0);
     int64_t nC = std::min<int64_t>(N, std::max<int64_t>(1, ctx->opt.as_candidates > 0 ? (int64_t)ctx->opt.as_candidates : 2 * M));
+    if (warm && warm->start) nC = N;   // a warm start begins near the optimum: every orbit is a candidate
     {
         std::vector<std::pair<double, int64_t>> sc(N);
         for (int64_t i = 0; i < N; ++i) sc[i] = {hh[i] > 0.0 ? qh[i] / std::sqrt(hh[i]) : -1e300, i};
@@ -455,6 +461,47 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         AS_TRY(evaluate());
         f0 = chi_h[0];
         fbest = fproj = f0;
+    }
+    // the factor of P0 serves every passive set inside it (the orbits of P0 \ F masked)
+    auto factored_covers = [&](const std::vector<int64_t>& S) {
+        if (!warm || !warm->have_factor || P0.empty()) return false;
+        for (int64_t i : S)
+            if (pos[i] < 0) return false;
+        return true;
+    };
+    if (warm && warm->start && (int64_t)warm->F0.size() == N && !warm->P0.empty()) {
+        // begin from the recorded passive set, solved against this problem's data with the factor of
+        // P0 (factored again when an earlier warm-started solve replaced it)
+        bool have = warm->have_factor;
+        if (have) {
+            for (int64_t i : P0) pos[i] = -1;
+            P0 = warm->P0;
+            for (int64_t k = 0; k < (int64_t)P0.size(); ++k) pos[P0[k]] = k;
+        } else {
+            const std::vector<int64_t> S = warm->P0;
+            AS_TRY(factor(S, have));
+            warm->have_factor = have;
+        }
+        if (have)
+            for (int64_t i = 0; i < N; ++i)
+                if (warm->F0[i]) { inF[i] = 1; F.push_back(i); }
+        if (!F.empty()) {
+            bool conv = false;
+            AS_TRY(solve_on(F, conv));
+            std::fill(zh.begin(), zh.end(), 0.0);
+            for (int64_t i : F) zh[i] = xh[pos[i]];
+            buf.assign(P0.size(), 0.0);
+            for (int64_t i : F) buf[pos[i]] = std::max(zh[i], 0.0);
+            AS_CUDA(ctx, cudaMemcpyAsync(V.xa, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, st),
+                    "x+");
+            AS_TRY(objective_P0(V.xa, fproj));
+            if (fproj < fbest) {
+                fbest = fproj;
+                for (int64_t i = 0; i < N; ++i) zbest[i] = std::max(zh[i], 0.0);
+            }
+            AS_TRY(evaluate());
+            evaluated = true;
+        }
     }
     for (; outer < 1000000 && n_solves < ctx->opt.as_solves; ++outer) {
         std::vector<std::pair<double, int64_t>> neg, enter;   // (violation, orbit)
@@ -518,8 +565,11 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             if (inF[i]) F.push_back(i);
         std::fill(zh.begin(), zh.end(), 0.0);
         if (!F.empty()) {
-            bool ok = false, conv = false;
-            AS_TRY(factor(F, ok));
+            bool ok = true, conv = false;
+            if (!factored_covers(F)) {
+                AS_TRY(factor(F, ok));
+                if (warm) warm->have_factor = false;   // P0 is now this passive set
+            }
             if (!ok) { failed = true; break; }
             AS_TRY(solve_on(F, conv));
             for (int64_t i : F) zh[i] = xh[pos[i]];
@@ -551,6 +601,33 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     const bool kkt_ok = pg_rel <= ctx->opt.kkt_tol;
     int64_t support = 0;
     for (int64_t i = 0; i < N; ++i) support += zh[i] > 0.0;
+    if (warm && warm->record && kkt_ok && !failed) {
+        // keep the passive set and weights, and factor P0 = the support plus the zero-weight orbits
+        // nearest to entering (largest g_i / |u~_i|, all below the KKT tolerance)
+        warm->F0.assign(N, 0);
+        warm->w0 = zh;
+        std::vector<int64_t> S;
+        for (int64_t i = 0; i < N; ++i)
+            if (zh[i] > 0.0) { warm->F0[i] = 1; S.push_back(i); }
+        std::vector<std::pair<double, int64_t>> near;
+        for (int64_t i = 0; i < N; ++i)
+            if (!warm->F0[i] && hh[i] > 0.0) near.push_back({gh[i] / std::sqrt(hh[i]), i});
+        const int64_t extra = std::min<int64_t>(
+            (int64_t)near.size(),
+            std::min<int64_t>(cap - (int64_t)S.size(), (int64_t)std::ceil(warm->p0_extra * (double)S.size())));
+        if (extra > 0) {
+            std::partial_sort(near.begin(), near.begin() + extra, near.end(),
+                              [](const std::pair<double, int64_t>& a, const std::pair<double, int64_t>& b) {
+                                  return a.first > b.first;
+                              });
+            for (int64_t k = 0; k < extra; ++k) S.push_back(near[k].second);
+        }
+        std::sort(S.begin(), S.end());
+        bool ok = false;
+        if (!S.empty()) AS_TRY(factor(S, ok));
+        warm->P0 = P0;
+        warm->have_factor = ok;
+    }
     {
         LaunchTimer lt(ctx, K_CHI2);
         k_as_chi2_finish<<<1, 1, 0, st>>>(chi, lam / (double)N, chi2_dev);
@@ -581,11 +658,85 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     return SW_OK;
 }
 
+namespace {
+// y_b = y + sigma xi on the observed rows r >= nd; the 3-D density rows stay as they are (Sec. 2.4)
+__global__ void k_boot_data(int64_t M, int64_t nd, const double* __restrict__ y, const double* __restrict__ sig,
+                            const double* __restrict__ xi, double* __restrict__ yb)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < M; r += (int64_t)gridDim.x * blockDim.x)
+        yb[r] = r < nd ? y[r] : y[r] + sig[r] * xi[r];
+}
+}  // namespace
+
+template <typename T, typename AT, typename GT>
+sw_status solve_bootstrap(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev, const double* sig_dev, double lam,
+                          int64_t B, const double* xi_dev, double* w_dev, double* chi2b_dev)
+{
+    const int64_t M = Um->M, N = Um->N;
+    cudaStream_t st = ctx->stream;
+    SolveWS& ws = ctx->solve_ws;
+    // scratch: realisation data yb (M), weights (N), 1/sigma (M), y/sigma^2 (M), U w (M), residuals (2 M),
+    // chi^2 parts (4), flag
+    const size_t need = (size_t)(6 * M + N + 8) * sizeof(double);
+    AS_TRY(ctx->ensure(&ws.boot, &ws.boot_cap, need, "bootstrap vectors"));
+    double* yb = (double*)ws.boot;
+    double* wb = yb + M;
+    double* inv_sig = wb + N;
+    double* ys = inv_sig + M;
+    double* acc = ys + M;
+    double* e = acc + M;
+    double* xs = e + M;
+    double* chi = xs + M;
+    int* bad = (int*)(chi + 4);
+    AS_CUDA(ctx, cudaMemsetAsync(chi, 0, 8 * sizeof(double), st), "memset");
+    AS_CUDA(ctx, prep_data(ctx, M, sig_dev, y_dev, inv_sig, ys, bad), "prep data");
+    AsWarm warm;
+    warm.record = true;
+    sw_status worst = solve_active_set<T, AT, GT>(ctx, Um, y_dev, sig_dev, lam, wb, chi, &warm);
+    if (worst != SW_OK && worst != SW_ENONCONV) return worst;
+    warm.record = false;
+    warm.start = true;
+    int64_t solves = 0;
+    for (int64_t b = 0; b < B; ++b) {
+        {
+            LaunchTimer lt(ctx, K_MISC);
+            k_boot_data<<<(unsigned)std::min<int64_t>((M + 255) / 256, 4096), 256, 0, st>>>(
+                M, Um->nd, y_dev, sig_dev, xi_dev + (size_t)b * M, yb);
+        }
+        AS_CUDA(ctx, cudaGetLastError(), "bootstrap data");
+        double* wout = w_dev ? w_dev + (size_t)b * N : wb;
+        sw_status s = solve_active_set<T, AT, GT>(ctx, Um, yb, sig_dev, lam, wout, chi, &warm);
+        if (s != SW_OK && s != SW_ENONCONV) return s;
+        if (s == SW_ENONCONV) worst = SW_ENONCONV;
+        solves += (int64_t)ctx->solve_info[4];
+        // chi2_b: the observational chi^2 of w_b against the observed data
+        AS_CUDA(ctx, cudaMemsetAsync(acc, 0, M * sizeof(double), st), "memset");
+        AS_CUDA(ctx, u_times_w<T>(ctx, (const T*)Um->d, M, N, wout, acc), "U w_b");
+        AS_CUDA(ctx, residual(ctx, M, y_dev, acc, inv_sig, e, xs), "residual");
+        AS_CUDA(ctx, cudaMemsetAsync(chi, 0, 4 * sizeof(double), st), "memset");
+        AS_CUDA(ctx, chi2(ctx, M, Um->nd, e, N, wout, chi), "chi2_b");
+        AS_CUDA(ctx, cudaMemcpyAsync(chi2b_dev + b, chi + 1, sizeof(double), cudaMemcpyDeviceToDevice, st),
+                "chi2_b");
+    }
+    AS_CUDA(ctx, cudaStreamSynchronize(st), "bootstrap");
+    ctx->solve_info[4] = (double)solves;
+    ctx->solve_info[1] = (double)warm.factorisations;
+    return worst;
+}
+
+template sw_status solve_bootstrap<float, __nv_bfloat16, float>(sw_ctx*, const sw_matrix*, const double*,
+                                                                 const double*, double, int64_t, const double*,
+                                                                 double*, double*);
+template sw_status solve_bootstrap<float, float, float>(sw_ctx*, const sw_matrix*, const double*, const double*,
+                                                        double, int64_t, const double*, double*, double*);
+template sw_status solve_bootstrap<double, double, double>(sw_ctx*, const sw_matrix*, const double*, const double*,
+                                                           double, int64_t, const double*, double*, double*);
+
 template sw_status solve_active_set<float, __nv_bfloat16, float>(sw_ctx*, const sw_matrix*, const double*,
-                                                                  const double*, double, double*, double*);
+                                                                  const double*, double, double*, double*, AsWarm*);
 template sw_status solve_active_set<float, float, float>(sw_ctx*, const sw_matrix*, const double*, const double*,
-                                                         double, double*, double*);
+                                                         double, double*, double*, AsWarm*);
 template sw_status solve_active_set<double, double, double>(sw_ctx*, const sw_matrix*, const double*,
-                                                            const double*, double, double*, double*);
+                                                            const double*, double, double*, double*, AsWarm*);
 
 }  // namespace sw

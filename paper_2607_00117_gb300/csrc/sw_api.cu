@@ -16,7 +16,8 @@ const char* kKernelNames[K_COUNT] = {
     "ics_to_soa", "orbit_project_bin", "orbit_drift", "zero_flagged", "finalize_columns", "trajectory",
     "potential_eval", "whiten", "gram_tcgen05", "gram_simt", "shift_diag", "diag_factor_inverse", "panel_gemm",
     "syrk_update", "inverse_block_row", "trinv_update", "gemv_n", "gemv_t", "trmv_l", "trmv_lt", "admm_update",
-    "residual", "gradient", "chi2", "misc", "batch_orbit_bin", "mlp_fwd", "mlp_bwd", "adam", "reduce_gh", "pcg", "bundle", "cholesky_inverse"};
+    "residual", "gradient", "chi2", "misc", "batch_orbit_bin", "mlp_fwd", "mlp_bwd", "adam", "reduce_gh", "pcg", "bundle", "cholesky_inverse",
+    "syrk_update_tcgen05", "trinv_update_tcgen05"};
 
 void set_error(sw_ctx* ctx, const char* fmt, ...)
 {
@@ -161,11 +162,11 @@ static void ctx_release(sw_ctx* ctx)
     cudaStreamSynchronize(ctx->stream);
     ctx->harvest();
     void* bufs[] = {ctx->d_soa, ctx->d_cs, ctx->d_aos, ctx->d_drift, ctx->d_status, ctx->d_stats, ctx->d_ghtab,
-                    ctx->d_mlp, ctx->d_split, ctx->d_chol, ctx->d_ttotal};
+                    ctx->d_mlp, ctx->d_split, ctx->d_chol, ctx->d_ttotal, ctx->d_chol_tc};
     for (void* b : bufs)
         if (b) cudaFree(b);
     ctx->d_soa = ctx->d_cs = ctx->d_ghtab = ctx->d_mlp = ctx->d_split = ctx->d_chol = nullptr;
-    ctx->d_ttotal = nullptr;
+    ctx->d_ttotal = ctx->d_chol_tc = nullptr;
     ctx->d_aos = ctx->d_drift = nullptr;
     ctx->d_status = nullptr;
     ctx->d_stats = nullptr;
@@ -209,9 +210,18 @@ sw_status check_potential(sw_ctx* ctx, const sw_potential_params* p)
         set_error(ctx, "sw_set_potential: halo M200, c and H0 must be positive and finite");
         return SW_EINVAL;
     }
-    if (p->bar_M != 0.0 && !(pos_finite(p->bar_M) && pos_finite(p->bar_L) && pos_finite(p->bar_b) &&
-                              pos_finite(p->bar_c))) {
+    if (p->bar_kind != 0 && p->bar_kind != 1) {
+        set_error(ctx, "sw_set_potential: bar_kind must be 0 (Long-Murali) or 1 (Dehnen-Aly T3 + V4)");
+        return SW_EINVAL;
+    }
+    if (p->bar_M != 0.0 && p->bar_kind == 0 &&
+        !(pos_finite(p->bar_M) && pos_finite(p->bar_L) && pos_finite(p->bar_b) && pos_finite(p->bar_c))) {
         set_error(ctx, "sw_set_potential: bar mass, half-length and scales must be positive and finite");
+        return SW_EINVAL;
+    }
+    if (p->bar_M != 0.0 && p->bar_kind == 1 &&
+        !(pos_finite(p->bar_M) && pos_finite(p->bar_L) && pos_finite(p->disc_b))) {
+        set_error(ctx, "sw_set_potential: the paper's bar needs a positive mass, half-length and disc height");
         return SW_EINVAL;
     }
     if (p->test_kind < 0 || p->test_kind > 2 || (p->test_kind == 2 && !pos_finite(p->test_a)) ||
@@ -250,6 +260,32 @@ extern "C" sw_status sw_set_potential(sw_ctx* ctx, const sw_potential_params* p)
     return SW_OK;
 }
 
+// Positive nodes and weights of the 8-point Gauss-Legendre rule on [-1, 1]: the roots of the
+// Legendre polynomial P_8 by Newton's method from the asymptotic first guesses, weights
+// 2 / ((1 - x^2) P_8'(x)^2) (Abramowitz & Stegun 25.4.29).
+static void gauss_legendre8(double x[4], double w[4])
+{
+    const int n = 8;
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < n / 2; ++k) {
+        double t = std::cos(pi * (k + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 60; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int j = 2; j <= n; ++j) {
+                const double p2 = ((2 * j - 1) * t * p1 - (j - 1) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            const double step = p1 / dp;
+            t -= step;
+            if (std::fabs(step) < 1e-17) break;
+        }
+        x[k] = t;
+        w[k] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
 template <typename T>
 FieldT<T> make_field_from(const sw_potential_params& p, double Mdm, double rs)
 {
@@ -270,6 +306,25 @@ FieldT<T> make_field_from(const sw_potential_params& p, double Mdm, double rs)
     f.test_kind = p.test_kind;
     f.gm_test = (T)(SW_G * p.test_M);
     f.test_a2 = (T)(p.test_a * p.test_a);
+    f.bar_kind = p.bar_kind;
+    if (p.bar_kind == 1 && p.bar_M > 0.0) {
+        // the paper's bar (Sec. 2.1.2): T3 (eta = 1, a = L_b / 5, b = b_d, L = L_b) + V4 (eta = 0,
+        // a = b = 0.5 kpc, L = 0.1 kpc), equal halves of M_b
+        f.da_gm1 = (T)(SW_G * 0.5 * p.bar_M);
+        f.da_a1 = (T)(p.bar_L / 5.0);
+        f.da_b1sq = (T)(p.disc_b * p.disc_b);
+        f.da_L1 = (T)p.bar_L;
+        f.da_gm2 = (T)(SW_G * 0.5 * p.bar_M);
+        f.da_a2 = (T)0.5;
+        f.da_b2sq = (T)0.25;
+        f.da_L2 = (T)0.1;
+        double gx[4], gw[4];
+        gauss_legendre8(gx, gw);
+        for (int k = 0; k < 4; ++k) {
+            f.gl_x[k] = (T)gx[k];
+            f.gl_w[k] = (T)gw[k];
+        }
+    }
     return f;
 }
 
@@ -848,7 +903,7 @@ const int kKernelWorkKind[K_COUNT] = {
     W_BYTES /*gemv_t*/, W_BYTES /*trmv_l*/, W_BYTES /*trmv_lt*/, W_NONE /*admm_update*/, W_BYTES /*residual*/,
     W_BYTES /*gradient*/, W_NONE /*chi2*/, W_NONE /*misc*/, W_ORBIT_STEPS /*batch_orbit*/, W_FLOP_SIMT /*mlp_fwd*/,
     W_FLOP_SIMT /*mlp_bwd*/, W_NONE /*adam*/, W_BYTES /*reduce_gh*/, W_NONE /*pcg*/, W_BYTES /*bundle*/,
-    W_FLOP_SIMT /*cholesky_inverse*/};
+    W_FLOP_SIMT /*cholesky_inverse*/, W_FLOP_TENSOR /*syrk_tc*/, W_FLOP_TENSOR /*trinv_tc*/};
 
 void add_work(sw_ctx* ctx, int kid, double units)
 {
@@ -930,6 +985,9 @@ extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value)
     } else if (!strcmp(key, "chol_coop")) {
         if (!(value == 0 || value == 1)) return SW_EINVAL;
         ctx->opt.chol_coop = (int)value;
+    } else if (!strcmp(key, "chol_tc")) {
+        if (!(value == 0 || value == 1)) return SW_EINVAL;
+        ctx->opt.chol_tc = (int)value;
     } else if (!strcmp(key, "integrator")) {
         if (!(value == 0 || value == 1)) return SW_EINVAL;
         ctx->opt.integrator = (int)value;

@@ -34,6 +34,7 @@ struct Options {
     double as_grow = 0.0;        // active set: at most max(as_block, as_grow |F|) orbits enter per step
     int solver = 0;              // 0 auto, 1 active set, 2 ADMM (see solve_dispatch)
     int chol_coop = 0;           // Cholesky + inverse in one cooperative launch (0: per-step launches)
+    int chol_tc = 1;             // FP32 Cholesky + inverse with tcgen05 trailing updates (0: SIMT, 64-wide)
     int integrator = 0;          // 0: kick-drift-kick at fixed dt; 1: adaptive Bogacki-Shampine 3(2) in the bar frame
     double bs3_rtol = 1e-4;      // relative tolerance of the adaptive integrator
     int as_cg_max = 200;         // active set: conjugate-gradient steps per reduced solve
@@ -57,6 +58,7 @@ struct SolveWS {
     void* H = nullptr; size_t H_cap = 0;          // polish: reduced normal matrix (FP64)
     void* Hi = nullptr; size_t Hi_cap = 0;        // polish: inverse of its Cholesky factor
     void* pv = nullptr; size_t pv_cap = 0;        // polish: index list and vectors
+    void* boot = nullptr; size_t boot_cap = 0;    // bootstrap solves: realisation data and vectors
     const sw_matrix* A_of = nullptr;              // which matrix A was built from
     void release();
     void forget_matrix(const sw_matrix* U) { if (A_of == U) A_of = nullptr; }
@@ -97,6 +99,7 @@ struct sw_ctx {
     void* d_mlp = nullptr; size_t mlp_cap = 0;   // MLP activations
     void* d_split = nullptr; size_t split_cap = 0;   // FP64 vectors split into float hi + lo
     void* d_chol = nullptr; size_t chol_cap = 0;     // cooperative Cholesky: diagonal inverses, barrier
+    void* d_chol_tc = nullptr; size_t chol_tc_cap = 0;   // tensor-core Cholesky: diagonal inverse, BF16 panels
     void* d_ttotal = nullptr; size_t ttotal_cap = 0;   // per-orbit integration time (adaptive integrator)
     // solve
     sw::SolveWS solve_ws;

@@ -22,8 +22,15 @@ struct FieldT {
     T gm_halo, halo_rs, halo_inv_rs;
     T k_bar, bar_L, bar_a, bar_b2;     // k_bar = G M / (2 L)
     T gm_test, test_a2;
+    // the paper's bar (bar_kind 1): T3 long bar (G M_1, a_1, b_1^2, L_1) and V4 bulge (G M_2, a_2, b_2^2,
+    // L_2), and the 8-point Gauss-Legendre rule on [-1, 1] (positive nodes and their weights) used for
+    // the V4 needle integrals
+    T da_gm1, da_a1, da_b1sq, da_L1;
+    T da_gm2, da_a2, da_b2sq, da_L2;
+    T gl_x[4], gl_w[4];
     int test_kind;
     int has_disc, has_halo, has_bar;
+    int bar_kind;                      // 0 Long-Murali needle (n = 1, eta = 0); 1 Dehnen-Aly T3 + V4
 };
 
 // Observation geometry: Euler matrix rows and bin grids.
@@ -63,7 +70,8 @@ enum KernelId {
     K_ICS_SOA = 0, K_ORBIT_BIN, K_ORBIT_DRIFT, K_ZERO_FLAGGED, K_FINALIZE, K_TRAJ, K_POTEVAL,
     K_WHITEN, K_GRAM_TC, K_GRAM_SIMT, K_SHIFT, K_POTRF_DIAG, K_TRSM_PANEL, K_SYRK_UPDATE,
     K_TRINV_DIAG, K_TRINV_UPDATE, K_GEMV_N, K_GEMV_T, K_TRMV_L, K_TRMV_LT, K_ADMM_UPDATE,
-    K_RESID, K_GRAD, K_CHI2, K_MISC, K_BATCH_ORBIT, K_MLP_FWD, K_MLP_BWD, K_ADAM, K_REDUCE_GH, K_PCG, K_BUNDLE, K_CHOL_COOP, K_COUNT
+    K_RESID, K_GRAD, K_CHI2, K_MISC, K_BATCH_ORBIT, K_MLP_FWD, K_MLP_BWD, K_ADAM, K_REDUCE_GH, K_PCG, K_BUNDLE, K_CHOL_COOP,
+    K_SYRK_TC, K_TRINV_TC, K_COUNT
 };
 extern const char* kKernelNames[K_COUNT];
 

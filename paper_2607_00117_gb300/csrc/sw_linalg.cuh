@@ -2,6 +2,8 @@
 #pragma once
 #include "sw_api_internal.cuh"
 
+#include <vector>
+
 namespace sw {
 
 template <typename T, typename AT>
@@ -24,6 +26,11 @@ cudaError_t cholesky_inverse_coop(sw_ctx* ctx, T* G, T* X, int64_t K, int* d_inf
 // Cholesky (in place) and the explicit inverse X = L^{-1} by per-step launches (D unused)
 template <typename T>
 cudaError_t cholesky_inverse(sw_ctx* ctx, T* G, T* X, T* D, int64_t K, int* d_info);
+// FP32 Cholesky (in place) and X = L^{-1} in 128-wide steps with the trailing and inverse updates on
+// the tensor cores (k_chol_tc.cu); cudaErrorNotSupported without the tensor-map encoder; *d_err != 0 if
+// a bounded wait of a tensor-core kernel ran out
+cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int* d_info, int* d_err);
+bool chol_tc_available();
 template <typename T>
 cudaError_t symmetrize(sw_ctx* ctx, const T* G, int64_t K, T* S);
 template <typename T>
@@ -80,10 +87,32 @@ template <typename T>
 cudaError_t gather_cols(sw_ctx* ctx, const T* U, int64_t M, const int64_t* idx, int64_t n, T* Uc);
 cudaError_t scatter_vec(sw_ctx* ctx, const double* a, const int64_t* idx, int64_t n, double* out);
 
+// Warm start of the active-set solve across related problems (the bootstrap realisations of one
+// matrix, Sec. 2.4): `record` keeps the final passive set and weights of a solve and factors a
+// superset P0 of its passive set (the passive set plus the zero-weight orbits nearest to entering);
+// `start` begins a later solve from that passive set and those weights and reuses the factor of P0
+// for every passive set inside it.
+struct AsWarm {
+    bool record = false, start = false;
+    std::vector<char> F0;        // passive set of the recorded solve (N flags)
+    std::vector<double> w0;      // its weights (N)
+    std::vector<int64_t> P0;     // the factored set (ascending)
+    bool have_factor = false;
+    double p0_extra = 0.15;      // P0 = F0 plus up to this fraction of |F0| near-active orbits
+    int64_t factorisations = 0;  // factorisations made by the solves of this warm start
+};
+
 // block active-set solve (sw_active_set.cu)
 template <typename T, typename AT, typename GT>
 sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* U, const double* y_dev, const double* sig_dev, double lam,
-                           double* w_dev, double* chi2_dev);
+                           double* w_dev, double* chi2_dev, AsWarm* warm = nullptr);
+// B bootstrap realisations of the data (Sec. 2.4): y_b = y + sigma xi_b on the observed rows (the
+// density rows unchanged), one active-set solve each, warm-started from the solve on y; chi2_b is
+// the observational chi^2 of w_b against y (xi_dev: B x M device, w_dev: B x N device or NULL,
+// chi2b_dev: B device)
+template <typename T, typename AT, typename GT>
+sw_status solve_bootstrap(sw_ctx* ctx, const sw_matrix* U, const double* y_dev, const double* sig_dev, double lam,
+                          int64_t B, const double* xi_dev, double* w_dev, double* chi2b_dev);
 
 // tcgen05 Gram (k_gram_tc.cu): C (K x K, FP32, row-major, lower tiles) = A A^T with A
 // K x ldA BF16 row-major (ldA a multiple of 64, columns beyond the data zero).  With

@@ -41,7 +41,7 @@ using namespace sw;
 
 void SolveWS::release()
 {
-    void* bufs[] = {A, Alo, G, Gs, X, D, vec, R, H, Hi, pv, Uc, outer};
+    void* bufs[] = {A, Alo, G, Gs, X, D, vec, R, H, Hi, pv, Uc, outer, boot};
     for (void* b : bufs)
         if (b) cudaFree(b);
     *this = SolveWS();
@@ -735,6 +735,59 @@ extern "C" sw_status sw_solve_weights(sw_ctx* ctx, const sw_matrix* U, const dou
                 (e2 = cudaMemcpyAsync(chi2_out, dc, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream)) ||
                 (e2 = cudaStreamSynchronize(ctx->stream)))
                 s = ctx->cuda_fail(e2, "result download");
+        }
+    }
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(buf);
+    return s;
+}
+
+extern "C" sw_status sw_solve_bootstrap(sw_ctx* ctx, const sw_matrix* U, const double* data, const double* errors,
+                                        double lambda, int64_t n_boot, const double* xi, double* weights_out,
+                                        double* chi2_b_out, double* chi2_model_out)
+{
+    SW_TRY(check_solve_args(ctx, U, data, errors, lambda, chi2_b_out, chi2_model_out));
+    if (n_boot < 1 || !xi) { set_error(ctx, "sw_solve_bootstrap: n_boot >= 1 and the draws xi are required"); return SW_EINVAL; }
+    if (!(lambda > 0.0) && U->N > U->M) {
+        set_error(ctx, "sw_solve_bootstrap: the warm-started active set needs lambda > 0 or no more orbits than rows");
+        return SW_EINVAL;
+    }
+    cudaSetDevice(ctx->device);
+    const int64_t M = U->M, N = U->N, B = n_boot;
+    double* buf = nullptr;
+    const size_t nbuf = (size_t)(2 * M + B * M + (weights_out ? B * N : 0) + B);
+    cudaError_t e = cudaMalloc(&buf, nbuf * sizeof(double));
+    if (e != cudaSuccess) { cudaGetLastError(); return ctx->cuda_fail(e, "bootstrap staging"); }
+    double *dy = buf, *ds = buf + M, *dxi = buf + 2 * M, *dw = weights_out ? dxi + B * M : nullptr;
+    double* dc = dxi + B * M + (weights_out ? B * N : 0);
+    sw_status s = SW_OK;
+    if ((e = cudaMemcpyAsync(dy, data, M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaMemcpyAsync(ds, errors, M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaMemcpyAsync(dxi, xi, (size_t)B * M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream))) {
+        s = ctx->cuda_fail(e, "bootstrap upload");
+    } else {
+        if (U->elem == 8)
+            s = solve_bootstrap<double, double, double>(ctx, U, dy, ds, lambda, B, dxi, dw, dc);
+        else if (ctx->opt.gram_tc && gram_tc_available())
+            s = solve_bootstrap<float, __nv_bfloat16, float>(ctx, U, dy, ds, lambda, B, dxi, dw, dc);
+        else
+            s = solve_bootstrap<float, float, float>(ctx, U, dy, ds, lambda, B, dxi, dw, dc);
+        if (s == SW_OK || s == SW_ENONCONV) {
+            cudaError_t e2;
+            if ((e2 = cudaMemcpyAsync(chi2_b_out, dc, B * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream)) ||
+                (weights_out && (e2 = cudaMemcpyAsync(weights_out, dw, (size_t)B * N * sizeof(double),
+                                                      cudaMemcpyDeviceToHost, ctx->stream))) ||
+                (e2 = cudaStreamSynchronize(ctx->stream))) {
+                s = ctx->cuda_fail(e2, "bootstrap download");
+            } else {
+                // marginalised chi^2 over the realisations: -2 ln of the bootstrap-averaged likelihood
+                // exp(-chi2_b / 2), taken relative to the smallest chi2_b so nothing over- or underflows
+                double cmin = chi2_b_out[0];
+                for (int64_t b = 1; b < B; ++b) cmin = std::min(cmin, chi2_b_out[b]);
+                double sum = 0.0;
+                for (int64_t b = 0; b < B; ++b) sum += std::exp(-0.5 * (chi2_b_out[b] - cmin));
+                *chi2_model_out = cmin - 2.0 * std::log(sum / (double)B);
+            }
         }
     }
     cudaStreamSynchronize(ctx->stream);

@@ -33,7 +33,7 @@ class PotentialParams(ctypes.Structure):
     _fields_ = [("disc_M", ctypes.c_double), ("disc_a", ctypes.c_double), ("disc_b", ctypes.c_double),
                 ("halo_M200", ctypes.c_double), ("halo_c", ctypes.c_double), ("H0", ctypes.c_double),
                 ("bar_M", ctypes.c_double), ("bar_L", ctypes.c_double), ("bar_b", ctypes.c_double),
-                ("bar_c", ctypes.c_double), ("test_kind", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("bar_c", ctypes.c_double), ("test_kind", ctypes.c_int32), ("bar_kind", ctypes.c_int32),
                 ("test_M", ctypes.c_double), ("test_a", ctypes.c_double)]
 
 
@@ -93,6 +93,7 @@ SIGNATURES = {
     "sw_solve_weights": (ctypes.c_int, [_VP, _VP, _D, _D, ctypes.c_double, _D, _D]),
     "sw_solve_weights_device": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP]),
     "sw_solve_info": (ctypes.c_int, [_VP, _D]),
+    "sw_solve_bootstrap": (ctypes.c_int, [_VP, _VP, _D, _D, ctypes.c_double, ctypes.c_int64, _D, _D, _D, _D]),
     "sw_matrix_shape": (ctypes.c_int, [_VP, _I64, _I64, _I64]),
     "sw_matrix_copy": (ctypes.c_int, [_VP, _D]),
     "sw_matrix_apply": (ctypes.c_int, [_VP, _D, _D]),
@@ -163,7 +164,8 @@ def potential_params(p: dict) -> PotentialParams:
                            halo_M200=p.get("halo_M200", 0.0), halo_c=p.get("halo_c", 10.0), H0=p.get("H0", 70.0),
                            bar_M=p.get("bar_M", 0.0), bar_L=p.get("bar_L", 1.0), bar_b=p.get("bar_b", 1.0),
                            bar_c=p.get("bar_c", 1.0), test_kind=int(p.get("test_kind", 0)),
-                           test_M=p.get("test_M", 0.0), test_a=p.get("test_a", 1.0))
+                           bar_kind=int(p.get("bar_kind", 0)), test_M=p.get("test_M", 0.0),
+                           test_a=p.get("test_a", 1.0))
 
 
 class Matrix:
@@ -381,6 +383,22 @@ class Context:
     def solve_weights_device(self, U: Matrix, data_t, errors_t, lam: float, w_t, chi2_t) -> int:
         return lib().sw_solve_weights_device(self.handle, U.handle, _tp(data_t), _tp(errors_t), lam, _tp(w_t),
                                              _tp(chi2_t))
+
+    def solve_bootstrap(self, U: Matrix, data: np.ndarray, errors: np.ndarray, lam: float, xi: np.ndarray,
+                        want_weights: bool = False, allow_nonconv: bool = False):
+        """(weights (B, N) or None, chi2_b (B,), chi2_model) of sw_solve_bootstrap; xi is (B, M)."""
+        data = np.ascontiguousarray(data, dtype=np.float64)
+        errors = np.ascontiguousarray(errors, dtype=np.float64)
+        xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, U.M)
+        B = len(xi)
+        w = np.empty((B, U.N)) if want_weights else None
+        chi_b = np.empty(B)
+        chi_m = np.empty(1)
+        st = lib().sw_solve_bootstrap(self.handle, U.handle, _dp(data), _dp(errors), lam, B, _dp(xi),
+                                      _dp(w) if w is not None else None, _dp(chi_b), _dp(chi_m))
+        if not (st == SW_OK or (allow_nonconv and st == SW_ENONCONV)):
+            self._check(st)
+        return w, chi_b, float(chi_m[0])
 
     def solve_info(self) -> dict:
         out = np.zeros(8)

@@ -9,9 +9,10 @@ for regular orbits (FP32 form against FP64); orbit-matrix L1 difference
 <= 1e-3 per orbit.
 
 Two readings make the FP32 gates well posed.  "Regular" means a twin orbit
-displaced by 1e-9 kpc separates by less than 20x over the 1e3 steps: FP32
-rounding of each step's force is ~1e-7 relative and accumulates to a few
-1e-6 over 1e3 steps, so a 1e-5 gate leaves room for little amplification.  The per-orbit matrix gate allows, on top of
+displaced by 1e-9 kpc separates by less than 1e4 x over the 1e3 steps; any
+other orbit is held to the oracle's own spread under perturbations of its
+initial condition (FP32 rounding of each step's force is ~1e-7 relative and
+accumulates to a few 1e-6 over 1e3 steps on regular orbits).  The per-orbit matrix gate allows, on top of
 1e-3, the moves of sample copies whose oracle coordinate lies within 2e-4
 bin widths of an edge (guard band, counted from the oracle trajectory); orbits
 whose oracle column itself moves by > 2e-4 under a 1e-7 relative change of the
@@ -30,6 +31,8 @@ pytestmark = pytest.mark.gpu
 W1 = inputs.WORKLOADS["axisym_2k"]
 W2 = inputs.WORKLOADS["barred_100k"]
 BARRED = dict(inputs.DISC_HALO, **inputs.BAR)
+# the paper's bar (Sec. 2.1.2): Dehnen-Aly T3 long bar + V4 bulge of total mass M_b, half-length L_b
+PAPER_BAR = dict(inputs.DISC_HALO, bar_M=1e10, bar_L=4.0, bar_kind=1)
 
 
 @pytest.fixture(scope="module")
@@ -61,6 +64,33 @@ def test_potential_and_force(sw, orc):
         assert np.all(np.abs(acc - acc_o) <= rtol * 4 * scale + 1e-30), prec
 
 
+def test_potential_and_force_paper_bar(sw, orc):
+    """The paper's Dehnen-Aly T3 + V4 bar (bar_kind 1) with the disc and halo, and the bar
+    alone, at 1e3 points against the oracle (its needle integrals by 48-point quadrature):
+    FP64 to 1e-11; FP32 potential to 1e-6 (total) and 3e-5 (bar alone, where the closed
+    forms' differences lose digits far from the needle), force to 5e-5 and 1e-4 of |a|
+    floored at 1e-3 of the median |a| (it vanishes at the centre, where only an absolute
+    error means anything)."""
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.normal(0, 3, (500, 3)), rng.normal(0, 12, (494, 3)),
+                        np.array([[0.0, 0, 0], [4.0, 0, 0], [-4.0, 0.01, 0], [0.05, 0, 0.02],
+                                  [30.0, -20.0, 5.0], [1e-4, 1e-4, 0]])])
+    bar_only = dict(disc_M=0.0, disc_a=3.0, disc_b=0.3, halo_M200=0.0, halo_c=10.0, bar_M=1e10, bar_L=4.0,
+                    bar_kind=1)
+    for pot, tol32 in ((PAPER_BAR, (1e-6, 5e-5)), (bar_only, (3e-5, 1e-4))):
+        phi_o, acc_o = orc.potential(orc.make_pot(pot), x)
+        n = np.linalg.norm(acc_o, axis=1, keepdims=True)
+        scale = np.maximum(n, 1e-3 * np.median(n))
+        for prec, (tp, ta) in (("fp64", (1e-11, 1e-11)), ("fp32", tol32)):
+            c = ctx_for(sw, prec, pot)
+            phi, acc = c.potential_eval(x)
+            np.testing.assert_allclose(phi, phi_o, rtol=tp)
+            assert np.all(np.abs(acc - acc_o) <= ta * scale), (prec, (np.abs(acc - acc_o) / scale).max())
+    c = sw.Context(0, "fp32")
+    with pytest.raises(sw.SwError):
+        c.set_potential(dict(PAPER_BAR, bar_kind=2))
+
+
 def _grid(W, **kw):
     g = dict(W["grid"]); g.update(kw)
     return g
@@ -70,9 +100,9 @@ def _counts(U, S, ncopy=4):
     return np.rint(U * ncopy * S).astype(np.int64)
 
 
-@pytest.mark.parametrize("pot_name", ["axisym", "barred"])
+@pytest.mark.parametrize("pot_name", ["axisym", "barred", "paper_bar"])
 def test_counts_bit_exact_64_steps_fp64(sw, orc, pot_name):
-    pot = inputs.DISC_HALO if pot_name == "axisym" else BARRED
+    pot = {"axisym": inputs.DISC_HALO, "barred": BARRED, "paper_bar": PAPER_BAR}[pot_name]
     omega = 0.0 if pot_name == "axisym" else 40.0
     grid = _grid(W1) if pot_name == "axisym" else _grid(W2, nx=20, ny=20, nv=16, nR=10, nphi=10, nz=5)
     ics = inputs.disc_ics(inputs.DISC_HALO, 700, seed=101)     # several 128-orbit tiles + ragged tail
@@ -125,29 +155,44 @@ def test_counts_fp32_outside_guard_band(sw, orc):
 def test_phase_space_fp32_regular_orbits(sw, orc):
     """Per-step relative error <= 1e-5 over 1e3 steps for regular orbits.  An
     orbit is regular if a twin displaced by 1e-9 kpc separates by less than
-    20 x over the same steps (oracle FP64).  The error at each step is relative
+    1e4 x over the same steps (oracle FP64).  The error at each step is relative
     to the orbit's own scale: |dx(t)| / max_t |x| and |dv(t)| / max_t |v| (a
     pointwise |v(t)| near a turning point would measure a phase error against a
-    vanishing speed)."""
+    vanishing speed).  Every other orbit is held to the oracle's own spread: its
+    error at each step is at most 3 x the largest deviation of the oracle's
+    trajectory under four seeded relative perturbations of 1e-6 of its initial
+    condition, plus 1e-5."""
     pot, omega = BARRED, 40.0
     ics = inputs.disc_ics(inputs.DISC_HALO, 64, seed=103)
     S, dt = 1000, inputs.DT_HALF_MYR
     po = orc.make_pot(pot)
     c = ctx_for(sw, "fp32", pot)
     tg = c.trajectory(ics, omega, dt, S)
-    n_regular = 0
+    n_regular, n_spread, worst = 0, 0, 0.0
     for i, ic in enumerate(ics):
         to = orc.trajectory(po, omega, dt, S, ic)
         ic2 = ic.copy(); ic2[0] += 1e-9
         t2 = orc.trajectory(po, omega, dt, S, ic2)
-        sep = np.linalg.norm(t2[:, :3] - to[:, :3], axis=1).max()
-        if sep > 20 * 1e-9:
-            continue
-        n_regular += 1
-        ex = np.linalg.norm(tg[i, :, :3] - to[:, :3], axis=1) / np.linalg.norm(to[:, :3], axis=1).max()
-        ev = np.linalg.norm(tg[i, :, 3:] - to[:, 3:], axis=1) / np.linalg.norm(to[:, 3:], axis=1).max()
-        assert max(ex.max(), ev.max()) <= 1e-5, (i, ex.max(), ev.max())
-    assert n_regular >= 12
+        amp = np.linalg.norm(t2[:, :3] - to[:, :3], axis=1).max() / 1e-9
+        sx = np.linalg.norm(to[:, :3], axis=1).max()
+        sv = np.linalg.norm(to[:, 3:], axis=1).max()
+        err = np.maximum(np.linalg.norm(tg[i, :, :3] - to[:, :3], axis=1) / sx,
+                         np.linalg.norm(tg[i, :, 3:] - to[:, 3:], axis=1) / sv)
+        if amp < 1e4:
+            n_regular += 1
+            worst = max(worst, err.max())
+            assert err.max() <= 1e-5, (i, amp, err.max())
+        else:
+            n_spread += 1
+            spread = np.zeros(S + 1)
+            rng = np.random.default_rng(6100 + i)
+            for _ in range(4):
+                tp = orc.trajectory(po, omega, dt, S, ic * (1 + 1e-6 * rng.standard_normal(6)))
+                spread = np.maximum(spread, np.maximum(np.linalg.norm(tp[:, :3] - to[:, :3], axis=1) / sx,
+                                                       np.linalg.norm(tp[:, 3:] - to[:, 3:], axis=1) / sv))
+            assert np.all(err <= 3 * spread + 1e-5), (i, amp, err.max(), spread.max())
+    print(f"phase space: {n_regular} regular orbits (largest error {worst:.3g}), {n_spread} under the spread gate")
+    assert n_regular + n_spread == len(ics) and n_regular >= len(ics) // 2
 
 
 def test_phase_space_fp64(sw, orc):
@@ -246,6 +291,50 @@ def test_drift_pass_and_quality_cut(sw, orc):
     assert status[7] == 2 and np.all(status[ok] == (d_o[ok] > 0.1))
     U = c.project(_grid(W2, nx=10, ny=10, nv=8, nR=5, nphi=4, nz=3)).copy()
     assert np.all(U[7] == 0)
+
+
+def _sampled_drift(orc, po, omega, dt, S, ic, every):
+    """The oracle's Jacobi drift max |E_J(t_n) - E_J(0)| / |E_J(0)| over the samples
+    n = every, 2 every, ... and the last step."""
+    to = orc.trajectory(po, omega, dt, S, ic)
+    e0 = orc.jacobi(po, omega, 0.0, to[0])
+    ns = sorted(set(range(every, S + 1, every)) | {S})
+    return max(abs(orc.jacobi(po, omega, n * dt, to[n]) - e0) / abs(e0) for n in ns)
+
+
+def test_drift_fp32_against_oracle(sw, orc):
+    """The FP32 form's Jacobi drift (Sec. 2.2.2) against the oracle's, orbit by orbit:
+    the drift pass of sw_integrate_library checks every step, the projection pass every
+    ej_every = 8 steps and the last (its default in FP32), and the oracle's drift is taken
+    at the same samples.  Gate: within 3 x the spread of the oracle's own drift under four
+    seeded relative perturbations of 1e-6 of the initial condition, plus 1e-6 + 1e-3 of
+    the drift; the quality-cut status agrees wherever the drift is not within that band
+    of the 0.1 cut."""
+    pot, omega = BARRED, 40.0
+    po = orc.make_pot(pot)
+    ics = inputs.disc_ics(inputs.DISC_HALO, 160, seed=108)
+    S, dt = 300, inputs.DT_HALF_MYR
+    c = ctx_for(sw, "fp32", pot)
+    drift_every, status_every = c.integrate_library(ics, omega, dt, S, want_drift=True)
+    c.project(_grid(W2, nx=10, ny=10, nv=8, nR=5, nphi=4, nz=3))
+    drift_8, status_8 = c.project_stats(len(ics))
+    rng = np.random.default_rng(5100)
+    xis = [rng.standard_normal(ics.shape) for _ in range(4)]
+    for every, dg, sg in ((1, drift_every, status_every), (8, drift_8, status_8)):
+        do = np.array([_sampled_drift(orc, po, omega, dt, S, ic, every) for ic in ics])
+        if every == 1:
+            np.testing.assert_allclose(do, orc.drift(po, omega, dt, S, ics), rtol=1e-12, atol=1e-15)
+        spread = np.zeros(len(ics))
+        for xi in xis:
+            dp = np.array([_sampled_drift(orc, po, omega, dt, S, ic, every) for ic in ics * (1 + 1e-6 * xi)])
+            spread = np.maximum(spread, np.abs(dp - do))
+        band = 3 * spread + 1e-6 + 1e-3 * do
+        diff = np.abs(dg - do)
+        print(f"FP32 drift every {every}: max |diff| {diff.max():.3g}, max diff / band {(diff / band).max():.3g}, "
+              f"largest drift {do.max():.3g}")
+        assert np.all(diff <= band), (every, np.flatnonzero(diff > band), diff[diff > band], band[diff > band])
+        clear = np.abs(do - 0.1) > band
+        np.testing.assert_array_equal(sg[clear], (do[clear] > 0.1).astype(np.uint8))
 
 
 def test_edge_cases(sw, orc):
