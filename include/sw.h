@@ -126,7 +126,9 @@ sw_status sw_integrate_library_device(sw_ctx* ctx, const double* ics_dev, int64_
  * (host, npix x 2 reference (v0, s) per pixel) is non-NULL, four Gauss-Hermite rows per pixel
  * (pixel*4 + m-1, m = 1..4) holding sum 2 sqrt(pi) alpha(w) H_m(w), w = (v_los - v0)/s.
  * Orbits whose Jacobi drift exceeds 0.1 or turn non-finite get zero columns.  *U_out receives a
- * device-resident matrix stored orbit-major (column i contiguous).  vb may be NULL in GH mode. */
+ * device-resident matrix stored orbit-major (column i contiguous).  vb may be NULL in GH mode.
+ * With the option project_bundle = n > 1 the matrix has n_orb / n columns, column j the mean of
+ * orbits j n .. j n + n - 1 (Sec. 2.2.1 orbit bundles), accumulated at bin time. */
 sw_status sw_project(sw_ctx* ctx, double incl, double pa, double bar_angle, const sw_pixel_grid* pix,
                      const sw_vbins* vb, const sw_density_grid* dens, const double* gh_v0_s, int mirror4,
                      sw_matrix** U_out);
@@ -279,6 +281,11 @@ int64_t sw_alloc_count(const sw_ctx* ctx);
  *                           orbit_direct_max orbits, ADMM otherwise; 1: always the active set; 2: always ADMM
  *                           (the paper's solver, Sec. 2.3, with FP64 refinement and the exact polish)
  *  "chol_coop" (0/1)        active set: Cholesky and its inverse in one cooperative launch (default 0)
+ *  "project_bundle" (>= 1)  orbits per column of sw_project's matrix (default 1): with n > 1 the n consecutive
+ *                           orbits of a bundle (Sec. 2.2.1) accumulate into one column at bin time, which holds
+ *                           their mean (counts / (copies nsteps n)); a realisation cut by the quality test adds a
+ *                           zero column to the mean (its counts are removed exactly, GH sums to rounding), as
+ *                           sw_bundle of the unbundled matrix; n must divide the orbit count; fixed-step KDK only
  *  "chol_tc" (0/1)          active set, FP32 form: Cholesky and its inverse in 128-wide steps with the trailing and
  *                           inverse updates on the tensor cores (BF16 hi + lo split, default 1); 0: FP32 SIMT updates
  *  "integrator" (0/1)       sw_project's integrator: 0 (default) kick-drift-kick at the fixed dt in the inertial

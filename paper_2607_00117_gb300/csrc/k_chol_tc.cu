@@ -44,20 +44,23 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
 }
 
 // ---------------------------------------------------------------------------
-// 1. Diagonal block: Cholesky and triangular inverse.  512 threads; thread
-// (ty, tx) = (t / 16, t % 16) owns rows i = ty + 32 r (r < 4) and columns
-// l = tx + 16 c (c < 8) of the 128 x 128 block.  Cholesky in the unscaled
-// form a_il -= a_ij a_lj / a_jj (column j of the result is a_ij / sqrt(a_jj)).
-// The update runs unconditionally over every owned element of the row and
-// column blocks that can still change: the column values of finished rows and
-// columns enter as zeros, and the upper-triangle elements it also touches are
-// never read.  The loops over the column block cb (factor) and the row block
-// rb (inverse) are unrolled so that every register index is a compile-time
-// constant (a selection by a runtime block index would put the arrays in local
-// memory).
+// 1. Diagonal block: Cholesky and triangular inverse.  256 threads; thread
+// (ty, tx) = (t / 16, t % 16) owns rows i = ty + 16 r and columns l = tx + 16 c
+// (r, c < 8) of the 128 x 128 block in registers.  Cholesky in the unscaled
+// form a_il -= a_ij a_lj / a_jj (column j of the result is a_ij / sqrt(a_jj)),
+// one CTA barrier per column: the owners of column j + 1 pass it on through
+// shared memory.  The update runs unconditionally over the owned row and
+// column blocks that can still change (the values of finished rows and
+// columns enter as zeros; the upper-triangle elements it also touches are
+// never read).  The pivot's reciprocal square root is the only special
+// function per step.  The loops over the column block cb (factor) and the row
+// block rb (inverse) are unrolled so that every register index is a
+// compile-time constant (a selection by a runtime block index would put the
+// arrays in local memory).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512, 1) k_diag128(float* __restrict__ G, int64_t ld, int64_t j0, int bs,
-                                                    float* __restrict__ D, int* info)
+constexpr int DIAG_THREADS = 256;
+__global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__ G, int64_t ld, int64_t j0, int bs,
+                                                             float* __restrict__ D, int* info)
 {
     extern __shared__ float sm[];
     float* Ls = sm;                 // DB x LP: the factor
@@ -65,17 +68,17 @@ __global__ void __launch_bounds__(512, 1) k_diag128(float* __restrict__ G, int64
     float* rowx = col + 2 * DB;     // 2 x DB: row k of the inverse (ping-pong)
     float* rdiag = rowx + 2 * DB;   // DB: 1 / L_jj
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
-    float a[4][8];
+    float a[8][8];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int i = ty + 32 * r, l = tx + 16 * c;
+            const int i = ty + 16 * r, l = tx + 16 * c;
             a[r][c] = (i < bs && l <= i) ? G[(size_t)(j0 + i) * ld + j0 + l] : 0.f;
         }
     if (tx == 0) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) col[ty + 32 * r] = a[r][0];
+        for (int r = 0; r < 8; ++r) col[ty + 16 * r] = a[r][0];
     }
     __syncthreads();
 #pragma unroll
@@ -90,21 +93,21 @@ __global__ void __launch_bounds__(512, 1) k_diag128(float* __restrict__ G, int64
                 if (t == 0 && info) atomicCAS(info, 0, (int)(j0 + j + 1));
                 d = 1e-30f;
             }
-            const float rd = 1.0f / d, rs = rsqrtf(d);
-            if (t == 0) rdiag[j] = 1.0f / (d * rs);   // d rs = sqrt(d) = L_jj
-            // column j is final: L_ij = a_ij / sqrt(d) for i >= j
+            const float rs = rsqrtf(d);       // 1 / L_jj
+            const float rd = rs * rs;         // 1 / a_jj
+            if (t == 0) rdiag[j] = rs;
+            // column j is final: L_ij = a_ij / sqrt(d) for i >= j (rows of block cb and below)
             if (tx == jj) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int i = ty + 32 * r;
+                for (int r = cb; r < 8; ++r) {
+                    const int i = ty + 16 * r;
                     if (i >= j && i < bs) Ls[i * LP + j] = a[r][cb] * rs;
                 }
             }
-            // rows i > j and columns l > j change; rows below 16 cb - 31 are finished
-            float ci[4], lj[8];
+            float ci[8], lj[8];
 #pragma unroll
-            for (int r = cb / 2; r < 4; ++r) {
-                const int i = ty + 32 * r;
+            for (int r = cb; r < 8; ++r) {
+                const int i = ty + 16 * r;
                 ci[r] = (i > j) ? col[b * DB + i] * rd : 0.f;
             }
 #pragma unroll
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(512, 1) k_diag128(float* __restrict__ G, int64
                 lj[c] = (l > j) ? col[b * DB + l] : 0.f;
             }
 #pragma unroll
-            for (int r = cb / 2; r < 4; ++r)
+            for (int r = cb; r < 8; ++r)
 #pragma unroll
                 for (int c = cb; c < 8; ++c) a[r][c] -= ci[r] * lj[c];
             // the owners of column j + 1 pass it on (block cb, or cb + 1 after its last column)
@@ -121,16 +124,16 @@ __global__ void __launch_bounds__(512, 1) k_diag128(float* __restrict__ G, int64
                 if (jj < 15) {
                     if (tx == jj + 1) {
 #pragma unroll
-                        for (int r = cb / 2; r < 4; ++r) {
-                            const int i = ty + 32 * r;
+                        for (int r = cb; r < 8; ++r) {
+                            const int i = ty + 16 * r;
                             if (i > j) col[(b ^ 1) * DB + i] = a[r][cb];
                         }
                     }
                 } else if (cb < 7) {
                     if (tx == 0) {
 #pragma unroll
-                        for (int r = cb / 2; r < 4; ++r) {
-                            const int i = ty + 32 * r;
+                        for (int r = cb; r < 8; ++r) {
+                            const int i = ty + 16 * r;
                             if (i > j) col[(b ^ 1) * DB + i] = a[r][cb < 7 ? cb + 1 : 7];
                         }
                     }
@@ -141,13 +144,13 @@ __global__ void __launch_bounds__(512, 1) k_diag128(float* __restrict__ G, int64
     }
     // ---- inverse X = L^{-1}, right-looking by rows: row k final = row k / L_kk, then
     // rows i > k lose L_ik * row k (whose entries beyond column k are zero).  Thread
-    // ownership as above, x starts as I.
-    float x[4][8];
+    // ownership as above (the factor's registers are free now), x starts as I.
+    float (&x)[8][8] = a;
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int i = ty + 32 * r, l = tx + 16 * c;
+            const int i = ty + 16 * r, l = tx + 16 * c;
             x[r][c] = (i == l && i < bs) ? 1.f : 0.f;
         }
     if (ty == 0) {   // row 0 (r = 0)
@@ -159,30 +162,28 @@ __global__ void __launch_bounds__(512, 1) k_diag128(float* __restrict__ G, int64
     }
     __syncthreads();
 #pragma unroll
-    for (int rb = 0; rb < 4; ++rb) {
+    for (int rb = 0; rb < 8; ++rb) {
 #pragma unroll 1
-        for (int kk = 0; kk < 32; ++kk) {
-            const int k = 32 * rb + kk;
+        for (int kk = 0; kk < 16; ++kk) {
+            const int k = 16 * rb + kk;
             if (k + 1 >= bs) break;
             const int b = k & 1;
-            // row k of X is zero beyond column k < 32 rb + 32: column blocks c <= 2 rb + 1 only
-            float xk[8], lik[4];
+            // row k of X is zero beyond column k < 16 rb + 16: column blocks c <= rb only
+            float xk[8], lik[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                if (c <= 2 * rb + 1) xk[c] = rowx[b * DB + tx + 16 * c];
+            for (int c = 0; c <= rb; ++c) xk[c] = rowx[b * DB + tx + 16 * c];
 #pragma unroll
-            for (int r = rb; r < 4; ++r) {
-                const int i = ty + 32 * r;
+            for (int r = rb; r < 8; ++r) {
+                const int i = ty + 16 * r;
                 lik[r] = (i > k && i < bs) ? Ls[i * LP + k] : 0.f;
             }
 #pragma unroll
-            for (int r = rb; r < 4; ++r)
+            for (int r = rb; r < 8; ++r)
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    if (c <= 2 * rb + 1) x[r][c] -= lik[r] * xk[c];
+                for (int c = 0; c <= rb; ++c) x[r][c] -= lik[r] * xk[c];
             // row k + 1 is now final up to its scaling: block rb, or rb + 1 after its last row
             const float s = rdiag[k + 1];
-            if (kk < 31) {
+            if (kk < 15) {
                 if (ty == kk + 1) {
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
@@ -190,12 +191,12 @@ __global__ void __launch_bounds__(512, 1) k_diag128(float* __restrict__ G, int64
                         rowx[(b ^ 1) * DB + tx + 16 * c] = x[rb][c];
                     }
                 }
-            } else if (rb < 3) {
+            } else if (rb < 7) {
                 if (ty == 0) {
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        x[rb < 3 ? rb + 1 : 3][c] *= s;
-                        rowx[(b ^ 1) * DB + tx + 16 * c] = x[rb < 3 ? rb + 1 : 3][c];
+                        x[rb < 7 ? rb + 1 : 7][c] *= s;
+                        rowx[(b ^ 1) * DB + tx + 16 * c] = x[rb < 7 ? rb + 1 : 7][c];
                     }
                 }
             }
@@ -203,10 +204,10 @@ __global__ void __launch_bounds__(512, 1) k_diag128(float* __restrict__ G, int64
         }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int i = ty + 32 * r, l = tx + 16 * c;
+            const int i = ty + 16 * r, l = tx + 16 * c;
             D[i * DB + l] = (i < bs && l <= i) ? x[r][c] : 0.f;
             if (i < bs && l <= i) G[(size_t)(j0 + i) * ld + j0 + l] = Ls[i * LP + l];
         }
@@ -230,14 +231,18 @@ __global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t
     float* Ds = As + PR * LP;    // DB x LP
     const int t = threadIdx.x;
     const int64_t row0 = (int64_t)blockIdx.x * PR;
+    // many loads in flight per thread: the staging is latency-bound otherwise
+#pragma unroll 8
     for (int e = t; e < PR * DB; e += 256) {
         const int i = e >> 7, l = e & (DB - 1);
         const int64_t gi = row0 + i;
         As[i * LP + l] = gi < m ? G[(size_t)(r0 + gi) * ld + j0 + l] : 0.f;
     }
-    for (int e = t; e < DB * DB; e += 256) {
-        const int i = e >> 7, l = e & (DB - 1);
-        Ds[i * LP + l] = D[e];
+#pragma unroll 4
+    for (int e4 = t; e4 < DB * DB / 4; e4 += 256) {
+        const float4 d4 = reinterpret_cast<const float4*>(D)[e4];
+        const int i = (4 * e4) >> 7, l = (4 * e4) & (DB - 1);
+        Ds[i * LP + l] = d4.x; Ds[i * LP + l + 1] = d4.y; Ds[i * LP + l + 2] = d4.z; Ds[i * LP + l + 3] = d4.w;
     }
     __syncthreads();
     const int tr = t >> 4, tc = t & 15;
@@ -296,14 +301,17 @@ __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t 
     __nv_bfloat16* Tl = Th + TC * (DB + 8);
     const int t = threadIdx.x;
     const int64_t c0 = (int64_t)blockIdx.x * TC;
+#pragma unroll 8
     for (int e = t; e < DB * TC; e += 256) {
         const int i = e / TC, cc = e % TC;
         const int64_t gc = c0 + cc;
         Ss[i * (TC + 4) + cc] = (i < bs && gc < ncols) ? X[(size_t)(j0 + i) * ld + gc] : 0.f;
     }
-    for (int e = t; e < DB * DB; e += 256) {
-        const int i = e >> 7, l = e & (DB - 1);
-        Ds[i * LP + l] = D[e];
+#pragma unroll 4
+    for (int e4 = t; e4 < DB * DB / 4; e4 += 256) {
+        const float4 d4 = reinterpret_cast<const float4*>(D)[e4];
+        const int i = (4 * e4) >> 7, l = (4 * e4) & (DB - 1);
+        Ds[i * LP + l] = d4.x; Ds[i * LP + l + 1] = d4.y; Ds[i * LP + l + 2] = d4.z; Ds[i * LP + l + 3] = d4.w;
     }
     __syncthreads();
     const int trow = t >> 4, tcol = t & 15;
@@ -357,21 +365,25 @@ __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t 
 constexpr size_t TRMM_SMEM = sizeof(float) * (DB * (TC + 4) + DB * LP) + 2 * sizeof(__nv_bfloat16) * TC * (DB + 8);
 
 // ---------------------------------------------------------------------------
-// 3, 5. C[m x n] (FP32, row-major, ldc) -= (A_hi + A_lo)(B_hi + B_lo)^T over a
-// contraction of 64 nk, the A and B operands K-major BF16 (rows of the maps),
-// in 128 x 128 tiles (LOWER: only tiles with tj <= ti).  Persistent: each CTA
-// (one per SM) walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0
-// issues TMA loads (128-byte swizzle) through a 3-stage ring, one thread of
-// warp 1 issues tcgen05.mma into one of two 128-column TMEM accumulators, and
-// warps 2-5 drain the other one (tcgen05.ld) and subtract it from C, so that a
-// tile's loads and products overlap the previous tile's epilogue.  Every wait
+// 3, 5. C[m x n] -= (A_hi + A_lo)(B_hi + B_lo)^T over a contraction of 64 nk, the
+// A and B operands K-major BF16 (rows of their maps), in 128 x 128 tiles (LOWER:
+// only tiles with tj <= ti); C is the FP32 region at (cy0, cx0) of the matrix
+// behind the map mc.  Persistent: each CTA (one per SM) walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0 issues TMA loads (128-byte
+// swizzle) through a 3-stage ring; one thread of warp 1 issues tcgen05.mma into
+// one of two 128-column TMEM accumulators; warps 2-5 drain the other: each
+// 128 x 32 slice goes TMEM -> registers -> negated into a swizzled shared-memory
+// box -> a TMA reduce-add into C, so the read-modify-write of C happens in L2
+// and no thread loads C.  The epilogue's decisions are taken by one thread and
+// shared through a named barrier, so its four warps never diverge.  Every wait
 // is bounded: on expiry the CTA records an error, stops issuing, waits for its
 // own copies and products in flight, frees TMEM and returns.
 // ---------------------------------------------------------------------------
 constexpr int BM = 128, BN = 128, BKC = 64;
 constexpr int OP_BYTES = BM * BKC * 2;                 // one 128 x 64 BF16 operand box
 constexpr int STAGES = 3, STAGE_BYTES = 4 * OP_BYTES;  // A_hi, B_hi, A_lo, B_lo
-constexpr int SUB_SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int CBOX_COLS = 32, CBOX_BYTES = BM * CBOX_COLS * 4;   // FP32 128 x 32 box of C
+constexpr int SUB_SMEM = STAGES * STAGE_BYTES + 2 * CBOX_BYTES + 1024 + 256;
 constexpr int SUB_THREADS = 192;
 constexpr uint32_t TMEM_COLS = 256;                    // two 128-column accumulators
 
@@ -392,18 +404,21 @@ __device__ __forceinline__ void tile_of(int64_t t, int64_t tiles_n, int64_t& ti,
 template <bool LOWER>
 __global__ void __launch_bounds__(SUB_THREADS, 1)
     k_tc_sub(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap ma_lo,
-             const __grid_constant__ CUtensorMap mb, const __grid_constant__ CUtensorMap mb_lo, int64_t m, int64_t n,
-             int64_t n_tiles, int64_t tiles_n, int nk, float* __restrict__ C, int64_t ldc, int* err)
+             const __grid_constant__ CUtensorMap mb, const __grid_constant__ CUtensorMap mb_lo,
+             const __grid_constant__ CUtensorMap mc, int cx0, int cy0, int64_t n_tiles, int64_t tiles_n, int nk,
+             int* err)
 {
     extern __shared__ unsigned char smraw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+    unsigned char* cstage = base + STAGES * STAGE_BYTES;   // two 1024-aligned C boxes
+    uint64_t* full = reinterpret_cast<uint64_t*>(cstage + 2 * CBOX_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* acc_full = empty + STAGES;
     uint64_t* acc_empty = acc_full + 2;
     uint64_t* drain = acc_empty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* epi_go = abort_flag + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -498,57 +513,53 @@ __global__ void __launch_bounds__(SUB_THREADS, 1)
         umma_commit(drain);
         mbar_wait(drain, 0);
     } else if (warp >= 2) {
-        // ---- epilogue: C -= accumulator.  A thread owns one row of the tile (its TMEM lane) and
-        // loads that row's 128 values of C before the accumulator is ready, so that the global
-        // latency overlaps the tile's loads and products.
-        const int q = warp & 3;   // TMEM lane quarter this warp may access
-        const bool vec = (((uintptr_t)C & 15) == 0) && ((ldc & 3) == 0);
+        // ---- epilogue (128 threads): C -= accumulator by TMA reduce-add of -accumulator boxes
+        const int q = warp & 3;              // TMEM lane quarter this warp may access
+        const int r = q * 32 + lane;         // tile row this thread drains
+        const bool leader = threadIdx.x == 64;
+        uint32_t chunk = 0;
         int64_t tc = 0;
-        for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x, ++tc) {
+        for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++tc) {
             int64_t ti, tj;
             tile_of<LOWER>(t, tiles_n, ti, tj);
             const int b = (int)(tc & 1);
             const uint32_t use = (uint32_t)(tc >> 1) & 1u;
-            const int64_t gi = ti * BM + q * 32 + lane, gj = tj * BN;
-            float* dst = C + (size_t)gi * ldc + gj;
-            const bool full_row = vec && gi < m && gj + BN <= n;
-            float4 cv[BN / 4];
-            if (full_row) {
-#pragma unroll
-                for (int k = 0; k < BN / 4; ++k) cv[k] = *reinterpret_cast<const float4*>(dst + 4 * k);
+            if (leader) {
+                const bool ok = !*abort_flag && mbar_wait(&acc_full[b], use);
+                if (!ok) *abort_flag = 1;
+                *epi_go = ok ? 1 : 0;
             }
-            if (!mbar_wait(&acc_full[b], use)) {
-                *abort_flag = 1;
-                break;
-            }
+            named_bar(1, 128);
+            if (!*epi_go) break;             // the same decision in all four warps
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-            for (int c0 = 0; c0 < BN; c0 += 32) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += CBOX_COLS, ++chunk) {
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0), v);
-                if (full_row) {
+                if (c0 + CBOX_COLS == BN) {   // the accumulator is in registers: hand the buffer back
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[b]);
+                }
+                unsigned char* box = cstage + (chunk & 1) * CBOX_BYTES;
+                if (leader) bulk_wait_read<1>();   // the box used two slices ago has been read
+                named_bar(1, 128);
+                // row r of the box: 128 bytes, 16-byte chunk j stored at j ^ (r mod 8) (128-byte swizzle)
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        float4& o = cv[(c0 + j) / 4];
-                        o.x -= __uint_as_float(v[j]);
-                        o.y -= __uint_as_float(v[j + 1]);
-                        o.z -= __uint_as_float(v[j + 2]);
-                        o.w -= __uint_as_float(v[j + 3]);
-                    }
-                } else if (gi < m) {
-                    for (int j = 0; j < 32; ++j)
-                        if (gj + c0 + j < n) dst[c0 + j] -= __uint_as_float(v[j]);
+                for (int j = 0; j < 8; ++j) {
+                    const float4 o = make_float4(-__uint_as_float(v[4 * j]), -__uint_as_float(v[4 * j + 1]),
+                                                 -__uint_as_float(v[4 * j + 2]), -__uint_as_float(v[4 * j + 3]));
+                    *reinterpret_cast<float4*>(box + r * 128 + ((j ^ (r & 7)) << 4)) = o;
+                }
+                fence_proxy_async_smem();
+                named_bar(1, 128);
+                if (leader) {
+                    tma_reduce_add_2d(&mc, cx0 + (int)(tj * BN) + c0, cy0 + (int)(ti * BM), box);
+                    bulk_commit();
                 }
             }
-            // the accumulator is in registers: hand the TMEM buffer back before storing
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[b]);
-            if (full_row) {
-#pragma unroll
-                for (int k = 0; k < BN / 4; ++k) *reinterpret_cast<float4*>(dst + 4 * k) = cv[k];
-            }
         }
+        if (leader) bulk_wait_all();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -559,10 +570,10 @@ __global__ void __launch_bounds__(SUB_THREADS, 1)
     }
 }
 
-__global__ void k_unit_diag(float* __restrict__ X, int64_t K)
+__global__ void k_unit_diag(float* __restrict__ X, int64_t K, int64_t ld)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < K) X[(size_t)i * K + i] = 1.f;
+    if (i < K) X[(size_t)i * ld + i] = 1.f;
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -582,6 +593,19 @@ static bool encoder()
     return true;
 }
 
+// K x K FP32, leading dimension ld (a multiple of 4): boxes of 32 x 128 with the 128-byte swizzle, the
+// target of the epilogue's reduce-add
+static bool make_cmap(CUtensorMap* map, float* C, int64_t K, int64_t ld)
+{
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)K};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {CBOX_COLS, BM};
+    cuuint32_t estr[2] = {1, 1};
+    return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)C, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // rows x 128 BF16, row-major (256-byte rows): boxes of 64 x 128 with the 128-byte swizzle
 static bool make_map(CUtensorMap* map, const __nv_bfloat16* A, int64_t rows)
 {
@@ -598,11 +622,12 @@ static bool make_map(CUtensorMap* map, const __nv_bfloat16* A, int64_t rows)
 
 bool chol_tc_available() { return ctc::encoder(); }
 
-cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int* d_info, int* d_err)
+cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int64_t ld, int* d_info, int* d_err)
 {
     using namespace ctc;
     if (K <= 0) return cudaSuccess;
-    if (!encoder() || K > 0x7fffff00LL) return cudaErrorNotSupported;
+    if (!encoder() || K > 0x7fff0000LL) return cudaErrorNotSupported;
+    if (ld < K || (ld & 3) || ((uintptr_t)G & 15) || ((uintptr_t)X & 15)) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
         cudaError_t e;
@@ -625,15 +650,16 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int*
     __nv_bfloat16* Pl = (__nv_bfloat16*)((char*)Ph + hbytes);
     __nv_bfloat16* XTh = (__nv_bfloat16*)((char*)Pl + hbytes);
     __nv_bfloat16* XTl = (__nv_bfloat16*)((char*)XTh + hbytes);
-    CUtensorMap mph, mpl, mxh, mxl;
-    if (!make_map(&mph, Ph, K) || !make_map(&mpl, Pl, K) || !make_map(&mxh, XTh, K) || !make_map(&mxl, XTl, K))
+    CUtensorMap mph, mpl, mxh, mxl, mg, mx;
+    if (!make_map(&mph, Ph, K) || !make_map(&mpl, Pl, K) || !make_map(&mxh, XTh, K) || !make_map(&mxl, XTl, K) ||
+        !make_cmap(&mg, G, K, ld) || !make_cmap(&mx, X, K, ld))
         return cudaErrorInvalidValue;
     cudaError_t e;
     // X = I
-    if ((e = cudaMemsetAsync(X, 0, (size_t)K * K * sizeof(float), st))) return e;
+    if ((e = cudaMemsetAsync(X, 0, (size_t)K * ld * sizeof(float), st))) return e;
     {
         LaunchTimer lt(ctx, K_MISC);
-        k_unit_diag<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(X, K);
+        k_unit_diag<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(X, K, ld);
     }
     const int64_t nb = (K + DB - 1) / DB;
     for (int64_t kb = 0; kb < nb; ++kb) {
@@ -643,14 +669,14 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int*
         {
             LaunchTimer lt(ctx, K_POTRF_DIAG);
             add_work(ctx, K_POTRF_DIAG, 2.0 * (double)bs * bs * bs / 3.0);
-            k_diag128<<<1, 512, DIAG_SMEM, st>>>(G, K, j0, bs, Dk, d_info);
+            k_diag128<<<1, DIAG_THREADS, DIAG_SMEM, st>>>(G, ld, j0, bs, Dk, d_info);
         }
         if ((e = cudaGetLastError())) return e;
         if (m > 0) {
             {
                 LaunchTimer lt(ctx, K_TRSM_PANEL);
                 add_work(ctx, K_TRSM_PANEL, (double)m * DB * DB);
-                k_panel128<<<(unsigned)((m + PR - 1) / PR), 256, PANEL_SMEM, st>>>(G, K, j0, r0, m, Dk, Ph, Pl);
+                k_panel128<<<(unsigned)((m + PR - 1) / PR), 256, PANEL_SMEM, st>>>(G, ld, j0, r0, m, Dk, Ph, Pl);
             }
             if ((e = cudaGetLastError())) return e;
             const int64_t T = (m + BM - 1) / BM, tiles = T * (T + 1) / 2;
@@ -658,14 +684,14 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int*
                 LaunchTimer lt(ctx, K_SYRK_TC);
                 add_work(ctx, K_SYRK_TC, (double)m * (double)(m + 1) * DB);
                 k_tc_sub<true><<<(unsigned)std::min<int64_t>(tiles, ctx_sms(ctx)), SUB_THREADS, SUB_SMEM, st>>>(
-                    mph, mpl, mph, mpl, m, m, tiles, T, DB / BKC, G + (size_t)r0 * K + r0, K, d_err);
+                    mph, mpl, mph, mpl, mg, (int)r0, (int)r0, tiles, T, DB / BKC, d_err);
             }
             if ((e = cudaGetLastError())) return e;
         }
         {
             LaunchTimer lt(ctx, K_TRINV_DIAG);
             add_work(ctx, K_TRINV_DIAG, (double)bs * bs * (double)r0);
-            k_trmm128<<<(unsigned)((r0 + TC - 1) / TC), 256, TRMM_SMEM, st>>>(X, K, j0, bs, r0, Dk, XTh, XTl);
+            k_trmm128<<<(unsigned)((r0 + TC - 1) / TC), 256, TRMM_SMEM, st>>>(X, ld, j0, bs, r0, Dk, XTh, XTl);
         }
         if ((e = cudaGetLastError())) return e;
         if (m > 0) {
@@ -673,7 +699,7 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int*
             LaunchTimer lt(ctx, K_TRINV_TC);
             add_work(ctx, K_TRINV_TC, 2.0 * (double)m * (double)r0 * DB);
             k_tc_sub<false><<<(unsigned)std::min<int64_t>(tiles, ctx_sms(ctx)), SUB_THREADS, SUB_SMEM, st>>>(
-                mph, mpl, mxh, mxl, m, r0, tiles, Tn, DB / BKC, X + (size_t)r0 * K, K, d_err);
+                mph, mpl, mxh, mxl, mx, 0, (int)r0, tiles, Tn, DB / BKC, d_err);
         }
         if ((e = cudaGetLastError())) return e;
     }

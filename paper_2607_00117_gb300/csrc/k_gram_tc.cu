@@ -42,7 +42,7 @@ constexpr uint32_t TMEM_COLS = 128;
 template <bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1) k_gram(const __grid_constant__ CUtensorMap map,
                                                      const __grid_constant__ CUtensorMap map_lo, int64_t K, int nk,
-                                                     float* __restrict__ C, int* err)
+                                                     float* __restrict__ C, int64_t ldc, int* err)
 {
     constexpr int STAGES = Cfg<SPLIT>::STAGES, STAGE_BYTES = Cfg<SPLIT>::STAGE_BYTES;
     extern __shared__ unsigned char smraw[];
@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram(const __grid_constant__ CUt
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
                 const int64_t gj0 = tj * BN + c0;
                 if (gi < K) {
-                    float* dst = C + (size_t)gi * K + gj0;
-                    if (gj0 + 32 <= K && (K & 3) == 0) {
+                    float* dst = C + (size_t)gi * ldc + gj0;
+                    if (gj0 + 32 <= K && (ldc & 3) == 0) {
 #pragma unroll
                         for (int j = 0; j < 32; j += 4)
                             *reinterpret_cast<float4*>(dst + j) =
@@ -207,8 +207,9 @@ static bool make_map(CUtensorMap* map, const __nv_bfloat16* A, int64_t K, int64_
 }
 
 cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, const __nv_bfloat16* A_lo, int64_t K, int64_t ldA, float* C,
-                    int* d_err)
+                    int* d_err, int64_t ldc)
 {
+    if (ldc <= 0) ldc = K;
     using namespace gtc;
     if (K <= 0) return cudaSuccess;
     if ((ldA % BKC) != 0 || ((uintptr_t)A & 15) != 0 || ((uintptr_t)A_lo & 15) != 0 || !encoder())
@@ -233,9 +234,11 @@ cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, const __nv_bfloat16* A_
     LaunchTimer lt(ctx, K_GRAM_TC);
     add_work(ctx, K_GRAM_TC, 2.0 * (double)tiles * BM * BM * (double)ldA * (split ? 3.0 : 1.0));
     if (split)
-        k_gram<true><<<(unsigned)tiles, THREADS, Cfg<true>::SMEM_BYTES, ctx_stream(ctx)>>>(map, map_lo, K, nk, C, d_err);
+        k_gram<true><<<(unsigned)tiles, THREADS, Cfg<true>::SMEM_BYTES, ctx_stream(ctx)>>>(map, map_lo, K, nk, C, ldc,
+                                                                                           d_err);
     else
-        k_gram<false><<<(unsigned)tiles, THREADS, Cfg<false>::SMEM_BYTES, ctx_stream(ctx)>>>(map, map_lo, K, nk, C, d_err);
+        k_gram<false><<<(unsigned)tiles, THREADS, Cfg<false>::SMEM_BYTES, ctx_stream(ctx)>>>(map, map_lo, K, nk, C, ldc,
+                                                                                             d_err);
     return cudaGetLastError();
 }
 

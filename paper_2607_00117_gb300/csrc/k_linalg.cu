@@ -256,10 +256,10 @@ __global__ void k_shift_diag(T* __restrict__ G, int64_t K, double shift)
 
 // G_ii += d_i (per-variable ridge)
 template <typename T>
-__global__ void k_shift_diag_vec(T* __restrict__ G, int64_t K, const double* __restrict__ d)
+__global__ void k_shift_diag_vec(T* __restrict__ G, int64_t K, int64_t ld, const double* __restrict__ d)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x)
-        G[(size_t)i * K + i] += (T)d[i];
+        G[(size_t)i * ld + i] += (T)d[i];
 }
 
 // Active-set reduced solve helpers: out_k = s_k * a_k (to working precision), and
@@ -933,14 +933,14 @@ cudaError_t shift_and_trace(sw_ctx* ctx, T* G, int64_t K, double* d_trace, doubl
 }
 
 template <typename T>
-cudaError_t shift_diag_vec(sw_ctx* ctx, T* G, int64_t K, const double* d)
+cudaError_t shift_diag_vec(sw_ctx* ctx, T* G, int64_t K, int64_t ld, const double* d)
 {
     LaunchTimer lt(ctx, K_SHIFT);
-    k_shift_diag_vec<T><<<cap_grid(K, 256, 1024), 256, 0, ctx_stream(ctx)>>>(G, K, d);
+    k_shift_diag_vec<T><<<cap_grid(K, 256, 1024), 256, 0, ctx_stream(ctx)>>>(G, K, ld, d);
     return cudaGetLastError();
 }
-template cudaError_t shift_diag_vec<float>(sw_ctx*, float*, int64_t, const double*);
-template cudaError_t shift_diag_vec<double>(sw_ctx*, double*, int64_t, const double*);
+template cudaError_t shift_diag_vec<float>(sw_ctx*, float*, int64_t, int64_t, const double*);
+template cudaError_t shift_diag_vec<double>(sw_ctx*, double*, int64_t, int64_t, const double*);
 
 template <typename GT>
 cudaError_t scale_to(sw_ctx* ctx, int64_t n, const double* a, const double* s, GT* out)

@@ -235,8 +235,12 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     std::vector<int64_t> P0;
     std::vector<int64_t> pos(N, -1);
     int n_factor = 0, n_solves = 0, cg_total = 0;
+    // the tensor-core factorisation wants 16-byte rows of G and X (TMA)
+    const bool fact_tc = sizeof(GT) == 4 && ctx->opt.chol_tc && !ctx->opt.chol_coop && chol_tc_available();
+    int64_t ldG = 0;   // leading dimension of the factored set's G and X
     auto factor = [&](const std::vector<int64_t>& S, bool& ok) -> sw_status {
         const int64_t nP = (int64_t)S.size();
+        ldG = fact_tc ? (nP + 3) / 4 * 4 : nP;
         ok = false;
         for (int64_t i : P0) pos[i] = -1;
         P0 = S;
@@ -245,8 +249,8 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         AS_TRY(ctx->ensure(&ws.Uc, &ws.Uc_cap, (size_t)nP * M * sizeof(T), "passive columns"));
         AS_TRY(ctx->ensure(&ws.A, &ws.A_cap, (size_t)nP * ldA * sizeof(AT), "passive matrix"));
         if (split) AS_TRY(ctx->ensure(&ws.Alo, &ws.Alo_cap, (size_t)nP * ldA * sizeof(AT), "passive matrix (lo)"));
-        AS_TRY(ctx->ensure(&ws.G, &ws.G_cap, (size_t)nP * nP * sizeof(GT), "reduced Gram"));
-        AS_TRY(ctx->ensure(&ws.X, &ws.X_cap, (size_t)nP * nP * sizeof(GT), "reduced inverse factor"));
+        AS_TRY(ctx->ensure(&ws.G, &ws.G_cap, (size_t)nP * ldG * sizeof(GT), "reduced Gram"));
+        AS_TRY(ctx->ensure(&ws.X, &ws.X_cap, (size_t)nP * ldG * sizeof(GT), "reduced inverse factor"));
         AS_TRY(ctx->ensure(&ws.D, &ws.D_cap, 64 * 64 * sizeof(GT), "block scratch"));
         T* Uc = (T*)ws.Uc;
         AT* A = (AT*)ws.A;
@@ -264,24 +268,24 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             AS_CUDA(ctx, cudaMemcpyAsync(V.ridge, rh.data(), nP * sizeof(double), cudaMemcpyHostToDevice, st), "ridge");
             AS_CUDA(ctx, cudaMemsetAsync(info, 0, sizeof(int), st), "memset");
             if constexpr (sizeof(AT) == 2) {
-                AS_CUDA(ctx, gram_tc(ctx, A, Alo, nP, ldA, (float*)G, gerr), "reduced Gram");
+                AS_CUDA(ctx, gram_tc(ctx, A, Alo, nP, ldA, (float*)G, gerr, ldG), "reduced Gram");
             } else {
                 AS_CUDA(ctx, (gemm<GT, true, true>(ctx, K_GRAM_SIMT, nP, nP, ldA, GT(1), (const GT*)A, ldA,
-                                                   (const GT*)A, ldA, GT(0), G, nP, 0)),
+                                                   (const GT*)A, ldA, GT(0), G, ldG, 0)),
                         "reduced Gram");
             }
-            AS_CUDA(ctx, shift_diag_vec<GT>(ctx, G, nP, V.ridge), "ridge");
+            AS_CUDA(ctx, shift_diag_vec<GT>(ctx, G, nP, ldG, V.ridge), "ridge");
             int* cerr = (int*)(V.scal + 12);
             AS_CUDA(ctx, cudaMemsetAsync(cerr, 0, sizeof(int), st), "memset");
             cudaError_t ce = ctx->opt.chol_coop ? cholesky_inverse_coop<GT>(ctx, G, (GT*)ws.X, nP, info, cerr)
                                                 : cudaErrorNotSupported;
             if constexpr (sizeof(GT) == 4) {
-                if (ce == cudaErrorNotSupported && !ctx->opt.chol_coop && ctx->opt.chol_tc)
-                    ce = cholesky_inverse_tc(ctx, (float*)G, (float*)ws.X, nP, info, gerr);
+                if (ce == cudaErrorNotSupported && fact_tc)
+                    ce = cholesky_inverse_tc(ctx, (float*)G, (float*)ws.X, nP, ldG, info, gerr);
             }
             if (ce == cudaErrorNotSupported) {
                 cudaGetLastError();
-                ce = cholesky_inverse<GT>(ctx, G, (GT*)ws.X, (GT*)ws.D, nP, info);
+                ce = ldG == nP ? cholesky_inverse<GT>(ctx, G, (GT*)ws.X, (GT*)ws.D, nP, info) : cudaErrorInvalidValue;
             }
             AS_CUDA(ctx, ce, "reduced Cholesky");
             int cerrh = 0;
@@ -316,10 +320,10 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         const int nb = cg_blocks(ctx, nP);
         auto precond = [&](const double* r, double* z) -> sw_status {   // z = m S X^T X S r
             AS_CUDA(ctx, scale_to<GT>(ctx, nP, r, V.sP, V.rs), "precondition");
-            AS_CUDA(ctx, (rowdot<GT, GT, GT, GT>(ctx, K_TRMV_L, X, nP, nP, nP, V.rs, V.t1, 1.0, 0.0, true)),
+            AS_CUDA(ctx, (rowdot<GT, GT, GT, GT>(ctx, K_TRMV_L, X, nP, nP, ldG, V.rs, V.t1, 1.0, 0.0, true)),
                     "precondition");
             AS_CUDA(ctx, cudaMemsetAsync(V.c, 0, nP * sizeof(GT), st), "memset");
-            AS_CUDA(ctx, (colcomb<GT, GT, GT, GT>(ctx, K_TRMV_LT, X, nP, nP, nP, V.t1, V.c, 1.0, true)),
+            AS_CUDA(ctx, (colcomb<GT, GT, GT, GT>(ctx, K_TRMV_LT, X, nP, nP, ldG, V.t1, V.c, 1.0, true)),
                     "precondition");
             AS_CUDA(ctx, cudaMemsetAsync(z, 0, nP * sizeof(double), st), "memset");
             AS_CUDA(ctx, axpy_scaled<GT>(ctx, nP, V.c, V.sP, z), "precondition");
@@ -476,6 +480,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         if (have) {
             for (int64_t i : P0) pos[i] = -1;
             P0 = warm->P0;
+            ldG = warm->ld;
             for (int64_t k = 0; k < (int64_t)P0.size(); ++k) pos[P0[k]] = k;
         } else {
             const std::vector<int64_t> S = warm->P0;
@@ -626,6 +631,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         bool ok = false;
         if (!S.empty()) AS_TRY(factor(S, ok));
         warm->P0 = P0;
+        warm->ld = ldG;
         warm->have_factor = ok;
     }
     {

@@ -162,11 +162,11 @@ static void ctx_release(sw_ctx* ctx)
     cudaStreamSynchronize(ctx->stream);
     ctx->harvest();
     void* bufs[] = {ctx->d_soa, ctx->d_cs, ctx->d_aos, ctx->d_drift, ctx->d_status, ctx->d_stats, ctx->d_ghtab,
-                    ctx->d_mlp, ctx->d_split, ctx->d_chol, ctx->d_ttotal, ctx->d_chol_tc};
+                    ctx->d_mlp, ctx->d_split, ctx->d_chol, ctx->d_ttotal, ctx->d_chol_tc, ctx->d_cut};
     for (void* b : bufs)
         if (b) cudaFree(b);
     ctx->d_soa = ctx->d_cs = ctx->d_ghtab = ctx->d_mlp = ctx->d_split = ctx->d_chol = nullptr;
-    ctx->d_ttotal = ctx->d_chol_tc = nullptr;
+    ctx->d_ttotal = ctx->d_chol_tc = ctx->d_cut = nullptr;
     ctx->d_aos = ctx->d_drift = nullptr;
     ctx->d_status = nullptr;
     ctx->d_stats = nullptr;
@@ -520,7 +520,14 @@ template GridT<double> make_grid<double>(double, double, double, const sw_pixel_
 template <typename T>
 static sw_status project_impl(sw_ctx* ctx, const GridT<T>& g, const double* gh_v0_s, sw_matrix** U_out)
 {
-    const int64_t N = ctx->n_orb, M = g.M;
+    const int64_t Norb = ctx->n_orb, M = g.M;
+    const int nb = ctx->opt.project_bundle;   // orbits per column (bundles accumulated at bin time)
+    if (nb > 1 && (Norb % nb != 0 || ctx->opt.integrator != 0)) {
+        set_error(ctx, "sw_project: project_bundle %d needs the kick-drift-kick integrator and must divide the %lld orbits",
+                  nb, (long long)Norb);
+        return SW_EINVAL;
+    }
+    const int64_t N = nb > 1 ? Norb / nb : Norb;   // columns
     sw_matrix* U = new sw_matrix();
     U->ctx = ctx;
     U->M = M; U->N = N; U->nd = g.nd; U->npix = g.npix; U->nkin = M - g.nd - g.npix;
@@ -541,6 +548,7 @@ static sw_status project_impl(sw_ctx* ctx, const GridT<T>& g, const double* gh_v
     m.g = g;
     m.U = U->d;
     m.ldu = M;
+    m.bundle = nb > 1 ? nb : 1;
     if (g.gh) {
         // per-pixel (v0, 1/s) table in the working precision
         std::vector<T> tab(2 * g.npix);
@@ -561,7 +569,7 @@ static sw_status project_impl(sw_ctx* ctx, const GridT<T>& g, const double* gh_v
         if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return fail(ctx->cuda_fail(e, "GH table"));
         m.gh_v0s = (const T*)ctx->d_ghtab;
     }
-    sw_status s = ctx->ensure_stats(N);
+    sw_status s = ctx->ensure_stats(Norb);
     if (s != SW_OK) return fail(s);
     if ((e = cudaMemsetAsync(ctx->d_stats, 0, 4 * sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
         return fail(ctx->cuda_fail(e, "memset"));
@@ -578,17 +586,48 @@ static sw_status project_impl(sw_ctx* ctx, const GridT<T>& g, const double* gh_v
         if ((e = launch_finalize_w<T>(ctx, U->d, M, N, (const double*)ctx->d_ttotal, g.ncopy)) != cudaSuccess)
             return fail(ctx->cuda_fail(e, "finalize"));
     } else {
-        if ((e = launch_orbit_bin<T>(ctx, m, (const T*)ctx->d_soa, N, ctx->nsteps, ctx->opt.ej_every, ctx->d_drift,
-                                     ctx->d_status, ctx->d_stats)) != cudaSuccess)
+        if ((e = launch_orbit_bin<T>(ctx, m, (const T*)ctx->d_soa, Norb, ctx->nsteps, ctx->opt.ej_every,
+                                     ctx->d_drift, ctx->d_status, ctx->d_stats)) != cudaSuccess)
             return fail(ctx->cuda_fail(e, "orbit kernel"));
-        if ((e = launch_zero_flagged<T>(ctx, U->d, M, N, ctx->d_status)) != cudaSuccess)
+        if (nb > 1) {
+            // a realisation cut by the quality test contributes a zero column to its bundle's mean:
+            // integrate the (rare) cut orbits again and subtract their counts, which restores the
+            // bundle's integer counts exactly (GH sums to rounding)
+            unsigned long long st[4];
+            if ((e = cudaMemcpyAsync(st, ctx->d_stats, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream)) ||
+                (e = cudaStreamSynchronize(ctx->stream)))
+                return fail(ctx->cuda_fail(e, "orbit statistics"));
+            if (st[1] + st[2] > 0) {
+                std::vector<uint8_t> sh(Norb);
+                if ((e = cudaMemcpyAsync(sh.data(), ctx->d_status, Norb, cudaMemcpyDeviceToHost, ctx->stream)) ||
+                    (e = cudaStreamSynchronize(ctx->stream)))
+                    return fail(ctx->cuda_fail(e, "orbit status"));
+                std::vector<int64_t> cut;
+                for (int64_t i = 0; i < Norb; ++i)
+                    if (sh[i] != ST_OK) cut.push_back(i);
+                s = ctx->ensure(&ctx->d_cut, &ctx->cut_cap, cut.size() * sizeof(int64_t), "cut orbits");
+                if (s != SW_OK) return fail(s);
+                if ((e = cudaMemcpyAsync(ctx->d_cut, cut.data(), cut.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                         ctx->stream)))
+                    return fail(ctx->cuda_fail(e, "cut orbits"));
+                ModelT<T> mc = m;
+                mc.sign = -1;
+                mc.orbit_list = (const int64_t*)ctx->d_cut;
+                mc.n_orb = (int64_t)cut.size();
+                if ((e = launch_orbit_bin<T>(ctx, mc, (const T*)ctx->d_soa, Norb, ctx->nsteps, ctx->opt.ej_every,
+                                             nullptr, nullptr, nullptr)) ||
+                    (e = cudaStreamSynchronize(ctx->stream)))   // the host list dies at return
+                    return fail(ctx->cuda_fail(e, "orbit kernel (cut realisations)"));
+            }
+        } else if ((e = launch_zero_flagged<T>(ctx, U->d, M, N, ctx->d_status)) != cudaSuccess) {
             return fail(ctx->cuda_fail(e, "zero flagged"));
+        }
         const int64_t count_rows = g.gh ? g.nd + g.npix : M;
-        const double norm = 1.0 / ((double)g.ncopy * (double)ctx->nsteps);
+        const double norm = 1.0 / ((double)g.ncopy * (double)ctx->nsteps * (double)(nb > 1 ? nb : 1));
         if ((e = launch_finalize<T>(ctx, U->d, M, N, count_rows, norm)) != cudaSuccess)
             return fail(ctx->cuda_fail(e, "finalize"));
     }
-    ctx->last_proj_n = N;
+    ctx->last_proj_n = Norb;
     ctx->live_matrices++;
     *U_out = U;
     return SW_OK;
@@ -985,6 +1024,9 @@ extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value)
     } else if (!strcmp(key, "chol_coop")) {
         if (!(value == 0 || value == 1)) return SW_EINVAL;
         ctx->opt.chol_coop = (int)value;
+    } else if (!strcmp(key, "project_bundle")) {
+        if (!(value >= 1.0 && value <= 1024.0 && value == std::floor(value))) return SW_EINVAL;
+        ctx->opt.project_bundle = (int)value;
     } else if (!strcmp(key, "chol_tc")) {
         if (!(value == 0 || value == 1)) return SW_EINVAL;
         ctx->opt.chol_tc = (int)value;

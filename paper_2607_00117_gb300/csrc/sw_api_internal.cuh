@@ -35,6 +35,7 @@ struct Options {
     int solver = 0;              // 0 auto, 1 active set, 2 ADMM (see solve_dispatch)
     int chol_coop = 0;           // Cholesky + inverse in one cooperative launch (0: per-step launches)
     int chol_tc = 1;             // FP32 Cholesky + inverse with tcgen05 trailing updates (0: SIMT, 64-wide)
+    int project_bundle = 1;      // orbits per column of sw_project's matrix (bundles accumulated at bin time)
     int integrator = 0;          // 0: kick-drift-kick at fixed dt; 1: adaptive Bogacki-Shampine 3(2) in the bar frame
     double bs3_rtol = 1e-4;      // relative tolerance of the adaptive integrator
     int as_cg_max = 200;         // active set: conjugate-gradient steps per reduced solve
@@ -100,6 +101,7 @@ struct sw_ctx {
     void* d_split = nullptr; size_t split_cap = 0;   // FP64 vectors split into float hi + lo
     void* d_chol = nullptr; size_t chol_cap = 0;     // cooperative Cholesky: diagonal inverses, barrier
     void* d_chol_tc = nullptr; size_t chol_tc_cap = 0;   // tensor-core Cholesky: diagonal inverse, BF16 panels
+    void* d_cut = nullptr; size_t cut_cap = 0;           // bundled projection: indices of cut realisations
     void* d_ttotal = nullptr; size_t ttotal_cap = 0;   // per-orbit integration time (adaptive integrator)
     // solve
     sw::SolveWS solve_ws;

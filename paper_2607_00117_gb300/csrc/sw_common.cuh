@@ -57,6 +57,12 @@ struct ModelT {
     int64_t n_orb;
     int64_t orbit_base;                // first orbit of this model in the state arrays
     int64_t ldu;                       // column stride of U (rows)
+    // orbit bundles accumulated at bin time: orbit i adds into column i / bundle (bundle <= 1: column i)
+    int bundle;
+    // sign < 0: subtract the orbits' counts (removes realisations cut by the quality test from a
+    // bundled column); orbit_list (nullable): thread k integrates orbit orbit_list[k]
+    int sign;
+    const int64_t* orbit_list;
 };
 
 // Per-orbit status codes (mirrors SW_ORBIT_*).

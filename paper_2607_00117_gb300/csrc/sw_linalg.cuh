@@ -29,12 +29,13 @@ cudaError_t cholesky_inverse(sw_ctx* ctx, T* G, T* X, T* D, int64_t K, int* d_in
 // FP32 Cholesky (in place) and X = L^{-1} in 128-wide steps with the trailing and inverse updates on
 // the tensor cores (k_chol_tc.cu); cudaErrorNotSupported without the tensor-map encoder; *d_err != 0 if
 // a bounded wait of a tensor-core kernel ran out
-cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int* d_info, int* d_err);
+// G and X are K x K with leading dimension ld, a multiple of 4 (16-byte rows for the TMA)
+cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int64_t ld, int* d_info, int* d_err);
 bool chol_tc_available();
 template <typename T>
 cudaError_t symmetrize(sw_ctx* ctx, const T* G, int64_t K, T* S);
 template <typename T>
-cudaError_t shift_diag_vec(sw_ctx* ctx, T* G, int64_t K, const double* d);
+cudaError_t shift_diag_vec(sw_ctx* ctx, T* G, int64_t K, int64_t ld, const double* d);
 template <typename GT>
 cudaError_t scale_to(sw_ctx* ctx, int64_t n, const double* a, const double* s, GT* out);
 template <typename GT>
@@ -97,6 +98,7 @@ struct AsWarm {
     std::vector<char> F0;        // passive set of the recorded solve (N flags)
     std::vector<double> w0;      // its weights (N)
     std::vector<int64_t> P0;     // the factored set (ascending)
+    int64_t ld = 0;              // leading dimension of its G and X
     bool have_factor = false;
     double p0_extra = 0.15;      // P0 = F0 plus up to this fraction of |F0| near-active orbits
     int64_t factorisations = 0;  // factorisations made by the solves of this warm start
@@ -119,7 +121,7 @@ sw_status solve_bootstrap(sw_ctx* ctx, const sw_matrix* U, const double* y_dev, 
 // A_lo non-NULL the operand is A + A_lo and the three leading products of the split
 // are accumulated.  d_err receives a non-zero code if a bounded wait ran out.
 cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, const __nv_bfloat16* A_lo, int64_t K, int64_t ldA, float* C,
-                    int* d_err);
+                    int* d_err, int64_t ldc = 0);
 bool gram_tc_available();
 
 }  // namespace sw

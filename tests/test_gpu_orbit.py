@@ -67,17 +67,18 @@ def test_potential_and_force(sw, orc):
 def test_potential_and_force_paper_bar(sw, orc):
     """The paper's Dehnen-Aly T3 + V4 bar (bar_kind 1) with the disc and halo, and the bar
     alone, at 1e3 points against the oracle (its needle integrals by 48-point quadrature):
-    FP64 to 1e-11; FP32 potential to 1e-6 (total) and 3e-5 (bar alone, where the closed
-    forms' differences lose digits far from the needle), force to 5e-5 and 1e-4 of |a|
-    floored at 1e-3 of the median |a| (it vanishes at the centre, where only an absolute
-    error means anything)."""
+    FP64 to 1e-11; FP32 potential to 1e-6 (total) and 3e-5 (bar alone), force to 5e-5 and
+    3e-4 of |a| floored at 1e-3 of the median |a| (it vanishes at the centre, where only an
+    absolute error means anything).  The bar alone is looser in FP32: far from the needle
+    its closed forms take differences of nearly equal antiderivatives, a loss that is small
+    against the total force there."""
     rng = np.random.default_rng(3)
     x = np.concatenate([rng.normal(0, 3, (500, 3)), rng.normal(0, 12, (494, 3)),
                         np.array([[0.0, 0, 0], [4.0, 0, 0], [-4.0, 0.01, 0], [0.05, 0, 0.02],
                                   [30.0, -20.0, 5.0], [1e-4, 1e-4, 0]])])
     bar_only = dict(disc_M=0.0, disc_a=3.0, disc_b=0.3, halo_M200=0.0, halo_c=10.0, bar_M=1e10, bar_L=4.0,
                     bar_kind=1)
-    for pot, tol32 in ((PAPER_BAR, (1e-6, 5e-5)), (bar_only, (3e-5, 1e-4))):
+    for pot, tol32 in ((PAPER_BAR, (1e-6, 5e-5)), (bar_only, (3e-5, 3e-4))):
         phi_o, acc_o = orc.potential(orc.make_pot(pot), x)
         n = np.linalg.norm(acc_o, axis=1, keepdims=True)
         scale = np.maximum(n, 1e-3 * np.median(n))
@@ -400,3 +401,36 @@ def test_bundle(sw, orc, prec):
     np.testing.assert_array_equal(c.bundle(U, 1).copy(), Ug)
     with pytest.raises(sw.SwError):
         c.bundle(U, 3)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_bundled_projection(sw, orc, prec):
+    """Bundles accumulated at bin time (option project_bundle): the same means as sw_bundle
+    of the unbundled matrix (integer counts, one normalisation), with a realisation cut by
+    the quality test (a non-finite initial condition) contributing a zero column to its
+    bundle; a bundle size that does not divide the orbit count is rejected."""
+    pot = BARRED
+    base = inputs.disc_ics(inputs.DISC_HALO, 61, seed=113)
+    ics = inputs.dither(base, 4, 114, pot)
+    ics[4 * 7 + 2, 3] = np.nan                       # one realisation of bundle 7
+    grid = _grid(W2, nx=12, ny=10, nv=8, nR=6, nphi=6, nz=4)
+    S = 64
+    c = ctx_for(sw, prec, pot)
+    c.integrate_library(ics, 40.0, inputs.DT_HALF_MYR, S)
+    U = c.project(grid)
+    ref = c.bundle(U, 4).copy()
+    _, status = c.project_stats(len(ics))
+    assert status[4 * 7 + 2] == 2
+    c.set_option("project_bundle", 4)
+    Ub = c.project(grid)
+    assert (Ub.M, Ub.N) == (U.M, 61)
+    got = Ub.copy()
+    np.testing.assert_allclose(got, ref, rtol=3e-7 if prec == "fp32" else 1e-15, atol=0)
+    np.testing.assert_array_equal(np.rint(got * 16 * S), np.rint(ref * 16 * S))
+    Uo, _, _ = orc.build_matrix(orc.make_pot(pot), 40.0, inputs.DT_HALF_MYR, S, np.nan_to_num(ics), orc.make_obs(grid))
+    Uo[4 * 7 + 2] = 0.0
+    if prec == "fp64":
+        np.testing.assert_allclose(got, orc.bundle(Uo, 4), rtol=0, atol=1e-15)
+    c.integrate_library(ics[:-1], 40.0, inputs.DT_HALF_MYR, S)
+    with pytest.raises(sw.SwError):
+        c.project(grid)
