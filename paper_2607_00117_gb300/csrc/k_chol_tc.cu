@@ -96,24 +96,21 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
             const float rs = rsqrtf(d);       // 1 / L_jj
             const float rd = rs * rs;         // 1 / a_jj
             if (t == 0) rdiag[j] = rs;
-            // column j is final: L_ij = a_ij / sqrt(d) for i >= j (rows of block cb and below)
-            if (tx == jj) {
-#pragma unroll
-                for (int r = cb; r < 8; ++r) {
-                    const int i = ty + 16 * r;
-                    if (i >= j && i < bs) Ls[i * LP + j] = a[r][cb] * rs;
-                }
-            }
+            // column j is final and sits in col[b] (rows >= j): L_ij = a_ij / sqrt(d), one row per thread
+            if (t < DB && t >= j && t < bs) Ls[t * LP + j] = col[b * DB + t] * rs;
+            // rows and columns of the blocks after cb are all beyond j: only block cb needs the test
             float ci[8], lj[8];
 #pragma unroll
             for (int r = cb; r < 8; ++r) {
                 const int i = ty + 16 * r;
-                ci[r] = (i > j) ? col[b * DB + i] * rd : 0.f;
+                const float v = col[b * DB + i] * rd;
+                ci[r] = (r > cb || i > j) ? v : 0.f;
             }
 #pragma unroll
             for (int c = cb; c < 8; ++c) {
                 const int l = tx + 16 * c;
-                lj[c] = (l > j) ? col[b * DB + l] : 0.f;
+                const float v = col[b * DB + l];
+                lj[c] = (c > cb || l > j) ? v : 0.f;
             }
 #pragma unroll
             for (int r = cb; r < 8; ++r)
@@ -175,7 +172,8 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
 #pragma unroll
             for (int r = rb; r < 8; ++r) {
                 const int i = ty + 16 * r;
-                lik[r] = (i > k && i < bs) ? Ls[i * LP + k] : 0.f;
+                const float v = Ls[i * LP + k];
+                lik[r] = ((r > rb || i > k) && i < bs) ? v : 0.f;
             }
 #pragma unroll
             for (int r = rb; r < 8; ++r)
@@ -219,16 +217,18 @@ constexpr size_t DIAG_SMEM = sizeof(float) * (DB * LP + 5 * DB);
 // 2. Panel: P = A D^T for m rows below the diagonal block (A = G[r0 + i][j0 ..
 // j0 + 127]), in place in G, and its BF16 hi + lo halves (m x 128 row-major).
 // 64 rows per CTA of 256 threads; thread (tr, tc) = (t / 16, t % 16) computes
-// rows 4 tr .. 4 tr + 3 and columns tc + 16 q (q < 8).
+// rows 4 tr .. 4 tr + 3 and columns 8 tc .. 8 tc + 7, reading D transposed
+// (DT[l][c] = D[c][l]) so that its eight columns are two 16-byte loads.
 // ---------------------------------------------------------------------------
 constexpr int PR = 64;
+constexpr int DTP = DB + 4;   // padded row of DT (16-byte aligned, conflict-free float4 rows)
 __global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t ld, int64_t j0, int64_t r0,
                                                   int64_t m, const float* __restrict__ D,
                                                   __nv_bfloat16* __restrict__ Ph, __nv_bfloat16* __restrict__ Pl)
 {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
     float* As = sm;              // PR x LP
-    float* Ds = As + PR * LP;    // DB x LP
+    float* DT = As + PR * LP;    // DB x DTP (16-byte aligned: PR * LP * 4 = 33 024 bytes)
     const int t = threadIdx.x;
     const int64_t row0 = (int64_t)blockIdx.x * PR;
     // many loads in flight per thread: the staging is latency-bound otherwise
@@ -241,8 +241,9 @@ __global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t
 #pragma unroll 4
     for (int e4 = t; e4 < DB * DB / 4; e4 += 256) {
         const float4 d4 = reinterpret_cast<const float4*>(D)[e4];
-        const int i = (4 * e4) >> 7, l = (4 * e4) & (DB - 1);
-        Ds[i * LP + l] = d4.x; Ds[i * LP + l + 1] = d4.y; Ds[i * LP + l + 2] = d4.z; Ds[i * LP + l + 3] = d4.w;
+        const int c = (4 * e4) >> 7, l = (4 * e4) & (DB - 1);
+        DT[l * DTP + c] = d4.x; DT[(l + 1) * DTP + c] = d4.y; DT[(l + 2) * DTP + c] = d4.z;
+        DT[(l + 3) * DTP + c] = d4.w;
     }
     __syncthreads();
     const int tr = t >> 4, tc = t & 15;
@@ -251,14 +252,14 @@ __global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
-    const int lmax = tc + 16 * 7;   // D[c][l] = 0 for l > c
 #pragma unroll 4
-    for (int l = 0; l <= lmax; ++l) {
-        float av[4], dv[8];
+    for (int l = 0; l < DB; ++l) {
+        float av[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) av[r] = As[(4 * tr + r) * LP + l];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) dv[q] = Ds[(tc + 16 * q) * LP + l];
+        const float4 d0 = *reinterpret_cast<const float4*>(&DT[l * DTP + 8 * tc]);
+        const float4 d1 = *reinterpret_cast<const float4*>(&DT[l * DTP + 8 * tc + 4]);
+        const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -268,36 +269,40 @@ __global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t
     for (int r = 0; r < 4; ++r) {
         const int64_t gi = row0 + 4 * tr + r;
         if (gi >= m) continue;
+        float* g = G + (size_t)(r0 + gi) * ld + j0 + 8 * tc;
+        uint32_t hw[4], lw[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int c = tc + 16 * q;
-            G[(size_t)(r0 + gi) * ld + j0 + c] = acc[r][q];
-            __nv_bfloat16 h, lo;
-            split_bf16(acc[r][q], h, lo);
-            Ph[(size_t)gi * DB + c] = h;
-            Pl[(size_t)gi * DB + c] = lo;
+        for (int q = 0; q < 8; q += 2) {
+            g[q] = acc[r][q];
+            g[q + 1] = acc[r][q + 1];
+            const __nv_bfloat162 h = __floats2bfloat162_rn(acc[r][q], acc[r][q + 1]);
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(acc[r][q] - __low2float(h), acc[r][q + 1] - __high2float(h));
+            hw[q / 2] = (uint32_t)__bfloat16_as_ushort(h.x) | ((uint32_t)__bfloat16_as_ushort(h.y) << 16);
+            lw[q / 2] = (uint32_t)__bfloat16_as_ushort(lo.x) | ((uint32_t)__bfloat16_as_ushort(lo.y) << 16);
         }
+        *reinterpret_cast<uint4*>(Ph + (size_t)gi * DB + 8 * tc) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(Pl + (size_t)gi * DB + 8 * tc) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     }
 }
 
-constexpr size_t PANEL_SMEM = sizeof(float) * (PR + DB) * LP;
+constexpr size_t PANEL_SMEM = sizeof(float) * (PR * LP + DB * DTP);
 
 // ---------------------------------------------------------------------------
 // 4. Block row of the inverse: X[j0 + i][c] <- sum_l D[i][l] X[j0 + l][c] for
 // the ncols leading columns (in place), and its transpose as BF16 hi + lo
 // halves: XT[c][i] (ncols x 128 row-major).  64 columns per CTA of 256 threads;
-// thread (trow, tcol) = (t / 16, t % 16) computes rows trow + 16 k (k < 8),
-// columns 4 tcol .. 4 tcol + 3.
+// thread (trow, tcol) = (t / 16, t % 16) computes rows 8 trow .. 8 trow + 7 and
+// columns 4 tcol .. 4 tcol + 3, reading D transposed (DT[l][i] = D[i][l]).
 // ---------------------------------------------------------------------------
 constexpr int TC = 64;
 __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t ld, int64_t j0, int bs,
                                                  int64_t ncols, const float* __restrict__ D,
                                                  __nv_bfloat16* __restrict__ XTh, __nv_bfloat16* __restrict__ XTl)
 {
-    extern __shared__ float sm[];
-    float* Ss = sm;                 // DB x (TC + 4)
-    float* Ds = Ss + DB * (TC + 4); // DB x LP
-    __nv_bfloat16* Th = reinterpret_cast<__nv_bfloat16*>(Ds + DB * LP);   // TC x (DB + 8)
+    extern __shared__ __align__(16) float sm[];
+    float* Ss = sm;                   // DB x (TC + 4)
+    float* DT = Ss + DB * (TC + 4);   // DB x DTP
+    __nv_bfloat16* Th = reinterpret_cast<__nv_bfloat16*>(DT + DB * DTP);   // TC x (DB + 8)
     __nv_bfloat16* Tl = Th + TC * (DB + 8);
     const int t = threadIdx.x;
     const int64_t c0 = (int64_t)blockIdx.x * TC;
@@ -311,7 +316,8 @@ __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t 
     for (int e4 = t; e4 < DB * DB / 4; e4 += 256) {
         const float4 d4 = reinterpret_cast<const float4*>(D)[e4];
         const int i = (4 * e4) >> 7, l = (4 * e4) & (DB - 1);
-        Ds[i * LP + l] = d4.x; Ds[i * LP + l + 1] = d4.y; Ds[i * LP + l + 2] = d4.z; Ds[i * LP + l + 3] = d4.w;
+        DT[l * DTP + i] = d4.x; DT[(l + 1) * DTP + i] = d4.y; DT[(l + 2) * DTP + i] = d4.z;
+        DT[(l + 3) * DTP + i] = d4.w;
     }
     __syncthreads();
     const int trow = t >> 4, tcol = t & 15;
@@ -320,24 +326,24 @@ __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t 
     for (int k = 0; k < 8; ++k)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[k][j] = 0.f;
-    const int lmax = trow + 16 * 7;   // D[i][l] = 0 for l > i
+    const int lmax = 8 * trow + 7;   // D[i][l] = 0 for l > i
 #pragma unroll 4
     for (int l = 0; l <= lmax; ++l) {
-        const float4 s = *reinterpret_cast<const float4*>(&Ss[l * (TC + 4) + 4 * tcol]);
-        float dv[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) dv[k] = Ds[(trow + 16 * k) * LP + l];
+        const float4 sv = *reinterpret_cast<const float4*>(&Ss[l * (TC + 4) + 4 * tcol]);
+        const float4 d0 = *reinterpret_cast<const float4*>(&DT[l * DTP + 8 * trow]);
+        const float4 d1 = *reinterpret_cast<const float4*>(&DT[l * DTP + 8 * trow + 4]);
+        const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            acc[k][0] += dv[k] * s.x;
-            acc[k][1] += dv[k] * s.y;
-            acc[k][2] += dv[k] * s.z;
-            acc[k][3] += dv[k] * s.w;
+            acc[k][0] += dv[k] * sv.x;
+            acc[k][1] += dv[k] * sv.y;
+            acc[k][2] += dv[k] * sv.z;
+            acc[k][3] += dv[k] * sv.w;
         }
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const int i = trow + 16 * k;
+        const int i = 8 * trow + k;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int cc = 4 * tcol + j;
@@ -362,7 +368,8 @@ __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t 
     }
 }
 
-constexpr size_t TRMM_SMEM = sizeof(float) * (DB * (TC + 4) + DB * LP) + 2 * sizeof(__nv_bfloat16) * TC * (DB + 8);
+constexpr size_t TRMM_SMEM =
+    sizeof(float) * (DB * (TC + 4) + DB * DTP) + 2 * sizeof(__nv_bfloat16) * TC * (DB + 8);
 
 // ---------------------------------------------------------------------------
 // 3, 5. C[m x n] -= (A_hi + A_lo)(B_hi + B_lo)^T over a contraction of 64 nk, the

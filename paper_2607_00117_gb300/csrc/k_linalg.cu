@@ -49,6 +49,35 @@ __global__ void k_whiten_orbit(const T* __restrict__ U, int64_t M, int64_t N, co
     }
 }
 
+// FP32 matrix -> BF16 hi + lo halves, orbit space, in FP32 arithmetic (the split keeps ~16 bits, so
+// FP32 products lose nothing; FP64 arithmetic here would make the pass FP64-bound on this part).
+// inv_sig_f: 1/sigma in FP32.  Each thread handles pairs of rows (one 4-byte BF16x2 store per half).
+__global__ void k_whiten_orbit_f32(const float* __restrict__ U, int64_t M, int64_t N,
+                                   const float* __restrict__ inv_sig_f, const double* __restrict__ cs,
+                                   __nv_bfloat16* __restrict__ A, __nv_bfloat16* __restrict__ Alo, int64_t ldA)
+{
+    for (int64_t i = blockIdx.x; i < N; i += gridDim.x) {
+        const float* col = U + (size_t)i * M;
+        const float c = (float)cs[i];
+        __nv_bfloat162* a2 = reinterpret_cast<__nv_bfloat162*>(A + (size_t)i * ldA);
+        __nv_bfloat162* l2 = reinterpret_cast<__nv_bfloat162*>(Alo + (size_t)i * ldA);
+        for (int64_t p = threadIdx.x; 2 * p < ldA; p += blockDim.x) {
+            const int64_t r = 2 * p;
+            const float v0 = r < M ? col[r] * inv_sig_f[r] * c : 0.f;
+            const float v1 = r + 1 < M ? col[r + 1] * inv_sig_f[r + 1] * c : 0.f;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            a2[p] = h;
+            if (Alo) l2[p] = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+        }
+    }
+}
+
+__global__ void k_to_float(int64_t n, const double* __restrict__ a, float* __restrict__ b)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
 template <typename T, typename AT>
 __global__ void k_whiten_transpose(const T* __restrict__ U, int64_t M, int64_t N, const double* __restrict__ inv_sig,
                                    const double* __restrict__ cs, AT* __restrict__ A, AT* __restrict__ Alo,
@@ -804,6 +833,18 @@ cudaError_t whiten(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* 
 {
     LaunchTimer lt(ctx, K_WHITEN);
     add_work(ctx, K_WHITEN, (double)M * N * (sizeof(T) + (Alo ? 2.0 : 1.0) * sizeof(AT)));
+    if constexpr (sizeof(T) == 4 && sizeof(AT) == 2) {
+        if (orbit_space && (ldA & 1) == 0) {
+            // 1/sigma in FP32 once per call (M values), then the FP32 pass
+            if (ctx->ensure(&ctx->d_invsig_f, &ctx->invsig_f_cap, (size_t)M * sizeof(float), "1/sigma (FP32)") !=
+                SW_OK)
+                return cudaErrorMemoryAllocation;
+            float* isf = (float*)ctx->d_invsig_f;
+            k_to_float<<<cap_grid(M, 256, 1024), 256, 0, ctx_stream(ctx)>>>(M, inv_sig, isf);
+            k_whiten_orbit_f32<<<cap_grid(N, 1, 65536), 256, 0, ctx_stream(ctx)>>>(U, M, N, isf, cs, A, Alo, ldA);
+            return cudaGetLastError();
+        }
+    }
     if (orbit_space) {
         k_whiten_orbit<T, AT><<<cap_grid(N, 1, 65536), 256, 0, ctx_stream(ctx)>>>(U, M, N, inv_sig, cs, A, Alo, ldA);
     } else {

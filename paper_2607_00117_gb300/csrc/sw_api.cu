@@ -162,11 +162,12 @@ static void ctx_release(sw_ctx* ctx)
     cudaStreamSynchronize(ctx->stream);
     ctx->harvest();
     void* bufs[] = {ctx->d_soa, ctx->d_cs, ctx->d_aos, ctx->d_drift, ctx->d_status, ctx->d_stats, ctx->d_ghtab,
-                    ctx->d_mlp, ctx->d_split, ctx->d_chol, ctx->d_ttotal, ctx->d_chol_tc, ctx->d_cut};
+                    ctx->d_mlp, ctx->d_split, ctx->d_chol, ctx->d_ttotal, ctx->d_chol_tc, ctx->d_cut,
+                    ctx->d_invsig_f};
     for (void* b : bufs)
         if (b) cudaFree(b);
     ctx->d_soa = ctx->d_cs = ctx->d_ghtab = ctx->d_mlp = ctx->d_split = ctx->d_chol = nullptr;
-    ctx->d_ttotal = ctx->d_chol_tc = ctx->d_cut = nullptr;
+    ctx->d_ttotal = ctx->d_chol_tc = ctx->d_cut = ctx->d_invsig_f = nullptr;
     ctx->d_aos = ctx->d_drift = nullptr;
     ctx->d_status = nullptr;
     ctx->d_stats = nullptr;

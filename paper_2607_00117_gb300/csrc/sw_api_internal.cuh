@@ -102,6 +102,7 @@ struct sw_ctx {
     void* d_chol = nullptr; size_t chol_cap = 0;     // cooperative Cholesky: diagonal inverses, barrier
     void* d_chol_tc = nullptr; size_t chol_tc_cap = 0;   // tensor-core Cholesky: diagonal inverse, BF16 panels
     void* d_cut = nullptr; size_t cut_cap = 0;           // bundled projection: indices of cut realisations
+    void* d_invsig_f = nullptr; size_t invsig_f_cap = 0; // whitening: 1/sigma in FP32
     void* d_ttotal = nullptr; size_t ttotal_cap = 0;   // per-orbit integration time (adaptive integrator)
     // solve
     sw::SolveWS solve_ws;

@@ -33,17 +33,25 @@ def test_roofline_entry_arithmetic():
         "k_simt": {"launches": 4, "ms": 8.0, "work": 4 * 4.0e10, "kind": "flop_simt"},
         "k_orbit": {"launches": 1, "ms": 100.0, "work": 1.0e9, "kind": "orbit_steps"},
     }
-    r = bench.roofline_entry("k_bytes", stats, 6000.0, 1700.0, 2070.0)
+    r = bench.roofline_entry("k_bytes", stats, 6000.0, 1700.0, 2070.0, 152)
     assert r["bound"] == "hbm" and math.isclose(r["achieved"], 3000.0) and math.isclose(r["frac"], 0.5)
-    r = bench.roofline_entry("k_tensor", stats, 6000.0, 1700.0, 2070.0)
+    r = bench.roofline_entry("k_tensor", stats, 6000.0, 1700.0, 2070.0, 152)
     assert r["bound"] == "tensor" and math.isclose(r["achieved"], 1000.0)
-    r = bench.roofline_entry("k_simt", stats, 6000.0, 1700.0, 2070.0)
+    r = bench.roofline_entry("k_simt", stats, 6000.0, 1700.0, 2070.0, 152)
     peak = 152 * 128 * 2 * 2070e6 / 1e12
     assert r["bound"] == "alu" and math.isclose(r["achieved"], 20.0) and math.isclose(r["peak"], peak)
     assert "one_sm_frac" not in r
     one = {"diag_factor_inverse": {"launches": 10, "ms": 0.5, "work": 10 * 1.0e5, "kind": "flop_simt"}}
-    r = bench.roofline_entry("diag_factor_inverse", one, 6000.0, 1700.0, 2070.0)
+    r = bench.roofline_entry("diag_factor_inverse", one, 6000.0, 1700.0, 2070.0, 152)
     assert math.isclose(r["achieved"], 2e-3) and math.isclose(r["one_sm_frac"], r["frac"] * 152)
-    r = bench.roofline_entry("k_orbit", stats, 6000.0, 1700.0, 2070.0)
+    r = bench.roofline_entry("k_orbit", stats, 6000.0, 1700.0, 2070.0, 152)
     assert math.isclose(r["achieved"], bench.OPS_PER_ORBIT_STEP * 1e9 / 0.1 / 1e12)
     assert math.isclose(r["peak"], 152 * 128 * 2070e6 / 1e12)
+    assert math.isclose(r["algorithmic_frac"], bench.ALG_OPS_PER_ORBIT_STEP * 1e9 / 0.1 / 1e12 / r["peak"])
+    # split products: the Gram counts the three issued, the factor updates the method's one
+    st3 = {"gram_tcgen05": {"launches": 1, "ms": 1.0, "work": 1.5e12, "kind": "flop_tensor"},
+           "syrk_update_tcgen05": {"launches": 1, "ms": 1.0, "work": 0.5e12, "kind": "flop_tensor"}}
+    g = bench.roofline_entry("gram_tcgen05", st3, 6000.0, 1500.0, 2070.0, 152)
+    assert math.isclose(g["frac"], 1.0) and math.isclose(g["method_frac"], 1.0 / 3.0)
+    y = bench.roofline_entry("syrk_update_tcgen05", st3, 6000.0, 1500.0, 2070.0, 152)
+    assert math.isclose(y["frac"], 1.0 / 3.0) and math.isclose(y["tensor_pipe_frac"], 1.0)
