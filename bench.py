@@ -60,8 +60,11 @@ def parse():
     ap.add_argument("--prof-steps", type=int, default=3, help="steps of the separate profiled pass")
     ap.add_argument("--n-mock", type=int, default=N_MOCK,
                     help="orbits of the mock library that makes the data (smaller for small ncu captures)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched_64", "surrogate"],
-                    help="batched_64: 64 trial potentials built in one persistent launch, then solved")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched_64", "surrogate", "large_300k"],
+                    help="batched_64: 64 trial potentials built in one persistent launch, then solved; "
+                         "large_300k: 300 000 orbits x 20 000 steps with per-sample Gauss-Hermite rows")
+    ap.add_argument("--ics", default=None, choices=["disc", "paper"],
+                    help="initial conditions of the library (default: the workload's; disc for barred_100k)")
     return ap.parse_args()
 
 
@@ -169,7 +172,7 @@ def make_data(sw, torch, W, rank, n_mock=N_MOCK):
     grid = W["grid"]
     ctx = sw.Context(0, "fp32")
     ctx.set_potential(W["potential"])
-    ics = inputs.disc_ics(W["potential"], n_mock, seed=W["seeds"]["ic"] + 500 + rank)
+    ics = inputs.workload_ics(W["potential"], n_mock, W["seeds"]["ic"] + 500 + rank, W.get("ics", "disc"))
     ctx.integrate_library(ics, W["omega_p"], W["dt"], W["nsteps"])
     Uh = ctx.project(grid)
     wt = inputs.true_weights(n_mock, W["seeds"]["w"]) * (W["n_orb"] / n_mock)
@@ -382,10 +385,12 @@ def run_sw(args):
     grid, N, S = W["grid"], W["n_orb"], W["nsteps"]
     hbm, bf16, bf16_sus, sm_max, peak_src = peaks()
 
+    if args.ics:
+        W["ics"] = args.ics
     v0s, y, sig = make_data(sw, torch, W, rank, args.n_mock)
     nb = W.get("bundle", 1)
     Nb = N // nb
-    base = inputs.disc_ics(W["potential"], Nb, seed=replica_seed(W["seeds"]["ic"], rank))
+    base = inputs.workload_ics(W["potential"], Nb, replica_seed(W["seeds"]["ic"], rank), W.get("ics", "disc"))
     ics = inputs.dither(base, nb, replica_seed(W["seeds"]["dither"], rank), W["potential"]) if nb > 1 else base
     dev = torch.device("cuda", local)
     ics_d = torch.from_numpy(ics).to(dev)
@@ -393,7 +398,10 @@ def run_sw(args):
     sig_d = torch.from_numpy(sig).to(dev)
     w_d = torch.empty(Nb, dtype=torch.float64, device=dev)
     chi_d = torch.empty(3, dtype=torch.float64, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    # a stream of our own (the default stream's handle is 0, which the library reads as "create a
+    # stream"): every launch of the library and the timing events share it
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     ctx = sw.Context(local, "fp32", stream.cuda_stream)
     ctx.set_potential(W["potential"])
     ctx.set_option("project_bundle", nb)       # bundles accumulated at bin time
@@ -529,7 +537,8 @@ def run_sw(args):
             "value": value, "unit": "orbit-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_orb": N, "bundles": Nb, "dithers_per_bundle": nb, "nsteps": S,
+            "config": {"workload": WORKLOAD, "ics": W.get("ics", "disc"), "n_orb": N, "bundles": Nb,
+                       "dithers_per_bundle": nb, "nsteps": S,
                        "rows_histogram": grid["nR"] * grid["nphi"] *
                        grid["nz"] + grid["nx"] * grid["ny"] * (1 + grid["nv"]), "rows_solve": M_gh,
                        "parallelism": f"replicas x{world}",
@@ -559,7 +568,8 @@ def bootstrap_leg(sw, ctx, Ug, y, sig, W, torch, B=100):
     Ug.free()
     return {"realisations": B, "seconds": dt, "ms_per_realisation": 1e3 * dt / B, "chi2_model": chi_m,
             "chi2_b_median": float(np.median(chi_b)), "chi2_b_std": float(np.std(chi_b)),
-            "reduced_solves": info["polish_solves"], "factorisations": info["refine_rounds"]}
+            "reduced_solves": info["polish_solves"], "factorisations": info["refine_rounds"],
+            "cg_steps": info["admm_iterations"]}
 
 
 def bs3_leg(sw, torch, W, ics_d, stream, local, n_sm, sm_mhz, nsteps=5000):
@@ -597,6 +607,116 @@ def bs3_leg(sw, torch, W, ics_d, stream, local, n_sm, sm_mhz, nsteps=5000):
                     "plus three per rejected trial"}
 
 
+def run_large(args):
+    """The large library (config 5): 300 000 orbits (75 000 initial conditions from the paper's
+    Jeans disc x 4 dithers) x 20 000 steps in the barred potential, projected with per-sample
+    Gauss-Hermite rows (60 x 60 pixels, mass + h1..h4, and 20 x 20 x 10 cells: M = 22 000), the
+    bundles accumulated at bin time (U: 22 000 x 75 000 FP32, 6.6 GB), and the weight solve.
+    The data come from an independent 20 000-orbit library of the same potential; the GH
+    references (v0, s) per pixel from its velocity histogram."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2607_00117_gb300 import sw
+    sw.lib()
+    W = dict(inputs.WORKLOADS["large_300k"])
+    if args.n_orb:
+        W["n_orb"] = args.n_orb - args.n_orb % W["bundle"]
+    if args.nsteps:
+        W["nsteps"] = args.nsteps
+    if args.ics:
+        W["ics"] = args.ics
+    grid, N, S, nb = W["grid"], W["n_orb"], W["nsteps"], W["bundle"]
+    Nb = N // nb
+    hbm, bf16, bf16_sus, sm_max, peak_src = peaks()
+    dev = torch.device("cuda", local)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    # ---- data: mock library -> velocity moments per pixel -> GH references -> GH data rows
+    n_mock = args.n_mock
+    ctxm = sw.Context(local, "fp32", stream.cuda_stream)
+    ctxm.set_potential(W["potential"])
+    ics_m = inputs.workload_ics(W["potential"], n_mock, W["seeds"]["ic"] + 500 + rank, W["ics"])
+    ctxm.integrate_library(ics_m, W["omega_p"], W["dt"], S)
+    ghist = dict(grid, gh=0)
+    Uh = ctxm.project(ghist)
+    wt = inputs.true_weights(n_mock, W["seeds"]["w"]) * (N / n_mock)
+    v0s, gh_err = inputs.gh_reference(pixel_moments_from_hist(Uh.apply(wt), ghist))
+    Uh.free()
+    Ugm = ctxm.project(grid, gh_v0s=v0s)
+    y0 = Ugm.apply(wt)
+    blocks = {"dens": (0, Ugm.blocks[0]), "pix": (Ugm.blocks[0], Ugm.blocks[0] + Ugm.blocks[1]),
+              "kin": (Ugm.blocks[0] + Ugm.blocks[1], Ugm.M)}
+    sig = inputs.mock_sigma(y0, blocks, gh_err=gh_err)
+    y = y0 + sig * inputs.noise(len(y0), W["seeds"]["noise"])
+    Ugm.free()
+    ctxm.close()
+    base = inputs.workload_ics(W["potential"], Nb, replica_seed(W["seeds"]["ic"], rank), W["ics"])
+    ics = inputs.dither(base, nb, replica_seed(W["seeds"]["dither"], rank), W["potential"])
+    ics_d = torch.from_numpy(ics).to(dev)
+    y_d, sig_d = torch.from_numpy(y).to(dev), torch.from_numpy(sig).to(dev)
+    w_d = torch.empty(Nb, dtype=torch.float64, device=dev)
+    chi_d = torch.empty(3, dtype=torch.float64, device=dev)
+    ctx = sw.Context(local, "fp32", stream.cuda_stream)
+    ctx.set_potential(W["potential"])
+    ctx.set_option("project_bundle", nb)
+    statuses = []
+
+    def step():
+        ctx.integrate_library_device(ics_d, W["omega_p"], W["dt"], S)
+        U = ctx.project(grid, gh_v0s=v0s)
+        st = ctx.solve_weights_device(U, y_d, sig_d, W["lam"], w_d, chi_d)
+        M = U.M
+        U.free()
+        statuses.append(sw.STATUS_NAMES[st])
+        return M
+
+    for _ in range(max(1, args.warmup)):
+        M = step()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    clocks = Clocks(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    info = ctx.solve_info()
+    chi2 = chi_d.cpu().numpy()
+    ctx.set_profiling(True)
+    ctx.reset_stats()
+    step()
+    torch.cuda.synchronize()
+    kstats = ctx.kernel_stats()
+    ctx.set_profiling(False)
+    if rank != 0:
+        return
+    sm_mhz = clk["sm_mhz"] if clk else sm_max
+    dom = max(kstats, key=lambda k: kstats[k]["ms"])
+    roof = roofline_entry(dom, kstats, hbm, bf16_sus, sm_mhz, n_sm)
+    roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(dom), "peak_source": peak_src})
+    line = {"metric": "orbit-steps/s (whole model evaluations, FP32 batched vs FP64 plain at matched chi^2)",
+            "value": N * S * args.steps * world / elapsed, "unit": "orbit-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "large_300k", "ics": W["ics"], "n_orb": N, "bundles": Nb, "nsteps": S, "rows": M,
+                       "gh_rows": "per sample (sum 2 sqrt(pi) alpha(w) H_m(w))",
+                       "matrix_gb": M * Nb * 4 / 1e9, "l2": "U (6.6 GB) far larger than L2"},
+            "models_per_s": args.steps * world / elapsed,
+            "chi2": {"total": float(chi2[0]), "obs": float(chi2[1]), "reg": float(chi2[2]), "solver": info,
+                     "status": statuses[-args.steps:]},
+            "roofline": roof,
+            "kernel_ms_per_step": {k: round(v["ms"], 3) for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])},
+            "gpu_launches": int(launches), "clocks": clk, "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args):
     """64 trial potentials of the 12-D box with orbit counts U(10k, 100k), 5 000
     steps, built in one persistent launch (autotuned, replayed from a CUDA graph),
@@ -619,7 +739,8 @@ def run_batched(args):
                           for k, (m, n) in enumerate(zip(models, counts))])
     npix = grid["nx"] * grid["ny"]
     v0s = np.tile(np.array([0.0, 150.0]), (K, npix, 1))
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     ctx = sw.Context(local, "fp32", stream.cuda_stream)
     b = sw.Batch(ctx, counts, S, grid)
     b.set_models([m["potential"] for m in models], [m["omega_p"] for m in models],
@@ -783,5 +904,7 @@ if __name__ == "__main__":
         run_batched(a)
     elif a.workload == "surrogate":
         run_surrogate(a)
+    elif a.workload == "large_300k":
+        run_large(a)
     else:
         run_sw(a)

@@ -374,8 +374,9 @@ constexpr size_t TRMM_SMEM =
 // ---------------------------------------------------------------------------
 // 3, 5. C[m x n] -= (A_hi + A_lo)(B_hi + B_lo)^T over a contraction of 64 nk, the
 // A and B operands K-major BF16 (rows of their maps), in 128 x 128 tiles (LOWER:
-// only tiles with tj <= ti); C is the FP32 region at (cy0, cx0) of the matrix
-// behind the map mc.  Persistent: each CTA (one per SM) walks the tiles
+// only tiles with tj <= ti), the operand rows of tile (ti, tj) starting at
+// ra0 + 128 ti and rb0 + 128 tj; C is the FP32 region at (cy0, cx0) of the
+// matrix behind the map mc.  Persistent: each CTA (one per SM) walks the tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0 issues TMA loads (128-byte
 // swizzle) through a 3-stage ring; one thread of warp 1 issues tcgen05.mma into
 // one of two 128-column TMEM accumulators; warps 2-5 drain the other: each
@@ -412,8 +413,8 @@ template <bool LOWER>
 __global__ void __launch_bounds__(SUB_THREADS, 1)
     k_tc_sub(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap ma_lo,
              const __grid_constant__ CUtensorMap mb, const __grid_constant__ CUtensorMap mb_lo,
-             const __grid_constant__ CUtensorMap mc, int cx0, int cy0, int64_t n_tiles, int64_t tiles_n, int nk,
-             int* err)
+             const __grid_constant__ CUtensorMap mc, int cx0, int cy0, int ra0, int rb0, int64_t n_tiles,
+             int64_t tiles_n, int nk, int* err)
 {
     extern __shared__ unsigned char smraw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -468,10 +469,10 @@ __global__ void __launch_bounds__(SUB_THREADS, 1)
                 }
                 unsigned char* sa = base + s * STAGE_BYTES;
                 mbar_expect_tx(&full[s], STAGE_BYTES);
-                tma_load_2d(sa, &ma, kc * BKC, (int)(ti * BM), &full[s]);
-                tma_load_2d(sa + OP_BYTES, &mb, kc * BKC, (int)(tj * BN), &full[s]);
-                tma_load_2d(sa + 2 * OP_BYTES, &ma_lo, kc * BKC, (int)(ti * BM), &full[s]);
-                tma_load_2d(sa + 3 * OP_BYTES, &mb_lo, kc * BKC, (int)(tj * BN), &full[s]);
+                tma_load_2d(sa, &ma, kc * BKC, ra0 + (int)(ti * BM), &full[s]);
+                tma_load_2d(sa + OP_BYTES, &mb, kc * BKC, rb0 + (int)(tj * BN), &full[s]);
+                tma_load_2d(sa + 2 * OP_BYTES, &ma_lo, kc * BKC, ra0 + (int)(ti * BM), &full[s]);
+                tma_load_2d(sa + 3 * OP_BYTES, &mb_lo, kc * BKC, rb0 + (int)(tj * BN), &full[s]);
             }
         }
         if (*abort_flag) {
@@ -647,19 +648,44 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
         attr = true;
     }
     cudaStream_t st = ctx_stream(ctx);
-    // scratch: D_k (128 x 128 FP32), the panel's and the inverse block row's BF16 halves (K x 128 each)
+    const bool la = ctx->opt.chol_lookahead != 0;
+    if (la && !ctx->stream2) {
+        if (cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->stream2 = nullptr;
+        }
+    }
+    cudaStream_t sb = la && ctx->stream2 ? ctx->stream2 : st;   // the bulk updates' stream
+    const bool two = sb != st;
+    // dependency events: rings of 3 for "panel k done" (P), "rest of the trailing update k done"
+    // (R) and "step k's bulk work done" (B); no dependency reaches further back than two steps
+    if (two && ctx->dep_events.size() < 9) {
+        while (ctx->dep_events.size() < 9) {
+            cudaEvent_t ev;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return cudaErrorUnknown;
+            ctx->dep_events.push_back(ev);
+        }
+    }
+    auto evP = [&](int64_t k) { return ctx->dep_events[0 + k % 3]; };
+    auto evR = [&](int64_t k) { return ctx->dep_events[3 + k % 3]; };
+    auto evB = [&](int64_t k) { return ctx->dep_events[6 + k % 3]; };
+    // scratch, double-buffered by step parity where the two streams overlap: D_k (128 x 128 FP32)
+    // and the panel's BF16 halves (K x 128 each); the inverse block row's halves (K x 128 each)
     const size_t dbytes = (size_t)DB * DB * sizeof(float);
     const size_t hbytes = ((size_t)K * DB * sizeof(__nv_bfloat16) + 255) & ~(size_t)255;
-    if (ctx->ensure(&ctx->d_chol_tc, &ctx->chol_tc_cap, dbytes + 4 * hbytes + 256, "factor scratch") != SW_OK)
+    if (ctx->ensure(&ctx->d_chol_tc, &ctx->chol_tc_cap, 2 * dbytes + 6 * hbytes + 256, "factor scratch") != SW_OK)
         return cudaErrorMemoryAllocation;
-    float* Dk = (float*)ctx->d_chol_tc;
-    __nv_bfloat16* Ph = (__nv_bfloat16*)((char*)ctx->d_chol_tc + dbytes);
-    __nv_bfloat16* Pl = (__nv_bfloat16*)((char*)Ph + hbytes);
-    __nv_bfloat16* XTh = (__nv_bfloat16*)((char*)Pl + hbytes);
-    __nv_bfloat16* XTl = (__nv_bfloat16*)((char*)XTh + hbytes);
-    CUtensorMap mph, mpl, mxh, mxl, mg, mx;
-    if (!make_map(&mph, Ph, K) || !make_map(&mpl, Pl, K) || !make_map(&mxh, XTh, K) || !make_map(&mxl, XTl, K) ||
-        !make_cmap(&mg, G, K, ld) || !make_cmap(&mx, X, K, ld))
+    char* base = (char*)ctx->d_chol_tc;
+    float* Dk[2] = {(float*)base, (float*)(base + dbytes)};
+    __nv_bfloat16* Ph[2] = {(__nv_bfloat16*)(base + 2 * dbytes), (__nv_bfloat16*)(base + 2 * dbytes + hbytes)};
+    __nv_bfloat16* Pl[2] = {(__nv_bfloat16*)(base + 2 * dbytes + 2 * hbytes),
+                            (__nv_bfloat16*)(base + 2 * dbytes + 3 * hbytes)};
+    __nv_bfloat16* XTh = (__nv_bfloat16*)(base + 2 * dbytes + 4 * hbytes);
+    __nv_bfloat16* XTl = (__nv_bfloat16*)(base + 2 * dbytes + 5 * hbytes);
+    CUtensorMap mph[2], mpl[2], mxh, mxl, mg, mx;
+    for (int b = 0; b < 2; ++b)
+        if (!make_map(&mph[b], Ph[b], K) || !make_map(&mpl[b], Pl[b], K)) return cudaErrorInvalidValue;
+    if (!make_map(&mxh, XTh, K) || !make_map(&mxl, XTl, K) || !make_cmap(&mg, G, K, ld) || !make_cmap(&mx, X, K, ld))
         return cudaErrorInvalidValue;
     cudaError_t e;
     // X = I
@@ -668,48 +694,85 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
         LaunchTimer lt(ctx, K_MISC);
         k_unit_diag<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(X, K, ld);
     }
+    const unsigned grid_cap = (unsigned)ctx_sms(ctx);
+    auto tc_launch = [&](cudaStream_t s, int kid, bool lower, const CUtensorMap& a, const CUtensorMap& al,
+                         const CUtensorMap& bm, const CUtensorMap& bl, const CUtensorMap& c, int cx0, int cy0,
+                         int ra0, int rb0, int64_t tiles, int64_t tiles_n, double flops) -> cudaError_t {
+        if (tiles <= 0) return cudaSuccess;
+        LaunchTimer lt(ctx, kid, s);
+        add_work(ctx, kid, flops);
+        const unsigned g = (unsigned)std::min<int64_t>(tiles, grid_cap);
+        if (lower)
+            k_tc_sub<true><<<g, SUB_THREADS, SUB_SMEM, s>>>(a, al, bm, bl, c, cx0, cy0, ra0, rb0, tiles, tiles_n,
+                                                           DB / BKC, d_err);
+        else
+            k_tc_sub<false><<<g, SUB_THREADS, SUB_SMEM, s>>>(a, al, bm, bl, c, cx0, cy0, ra0, rb0, tiles, tiles_n,
+                                                            DB / BKC, d_err);
+        return cudaGetLastError();
+    };
+    // Step k.  Stream A (the context's): diagonal block, panel and the trailing update's first
+    // tile column (the next diagonal block's column), the chain every later step waits for.
+    // Stream B: the rest of the trailing update, the inverse's block row and its update of the
+    // rows below -- the bulk work, which overlaps the next steps' chain.  Without a second
+    // stream everything runs in this order on A.
     const int64_t nb = (K + DB - 1) / DB;
     for (int64_t kb = 0; kb < nb; ++kb) {
         const int64_t j0 = kb * DB;
         const int bs = (int)(K - j0 < DB ? K - j0 : DB);
         const int64_t r0 = j0 + bs, m = K - r0;
+        const int par = (int)(kb & 1);
+        // the buffers of parity par were last read by step kb - 2's bulk work
+        if (two && kb >= 2 && (e = cudaStreamWaitEvent(st, evB(kb - 2), 0))) return e;
         {
             LaunchTimer lt(ctx, K_POTRF_DIAG);
             add_work(ctx, K_POTRF_DIAG, 2.0 * (double)bs * bs * bs / 3.0);
-            k_diag128<<<1, DIAG_THREADS, DIAG_SMEM, st>>>(G, ld, j0, bs, Dk, d_info);
+            k_diag128<<<1, DIAG_THREADS, DIAG_SMEM, st>>>(G, ld, j0, bs, Dk[par], d_info);
         }
         if ((e = cudaGetLastError())) return e;
+        const int64_t T = (m + BM - 1) / BM;
         if (m > 0) {
             {
                 LaunchTimer lt(ctx, K_TRSM_PANEL);
                 add_work(ctx, K_TRSM_PANEL, (double)m * DB * DB);
-                k_panel128<<<(unsigned)((m + PR - 1) / PR), 256, PANEL_SMEM, st>>>(G, ld, j0, r0, m, Dk, Ph, Pl);
-            }
-            if ((e = cudaGetLastError())) return e;
-            const int64_t T = (m + BM - 1) / BM, tiles = T * (T + 1) / 2;
-            {
-                LaunchTimer lt(ctx, K_SYRK_TC);
-                add_work(ctx, K_SYRK_TC, (double)m * (double)(m + 1) * DB);
-                k_tc_sub<true><<<(unsigned)std::min<int64_t>(tiles, ctx_sms(ctx)), SUB_THREADS, SUB_SMEM, st>>>(
-                    mph, mpl, mph, mpl, mg, (int)r0, (int)r0, tiles, T, DB / BKC, d_err);
+                k_panel128<<<(unsigned)((m + PR - 1) / PR), 256, PANEL_SMEM, st>>>(G, ld, j0, r0, m, Dk[par],
+                                                                                   Ph[par], Pl[par]);
             }
             if ((e = cudaGetLastError())) return e;
         }
+        if (two && (e = cudaEventRecord(evP(kb), st))) return e;
+        if (m > 0) {
+            // the first tile column: column block kb + 1, last updated by step kb - 1's rest
+            if (two && kb >= 1 && (e = cudaStreamWaitEvent(st, evR(kb - 1), 0))) return e;
+            if ((e = tc_launch(st, K_SYRK_TC, false, mph[par], mpl[par], mph[par], mpl[par], mg, (int)r0, (int)r0, 0,
+                               0, T, 1, 2.0 * (double)m * std::min<int64_t>(m, BN) * DB)))
+                return e;
+        }
+        // ---- bulk work on stream B
+        if (two && (e = cudaStreamWaitEvent(sb, evP(kb), 0))) return e;
+        if (T > 1) {
+            const int64_t T1 = T - 1;
+            const double mr = (double)(m - BN);
+            if ((e = tc_launch(sb, K_SYRK_TC, true, mph[par], mpl[par], mph[par], mpl[par], mg, (int)(r0 + BN),
+                               (int)(r0 + BN), BN, BN, T1 * (T1 + 1) / 2, T1, mr * (mr + 1.0) * DB)))
+                return e;
+        }
+        if (two && (e = cudaEventRecord(evR(kb), sb))) return e;
         {
-            LaunchTimer lt(ctx, K_TRINV_DIAG);
+            LaunchTimer lt(ctx, K_TRINV_DIAG, sb);
             add_work(ctx, K_TRINV_DIAG, (double)bs * bs * (double)r0);
-            k_trmm128<<<(unsigned)((r0 + TC - 1) / TC), 256, TRMM_SMEM, st>>>(X, ld, j0, bs, r0, Dk, XTh, XTl);
+            k_trmm128<<<(unsigned)((r0 + TC - 1) / TC), 256, TRMM_SMEM, sb>>>(X, ld, j0, bs, r0, Dk[par], XTh, XTl);
         }
         if ((e = cudaGetLastError())) return e;
         if (m > 0) {
-            const int64_t Tm = (m + BM - 1) / BM, Tn = (r0 + BN - 1) / BN, tiles = Tm * Tn;
-            LaunchTimer lt(ctx, K_TRINV_TC);
-            add_work(ctx, K_TRINV_TC, 2.0 * (double)m * (double)r0 * DB);
-            k_tc_sub<false><<<(unsigned)std::min<int64_t>(tiles, ctx_sms(ctx)), SUB_THREADS, SUB_SMEM, st>>>(
-                mph, mpl, mxh, mxl, mx, 0, (int)r0, tiles, Tn, DB / BKC, d_err);
+            const int64_t Tn = (r0 + BN - 1) / BN;
+            if ((e = tc_launch(sb, K_TRINV_TC, false, mph[par], mpl[par], mxh, mxl, mx, 0, (int)r0, 0, 0, T * Tn, Tn,
+                               2.0 * (double)m * (double)r0 * DB)))
+                return e;
         }
-        if ((e = cudaGetLastError())) return e;
+        if (two && (e = cudaEventRecord(evB(kb), sb))) return e;
     }
+    // the caller's stream sees the whole factorisation
+    if (two && (e = cudaStreamWaitEvent(st, evB(nb - 1), 0))) return e;
     return cudaSuccess;
 }
 

@@ -572,8 +572,26 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         if (!F.empty()) {
             bool ok = true, conv = false;
             if (!factored_covers(F)) {
-                AS_TRY(factor(F, ok));
-                if (warm) warm->have_factor = false;   // P0 is now this passive set
+                // a warm-started solve grows the kept set to P0 U F while the orbits it masks stay a
+                // minority, so that later solves of the same matrix keep reusing one factor
+                std::vector<int64_t> S;
+                if (warm && warm->start && warm->have_factor) {
+                    S = P0;
+                    for (int64_t i : F)
+                        if (pos[i] < 0) S.push_back(i);
+                    std::sort(S.begin(), S.end());
+                }
+                const bool grow = !S.empty() && (int64_t)S.size() <= cap &&
+                                  (double)S.size() <= 1.3 * (double)F.size() + 256.0;
+                if (grow) {
+                    AS_TRY(factor(S, ok));
+                    warm->P0 = P0;
+                    warm->ld = ldG;
+                    warm->have_factor = ok;
+                } else {
+                    AS_TRY(factor(F, ok));
+                    if (warm) warm->have_factor = false;   // P0 is now this passive set
+                }
             }
             if (!ok) { failed = true; break; }
             AS_TRY(solve_on(F, conv));
@@ -702,7 +720,7 @@ sw_status solve_bootstrap(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev,
     if (worst != SW_OK && worst != SW_ENONCONV) return worst;
     warm.record = false;
     warm.start = true;
-    int64_t solves = 0;
+    int64_t solves = 0, cg = 0;
     for (int64_t b = 0; b < B; ++b) {
         {
             LaunchTimer lt(ctx, K_MISC);
@@ -715,6 +733,7 @@ sw_status solve_bootstrap(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev,
         if (s != SW_OK && s != SW_ENONCONV) return s;
         if (s == SW_ENONCONV) worst = SW_ENONCONV;
         solves += (int64_t)ctx->solve_info[4];
+        cg += (int64_t)ctx->solve_info[0];
         // chi2_b: the observational chi^2 of w_b against the observed data
         AS_CUDA(ctx, cudaMemsetAsync(acc, 0, M * sizeof(double), st), "memset");
         AS_CUDA(ctx, u_times_w<T>(ctx, (const T*)Um->d, M, N, wout, acc), "U w_b");
@@ -727,6 +746,7 @@ sw_status solve_bootstrap(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev,
     AS_CUDA(ctx, cudaStreamSynchronize(st), "bootstrap");
     ctx->solve_info[4] = (double)solves;
     ctx->solve_info[1] = (double)warm.factorisations;
+    ctx->solve_info[0] = (double)cg;
     return worst;
 }
 

@@ -33,21 +33,23 @@ void set_error(sw_ctx* ctx, const char* fmt, ...)
 cudaStream_t ctx_stream(sw_ctx* ctx) { return ctx->stream; }
 int ctx_sms(const sw_ctx* ctx) { return ctx->n_sm; }
 
-LaunchTimer::LaunchTimer(sw_ctx* c, int kid) : ctx(c), id(kid), on(c && c->prof)
+LaunchTimer::LaunchTimer(sw_ctx* c, int kid) : LaunchTimer(c, kid, c ? c->stream : nullptr) {}
+
+LaunchTimer::LaunchTimer(sw_ctx* c, int kid, cudaStream_t s) : ctx(c), id(kid), on(c && c->prof), st(s)
 {
     if (!ctx) return;
     ctx->launches++;
     ctx->k_launch[id]++;
     if (on) {
         cudaEvent_t a = ctx->take_event(), b = ctx->take_event();
-        cudaEventRecord(a, ctx->stream);
+        cudaEventRecord(a, st);
         ctx->recs.push_back({id, a, b});
     }
 }
 
 LaunchTimer::~LaunchTimer()
 {
-    if (on) cudaEventRecord(ctx->recs.back().b, ctx->stream);
+    if (on) cudaEventRecord(ctx->recs.back().b, st);
 }
 
 }  // namespace sw
@@ -174,6 +176,10 @@ static void ctx_release(sw_ctx* ctx)
     ctx->solve_ws.release();
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
     ctx->pool.clear();
+    for (cudaEvent_t e : ctx->dep_events) cudaEventDestroy(e);
+    ctx->dep_events.clear();
+    if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
+    ctx->stream2 = nullptr;
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     ctx->stream = nullptr;
     cudaGetLastError();
@@ -1028,6 +1034,9 @@ extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value)
     } else if (!strcmp(key, "project_bundle")) {
         if (!(value >= 1.0 && value <= 1024.0 && value == std::floor(value))) return SW_EINVAL;
         ctx->opt.project_bundle = (int)value;
+    } else if (!strcmp(key, "chol_lookahead")) {
+        if (!(value == 0 || value == 1)) return SW_EINVAL;
+        ctx->opt.chol_lookahead = (int)value;
     } else if (!strcmp(key, "chol_tc")) {
         if (!(value == 0 || value == 1)) return SW_EINVAL;
         ctx->opt.chol_tc = (int)value;

@@ -35,6 +35,7 @@ struct Options {
     int solver = 0;              // 0 auto, 1 active set, 2 ADMM (see solve_dispatch)
     int chol_coop = 0;           // Cholesky + inverse in one cooperative launch (0: per-step launches)
     int chol_tc = 1;             // FP32 Cholesky + inverse with tcgen05 trailing updates (0: SIMT, 64-wide)
+    int chol_lookahead = 1;      // tensor-core factorisation: bulk updates on a second stream (1) or in line (0)
     int project_bundle = 1;      // orbits per column of sw_project's matrix (bundles accumulated at bin time)
     int integrator = 0;          // 0: kick-drift-kick at fixed dt; 1: adaptive Bogacki-Shampine 3(2) in the bar frame
     double bs3_rtol = 1e-4;      // relative tolerance of the adaptive integrator
@@ -110,6 +111,9 @@ struct sw_ctx {
     // lifetime: matrices keep their context alive until the last one is freed
     int64_t live_matrices = 0;
     bool destroyed = false;
+    // second stream (the factorisation's bulk updates) and dependency events between the two
+    cudaStream_t stream2 = nullptr;
+    std::vector<cudaEvent_t> dep_events;
     // profiling
     bool prof = false;
     std::vector<sw::LaunchRec> recs;

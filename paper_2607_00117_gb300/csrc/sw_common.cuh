@@ -82,8 +82,9 @@ enum KernelId {
 extern const char* kKernelNames[K_COUNT];
 
 struct LaunchTimer {
-    sw_ctx* ctx; int id; bool on;
-    LaunchTimer(sw_ctx* c, int kid);
+    sw_ctx* ctx; int id; bool on; cudaStream_t st;
+    LaunchTimer(sw_ctx* c, int kid);                    // on the context's stream
+    LaunchTimer(sw_ctx* c, int kid, cudaStream_t s);    // on another stream of the context
     ~LaunchTimer();
 };
 

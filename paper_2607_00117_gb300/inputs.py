@@ -20,13 +20,16 @@ Sec. 3.1 ~600 apertures, Sec. 3.2.4 600 density cells, N_GH = 4):
 * ``barred_100k`` -- same disc and halo + Long-Murali bar (1e10 Msun, L = 4,
   a = 1, b = 0.5 kpc) rotating at Omega_p = 40 km/s/kpc; 100 000 orbits x
   10 000 steps; incl 45 deg, bar angle 30 deg; 50 x 50 pixels x 32 velocity
-  bins; 20 x 20 x 10 cells (M = 86 500).
+  bins; 20 x 20 x 10 cells (M = 86 500); 25 000 initial conditions drawn by the
+  configurations' disc recipe (disc_ics) x 4 dithered realisations (orbit bundles).
 * ``batched_64``  -- 64 trial potentials from a 12-D box, orbit counts
   U(10k, 100k), 5 000 steps; 30 x 20 pixels of 0.5 kpc (600 apertures, the
   paper's 60" x 40" field at 0.25 kpc/") with mass + GH h1..h4 rows, and
   10 x 12 x 5 = 600 density cells (M = 3 600).
 * ``large_300k``  -- the barred potential; 300 000 orbits x 20 000 steps;
-  60 x 60 pixels with mass + GH h1..h4 rows; 20 x 20 x 10 cells (M = 22 000).
+  60 x 60 pixels with mass + GH h1..h4 rows; 20 x 20 x 10 cells (M = 22 000);
+  75 000 initial conditions from the paper's double-exponential disc with Jeans
+  velocities (paper_ics, Sec. 2.2.1) x 4 dithered realisations.
 """
 from __future__ import annotations
 
@@ -57,13 +60,13 @@ WORKLOADS = {
                       lam=1.0),
     "barred_100k": dict(potential=dict(DISC_HALO, **BAR), omega_p=40.0, n_orb=100_000, nsteps=10_000,
                         dt=DT_HALF_MYR, grid=_grid(50, 50, 32, 20, 20, 10, 45 * DEG, 30 * DEG),
-                        seeds=dict(ic=1002, w=2001, noise=2002, dither=1003), lam=1.0, bundle=4),
+                        seeds=dict(ic=1002, w=2001, noise=2002, dither=1003), lam=1.0, bundle=4, ics="disc"),
     "batched_64": dict(n_models=64, nsteps=5000, dt=DT_HALF_MYR, n_orb_range=(10_000, 100_000),
                        grid=_grid(30, 20, 40, 10, 12, 5, 0.0, gh=1), seeds=dict(box=3001, data=3100),
                        lam=1.0),
     "large_300k": dict(potential=dict(DISC_HALO, **BAR), omega_p=40.0, n_orb=300_000, nsteps=20_000,
                        dt=DT_HALF_MYR, grid=_grid(60, 60, 40, 20, 20, 10, 45 * DEG, 30 * DEG, gh=1),
-                       seeds=dict(ic=1005, w=2001, noise=2002), lam=1.0),
+                       seeds=dict(ic=1005, w=2001, noise=2002, dither=1006), lam=1.0, bundle=4, ics="paper"),
 }
 
 # 12-D trial box (disc M,a,b; bar M,L,b,c; Omega_p; halo M200,c; incl; bar angle).
@@ -145,6 +148,17 @@ def disc_ics(p: dict, n: int, seed: int, Rmax: float = 20.0, zmax: float = 3.0,
     vy = vt * np.cos(ph) + sigma_v * rng.standard_normal(n)
     vz = sigma_v * rng.standard_normal(n)
     return np.ascontiguousarray(np.stack([x, y, z, vx, vy, vz], 1))
+
+
+def workload_ics(p: dict, n: int, seed: int, kind: str = "disc") -> np.ndarray:
+    """(n, 6) initial conditions of a workload: "disc" (disc_ics: the configurations' recipe of
+    disc-density positions and scaled circular velocities) or "paper" (paper_ics: the paper's
+    double-exponential disc with Jeans velocities, Sec. 2.2.1)."""
+    if kind == "paper":
+        return paper_ics(p, n, seed)
+    if kind == "disc":
+        return disc_ics(p, n, seed)
+    raise ValueError(kind)
 
 
 def dither(ics: np.ndarray, n: int, seed: int, p: dict, dx: float = 0.1, dv_frac: float = 0.05) -> np.ndarray:
