@@ -47,16 +47,18 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
 // 1. Diagonal block: Cholesky and triangular inverse.  256 threads; thread
 // (ty, tx) = (t / 16, t % 16) owns rows i = ty + 16 r and columns l = tx + 16 c
 // (r, c < 8) of the 128 x 128 block in registers.  Cholesky in the unscaled
-// form a_il -= a_ij a_lj / a_jj (column j of the result is a_ij / sqrt(a_jj)),
-// one CTA barrier per column: the owners of column j + 1 pass it on through
-// shared memory.  The update runs unconditionally over the owned row and
-// column blocks that can still change (the values of finished rows and
-// columns enter as zeros; the upper-triangle elements it also touches are
-// never read).  The pivot's reciprocal square root is the only special
-// function per step.  The loops over the column block cb (factor) and the row
-// block rb (inverse) are unrolled so that every register index is a
-// compile-time constant (a selection by a runtime block index would put the
-// arrays in local memory).
+// form a_il -= a_ij a_lj / a_jj, two columns per CTA barrier: at a pair (j,
+// j + 1) shared memory holds column j and column j + 1 as they stand before
+// column j's update; every thread forms column j + 1's update and both pivots
+// itself (the pivots' reciprocal square roots are the only special functions)
+// and applies the rank-2 update to its elements; the owners of columns j + 2
+// and j + 3 then pass them on.  The inverse X = L^{-1} runs the same way by
+// pairs of rows.  The update runs unconditionally over the owned row and
+// column blocks that can still change (finished rows and columns enter as
+// zeros; the upper-triangle elements it also touches are never read).  The
+// loops over the column block cb (factor) and the row block rb (inverse) are
+// unrolled so that every register index is a compile-time constant (a
+// selection by a runtime block index would put the arrays in local memory).
 // ---------------------------------------------------------------------------
 constexpr int DIAG_THREADS = 256;
 __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__ G, int64_t ld, int64_t j0, int bs,
@@ -64,9 +66,9 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
 {
     extern __shared__ float sm[];
     float* Ls = sm;                 // DB x LP: the factor
-    float* col = Ls + DB * LP;      // 2 x DB: column j of the working matrix (ping-pong)
-    float* rowx = col + 2 * DB;     // 2 x DB: row k of the inverse (ping-pong)
-    float* rdiag = rowx + 2 * DB;   // DB: 1 / L_jj
+    float* c0b = Ls + DB * LP;      // 2 x DB: column j (factor) / row k (inverse), ping-pong
+    float* c1b = c0b + 2 * DB;      // 2 x DB: column j + 1 / row k + 1, before the pair's first update
+    float* rdiag = c1b + 2 * DB;    // DB: 1 / L_jj
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
     float a[8][8];
 #pragma unroll
@@ -78,70 +80,100 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
         }
     if (tx == 0) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) col[ty + 16 * r] = a[r][0];
+        for (int r = 0; r < 8; ++r) c0b[ty + 16 * r] = a[r][0];
+    }
+    if (tx == 1) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) c1b[ty + 16 * r] = a[r][0];
     }
     __syncthreads();
 #pragma unroll
     for (int cb = 0; cb < 8; ++cb) {
 #pragma unroll 1
-        for (int jj = 0; jj < 16; ++jj) {
-            const int j = 16 * cb + jj;
+        for (int jj = 0; jj < 16; jj += 2) {
+            const int j = 16 * cb + jj, j1 = j + 1;
             if (j >= bs) break;
-            const int b = j & 1;
-            float d = col[b * DB + j];
-            if (!(d > 0.f)) {
+            const bool has1 = j1 < bs;
+            const int b = (j >> 1) & 1;
+            float d0 = c0b[b * DB + j];
+            if (!(d0 > 0.f)) {
                 if (t == 0 && info) atomicCAS(info, 0, (int)(j0 + j + 1));
-                d = 1e-30f;
+                d0 = 1e-30f;
             }
-            const float rs = rsqrtf(d);       // 1 / L_jj
-            const float rd = rs * rs;         // 1 / a_jj
-            if (t == 0) rdiag[j] = rs;
-            // column j is final and sits in col[b] (rows >= j): L_ij = a_ij / sqrt(d), one row per thread
-            if (t < DB && t >= j && t < bs) Ls[t * LP + j] = col[b * DB + t] * rs;
-            // rows and columns of the blocks after cb are all beyond j: only block cb needs the test
-            float ci[8], lj[8];
+            const float rs0 = rsqrtf(d0), rd0 = rs0 * rs0;
+            const float cj = has1 ? c0b[b * DB + j1] : 0.f;   // a_(j+1, j)
+            const float f = cj * rd0;                         // column j + 1 loses f x column j
+            float d1 = has1 ? c1b[b * DB + j1] - cj * f : 1.f;
+            if (!(d1 > 0.f)) {
+                if (t == 0 && info) atomicCAS(info, 0, (int)(j0 + j1 + 1));
+                d1 = 1e-30f;
+            }
+            const float rs1 = rsqrtf(d1), rd1 = rs1 * rs1;
+            if (t == 0) {
+                rdiag[j] = rs0;
+                if (has1) rdiag[j1] = rs1;
+            }
+            // columns j and j + 1 are final: L_ij = a_ij / sqrt(d0), L_i(j+1) = (a_i(j+1) - f a_ij) / sqrt(d1)
+            if (t < DB) {
+                const float u = c0b[b * DB + t], v = c1b[b * DB + t];
+                if (t >= j && t < bs) Ls[t * LP + j] = u * rs0;
+                if (has1 && t >= j1 && t < bs) Ls[t * LP + j1] = (v - u * f) * rs1;
+            }
+            // rows and columns beyond j + 1 change; those of the blocks after cb all lie beyond it
+            float p0[8], p1[8], q0[8], q1[8];
 #pragma unroll
             for (int r = cb; r < 8; ++r) {
                 const int i = ty + 16 * r;
-                const float v = col[b * DB + i] * rd;
-                ci[r] = (r > cb || i > j) ? v : 0.f;
+                const float u = c0b[b * DB + i], v = c1b[b * DB + i];
+                const bool ok = r > cb || i > j1;
+                p0[r] = ok ? u * rd0 : 0.f;
+                p1[r] = ok ? (v - u * f) * rd1 : 0.f;
             }
 #pragma unroll
             for (int c = cb; c < 8; ++c) {
                 const int l = tx + 16 * c;
-                const float v = col[b * DB + l];
-                lj[c] = (c > cb || l > j) ? v : 0.f;
+                const float u = c0b[b * DB + l], v = c1b[b * DB + l];
+                const bool ok = c > cb || l > j1;
+                q0[c] = ok ? u : 0.f;
+                q1[c] = ok ? v - u * f : 0.f;
             }
 #pragma unroll
             for (int r = cb; r < 8; ++r)
 #pragma unroll
-                for (int c = cb; c < 8; ++c) a[r][c] -= ci[r] * lj[c];
-            // the owners of column j + 1 pass it on (block cb, or cb + 1 after its last column)
-            if (j + 1 < bs) {
-                if (jj < 15) {
-                    if (tx == jj + 1) {
+                for (int c = cb; c < 8; ++c) a[r][c] -= p0[r] * q0[c] + p1[r] * q1[c];
+            // the owners of columns j + 2 and j + 3 pass them on (block cb, or cb + 1 after its last pair)
+            if (j + 2 < bs) {
+                if (jj < 14) {
+                    if (tx == jj + 2) {
 #pragma unroll
-                        for (int r = cb; r < 8; ++r) {
-                            const int i = ty + 16 * r;
-                            if (i > j) col[(b ^ 1) * DB + i] = a[r][cb];
-                        }
+                        for (int r = cb; r < 8; ++r)
+                            if (ty + 16 * r > j1) c0b[(b ^ 1) * DB + ty + 16 * r] = a[r][cb];
+                    }
+                    if (tx == jj + 3) {
+#pragma unroll
+                        for (int r = cb; r < 8; ++r)
+                            if (ty + 16 * r > j1) c1b[(b ^ 1) * DB + ty + 16 * r] = a[r][cb];
                     }
                 } else if (cb < 7) {
                     if (tx == 0) {
 #pragma unroll
-                        for (int r = cb; r < 8; ++r) {
-                            const int i = ty + 16 * r;
-                            if (i > j) col[(b ^ 1) * DB + i] = a[r][cb < 7 ? cb + 1 : 7];
-                        }
+                        for (int r = cb; r < 8; ++r)
+                            if (ty + 16 * r > j1) c0b[(b ^ 1) * DB + ty + 16 * r] = a[r][cb < 7 ? cb + 1 : 7];
+                    }
+                    if (tx == 1) {
+#pragma unroll
+                        for (int r = cb; r < 8; ++r)
+                            if (ty + 16 * r > j1) c1b[(b ^ 1) * DB + ty + 16 * r] = a[r][cb < 7 ? cb + 1 : 7];
                     }
                 }
             }
             __syncthreads();
         }
     }
-    // ---- inverse X = L^{-1}, right-looking by rows: row k final = row k / L_kk, then
-    // rows i > k lose L_ik * row k (whose entries beyond column k are zero).  Thread
-    // ownership as above (the factor's registers are free now), x starts as I.
+    // ---- inverse X = L^{-1}, right-looking by pairs of rows: with rows k and k + 1 pending
+    // (every update from rows < k applied, unscaled), row k is final as x_k / L_kk, row k + 1 as
+    // (x_(k+1) - L_(k+1)k row k) / L_(k+1)(k+1), and rows i > k + 1 lose L_ik row k +
+    // L_i(k+1) row (k + 1).  Thread ownership as above (the factor's registers are free now).
     float (&x)[8][8] = a;
 #pragma unroll
     for (int r = 0; r < 8; ++r)
@@ -150,51 +182,69 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
             const int i = ty + 16 * r, l = tx + 16 * c;
             x[r][c] = (i == l && i < bs) ? 1.f : 0.f;
         }
-    if (ty == 0) {   // row 0 (r = 0)
+    if (ty < 2) {   // rows 0 and 1 (r = 0) are pending as they are
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            x[0][c] *= rdiag[0];
-            rowx[tx + 16 * c] = x[0][c];
-        }
+        for (int c = 0; c < 8; ++c) (ty == 0 ? c0b : c1b)[tx + 16 * c] = x[0][c];
     }
     __syncthreads();
 #pragma unroll
     for (int rb = 0; rb < 8; ++rb) {
 #pragma unroll 1
-        for (int kk = 0; kk < 16; ++kk) {
-            const int k = 16 * rb + kk;
-            if (k + 1 >= bs) break;
-            const int b = k & 1;
-            // row k of X is zero beyond column k < 16 rb + 16: column blocks c <= rb only
-            float xk[8], lik[8];
+        for (int kk = 0; kk < 16; kk += 2) {
+            const int k = 16 * rb + kk, k1 = k + 1;
+            if (k >= bs) break;
+            const bool has1 = k1 < bs;
+            const int b = (k >> 1) & 1;
+            const float s0 = rdiag[k], s1 = has1 ? rdiag[k1] : 0.f;
+            const float lkk = has1 ? Ls[k1 * LP + k] : 0.f;
+            // the final rows k and k + 1 at this thread's columns (nonzero only in blocks c <= rb)
+            float xk[8], xk1[8];
 #pragma unroll
-            for (int c = 0; c <= rb; ++c) xk[c] = rowx[b * DB + tx + 16 * c];
+            for (int c = 0; c <= rb; ++c) {
+                const int l = tx + 16 * c;
+                xk[c] = c0b[b * DB + l] * s0;
+                xk1[c] = (c1b[b * DB + l] - lkk * xk[c]) * s1;
+            }
+            if (ty == kk) {
+#pragma unroll
+                for (int c = 0; c <= rb; ++c) x[rb][c] = xk[c];
+            }
+            if (ty == kk + 1 && has1) {
+#pragma unroll
+                for (int c = 0; c <= rb; ++c) x[rb][c] = xk1[c];
+            }
+            float l0[8], l1[8];
 #pragma unroll
             for (int r = rb; r < 8; ++r) {
                 const int i = ty + 16 * r;
-                const float v = Ls[i * LP + k];
-                lik[r] = ((r > rb || i > k) && i < bs) ? v : 0.f;
+                const float u = Ls[i * LP + k], v = Ls[i * LP + k1];
+                const bool ok = (r > rb || i > k1) && i < bs;
+                l0[r] = ok ? u : 0.f;
+                l1[r] = ok && has1 ? v : 0.f;
             }
 #pragma unroll
             for (int r = rb; r < 8; ++r)
 #pragma unroll
-                for (int c = 0; c <= rb; ++c) x[r][c] -= lik[r] * xk[c];
-            // row k + 1 is now final up to its scaling: block rb, or rb + 1 after its last row
-            const float s = rdiag[k + 1];
-            if (kk < 15) {
-                if (ty == kk + 1) {
+                for (int c = 0; c <= rb; ++c) x[r][c] -= l0[r] * xk[c] + l1[r] * xk1[c];
+            // the owners of rows k + 2 and k + 3 pass them on, pending (block rb, or rb + 1)
+            if (k + 2 < bs) {
+                if (kk < 14) {
+                    if (ty == kk + 2) {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        x[rb][c] *= s;
-                        rowx[(b ^ 1) * DB + tx + 16 * c] = x[rb][c];
+                        for (int c = 0; c < 8; ++c) c0b[(b ^ 1) * DB + tx + 16 * c] = x[rb][c];
                     }
-                }
-            } else if (rb < 7) {
-                if (ty == 0) {
+                    if (ty == kk + 3) {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        x[rb < 7 ? rb + 1 : 7][c] *= s;
-                        rowx[(b ^ 1) * DB + tx + 16 * c] = x[rb < 7 ? rb + 1 : 7][c];
+                        for (int c = 0; c < 8; ++c) c1b[(b ^ 1) * DB + tx + 16 * c] = x[rb][c];
+                    }
+                } else if (rb < 7) {
+                    if (ty == 0) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) c0b[(b ^ 1) * DB + tx + 16 * c] = x[rb < 7 ? rb + 1 : 7][c];
+                    }
+                    if (ty == 1) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) c1b[(b ^ 1) * DB + tx + 16 * c] = x[rb < 7 ? rb + 1 : 7][c];
                     }
                 }
             }

@@ -572,26 +572,8 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         if (!F.empty()) {
             bool ok = true, conv = false;
             if (!factored_covers(F)) {
-                // a warm-started solve grows the kept set to P0 U F while the orbits it masks stay a
-                // minority, so that later solves of the same matrix keep reusing one factor
-                std::vector<int64_t> S;
-                if (warm && warm->start && warm->have_factor) {
-                    S = P0;
-                    for (int64_t i : F)
-                        if (pos[i] < 0) S.push_back(i);
-                    std::sort(S.begin(), S.end());
-                }
-                const bool grow = !S.empty() && (int64_t)S.size() <= cap &&
-                                  (double)S.size() <= 1.3 * (double)F.size() + 256.0;
-                if (grow) {
-                    AS_TRY(factor(S, ok));
-                    warm->P0 = P0;
-                    warm->ld = ldG;
-                    warm->have_factor = ok;
-                } else {
-                    AS_TRY(factor(F, ok));
-                    if (warm) warm->have_factor = false;   // P0 is now this passive set
-                }
+                AS_TRY(factor(F, ok));
+                if (warm) warm->have_factor = false;   // P0 is now this passive set
             }
             if (!ok) { failed = true; break; }
             AS_TRY(solve_on(F, conv));
