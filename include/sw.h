@@ -188,6 +188,19 @@ sw_status sw_solve_bootstrap(sw_ctx* ctx, const sw_matrix* U, const double* data
                              int64_t n_boot, const double* xi, double* weights_out, double* chi2_b_out,
                              double* chi2_model_out);
 
+/* The preconditioner of the active-set solve's reduced systems (Sec. 2.3 solves them by
+ * conjugate gradients here): the Cholesky factor L of a symmetric positive definite K x K matrix
+ * and the explicit inverse X = L^{-1}, exactly as the solve forms them, exposed so that they can be
+ * checked on their own.  gram: host, K x K row-major FP32, only the lower triangle read; L_out,
+ * X_out: host K x K row-major (L in the lower triangle, the upper triangle as given; X lower
+ * triangular).  mode 0: 128-wide blocked steps with tensor-core trailing and inverse updates
+ * (BF16 hi + lo operands, ~1e-4 relative); mode 1: 64-wide blocked FP32 SIMT.  *info_out: 0, or
+ * j + 1 if the j-th pivot was not positive (the factorisation then continues with a tiny pivot).
+ * Allocates and frees its own device buffers.  Errors: SW_EINVAL (NULL, K outside 1 .. 65 536,
+ * mode), SW_ECUDA (no tensor-map encoder for mode 0), SW_ETIMEOUT (a bounded device wait ran out). */
+sw_status sw_factor_preconditioner(sw_ctx* ctx, const float* gram, int64_t K, int mode, float* L_out, float* X_out,
+                                   int* info_out);
+
 /* Solver diagnostics of the last solve: out[0] ADMM iterations, out[1] refinement rounds,
  * out[2] final KKT projected-gradient infinity norm (scaled by max |U~^T y~|), out[3] 1 if the
  * orbits outnumbered the constraints (working-set or constraint-space form), out[4] number of

@@ -2,11 +2,10 @@
 // inverse X = L^{-1}: the preconditioner of the weight solve's reduced systems
 // (Sec. 2.3).  Blocked right-looking in 128-wide steps; at step k
 //
-//   1. k_diag128 (one CTA): L_kk = chol(A_kk) and D_k = L_kk^{-1}.  A chain of
-//      128 column steps for the factor and 128 row steps for the inverse, each
-//      thread holding a fixed 4 x 8 set of the block's elements in registers
-//      and one CTA barrier per step (column j, or row k of the inverse, is
-//      passed through shared memory by the threads that own it);
+//   1. k_diag128 (one CTA): L_kk = chol(A_kk) and D_k = L_kk^{-1}, blocked by
+//      32 in shared memory: one warp factors and inverts each 32 x 32 diagonal
+//      sub-block in registers while the other warps assemble the inverse's
+//      earlier block rows; panels and trailing updates use all threads;
 //   2. k_panel128: the panel below, L_ik = A_ik D_k^T (FP32, in place), also
 //      written as BF16 hi + lo halves (the split operand of step 3);
 //   3. k_tc_sub<lower>: the trailing update A_ij -= L_ik L_jk^T on the 5th-
@@ -44,244 +43,361 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
 }
 
 // ---------------------------------------------------------------------------
-// 1. Diagonal block: Cholesky and triangular inverse.  256 threads; thread
-// (ty, tx) = (t / 16, t % 16) owns rows i = ty + 16 r and columns l = tx + 16 c
-// (r, c < 8) of the 128 x 128 block in registers.  Cholesky in the unscaled
-// form a_il -= a_ij a_lj / a_jj, two columns per CTA barrier: at a pair (j,
-// j + 1) shared memory holds column j and column j + 1 as they stand before
-// column j's update; every thread forms column j + 1's update and both pivots
-// itself (the pivots' reciprocal square roots are the only special functions)
-// and applies the rank-2 update to its elements; the owners of columns j + 2
-// and j + 3 then pass them on.  The inverse X = L^{-1} runs the same way by
-// pairs of rows.  The update runs unconditionally over the owned row and
-// column blocks that can still change (finished rows and columns enter as
-// zeros; the upper-triangle elements it also touches are never read).  The
-// loops over the column block cb (factor) and the row block rb (inverse) are
-// unrolled so that every register index is a compile-time constant (a
-// selection by a runtime block index would put the arrays in local memory).
+// 1. Diagonal block: Cholesky and triangular inverse, blocked by 32 inside the
+// CTA (256 threads).  The block sits in shared memory (A, row pitch AP; rows
+// and columns beyond bs are an identity, so a short last block needs no
+// special case).  For each 32-wide sub-block s, with the rows below it R_s:
+//   A. warp 0 factors the diagonal sub-block L_ss, one row per lane in
+//      registers: the pivot of column j + 1 is formed by its own lane and
+//      broadcast by one shuffle, the next two columns are updated through
+//      shuffles and the rest through the transposed column buffer CT.
+//      Meanwhile warps 1-7 apply the part of the previous step's trailing
+//      update that the next steps need last (columns beyond sub-block s + 1)
+//      and advance the inverse (below);
+//   B. one thread per row of R_s solves L_is L_ss^T = A_is by forward
+//      substitution (warps 1-3), while warp 0 inverts L_ss (one column of
+//      X_ss per lane);
+//   C. all threads update column block s + 1 by the new panel.
+// The inverse X = L^{-1} below the diagonal, by block rows r: T_j = sum_{k=j}
+// ^{r-1} L_rk X_kj (formed while sub-block r is factored) and X_rj = -X_rr T_j
+// (formed while sub-block r + 1 is factored; the last block row at the end).
+// Every register index is static (the 32-step loops are unrolled).
 // ---------------------------------------------------------------------------
 constexpr int DIAG_THREADS = 256;
-__global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__ G, int64_t ld, int64_t j0, int bs,
-                                                             float* __restrict__ D, int* info)
+constexpr int AP = DB + 4;    // row pitch: 16-byte rows, consecutive rows in distinct bank groups
+constexpr int SB = 32;        // sub-block width
+constexpr int CTP = SB + 4;   // pitch of the 32-wide buffers
+constexpr int TBUF = 3 * SB * CTP;
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float dot4(float4 a, float4 b, float acc)
 {
-    extern __shared__ float sm[];
-    float* Ls = sm;                 // DB x LP: the factor
-    float* c0b = Ls + DB * LP;      // 2 x DB: column j (factor) / row k (inverse), ping-pong
-    float* c1b = c0b + 2 * DB;      // 2 x DB: column j + 1 / row k + 1, before the pair's first update
-    float* rdiag = c1b + 2 * DB;    // DB: 1 / L_jj
-    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
-    float a[8][8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int i = ty + 16 * r, l = tx + 16 * c;
-            a[r][c] = (i < bs && l <= i) ? G[(size_t)(j0 + i) * ld + j0 + l] : 0.f;
-        }
-    if (tx == 0) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) c0b[ty + 16 * r] = a[r][0];
-    }
-    if (tx == 1) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) c1b[ty + 16 * r] = a[r][0];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int cb = 0; cb < 8; ++cb) {
-#pragma unroll 1
-        for (int jj = 0; jj < 16; jj += 2) {
-            const int j = 16 * cb + jj, j1 = j + 1;
-            if (j >= bs) break;
-            const bool has1 = j1 < bs;
-            const int b = (j >> 1) & 1;
-            float d0 = c0b[b * DB + j];
-            if (!(d0 > 0.f)) {
-                if (t == 0 && info) atomicCAS(info, 0, (int)(j0 + j + 1));
-                d0 = 1e-30f;
-            }
-            const float rs0 = rsqrtf(d0), rd0 = rs0 * rs0;
-            const float cj = has1 ? c0b[b * DB + j1] : 0.f;   // a_(j+1, j)
-            const float f = cj * rd0;                         // column j + 1 loses f x column j
-            float d1 = has1 ? c1b[b * DB + j1] - cj * f : 1.f;
-            if (!(d1 > 0.f)) {
-                if (t == 0 && info) atomicCAS(info, 0, (int)(j0 + j1 + 1));
-                d1 = 1e-30f;
-            }
-            const float rs1 = rsqrtf(d1), rd1 = rs1 * rs1;
-            if (t == 0) {
-                rdiag[j] = rs0;
-                if (has1) rdiag[j1] = rs1;
-            }
-            // columns j and j + 1 are final: L_ij = a_ij / sqrt(d0), L_i(j+1) = (a_i(j+1) - f a_ij) / sqrt(d1)
-            if (t < DB) {
-                const float u = c0b[b * DB + t], v = c1b[b * DB + t];
-                if (t >= j && t < bs) Ls[t * LP + j] = u * rs0;
-                if (has1 && t >= j1 && t < bs) Ls[t * LP + j1] = (v - u * f) * rs1;
-            }
-            // rows and columns beyond j + 1 change; those of the blocks after cb all lie beyond it
-            float p0[8], p1[8], q0[8], q1[8];
-#pragma unroll
-            for (int r = cb; r < 8; ++r) {
-                const int i = ty + 16 * r;
-                const float u = c0b[b * DB + i], v = c1b[b * DB + i];
-                const bool ok = r > cb || i > j1;
-                p0[r] = ok ? u * rd0 : 0.f;
-                p1[r] = ok ? (v - u * f) * rd1 : 0.f;
-            }
-#pragma unroll
-            for (int c = cb; c < 8; ++c) {
-                const int l = tx + 16 * c;
-                const float u = c0b[b * DB + l], v = c1b[b * DB + l];
-                const bool ok = c > cb || l > j1;
-                q0[c] = ok ? u : 0.f;
-                q1[c] = ok ? v - u * f : 0.f;
-            }
-#pragma unroll
-            for (int r = cb; r < 8; ++r)
-#pragma unroll
-                for (int c = cb; c < 8; ++c) a[r][c] -= p0[r] * q0[c] + p1[r] * q1[c];
-            // the owners of columns j + 2 and j + 3 pass them on (block cb, or cb + 1 after its last pair)
-            if (j + 2 < bs) {
-                if (jj < 14) {
-                    if (tx == jj + 2) {
-#pragma unroll
-                        for (int r = cb; r < 8; ++r)
-                            if (ty + 16 * r > j1) c0b[(b ^ 1) * DB + ty + 16 * r] = a[r][cb];
-                    }
-                    if (tx == jj + 3) {
-#pragma unroll
-                        for (int r = cb; r < 8; ++r)
-                            if (ty + 16 * r > j1) c1b[(b ^ 1) * DB + ty + 16 * r] = a[r][cb];
-                    }
-                } else if (cb < 7) {
-                    if (tx == 0) {
-#pragma unroll
-                        for (int r = cb; r < 8; ++r)
-                            if (ty + 16 * r > j1) c0b[(b ^ 1) * DB + ty + 16 * r] = a[r][cb < 7 ? cb + 1 : 7];
-                    }
-                    if (tx == 1) {
-#pragma unroll
-                        for (int r = cb; r < 8; ++r)
-                            if (ty + 16 * r > j1) c1b[(b ^ 1) * DB + ty + 16 * r] = a[r][cb < 7 ? cb + 1 : 7];
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    // ---- inverse X = L^{-1}, right-looking by pairs of rows: with rows k and k + 1 pending
-    // (every update from rows < k applied, unscaled), row k is final as x_k / L_kk, row k + 1 as
-    // (x_(k+1) - L_(k+1)k row k) / L_(k+1)(k+1), and rows i > k + 1 lose L_ik row k +
-    // L_i(k+1) row (k + 1).  Thread ownership as above (the factor's registers are free now).
-    float (&x)[8][8] = a;
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int i = ty + 16 * r, l = tx + 16 * c;
-            x[r][c] = (i == l && i < bs) ? 1.f : 0.f;
-        }
-    if (ty < 2) {   // rows 0 and 1 (r = 0) are pending as they are
-#pragma unroll
-        for (int c = 0; c < 8; ++c) (ty == 0 ? c0b : c1b)[tx + 16 * c] = x[0][c];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int rb = 0; rb < 8; ++rb) {
-#pragma unroll 1
-        for (int kk = 0; kk < 16; kk += 2) {
-            const int k = 16 * rb + kk, k1 = k + 1;
-            if (k >= bs) break;
-            const bool has1 = k1 < bs;
-            const int b = (k >> 1) & 1;
-            const float s0 = rdiag[k], s1 = has1 ? rdiag[k1] : 0.f;
-            const float lkk = has1 ? Ls[k1 * LP + k] : 0.f;
-            // the final rows k and k + 1 at this thread's columns (nonzero only in blocks c <= rb)
-            float xk[8], xk1[8];
-#pragma unroll
-            for (int c = 0; c <= rb; ++c) {
-                const int l = tx + 16 * c;
-                xk[c] = c0b[b * DB + l] * s0;
-                xk1[c] = (c1b[b * DB + l] - lkk * xk[c]) * s1;
-            }
-            if (ty == kk) {
-#pragma unroll
-                for (int c = 0; c <= rb; ++c) x[rb][c] = xk[c];
-            }
-            if (ty == kk + 1 && has1) {
-#pragma unroll
-                for (int c = 0; c <= rb; ++c) x[rb][c] = xk1[c];
-            }
-            float l0[8], l1[8];
-#pragma unroll
-            for (int r = rb; r < 8; ++r) {
-                const int i = ty + 16 * r;
-                const float u = Ls[i * LP + k], v = Ls[i * LP + k1];
-                const bool ok = (r > rb || i > k1) && i < bs;
-                l0[r] = ok ? u : 0.f;
-                l1[r] = ok && has1 ? v : 0.f;
-            }
-#pragma unroll
-            for (int r = rb; r < 8; ++r)
-#pragma unroll
-                for (int c = 0; c <= rb; ++c) x[r][c] -= l0[r] * xk[c] + l1[r] * xk1[c];
-            // the owners of rows k + 2 and k + 3 pass them on, pending (block rb, or rb + 1)
-            if (k + 2 < bs) {
-                if (kk < 14) {
-                    if (ty == kk + 2) {
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) c0b[(b ^ 1) * DB + tx + 16 * c] = x[rb][c];
-                    }
-                    if (ty == kk + 3) {
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) c1b[(b ^ 1) * DB + tx + 16 * c] = x[rb][c];
-                    }
-                } else if (rb < 7) {
-                    if (ty == 0) {
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) c0b[(b ^ 1) * DB + tx + 16 * c] = x[rb < 7 ? rb + 1 : 7][c];
-                    }
-                    if (ty == 1) {
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) c1b[(b ^ 1) * DB + tx + 16 * c] = x[rb < 7 ? rb + 1 : 7][c];
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int i = ty + 16 * r, l = tx + 16 * c;
-            D[i * DB + l] = (i < bs && l <= i) ? x[r][c] : 0.f;
-            if (i < bs && l <= i) G[(size_t)(j0 + i) * ld + j0 + l] = Ls[i * LP + l];
-        }
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, acc))));
 }
 
-constexpr size_t DIAG_SMEM = sizeof(float) * (DB * LP + 5 * DB);
+// T_j = sum_{k=j}^{r-1} L_rk X_kj for j < r into Tb (quad q: row a, columns 4 (q & 7) .. + 3 of T_j, j = q >> 8)
+__device__ __forceinline__ void inverse_t_part(const float* __restrict__ A, const float* __restrict__ X,
+                                               float* __restrict__ Tb, int r, int tid, int NT)
+{
+    for (int q = tid; q < 256 * r; q += NT) {
+        const int j = q >> 8, a = (q & 255) >> 3, b4 = (q & 7) * 4;
+        const float* pr = A + (SB * r + a) * AP;
+        const float* xc = X + SB * j + b4;
+        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+#pragma unroll 2
+        for (int c = SB * j; c < SB * r; c += 8) {
+            const float4 p0 = ld4(pr + c), p1 = ld4(pr + c + 4);
+            const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float4 x = ld4(xc + (c + u) * AP);
+                float4& acc = (u & 1) ? acc1 : acc0;
+                acc.x = fmaf(pv[u], x.x, acc.x);
+                acc.y = fmaf(pv[u], x.y, acc.y);
+                acc.z = fmaf(pv[u], x.z, acc.z);
+                acc.w = fmaf(pv[u], x.w, acc.w);
+            }
+        }
+        *reinterpret_cast<float4*>(Tb + (j * SB + a) * CTP + b4) =
+            make_float4(acc0.x + acc1.x, acc0.y + acc1.y, acc0.z + acc1.z, acc0.w + acc1.w);
+    }
+}
+
+// X_rj = -X_rr T_j for j < r (X_rr lower triangular: columns c <= a)
+__device__ __forceinline__ void inverse_x_part(float* __restrict__ X, const float* __restrict__ Tb, int r, int tid,
+                                               int NT)
+{
+    for (int q = tid; q < 256 * r; q += NT) {
+        const int j = q >> 8, a = (q & 255) >> 3, b4 = (q & 7) * 4;
+        const float* xr = X + (SB * r + a) * AP + SB * r;
+        const float* tj = Tb + j * SB * CTP + b4;
+        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+        const int cmax = (a | 3) + 1;
+        for (int c = 0; c < cmax; c += 4) {
+            const float4 p = ld4(xr + c);
+            const float pv[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 t4 = ld4(tj + (c + u) * CTP);
+                float4& acc = (u & 1) ? acc1 : acc0;
+                acc.x = fmaf(pv[u], t4.x, acc.x);
+                acc.y = fmaf(pv[u], t4.y, acc.y);
+                acc.z = fmaf(pv[u], t4.z, acc.z);
+                acc.w = fmaf(pv[u], t4.w, acc.w);
+            }
+        }
+        *reinterpret_cast<float4*>(X + (SB * r + a) * AP + SB * j + b4) =
+            make_float4(-(acc0.x + acc1.x), -(acc0.y + acc1.y), -(acc0.z + acc1.z), -(acc0.w + acc1.w));
+    }
+}
+
+// A[i][j] -= sum_k A[i][p0 + k] A[j][p0 + k] over the lower 4 x 4 tiles of rows and columns r0 .. 127
+__device__ __forceinline__ void trailing_rest(float* __restrict__ A, int p0, int r0, int tid, int NT)
+{
+    const int nt = (DB - r0) >> 2;
+    for (int q = tid; q < nt * nt; q += NT) {
+        const int ti = q / nt, tj = q - ti * nt;
+        if (tj > ti) continue;
+        const float* ra = A + (r0 + 4 * ti) * AP + p0;
+        const float* rb = A + (r0 + 4 * tj) * AP + p0;
+        float acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+#pragma unroll 2
+        for (int k = 0; k < SB; k += 4) {
+            float4 u[4], v[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) u[r] = ld4(ra + r * AP + k);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] = ld4(rb + c * AP + k);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = dot4(u[r], v[c], acc[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            float4* o = reinterpret_cast<float4*>(A + (r0 + 4 * ti + r) * AP + r0 + 4 * tj);
+            float4 v = *o;
+            v.x -= acc[r][0]; v.y -= acc[r][1]; v.z -= acc[r][2]; v.w -= acc[r][3];
+            *o = v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__ G, int64_t ld, int64_t j0, int bs,
+                                                             float* __restrict__ D /* D_k^T */, int* info)
+{
+    extern __shared__ __align__(16) float sm[];
+    float* A = sm;                  // DB x AP: the block, then L
+    float* X = A + DB * AP;         // DB x AP: L^{-1}
+    float* CT = X + DB * AP;        // SB x CTP: CT[j][i] = L(c0 + i, c0 + j) of the current sub-block
+    float* Tb = CT + SB * CTP;      // 2 x TBUF: the sums T_j of an inverse block row, by parity of r
+    float* RR = Tb + 2 * TBUF;      // SB: 1 / L_jj of the current sub-block
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    // ---- load: 16 rows x 16-byte chunks per thread, all in flight; identity beyond bs; X = 0
+    {
+        float4 v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = t + DIAG_THREADS * u, i = e >> 5, l4 = (e & 31) * 4;
+            const float* g = G + (size_t)(j0 + i) * ld + j0 + l4;
+            if (i < bs && l4 + 3 < bs) {
+                v[u] = ld4(g);
+            } else {
+                float w[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) w[c] = (i < bs && l4 + c < bs) ? g[c] : (i == l4 + c ? 1.f : 0.f);
+                v[u] = make_float4(w[0], w[1], w[2], w[3]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = t + DIAG_THREADS * u, i = e >> 5, l4 = (e & 31) * 4;
+            *reinterpret_cast<float4*>(A + i * AP + l4) = v[u];
+            *reinterpret_cast<float4*>(X + i * AP + l4) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int s = 0; s < DB / SB; ++s) {
+        const int c0 = SB * s;
+        // ======== A
+        if (warp == 0) {
+            float a[SB];
+#pragma unroll
+            for (int k = 0; k < SB; k += 4) {
+                const float4 v = ld4(A + (c0 + lane) * AP + c0 + k);
+                a[k] = v.x; a[k + 1] = v.y; a[k + 2] = v.z; a[k + 3] = v.w;
+            }
+            float d = __shfl_sync(0xffffffffu, a[0], 0);
+#pragma unroll
+            for (int j = 0; j < SB; ++j) {
+                if (!(d > 0.f)) {
+                    if (lane == 0 && info && c0 + j < bs) atomicCAS(info, 0, (int)(j0 + c0 + j + 1));
+                    d = 1e-30f;
+                }
+                const float r = rsqrtf(d);
+                if (lane == 0) RR[j] = r;
+                const float lij = lane >= j ? a[j] * r : 0.f;
+                a[j] = lij;
+                CT[j * CTP + lane] = lij;
+                if (j + 1 < SB) {
+                    // the next pivot: lane j + 1 subtracts its own l_(j+1) j^2, one shuffle broadcasts it
+                    const float dn = a[j + 1] - lij * lij;
+                    d = __shfl_sync(0xffffffffu, dn, j + 1);
+                    const float l1 = __shfl_sync(0xffffffffu, lij, j + 1);
+                    a[j + 1] -= lij * l1;
+                    if (j + 2 < SB) {
+                        const float l2 = __shfl_sync(0xffffffffu, lij, j + 2 < SB ? j + 2 : 0);
+                        a[j + 2] -= lij * l2;
+                    }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int k4 = ((j + 3) & ~3); k4 < SB; k4 += 4) {
+                    const float4 c = ld4(CT + j * CTP + k4);
+                    if (k4 + 0 >= j + 3) a[k4 + 0] -= lij * c.x;
+                    if (k4 + 1 >= j + 3) a[k4 + 1] -= lij * c.y;
+                    if (k4 + 2 >= j + 3) a[k4 + 2] -= lij * c.z;
+                    if (k4 + 3 >= j + 3) a[k4 + 3] -= lij * c.w;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < SB; k += 4)
+                *reinterpret_cast<float4*>(A + (c0 + lane) * AP + c0 + k) =
+                    make_float4(k <= lane ? a[k] : 0.f, k + 1 <= lane ? a[k + 1] : 0.f,
+                                k + 2 <= lane ? a[k + 2] : 0.f, k + 3 <= lane ? a[k + 3] : 0.f);
+        } else {
+            const int tid = t - 32, NT = DIAG_THREADS - 32;
+            auto bar = [] { asm volatile("bar.sync 1, %0;" ::"n"(DIAG_THREADS - 32) : "memory"); };
+            // the previous panel's update of columns beyond sub-block s + 1 (columns of s + 1 were done in C)
+            if (s >= 1 && s <= 2) trailing_rest(A, c0 - SB, c0 + SB, tid, NT);
+            // X_(s-1) j = -X_(s-1)(s-1) T_j, then T_j of block row s (it needs block row s - 1)
+            if (s >= 2) {
+                inverse_x_part(X, Tb + ((s - 1) & 1) * TBUF, s - 1, tid, NT);
+                bar();
+            }
+            if (s >= 1) inverse_t_part(A, X, Tb + (s & 1) * TBUF, s, tid, NT);
+        }
+        __syncthreads();
+        // ======== B
+        if (warp == 0) {
+            // X_ss = L_ss^{-1}, lane l holds column l
+            float x[SB];
+#pragma unroll
+            for (int i = 0; i < SB; ++i) x[i] = i == lane ? 1.f : 0.f;
+#pragma unroll
+            for (int k = 0; k < SB; ++k) {
+                x[k] *= RR[k];
+#pragma unroll
+                for (int i4 = ((k + 1) & ~3); i4 < SB; i4 += 4) {
+                    const float4 c = ld4(CT + k * CTP + i4);
+                    if (i4 + 0 > k) x[i4 + 0] -= c.x * x[k];
+                    if (i4 + 1 > k) x[i4 + 1] -= c.y * x[k];
+                    if (i4 + 2 > k) x[i4 + 2] -= c.z * x[k];
+                    if (i4 + 3 > k) x[i4 + 3] -= c.w * x[k];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < SB; ++i) X[(c0 + i) * AP + c0 + lane] = x[i];
+        } else if (t - 32 < DB - c0 - SB) {
+            // row i of the panel: y L_ss^T = a_i by forward substitution
+            const int i = c0 + SB + (t - 32);
+            float y[SB];
+#pragma unroll
+            for (int k = 0; k < SB; k += 4) {
+                const float4 v = ld4(A + i * AP + c0 + k);
+                y[k] = v.x; y[k + 1] = v.y; y[k + 2] = v.z; y[k + 3] = v.w;
+            }
+#pragma unroll
+            for (int k = 0; k < SB; ++k) {
+                y[k] *= RR[k];
+#pragma unroll
+                for (int j4 = ((k + 1) & ~3); j4 < SB; j4 += 4) {
+                    const float4 c = ld4(CT + k * CTP + j4);
+                    if (j4 + 0 > k) y[j4 + 0] -= c.x * y[k];
+                    if (j4 + 1 > k) y[j4 + 1] -= c.y * y[k];
+                    if (j4 + 2 > k) y[j4 + 2] -= c.z * y[k];
+                    if (j4 + 3 > k) y[j4 + 3] -= c.w * y[k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < SB; k += 4)
+                *reinterpret_cast<float4*>(A + i * AP + c0 + k) = make_float4(y[k], y[k + 1], y[k + 2], y[k + 3]);
+        }
+        __syncthreads();
+        if (s == DB / SB - 1) break;
+        // ======== C: column block s + 1 -= panel (rows c0 + 32 .. 127); thread (cg, rs) = (t % 8, t / 8)
+        // forms columns c0 + 32 + cg + 8 jj of rows c0 + 32 + rs + 32 rr
+        {
+            const int cg = t & 7, rs = t >> 3, nrb = 3 - s, c1 = c0 + SB;
+            float acc[3][4];
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[rr][jj] = 0.f;
+#pragma unroll 2
+            for (int k = 0; k < SB; k += 4) {
+                float4 xv[4];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) xv[jj] = ld4(A + (c1 + cg + 8 * jj) * AP + c0 + k);
+#pragma unroll
+                for (int rr = 0; rr < 3; ++rr) {
+                    if (rr < nrb) {
+                        const float4 av = ld4(A + (c1 + rs + SB * rr) * AP + c0 + k);
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) acc[rr][jj] = dot4(av, xv[jj], acc[rr][jj]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr)
+                if (rr < nrb) {
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) A[(c1 + rs + SB * rr) * AP + c1 + cg + 8 * jj] -= acc[rr][jj];
+                }
+        }
+        __syncthreads();
+    }
+    // ---- the last block row of the inverse (its sums were formed while sub-block 3 was factored)
+    inverse_x_part(X, Tb + ((DB / SB - 1) & 1) * TBUF, DB / SB - 1, t, DIAG_THREADS);
+    __syncthreads();
+    // ---- L back into G (lower triangle of the block, 16-byte stores where the chunk lies in it)
+#pragma unroll 4
+    for (int u = 0; u < 16; ++u) {
+        const int e = t + DIAG_THREADS * u, i = e >> 5, l4 = (e & 31) * 4;
+        if (i >= bs || l4 > i) continue;
+        float* g = G + (size_t)(j0 + i) * ld + j0 + l4;
+        const float4 v = ld4(A + i * AP + l4);
+        if (l4 + 3 <= i && l4 + 3 < bs) {
+            *reinterpret_cast<float4*>(g) = v;
+        } else {
+            const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (l4 + c <= i && l4 + c < bs) g[c] = w[c];
+        }
+    }
+    // D transposed, Dt[l][c] = D[c][l] (zero outside c < bs, l <= c): thread (c, half) reads rows of X as
+    // 16-byte vectors and writes four rows of Dt, each write coalesced over c
+    {
+        const int c = t & (DB - 1), h = t >> 7;
+        const bool cin = c < bs;
+#pragma unroll 4
+        for (int l4 = 4 * h; l4 < DB; l4 += 8) {
+            const float4 v = ld4(X + c * AP + l4);
+            D[(l4 + 0) * DB + c] = cin && l4 + 0 <= c ? v.x : 0.f;
+            D[(l4 + 1) * DB + c] = cin && l4 + 1 <= c ? v.y : 0.f;
+            D[(l4 + 2) * DB + c] = cin && l4 + 2 <= c ? v.z : 0.f;
+            D[(l4 + 3) * DB + c] = cin && l4 + 3 <= c ? v.w : 0.f;
+        }
+    }
+}
+
+constexpr size_t DIAG_SMEM = sizeof(float) * (2 * DB * AP + SB * CTP + 2 * TBUF + SB);
 
 // ---------------------------------------------------------------------------
 // 2. Panel: P = A D^T for m rows below the diagonal block (A = G[r0 + i][j0 ..
 // j0 + 127]), in place in G, and its BF16 hi + lo halves (m x 128 row-major).
-// 64 rows per CTA of 256 threads; thread (tr, tc) = (t / 16, t % 16) computes
-// rows 4 tr .. 4 tr + 3 and columns 8 tc .. 8 tc + 7, reading D transposed
-// (DT[l][c] = D[c][l]) so that its eight columns are two 16-byte loads.
+// 32 rows per CTA of 256 threads; thread (tr, tc) = (t / 16, t % 16) computes
+// rows 2 tr, 2 tr + 1 and columns 4 tc .. 4 tc + 3 and 64 + 4 tc .. 64 + 4 tc +
+// 3 (two 16-byte loads of a row of D^T in distinct bank groups).  D arrives
+// transposed (Dt[l][c] = D[c][l]) and is staged by 16-byte copies.
 // ---------------------------------------------------------------------------
-constexpr int PR = 64;
+constexpr int PR = 32;
 constexpr int DTP = DB + 4;   // padded row of DT (16-byte aligned, conflict-free float4 rows)
 __global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t ld, int64_t j0, int64_t r0,
-                                                  int64_t m, const float* __restrict__ D,
+                                                  int64_t m, const float* __restrict__ Dt,
                                                   __nv_bfloat16* __restrict__ Ph, __nv_bfloat16* __restrict__ Pl)
 {
     extern __shared__ __align__(16) float sm[];
-    float* As = sm;              // PR x LP
-    float* DT = As + PR * LP;    // DB x DTP (16-byte aligned: PR * LP * 4 = 33 024 bytes)
+    float* DT = sm;              // DB x DTP
+    float* As = DT + DB * DTP;   // PR x LP
     const int t = threadIdx.x;
     const int64_t row0 = (int64_t)blockIdx.x * PR;
-    // many loads in flight per thread: the staging is latency-bound otherwise
 #pragma unroll 8
     for (int e = t; e < PR * DB; e += 256) {
         const int i = e >> 7, l = e & (DB - 1);
@@ -290,48 +406,48 @@ __global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t
     }
 #pragma unroll 4
     for (int e4 = t; e4 < DB * DB / 4; e4 += 256) {
-        const float4 d4 = reinterpret_cast<const float4*>(D)[e4];
-        const int c = (4 * e4) >> 7, l = (4 * e4) & (DB - 1);
-        DT[l * DTP + c] = d4.x; DT[(l + 1) * DTP + c] = d4.y; DT[(l + 2) * DTP + c] = d4.z;
-        DT[(l + 3) * DTP + c] = d4.w;
+        const int l = (4 * e4) >> 7, c = (4 * e4) & (DB - 1);
+        *reinterpret_cast<float4*>(DT + l * DTP + c) = reinterpret_cast<const float4*>(Dt)[e4];
     }
     __syncthreads();
     const int tr = t >> 4, tc = t & 15;
-    float acc[4][8];
+    float acc[2][8];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
-#pragma unroll 4
+#pragma unroll 8
     for (int l = 0; l < DB; ++l) {
-        float av[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) av[r] = As[(4 * tr + r) * LP + l];
-        const float4 d0 = *reinterpret_cast<const float4*>(&DT[l * DTP + 8 * tc]);
-        const float4 d1 = *reinterpret_cast<const float4*>(&DT[l * DTP + 8 * tc + 4]);
+        const float a0 = As[(2 * tr) * LP + l], a1 = As[(2 * tr + 1) * LP + l];
+        const float4 d0 = *reinterpret_cast<const float4*>(&DT[l * DTP + 4 * tc]);
+        const float4 d1 = *reinterpret_cast<const float4*>(&DT[l * DTP + 64 + 4 * tc]);
         const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[r][q] += av[r] * dv[q];
+        for (int q = 0; q < 8; ++q) {
+            acc[0][q] += a0 * dv[q];
+            acc[1][q] += a1 * dv[q];
+        }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int64_t gi = row0 + 4 * tr + r;
+    for (int r = 0; r < 2; ++r) {
+        const int64_t gi = row0 + 2 * tr + r;
         if (gi >= m) continue;
-        float* g = G + (size_t)(r0 + gi) * ld + j0 + 8 * tc;
-        uint32_t hw[4], lw[4];
 #pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-            g[q] = acc[r][q];
-            g[q + 1] = acc[r][q + 1];
-            const __nv_bfloat162 h = __floats2bfloat162_rn(acc[r][q], acc[r][q + 1]);
-            const __nv_bfloat162 lo = __floats2bfloat162_rn(acc[r][q] - __low2float(h), acc[r][q + 1] - __high2float(h));
-            hw[q / 2] = (uint32_t)__bfloat16_as_ushort(h.x) | ((uint32_t)__bfloat16_as_ushort(h.y) << 16);
-            lw[q / 2] = (uint32_t)__bfloat16_as_ushort(lo.x) | ((uint32_t)__bfloat16_as_ushort(lo.y) << 16);
+        for (int hf = 0; hf < 2; ++hf) {
+            const int c = 64 * hf + 4 * tc;
+            const float* v = &acc[r][4 * hf];
+            *reinterpret_cast<float4*>(G + (size_t)(r0 + gi) * ld + j0 + c) = make_float4(v[0], v[1], v[2], v[3]);
+            uint32_t hw[2], lw[2];
+#pragma unroll
+            for (int q = 0; q < 4; q += 2) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v[q], v[q + 1]);
+                const __nv_bfloat162 lo = __floats2bfloat162_rn(v[q] - __low2float(h), v[q + 1] - __high2float(h));
+                hw[q / 2] = (uint32_t)__bfloat16_as_ushort(h.x) | ((uint32_t)__bfloat16_as_ushort(h.y) << 16);
+                lw[q / 2] = (uint32_t)__bfloat16_as_ushort(lo.x) | ((uint32_t)__bfloat16_as_ushort(lo.y) << 16);
+            }
+            *reinterpret_cast<uint2*>(Ph + (size_t)gi * DB + c) = make_uint2(hw[0], hw[1]);
+            *reinterpret_cast<uint2*>(Pl + (size_t)gi * DB + c) = make_uint2(lw[0], lw[1]);
         }
-        *reinterpret_cast<uint4*>(Ph + (size_t)gi * DB + 8 * tc) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(Pl + (size_t)gi * DB + 8 * tc) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     }
 }
 
@@ -340,19 +456,21 @@ constexpr size_t PANEL_SMEM = sizeof(float) * (PR * LP + DB * DTP);
 // ---------------------------------------------------------------------------
 // 4. Block row of the inverse: X[j0 + i][c] <- sum_l D[i][l] X[j0 + l][c] for
 // the ncols leading columns (in place), and its transpose as BF16 hi + lo
-// halves: XT[c][i] (ncols x 128 row-major).  64 columns per CTA of 256 threads;
-// thread (trow, tcol) = (t / 16, t % 16) computes rows 8 trow .. 8 trow + 7 and
-// columns 4 tcol .. 4 tcol + 3, reading D transposed (DT[l][i] = D[i][l]).
+// halves: XT[c][i] (ncols x 128 row-major).  32 columns per CTA of 256
+// threads; thread (trow, tcol) = (t / 16, t % 16) computes rows 8 trow .. 8
+// trow + 7 and columns 2 tcol, 2 tcol + 1.  D arrives transposed (Dt[l][i] =
+// D[i][l]) and is staged by 16-byte copies.
 // ---------------------------------------------------------------------------
-constexpr int TC = 64;
+constexpr int TC = 32;
+constexpr int SSP = TC + 4;
 __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t ld, int64_t j0, int bs,
-                                                 int64_t ncols, const float* __restrict__ D,
+                                                 int64_t ncols, const float* __restrict__ Dt,
                                                  __nv_bfloat16* __restrict__ XTh, __nv_bfloat16* __restrict__ XTl)
 {
     extern __shared__ __align__(16) float sm[];
-    float* Ss = sm;                   // DB x (TC + 4)
-    float* DT = Ss + DB * (TC + 4);   // DB x DTP
-    __nv_bfloat16* Th = reinterpret_cast<__nv_bfloat16*>(DT + DB * DTP);   // TC x (DB + 8)
+    float* DT = sm;                   // DB x DTP
+    float* Ss = DT + DB * DTP;        // DB x SSP
+    __nv_bfloat16* Th = reinterpret_cast<__nv_bfloat16*>(Ss + DB * SSP);   // TC x (DB + 8)
     __nv_bfloat16* Tl = Th + TC * (DB + 8);
     const int t = threadIdx.x;
     const int64_t c0 = (int64_t)blockIdx.x * TC;
@@ -360,26 +478,22 @@ __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t 
     for (int e = t; e < DB * TC; e += 256) {
         const int i = e / TC, cc = e % TC;
         const int64_t gc = c0 + cc;
-        Ss[i * (TC + 4) + cc] = (i < bs && gc < ncols) ? X[(size_t)(j0 + i) * ld + gc] : 0.f;
+        Ss[i * SSP + cc] = (i < bs && gc < ncols) ? X[(size_t)(j0 + i) * ld + gc] : 0.f;
     }
 #pragma unroll 4
     for (int e4 = t; e4 < DB * DB / 4; e4 += 256) {
-        const float4 d4 = reinterpret_cast<const float4*>(D)[e4];
-        const int i = (4 * e4) >> 7, l = (4 * e4) & (DB - 1);
-        DT[l * DTP + i] = d4.x; DT[(l + 1) * DTP + i] = d4.y; DT[(l + 2) * DTP + i] = d4.z;
-        DT[(l + 3) * DTP + i] = d4.w;
+        const int l = (4 * e4) >> 7, i = (4 * e4) & (DB - 1);
+        *reinterpret_cast<float4*>(DT + l * DTP + i) = reinterpret_cast<const float4*>(Dt)[e4];
     }
     __syncthreads();
     const int trow = t >> 4, tcol = t & 15;
-    float acc[8][4];
+    float acc[8][2];
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[k][j] = 0.f;
+    for (int k = 0; k < 8; ++k) acc[k][0] = acc[k][1] = 0.f;
     const int lmax = 8 * trow + 7;   // D[i][l] = 0 for l > i
 #pragma unroll 4
     for (int l = 0; l <= lmax; ++l) {
-        const float4 sv = *reinterpret_cast<const float4*>(&Ss[l * (TC + 4) + 4 * tcol]);
+        const float2 sv = *reinterpret_cast<const float2*>(&Ss[l * SSP + 2 * tcol]);
         const float4 d0 = *reinterpret_cast<const float4*>(&DT[l * DTP + 8 * trow]);
         const float4 d1 = *reinterpret_cast<const float4*>(&DT[l * DTP + 8 * trow + 4]);
         const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
@@ -387,16 +501,14 @@ __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t 
         for (int k = 0; k < 8; ++k) {
             acc[k][0] += dv[k] * sv.x;
             acc[k][1] += dv[k] * sv.y;
-            acc[k][2] += dv[k] * sv.z;
-            acc[k][3] += dv[k] * sv.w;
         }
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int i = 8 * trow + k;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int cc = 4 * tcol + j;
+        for (int j = 0; j < 2; ++j) {
+            const int cc = 2 * tcol + j;
             const int64_t gc = c0 + cc;
             if (i < bs && gc < ncols) X[(size_t)(j0 + i) * ld + gc] = acc[k][j];
             __nv_bfloat16 h, lo;
@@ -406,7 +518,7 @@ __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t 
         }
     }
     __syncthreads();
-    // coalesced rows of XT: 64 columns x 128 BF16 = 16 chunks of 16 bytes per row and half
+    // coalesced rows of XT: 32 columns x 128 BF16 = 16 chunks of 16 bytes per row and half
     for (int e = t; e < TC * 16; e += 256) {
         const int cc = e >> 4, ch = e & 15;
         const int64_t gc = c0 + cc;
@@ -418,8 +530,7 @@ __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t 
     }
 }
 
-constexpr size_t TRMM_SMEM =
-    sizeof(float) * (DB * (TC + 4) + DB * DTP) + 2 * sizeof(__nv_bfloat16) * TC * (DB + 8);
+constexpr size_t TRMM_SMEM = sizeof(float) * (DB * DTP + DB * SSP) + 2 * sizeof(__nv_bfloat16) * TC * (DB + 8);
 
 // ---------------------------------------------------------------------------
 // 3, 5. C[m x n] -= (A_hi + A_lo)(B_hi + B_lo)^T over a contraction of 64 nk, the

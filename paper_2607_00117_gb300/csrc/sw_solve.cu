@@ -824,3 +824,56 @@ extern "C" sw_status sw_matrix_apply(const sw_matrix* U, const double* w, double
     cudaFree(buf);
     return s;
 }
+
+extern "C" sw_status sw_factor_preconditioner(sw_ctx* ctx, const float* gram, int64_t K, int mode, float* L_out,
+                                              float* X_out, int* info_out)
+{
+    CHECK_CTX(ctx);
+    if (!gram || !L_out || !X_out || !info_out || K <= 0 || K > 65536 || (mode != 0 && mode != 1)) {
+        set_error(ctx, "sw_factor_preconditioner: bad arguments");
+        return SW_EINVAL;
+    }
+    cudaSetDevice(ctx->device);
+    cudaGetLastError();
+    if (mode == 0 && !chol_tc_available()) {
+        set_error(ctx, "sw_factor_preconditioner: the tensor-map encoder is unavailable");
+        return SW_ECUDA;
+    }
+    const int64_t ld = mode == 0 ? (K + 3) / 4 * 4 : K;
+    cudaStream_t st = ctx->stream;
+    float *G = nullptr, *X = nullptr, *D = nullptr;
+    int* flags = nullptr;
+    sw_status s = SW_OK;
+    cudaError_t e;
+    if ((e = cudaMalloc(&G, (size_t)K * ld * sizeof(float))) || (e = cudaMalloc(&X, (size_t)K * ld * sizeof(float))) ||
+        (e = cudaMalloc(&D, 64 * 64 * sizeof(float))) || (e = cudaMalloc(&flags, 2 * sizeof(int)))) {
+        cudaGetLastError();
+        s = ctx->cuda_fail(e, "factor buffers");
+    }
+    int fh[2] = {0, 0};
+    if (s == SW_OK) {
+        if ((e = cudaMemcpy2DAsync(G, ld * sizeof(float), gram, K * sizeof(float), K * sizeof(float), K,
+                                   cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), st)) ||
+            (e = mode == 0 ? cholesky_inverse_tc(ctx, G, X, K, ld, flags, flags + 1)
+                           : cholesky_inverse<float>(ctx, G, X, D, K, flags)) ||
+            (e = cudaMemcpy2DAsync(L_out, K * sizeof(float), G, ld * sizeof(float), K * sizeof(float), K,
+                                   cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaMemcpy2DAsync(X_out, K * sizeof(float), X, ld * sizeof(float), K * sizeof(float), K,
+                                   cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaMemcpyAsync(fh, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st)))
+            s = ctx->cuda_fail(e, "preconditioner factorisation");
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(G);
+    cudaFree(X);
+    cudaFree(D);
+    cudaFree(flags);
+    if (s == SW_OK && fh[1]) {
+        set_error(ctx, "sw_factor_preconditioner: a tensor-core update timed out");
+        s = SW_ETIMEOUT;
+    }
+    *info_out = fh[0];
+    return s;
+}

@@ -56,6 +56,8 @@ class DensityGrid(ctypes.Structure):
 _D = ctypes.POINTER(ctypes.c_double)
 _U8 = ctypes.POINTER(ctypes.c_uint8)
 _I64 = ctypes.POINTER(ctypes.c_int64)
+_F = ctypes.POINTER(ctypes.c_float)
+_I32 = ctypes.POINTER(ctypes.c_int32)
 _VP = ctypes.c_void_p
 _lib = None
 
@@ -94,6 +96,7 @@ SIGNATURES = {
     "sw_solve_weights_device": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP]),
     "sw_solve_info": (ctypes.c_int, [_VP, _D]),
     "sw_solve_bootstrap": (ctypes.c_int, [_VP, _VP, _D, _D, ctypes.c_double, ctypes.c_int64, _D, _D, _D, _D]),
+    "sw_factor_preconditioner": (ctypes.c_int, [_VP, _F, ctypes.c_int64, ctypes.c_int, _F, _F, _I32]),
     "sw_matrix_shape": (ctypes.c_int, [_VP, _I64, _I64, _I64]),
     "sw_matrix_copy": (ctypes.c_int, [_VP, _D]),
     "sw_matrix_apply": (ctypes.c_int, [_VP, _D, _D]),
@@ -136,6 +139,16 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
 def _dp(a: np.ndarray):
     assert a.dtype == np.float64 and a.flags.c_contiguous, "expected a C-contiguous float64 array"
     return a.ctypes.data_as(_D)
+
+
+def _fp(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags.c_contiguous, "expected a C-contiguous float32 array"
+    return a.ctypes.data_as(_F)
+
+
+def _ip(a: np.ndarray):
+    assert a.dtype == np.int32 and a.flags.c_contiguous, "expected a C-contiguous int32 array"
+    return a.ctypes.data_as(_I32)
 
 
 def _tp(t) -> int:
@@ -441,6 +454,17 @@ class Context:
 
     def launch_count(self) -> int:
         return lib().sw_launch_count(self.handle)
+
+    def factor_preconditioner(self, gram: np.ndarray, mode: int = 0):
+        """(L, X = L^-1, info) of sw_factor_preconditioner for a K x K FP32 matrix (lower triangle read)."""
+        G = np.ascontiguousarray(gram, dtype=np.float32)
+        K = G.shape[0]
+        assert G.shape == (K, K)
+        L = np.empty((K, K), np.float32)
+        X = np.empty((K, K), np.float32)
+        info = np.zeros(1, np.int32)
+        self._check(lib().sw_factor_preconditioner(self.handle, _fp(G), K, mode, _fp(L), _fp(X), _ip(info)))
+        return L, X, int(info[0])
 
     def alloc_count(self) -> int:
         return lib().sw_alloc_count(self.handle)
