@@ -299,6 +299,9 @@ int64_t sw_alloc_count(const sw_ctx* ctx);
  *                           their mean (counts / (copies nsteps n)); a realisation cut by the quality test adds a
  *                           zero column to the mean (its counts are removed exactly, GH sums to rounding), as
  *                           sw_bundle of the unbundled matrix; n must divide the orbit count; fixed-step KDK only
+ *  "matrix_cache" (0/1)     sw_matrix_free keeps the freed matrix's device buffer in its context for the next
+ *                           matrix of about the same size (at most four buffers; released by sw_destroy, on an
+ *                           allocation failure, or by setting 0) instead of returning it to the driver (default 1)
  *  "chol_tc" (0/1)          active set, FP32 form: Cholesky and its inverse in 128-wide steps with the trailing and
  *                           inverse updates on the tensor cores (BF16 hi + lo split, default 1); 0: FP32 SIMT updates
  *  "integrator" (0/1)       sw_project's integrator: 0 (default) kick-drift-kick at the fixed dt in the inertial

@@ -563,51 +563,110 @@ struct FF {
     float h, l;
 };
 
-__device__ __forceinline__ void ff_add_prod(FF& s, float u, float xh, float xl)
+
+// Running double-float sum: s.h keeps the rounded sum, s.l the exact rounding errors of its
+// additions (two-sum) and the low parts of the products; ff_renorm folds s.l back (fast two-sum,
+// |s.l| << |s.h|) every few terms, so that s.l stays ~2^-24 of the sum and its own rounding
+// ~2^-48.
+__device__ __forceinline__ void ff_acc(FF& s, float u, float xh, float xl)
 {
     const float ph = u * xh;
-    const float pl = fmaf(u, xh, -ph) + u * xl;
+    const float pl = fmaf(u, xl, fmaf(u, xh, -ph));
     const float t = s.h + ph;
     const float bb = t - s.h;
-    const float e = (s.h - (t - bb)) + (ph - bb) + s.l + pl;
-    s.h = t + e;
-    s.l = e - (s.h - t);
+    s.l += ((s.h - (t - bb)) + (ph - bb)) + pl;
+    s.h = t;
 }
 
-// acc[r] += sum_i U[i, r] w[i] with w split into (wh, wl); zero weights skipped
+__device__ __forceinline__ void ff_renorm(FF& s)
+{
+    const float t = s.h + s.l;
+    s.l -= t - s.h;
+    s.h = t;
+}
+
+__device__ __forceinline__ double ff_value(const FF& s) { return (double)s.h + (double)s.l; }
+
+// acc[r] += sum_i U[i, r] w[i] with w split into (wh, wl); zero weights skipped.  VEC: each thread
+// owns four consecutive rows (16-byte loads; M a multiple of 4 and U 16-byte aligned), four
+// orbits in flight
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_u_times_w_ff(const float* __restrict__ U, int64_t M, int64_t N,
                                                       const float* __restrict__ wh, const float* __restrict__ wl,
                                                       double* __restrict__ acc, int64_t orbits_per_split)
 {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * (VEC ? 4 : 1);
     if (r >= M) return;
     const int64_t i0 = (int64_t)blockIdx.y * orbits_per_split;
     int64_t i1 = i0 + orbits_per_split;
     if (i1 > N) i1 = N;
-    // four independent double-float sums keep four loads in flight per thread
-    FF s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    int64_t i = i0;
-    for (; i + 4 <= i1; i += 4) {
-        float u[4], h[4], l[4];
+    if (i1 <= i0) return;
+    if constexpr (VEC) {
+        FF s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        int64_t i = i0;
+        for (; i + 4 <= i1; i += 4) {
+            float4 u[4];
+            float h[4], l[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            h[q] = wh[i + q];
-            l[q] = wl[i + q];
-            u[q] = h[q] != 0.f ? U[(size_t)(i + q) * M + r] : 0.f;
+            for (int q = 0; q < 4; ++q) {
+                h[q] = wh[i + q];
+                l[q] = wl[i + q];
+                u[q] = h[q] != 0.f ? *reinterpret_cast<const float4*>(U + (size_t)(i + q) * M + r)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ff_acc(s[0], u[q].x, h[q], l[q]);
+                ff_acc(s[1], u[q].y, h[q], l[q]);
+                ff_acc(s[2], u[q].z, h[q], l[q]);
+                ff_acc(s[3], u[q].w, h[q], l[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ff_renorm(s[q]);
+        }
+        for (; i < i1; ++i) {
+            const float h = wh[i];
+            if (h == 0.f) continue;
+            const float4 u = *reinterpret_cast<const float4*>(U + (size_t)i * M + r);
+            const float l = wl[i];
+            ff_acc(s[0], u.x, h, l); ff_acc(s[1], u.y, h, l); ff_acc(s[2], u.z, h, l); ff_acc(s[3], u.w, h, l);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ff_renorm(s[q]);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ff_add_prod(s[q], u[q], h[q], l[q]);
+        for (int q = 0; q < 4; ++q) atomicAdd(acc + r + q, ff_value(s[q]));
+    } else {
+        // four independent double-float sums keep four loads in flight per thread
+        FF s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        int64_t i = i0;
+        for (; i + 4 <= i1; i += 4) {
+            float u[4], h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                h[q] = wh[i + q];
+                l[q] = wl[i + q];
+                u[q] = h[q] != 0.f ? U[(size_t)(i + q) * M + r] : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ff_acc(s[q], u[q], h[q], l[q]);
+                ff_renorm(s[q]);
+            }
+        }
+        for (; i < i1; ++i) {
+            const float h = wh[i];
+            if (h != 0.f) {
+                ff_acc(s[0], U[(size_t)i * M + r], h, wl[i]);
+                ff_renorm(s[0]);
+            }
+        }
+        atomicAdd(acc + r, (ff_value(s[0]) + ff_value(s[1])) + (ff_value(s[2]) + ff_value(s[3])));
     }
-    for (; i < i1; ++i) {
-        const float h = wh[i];
-        if (h != 0.f) ff_add_prod(s[0], U[(size_t)i * M + r], h, wl[i]);
-    }
-    if (i1 > i0)
-        atomicAdd(acc + r, (((double)s[0].h + (double)s[0].l) + ((double)s[1].h + (double)s[1].l)) +
-                               (((double)s[2].h + (double)s[2].l) + ((double)s[3].h + (double)s[3].l)));
 }
 
-// out[i] = sum_r U[i, r] x[r] with x split into (xh, xl); one warp per orbit
+// out[i] = sum_r U[i, r] x[r] with x split into (xh, xl); one warp per orbit.  VEC: each lane reads
+// four consecutive rows (16-byte loads), two such loads in flight
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_ut_times_x_ff(const float* __restrict__ U, int64_t M, int64_t N,
                                                        const float* __restrict__ xh, const float* __restrict__ xl,
                                                        double* __restrict__ out)
@@ -618,21 +677,53 @@ __global__ void __launch_bounds__(256) k_ut_times_x_ff(const float* __restrict__
     for (int64_t i = warp; i < N; i += nwarp) {
         const float* col = U + (size_t)i * M;
         FF s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        int64_t r = lane;
-        for (; r + 96 < M; r += 128) {
-            float u[4], h[4], l[4];
+        if constexpr (VEC) {
+            int64_t r = 4 * lane;
+            for (; r + 128 + 3 < M; r += 256) {
+                const float4 u0 = *reinterpret_cast<const float4*>(col + r);
+                const float4 u1 = *reinterpret_cast<const float4*>(col + r + 128);
+                const float4 h0 = *reinterpret_cast<const float4*>(xh + r);
+                const float4 h1 = *reinterpret_cast<const float4*>(xh + r + 128);
+                const float4 l0 = *reinterpret_cast<const float4*>(xl + r);
+                const float4 l1 = *reinterpret_cast<const float4*>(xl + r + 128);
+                ff_acc(s[0], u0.x, h0.x, l0.x); ff_acc(s[1], u0.y, h0.y, l0.y);
+                ff_acc(s[2], u0.z, h0.z, l0.z); ff_acc(s[3], u0.w, h0.w, l0.w);
+                ff_acc(s[0], u1.x, h1.x, l1.x); ff_acc(s[1], u1.y, h1.y, l1.y);
+                ff_acc(s[2], u1.z, h1.z, l1.z); ff_acc(s[3], u1.w, h1.w, l1.w);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                u[q] = col[r + 32 * q];
-                h[q] = xh[r + 32 * q];
-                l[q] = xl[r + 32 * q];
+                for (int q = 0; q < 4; ++q) ff_renorm(s[q]);
             }
+            for (; r + 3 < M; r += 128) {
+                const float4 u0 = *reinterpret_cast<const float4*>(col + r);
+                const float4 h0 = *reinterpret_cast<const float4*>(xh + r);
+                const float4 l0 = *reinterpret_cast<const float4*>(xl + r);
+                ff_acc(s[0], u0.x, h0.x, l0.x); ff_acc(s[1], u0.y, h0.y, l0.y);
+                ff_acc(s[2], u0.z, h0.z, l0.z); ff_acc(s[3], u0.w, h0.w, l0.w);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) ff_add_prod(s[q], u[q], h[q], l[q]);
+                for (int q = 0; q < 4; ++q) ff_renorm(s[q]);
+            }
+        } else {
+            int64_t r = lane;
+            for (; r + 96 < M; r += 128) {
+                float u[4], h[4], l[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    u[q] = col[r + 32 * q];
+                    h[q] = xh[r + 32 * q];
+                    l[q] = xl[r + 32 * q];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    ff_acc(s[q], u[q], h[q], l[q]);
+                    ff_renorm(s[q]);
+                }
+            }
+            for (; r < M; r += 32) {
+                ff_acc(s[0], col[r], xh[r], xl[r]);
+                ff_renorm(s[0]);
+            }
         }
-        for (; r < M; r += 32) ff_add_prod(s[0], col[r], xh[r], xl[r]);
-        double d = (((double)s[0].h + (double)s[0].l) + ((double)s[1].h + (double)s[1].l)) +
-                   (((double)s[2].h + (double)s[2].l) + ((double)s[3].h + (double)s[3].l));
+        double d = (ff_value(s[0]) + ff_value(s[1])) + (ff_value(s[2]) + ff_value(s[3]));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
         if (lane == 0) out[i] = d;
@@ -1093,6 +1184,22 @@ static cudaError_t split_ff(sw_ctx* ctx, const double* x, int64_t n, float** hi,
     return cudaGetLastError();
 }
 
+// U w for an FP32 matrix with w already split: rows in 16-byte groups when the columns allow it
+static void launch_u_times_w_ff(sw_ctx* ctx, const float* U, int64_t M, int64_t N, const float* wh, const float* wl,
+                                double* acc)
+{
+    const bool vec = M % 4 == 0 && ((uintptr_t)U & 15) == 0;
+    const int64_t rows_per_cta = vec ? 1024 : 256;
+    const unsigned gx = (unsigned)((M + rows_per_cta - 1) / rows_per_cta);
+    int64_t want = (ctx_sms(ctx) * 16 + gx - 1) / gx;
+    if (want < 1) want = 1;
+    int64_t ops = (N + want - 1) / want;
+    if (ops < 16) ops = 16;
+    const unsigned gy = (unsigned)((N + ops - 1) / ops);
+    if (vec) k_u_times_w_ff<true><<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(U, M, N, wh, wl, acc, ops);
+    else k_u_times_w_ff<false><<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(U, M, N, wh, wl, acc, ops);
+}
+
 template <typename T>
 cudaError_t u_times_w(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const double* w, double* acc)
 {
@@ -1108,7 +1215,7 @@ cudaError_t u_times_w(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const doubl
         float *wh, *wl;
         cudaError_t e = split_ff(ctx, w, N, &wh, &wl);
         if (e) return e;
-        k_u_times_w_ff<<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(U, M, N, wh, wl, acc, ops);
+        launch_u_times_w_ff(ctx, U, M, N, wh, wl, acc);
     } else {
         k_u_times_w<T><<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(U, M, N, w, acc, ops);
     }
@@ -1120,14 +1227,8 @@ cudaError_t u_times_w_presplit(sw_ctx* ctx, const float* U, int64_t M, int64_t N
 {
     LaunchTimer lt(ctx, K_RESID);
     add_work(ctx, K_RESID, (double)M * N * sizeof(float) + 8.0 * (N + 2.0 * M));
-    unsigned gx = (unsigned)((M + 255) / 256);
-    int64_t want = (ctx_sms(ctx) * 16 + gx - 1) / gx;
-    if (want < 1) want = 1;
-    int64_t ops = (N + want - 1) / want;
-    if (ops < 16) ops = 16;
-    unsigned gy = (unsigned)((N + ops - 1) / ops);
     k_split_ff<<<cap_grid(N, 256, 4096), 256, 0, ctx_stream(ctx)>>>(N, w, wh, wl);
-    k_u_times_w_ff<<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(U, M, N, wh, wl, acc, ops);
+    launch_u_times_w_ff(ctx, U, M, N, wh, wl, acc);
     return cudaGetLastError();
 }
 
@@ -1148,7 +1249,13 @@ cudaError_t ut_times_x(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const doub
         float *xh, *xl;
         cudaError_t e = split_ff(ctx, xs, M, &xh, &xl);
         if (e) return e;
-        k_ut_times_x_ff<<<cap_grid(N * 32, 256, ctx_sms(ctx) * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xh, xl, out);
+        const bool vec = M % 4 == 0 && ((uintptr_t)U & 15) == 0 && ((uintptr_t)xh & 15) == 0 && ((uintptr_t)xl & 15) == 0;
+        if (vec)
+            k_ut_times_x_ff<true><<<cap_grid(N * 32, 256, ctx_sms(ctx) * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xh, xl,
+                                                                                                        out);
+        else
+            k_ut_times_x_ff<false><<<cap_grid(N * 32, 256, ctx_sms(ctx) * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xh,
+                                                                                                         xl, out);
     } else {
         k_ut_times_x<T><<<cap_grid(N * 32, 256, ctx_sms(ctx) * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xs, out);
     }

@@ -168,6 +168,10 @@ static void ctx_release(sw_ctx* ctx)
                     ctx->d_invsig_f};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    for (auto& b : ctx->mat_cache) cudaFree(b.first);
+    ctx->mat_cache.clear();
+    if (ctx->d_ghw) cudaFree(ctx->d_ghw);
+    ctx->d_ghw = nullptr;
     ctx->d_soa = ctx->d_cs = ctx->d_ghtab = ctx->d_mlp = ctx->d_split = ctx->d_chol = nullptr;
     ctx->d_ttotal = ctx->d_chol_tc = ctx->d_cut = ctx->d_invsig_f = nullptr;
     ctx->d_aos = ctx->d_drift = nullptr;
@@ -524,6 +528,45 @@ template GridT<float> make_grid<float>(double, double, double, const sw_pixel_gr
 template GridT<double> make_grid<double>(double, double, double, const sw_pixel_grid*, const sw_vbins*,
                                          const sw_density_grid*, int, int);
 
+// Matrix buffers: a freed matrix's buffer is kept by its context and handed to the next matrix
+// whose size it covers with at most 1/8 to spare; a failed allocation first returns the kept
+// buffers to the driver and tries again.
+static cudaError_t matrix_alloc(sw_ctx* ctx, void** d, size_t bytes)
+{
+    for (size_t k = 0; k < ctx->mat_cache.size(); ++k) {
+        const size_t have = ctx->mat_cache[k].second;
+        if (have >= bytes && have - bytes <= bytes / 8) {
+            *d = ctx->mat_cache[k].first;
+            ctx->mat_cache.erase(ctx->mat_cache.begin() + k);
+            return cudaSuccess;
+        }
+    }
+    cudaError_t e = cudaMalloc(d, bytes);
+    if (e != cudaSuccess && !ctx->mat_cache.empty()) {
+        cudaGetLastError();
+        for (auto& b : ctx->mat_cache) cudaFree(b.first);
+        ctx->mat_cache.clear();
+        e = cudaMalloc(d, bytes);
+    }
+    return e;
+}
+
+static void matrix_release(sw_ctx* ctx, void* d, size_t bytes)
+{
+    if (!d) return;
+    if (ctx->destroyed || !ctx->opt.matrix_cache) {
+        cudaFree(d);
+        return;
+    }
+    ctx->mat_cache.emplace_back(d, bytes);
+    while (ctx->mat_cache.size() > 4) {   // the oldest goes back first
+        cudaFree(ctx->mat_cache.front().first);
+        ctx->mat_cache.erase(ctx->mat_cache.begin());
+    }
+}
+
+static size_t matrix_bytes(const sw_matrix* U) { return (size_t)U->M * (size_t)U->N * (size_t)U->elem; }
+
 template <typename T>
 static sw_status project_impl(sw_ctx* ctx, const GridT<T>& g, const double* gh_v0_s, sw_matrix** U_out)
 {
@@ -542,14 +585,14 @@ static sw_status project_impl(sw_ctx* ctx, const GridT<T>& g, const double* gh_v
     U->device = ctx->device;
     U->nv = g.nv; U->v0 = (double)g.v0; U->dv = (double)g.dv;
     size_t bytes = (size_t)M * (size_t)N * sizeof(T);
-    cudaError_t e = cudaMalloc(&U->d, bytes);
+    cudaError_t e = matrix_alloc(ctx, &U->d, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete U;
         set_error(ctx, "cudaMalloc(%zu bytes) for the orbit matrix failed: %s", bytes, cudaGetErrorString(e));
         return SW_ENOMEM;
     }
-    auto fail = [&](sw_status s) { cudaFree(U->d); delete U; return s; };
+    auto fail = [&](sw_status s) { matrix_release(ctx, U->d, bytes); delete U; return s; };
     if ((e = cudaMemsetAsync(U->d, 0, bytes, ctx->stream)) != cudaSuccess) return fail(ctx->cuda_fail(e, "memset U"));
     ModelT<T> m = base_model<T>(ctx);
     m.g = g;
@@ -723,19 +766,24 @@ static sw_status reduce_gh_impl(sw_ctx* ctx, const sw_matrix* Uh, const double* 
     G->d = nullptr;
     G->M = Mg; G->nkin = 4 * npix; G->gh = 1;
     cudaError_t e;
-    if ((e = cudaMalloc(&dW, W.size() * sizeof(T))) || (e = cudaMalloc(&G->d, (size_t)Mg * N * sizeof(T)))) {
+    const size_t gbytes = (size_t)Mg * N * sizeof(T);
+    if (ctx->ensure(&ctx->d_ghw, &ctx->ghw_cap, W.size() * sizeof(T), "GH weights") != SW_OK) {
+        delete G;
+        return SW_ENOMEM;
+    }
+    dW = ctx->d_ghw;
+    if ((e = matrix_alloc(ctx, &G->d, gbytes))) {
         cudaGetLastError();
-        cudaFree(dW); cudaFree(G->d); delete G;
+        delete G;
         set_error(ctx, "sw_reduce_gh: allocation failed");
         return SW_ENOMEM;
     }
     if ((e = cudaMemcpyAsync(dW, W.data(), W.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream)) ||
         (e = launch_reduce_gh<T>(ctx, Uh->d, Uh->M, N, nd, npix, nv, dW, G->d, Mg)) ||
         (e = cudaStreamSynchronize(ctx->stream))) {
-        cudaFree(dW); cudaFree(G->d); delete G;
+        matrix_release(ctx, G->d, gbytes); delete G;
         return ctx->cuda_fail(e, "reduce GH");
     }
-    cudaFree(dW);
     ctx->live_matrices++;
     *out = G;
     return SW_OK;
@@ -768,7 +816,7 @@ extern "C" sw_status sw_bundle(sw_ctx* ctx, const sw_matrix* U, int64_t n, sw_ma
     B->d = nullptr;
     B->N = U->N / n;
     const size_t bytes = (size_t)U->M * (size_t)B->N * (size_t)U->elem;
-    cudaError_t e = cudaMalloc(&B->d, bytes);
+    cudaError_t e = matrix_alloc(ctx, &B->d, bytes);
     if (e) {
         cudaGetLastError();
         delete B;
@@ -779,7 +827,7 @@ extern "C" sw_status sw_bundle(sw_ctx* ctx, const sw_matrix* U, int64_t n, sw_ma
                      : launch_bundle<float>(ctx, U->d, U->M, B->N, (int)n, B->d);
     if (!e) e = cudaStreamSynchronize(ctx->stream);
     if (e) {
-        cudaFree(B->d);
+        matrix_release(ctx, B->d, bytes);
         delete B;
         return ctx->cuda_fail(e, "bundle");
     }
@@ -831,7 +879,7 @@ extern "C" sw_status sw_matrix_free(sw_matrix* U)
     } else {
         cudaDeviceSynchronize();
     }
-    if (U->d) cudaFree(U->d);
+    matrix_release(ctx, U->d, matrix_bytes(U));
     cudaGetLastError();
     delete U;
     if (--ctx->live_matrices == 0 && ctx->destroyed) delete ctx;
@@ -1031,6 +1079,14 @@ extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value)
     } else if (!strcmp(key, "chol_coop")) {
         if (!(value == 0 || value == 1)) return SW_EINVAL;
         ctx->opt.chol_coop = (int)value;
+    } else if (!strcmp(key, "matrix_cache")) {
+        if (!(value == 0 || value == 1)) return SW_EINVAL;
+        ctx->opt.matrix_cache = (int)value;
+        if (!value) {
+            cudaSetDevice(ctx->device);
+            for (auto& b : ctx->mat_cache) cudaFree(b.first);
+            ctx->mat_cache.clear();
+        }
     } else if (!strcmp(key, "project_bundle")) {
         if (!(value >= 1.0 && value <= 1024.0 && value == std::floor(value))) return SW_EINVAL;
         ctx->opt.project_bundle = (int)value;

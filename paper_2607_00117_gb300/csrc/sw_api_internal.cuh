@@ -37,6 +37,7 @@ struct Options {
     int chol_tc = 1;             // FP32 Cholesky + inverse with tcgen05 trailing updates (0: SIMT, 64-wide)
     int chol_lookahead = 1;      // tensor-core factorisation: bulk updates on a second stream (1) or in line (0)
     int project_bundle = 1;      // orbits per column of sw_project's matrix (bundles accumulated at bin time)
+    int matrix_cache = 1;        // keep freed matrix buffers for reuse by the next matrices of this context
     int integrator = 0;          // 0: kick-drift-kick at fixed dt; 1: adaptive Bogacki-Shampine 3(2) in the bar frame
     double bs3_rtol = 1e-4;      // relative tolerance of the adaptive integrator
     int as_cg_max = 200;         // active set: conjugate-gradient steps per reduced solve
@@ -104,6 +105,10 @@ struct sw_ctx {
     void* d_chol_tc = nullptr; size_t chol_tc_cap = 0;   // tensor-core Cholesky: diagonal inverse, BF16 panels
     void* d_cut = nullptr; size_t cut_cap = 0;           // bundled projection: indices of cut realisations
     void* d_invsig_f = nullptr; size_t invsig_f_cap = 0; // whitening: 1/sigma in FP32
+    // device buffers of freed matrices, kept for the next matrices (the orbit matrix of a model is
+    // rebuilt at the same size for every model: a cudaMalloc / cudaFree of gigabytes per model avoided)
+    std::vector<std::pair<void*, size_t>> mat_cache;
+    void* d_ghw = nullptr; size_t ghw_cap = 0;            // GH weights of sw_reduce_gh
     void* d_ttotal = nullptr; size_t ttotal_cap = 0;   // per-orbit integration time (adaptive integrator)
     // solve
     sw::SolveWS solve_ws;
