@@ -75,59 +75,74 @@ __device__ __forceinline__ float dot4(float4 a, float4 b, float acc)
     return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, acc))));
 }
 
-// T_j = sum_{k=j}^{r-1} L_rk X_kj for j < r into Tb (quad q: row a, columns 4 (q & 7) .. + 3 of T_j, j = q >> 8)
+// T_j = sum_{k=j}^{r-1} L_rk X_kj for j < r into Tb: 4 x 4 tiles, tile q = (j, ta, tb) with rows
+// 4 ta .. 4 ta + 3 and columns 4 tb .. 4 tb + 3 of T_j (consecutive q: consecutive tb, so the
+// rows of X are read by eight threads at distinct 16-byte chunks and the rows of L are shared)
 __device__ __forceinline__ void inverse_t_part(const float* __restrict__ A, const float* __restrict__ X,
                                                float* __restrict__ Tb, int r, int tid, int NT)
 {
-    for (int q = tid; q < 256 * r; q += NT) {
-        const int j = q >> 8, a = (q & 255) >> 3, b4 = (q & 7) * 4;
-        const float* pr = A + (SB * r + a) * AP;
-        const float* xc = X + SB * j + b4;
-        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+    for (int q = tid; q < 64 * r; q += NT) {
+        const int j = q >> 6, ta = (q >> 3) & 7, tb = q & 7;
+        const float* pr = A + (SB * r + 4 * ta) * AP;
+        const float* xc = X + SB * j + 4 * tb;
+        float acc[4][4] = {};
 #pragma unroll 2
-        for (int c = SB * j; c < SB * r; c += 8) {
-            const float4 p0 = ld4(pr + c), p1 = ld4(pr + c + 4);
-            const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+        for (int c = SB * j; c < SB * r; c += 4) {
+            float4 p[4], x[4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float4 x = ld4(xc + (c + u) * AP);
-                float4& acc = (u & 1) ? acc1 : acc0;
-                acc.x = fmaf(pv[u], x.x, acc.x);
-                acc.y = fmaf(pv[u], x.y, acc.y);
-                acc.z = fmaf(pv[u], x.z, acc.z);
-                acc.w = fmaf(pv[u], x.w, acc.w);
+            for (int u = 0; u < 4; ++u) p[u] = ld4(pr + u * AP + c);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = ld4(xc + (c + u) * AP);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float pv[4] = {p[u].x, p[u].y, p[u].z, p[u].w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    acc[u][0] = fmaf(pv[k], x[k].x, acc[u][0]);
+                    acc[u][1] = fmaf(pv[k], x[k].y, acc[u][1]);
+                    acc[u][2] = fmaf(pv[k], x[k].z, acc[u][2]);
+                    acc[u][3] = fmaf(pv[k], x[k].w, acc[u][3]);
+                }
             }
         }
-        *reinterpret_cast<float4*>(Tb + (j * SB + a) * CTP + b4) =
-            make_float4(acc0.x + acc1.x, acc0.y + acc1.y, acc0.z + acc1.z, acc0.w + acc1.w);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            *reinterpret_cast<float4*>(Tb + (j * SB + 4 * ta + u) * CTP + 4 * tb) =
+                make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
     }
 }
 
-// X_rj = -X_rr T_j for j < r (X_rr lower triangular: columns c <= a)
+// X_rj = -X_rr T_j for j < r (X_rr lower triangular: columns c <= row), 4 x 4 tiles as above
 __device__ __forceinline__ void inverse_x_part(float* __restrict__ X, const float* __restrict__ Tb, int r, int tid,
                                                int NT)
 {
-    for (int q = tid; q < 256 * r; q += NT) {
-        const int j = q >> 8, a = (q & 255) >> 3, b4 = (q & 7) * 4;
-        const float* xr = X + (SB * r + a) * AP + SB * r;
-        const float* tj = Tb + j * SB * CTP + b4;
-        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
-        const int cmax = (a | 3) + 1;
-        for (int c = 0; c < cmax; c += 4) {
-            const float4 p = ld4(xr + c);
-            const float pv[4] = {p.x, p.y, p.z, p.w};
+    for (int q = tid; q < 64 * r; q += NT) {
+        const int j = q >> 6, ta = (q >> 3) & 7, tb = q & 7;
+        const float* xr = X + (SB * r + 4 * ta) * AP + SB * r;
+        const float* tj = Tb + j * SB * CTP + 4 * tb;
+        float acc[4][4] = {};
+        for (int c = 0; c <= 4 * ta; c += 4) {
+            float4 p[4], t4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) p[u] = ld4(xr + u * AP + c);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) t4[u] = ld4(tj + (c + u) * CTP);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const float4 t4 = ld4(tj + (c + u) * CTP);
-                float4& acc = (u & 1) ? acc1 : acc0;
-                acc.x = fmaf(pv[u], t4.x, acc.x);
-                acc.y = fmaf(pv[u], t4.y, acc.y);
-                acc.z = fmaf(pv[u], t4.z, acc.z);
-                acc.w = fmaf(pv[u], t4.w, acc.w);
+                const float pv[4] = {p[u].x, p[u].y, p[u].z, p[u].w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    acc[u][0] = fmaf(pv[k], t4[k].x, acc[u][0]);
+                    acc[u][1] = fmaf(pv[k], t4[k].y, acc[u][1]);
+                    acc[u][2] = fmaf(pv[k], t4[k].z, acc[u][2]);
+                    acc[u][3] = fmaf(pv[k], t4[k].w, acc[u][3]);
+                }
             }
         }
-        *reinterpret_cast<float4*>(X + (SB * r + a) * AP + SB * j + b4) =
-            make_float4(-(acc0.x + acc1.x), -(acc0.y + acc1.y), -(acc0.z + acc1.z), -(acc0.w + acc1.w));
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            *reinterpret_cast<float4*>(X + (SB * r + 4 * ta + u) * AP + SB * j + 4 * tb) =
+                make_float4(-acc[u][0], -acc[u][1], -acc[u][2], -acc[u][3]);
     }
 }
 
@@ -168,7 +183,8 @@ __device__ __forceinline__ void trailing_rest(float* __restrict__ A, int p0, int
 }
 
 __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__ G, int64_t ld, int64_t j0, int bs,
-                                                             float* __restrict__ D /* D_k^T */, int* info)
+                                                             float* __restrict__ D /* D_k^T */, int* info,
+                                                             int write_L)
 {
     extern __shared__ __align__(16) float sm[];
     float* A = sm;                  // DB x AP: the block, then L
@@ -177,13 +193,15 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
     float* Tb = CT + SB * CTP;      // 2 x TBUF: the sums T_j of an inverse block row, by parity of r
     float* RR = Tb + 2 * TBUF;      // SB: 1 / L_jj of the current sub-block
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    // ---- load: 16 rows x 16-byte chunks per thread, all in flight; identity beyond bs; X = 0
+    // ---- load the lower triangle (16-byte chunks that reach it; the rest of A is never read), all
+    // in flight; rows beyond bs are the identity; X = 0
     {
         float4 v[16];
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int e = t + DIAG_THREADS * u, i = e >> 5, l4 = (e & 31) * 4;
             const float* g = G + (size_t)(j0 + i) * ld + j0 + l4;
+            if (l4 > i) continue;
             if (i < bs && l4 + 3 < bs) {
                 v[u] = ld4(g);
             } else {
@@ -196,7 +214,7 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int e = t + DIAG_THREADS * u, i = e >> 5, l4 = (e & 31) * 4;
-            *reinterpret_cast<float4*>(A + i * AP + l4) = v[u];
+            if (l4 <= i) *reinterpret_cast<float4*>(A + i * AP + l4) = v[u];
             *reinterpret_cast<float4*>(X + i * AP + l4) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
@@ -213,38 +231,27 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
                 a[k] = v.x; a[k + 1] = v.y; a[k + 2] = v.z; a[k + 3] = v.w;
             }
             float d = __shfl_sync(0xffffffffu, a[0], 0);
+            float rmine = 0.f;   // 1 / L_jj of this lane's column j = lane
+            int bad = 0;         // first non-positive pivot of the sub-block, plus one
 #pragma unroll
             for (int j = 0; j < SB; ++j) {
-                if (!(d > 0.f)) {
-                    if (lane == 0 && info && c0 + j < bs) atomicCAS(info, 0, (int)(j0 + c0 + j + 1));
-                    d = 1e-30f;
-                }
-                const float r = rsqrtf(d);
-                if (lane == 0) RR[j] = r;
+                const bool ok = d > 0.f;
+                bad = (!ok && bad == 0 && c0 + j < bs) ? j + 1 : bad;
+                const float r = rsqrtf(ok ? d : 1e-30f);
+                rmine = lane == j ? r : rmine;
                 const float lij = lane >= j ? a[j] * r : 0.f;
                 a[j] = lij;
                 CT[j * CTP + lane] = lij;
                 if (j + 1 < SB) {
                     // the next pivot: lane j + 1 subtracts its own l_(j+1) j^2, one shuffle broadcasts it
                     const float dn = a[j + 1] - lij * lij;
-                    d = __shfl_sync(0xffffffffu, dn, j + 1);
-                    const float l1 = __shfl_sync(0xffffffffu, lij, j + 1);
-                    a[j + 1] -= lij * l1;
-                    if (j + 2 < SB) {
-                        const float l2 = __shfl_sync(0xffffffffu, lij, j + 2 < SB ? j + 2 : 0);
-                        a[j + 2] -= lij * l2;
-                    }
+                    d = __shfl_sync(0xffffffffu, dn, j + 1 < SB ? j + 1 : 0);
                 }
-                __syncwarp();
 #pragma unroll
-                for (int k4 = ((j + 3) & ~3); k4 < SB; k4 += 4) {
-                    const float4 c = ld4(CT + j * CTP + k4);
-                    if (k4 + 0 >= j + 3) a[k4 + 0] -= lij * c.x;
-                    if (k4 + 1 >= j + 3) a[k4 + 1] -= lij * c.y;
-                    if (k4 + 2 >= j + 3) a[k4 + 2] -= lij * c.z;
-                    if (k4 + 3 >= j + 3) a[k4 + 3] -= lij * c.w;
-                }
+                for (int k = j + 1; k < SB; ++k) a[k] -= lij * __shfl_sync(0xffffffffu, lij, k);
             }
+            RR[lane] = rmine;
+            if (bad && lane == 0 && info) atomicCAS(info, 0, (int)(j0 + c0 + bad));
 #pragma unroll
             for (int k = 0; k < SB; k += 4)
                 *reinterpret_cast<float4*>(A + (c0 + lane) * AP + c0 + k) =
@@ -266,12 +273,17 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
         // ======== B
         if (warp == 0) {
             // X_ss = L_ss^{-1}, lane l holds column l
-            float x[SB];
+            float x[SB], rr[SB];
+#pragma unroll
+            for (int i = 0; i < SB; i += 4) {
+                const float4 v = ld4(RR + i);
+                rr[i] = v.x; rr[i + 1] = v.y; rr[i + 2] = v.z; rr[i + 3] = v.w;
+            }
 #pragma unroll
             for (int i = 0; i < SB; ++i) x[i] = i == lane ? 1.f : 0.f;
 #pragma unroll
             for (int k = 0; k < SB; ++k) {
-                x[k] *= RR[k];
+                x[k] *= rr[k];
 #pragma unroll
                 for (int i4 = ((k + 1) & ~3); i4 < SB; i4 += 4) {
                     const float4 c = ld4(CT + k * CTP + i4);
@@ -286,15 +298,17 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
         } else if (t - 32 < DB - c0 - SB) {
             // row i of the panel: y L_ss^T = a_i by forward substitution
             const int i = c0 + SB + (t - 32);
-            float y[SB];
+            float y[SB], rr[SB];
 #pragma unroll
             for (int k = 0; k < SB; k += 4) {
                 const float4 v = ld4(A + i * AP + c0 + k);
                 y[k] = v.x; y[k + 1] = v.y; y[k + 2] = v.z; y[k + 3] = v.w;
+                const float4 w = ld4(RR + k);
+                rr[k] = w.x; rr[k + 1] = w.y; rr[k + 2] = w.z; rr[k + 3] = w.w;
             }
 #pragma unroll
             for (int k = 0; k < SB; ++k) {
-                y[k] *= RR[k];
+                y[k] *= rr[k];
 #pragma unroll
                 for (int j4 = ((k + 1) & ~3); j4 < SB; j4 += 4) {
                     const float4 c = ld4(CT + k * CTP + j4);
@@ -345,29 +359,34 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
     // ---- the last block row of the inverse (its sums were formed while sub-block 3 was factored)
     inverse_x_part(X, Tb + ((DB / SB - 1) & 1) * TBUF, DB / SB - 1, t, DIAG_THREADS);
     __syncthreads();
-    // ---- L back into G (lower triangle of the block, 16-byte stores where the chunk lies in it)
+    // ---- L back into G when asked (lower triangle of the block, 16-byte stores where the chunk lies in
+    // it; the factorisation itself needs only D and the panels)
+    if (write_L) {
 #pragma unroll 4
-    for (int u = 0; u < 16; ++u) {
-        const int e = t + DIAG_THREADS * u, i = e >> 5, l4 = (e & 31) * 4;
-        if (i >= bs || l4 > i) continue;
-        float* g = G + (size_t)(j0 + i) * ld + j0 + l4;
-        const float4 v = ld4(A + i * AP + l4);
-        if (l4 + 3 <= i && l4 + 3 < bs) {
-            *reinterpret_cast<float4*>(g) = v;
-        } else {
-            const float w[4] = {v.x, v.y, v.z, v.w};
+        for (int u = 0; u < 16; ++u) {
+            const int e = t + DIAG_THREADS * u, i = e >> 5, l4 = (e & 31) * 4;
+            if (i >= bs || l4 > i) continue;
+            float* g = G + (size_t)(j0 + i) * ld + j0 + l4;
+            const float4 v = ld4(A + i * AP + l4);
+            if (l4 + 3 <= i && l4 + 3 < bs) {
+                *reinterpret_cast<float4*>(g) = v;
+            } else {
+                const float w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (l4 + c <= i && l4 + c < bs) g[c] = w[c];
+                for (int c = 0; c < 4; ++c)
+                    if (l4 + c <= i && l4 + c < bs) g[c] = w[c];
+            }
         }
     }
     // D transposed, Dt[l][c] = D[c][l] (zero outside c < bs, l <= c): thread (c, half) reads rows of X as
-    // 16-byte vectors and writes four rows of Dt, each write coalesced over c
+    // 16-byte vectors and writes four rows of Dt, each write coalesced over c.  Groups of four rows
+    // wholly above the diagonal (l4 > c) are not written: the readers take them as zero
     {
         const int c = t & (DB - 1), h = t >> 7;
         const bool cin = c < bs;
 #pragma unroll 4
         for (int l4 = 4 * h; l4 < DB; l4 += 8) {
+            if (l4 > c) continue;
             const float4 v = ld4(X + c * AP + l4);
             D[(l4 + 0) * DB + c] = cin && l4 + 0 <= c ? v.x : 0.f;
             D[(l4 + 1) * DB + c] = cin && l4 + 1 <= c ? v.y : 0.f;
@@ -407,7 +426,8 @@ __global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t
 #pragma unroll 4
     for (int e4 = t; e4 < DB * DB / 4; e4 += 256) {
         const int l = (4 * e4) >> 7, c = (4 * e4) & (DB - 1);
-        *reinterpret_cast<float4*>(DT + l * DTP + c) = reinterpret_cast<const float4*>(Dt)[e4];
+        *reinterpret_cast<float4*>(DT + l * DTP + c) =
+            (l & ~3) > c ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(Dt)[e4];
     }
     __syncthreads();
     const int tr = t >> 4, tc = t & 15;
@@ -483,7 +503,8 @@ __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t 
 #pragma unroll 4
     for (int e4 = t; e4 < DB * DB / 4; e4 += 256) {
         const int l = (4 * e4) >> 7, i = (4 * e4) & (DB - 1);
-        *reinterpret_cast<float4*>(DT + l * DTP + i) = reinterpret_cast<const float4*>(Dt)[e4];
+        *reinterpret_cast<float4*>(DT + l * DTP + i) =
+            (l & ~3) > i ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(Dt)[e4];
     }
     __syncthreads();
     const int trow = t >> 4, tcol = t & 15;
@@ -791,7 +812,8 @@ static bool make_map(CUtensorMap* map, const __nv_bfloat16* A, int64_t rows)
 
 bool chol_tc_available() { return ctc::encoder(); }
 
-cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int64_t ld, int* d_info, int* d_err)
+cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int64_t ld, int* d_info, int* d_err,
+                                bool keep_L)
 {
     using namespace ctc;
     if (K <= 0) return cudaSuccess;
@@ -856,13 +878,15 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
         k_unit_diag<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(X, K, ld);
     }
     const unsigned grid_cap = (unsigned)ctx_sms(ctx);
+    // the bulk updates (stream B) may leave SMs free for the next steps' chain on stream A
+    const unsigned bulk_cap = (unsigned)std::max(1, ctx_sms(ctx) - (two ? ctx->opt.chol_reserve_sms : 0));
     auto tc_launch = [&](cudaStream_t s, int kid, bool lower, const CUtensorMap& a, const CUtensorMap& al,
                          const CUtensorMap& bm, const CUtensorMap& bl, const CUtensorMap& c, int cx0, int cy0,
                          int ra0, int rb0, int64_t tiles, int64_t tiles_n, double flops) -> cudaError_t {
         if (tiles <= 0) return cudaSuccess;
         LaunchTimer lt(ctx, kid, s);
         add_work(ctx, kid, flops);
-        const unsigned g = (unsigned)std::min<int64_t>(tiles, grid_cap);
+        const unsigned g = (unsigned)std::min<int64_t>(tiles, s == st ? grid_cap : bulk_cap);
         if (lower)
             k_tc_sub<true><<<g, SUB_THREADS, SUB_SMEM, s>>>(a, al, bm, bl, c, cx0, cy0, ra0, rb0, tiles, tiles_n,
                                                            DB / BKC, d_err);
@@ -887,7 +911,7 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
         {
             LaunchTimer lt(ctx, K_POTRF_DIAG);
             add_work(ctx, K_POTRF_DIAG, 2.0 * (double)bs * bs * bs / 3.0);
-            k_diag128<<<1, DIAG_THREADS, DIAG_SMEM, st>>>(G, ld, j0, bs, Dk[par], d_info);
+            k_diag128<<<1, DIAG_THREADS, DIAG_SMEM, st>>>(G, ld, j0, bs, Dk[par], d_info, keep_L ? 1 : 0);
         }
         if ((e = cudaGetLastError())) return e;
         const int64_t T = (m + BM - 1) / BM;

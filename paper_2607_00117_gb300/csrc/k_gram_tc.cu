@@ -42,7 +42,7 @@ constexpr uint32_t TMEM_COLS = 128;
 template <bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1) k_gram(const __grid_constant__ CUtensorMap map,
                                                      const __grid_constant__ CUtensorMap map_lo, int64_t K, int nk,
-                                                     float* __restrict__ C, int64_t ldc, int* err)
+                                                     float* __restrict__ C, int64_t ldc, int* err, int64_t t_off)
 {
     constexpr int STAGES = Cfg<SPLIT>::STAGES, STAGE_BYTES = Cfg<SPLIT>::STAGE_BYTES;
     extern __shared__ unsigned char smraw[];
@@ -54,8 +54,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_gram(const __grid_constant__ CUt
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-    // lower-triangular tile (ti >= tj) from the linear block index
-    const int64_t t = blockIdx.x;
+    // lower-triangular tile (ti >= tj) from the linear block index (tiles before t_off skipped)
+    const int64_t t = blockIdx.x + t_off;
     int64_t ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
     while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
     while (ti * (ti + 1) / 2 > t) --ti;
@@ -207,7 +207,7 @@ static bool make_map(CUtensorMap* map, const __nv_bfloat16* A, int64_t K, int64_
 }
 
 cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, const __nv_bfloat16* A_lo, int64_t K, int64_t ldA, float* C,
-                    int* d_err, int64_t ldc)
+                    int* d_err, int64_t ldc, int64_t row_tile0)
 {
     if (ldc <= 0) ldc = K;
     using namespace gtc;
@@ -229,16 +229,45 @@ cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, const __nv_bfloat16* A_
         attr[split] = true;
     }
     const int64_t T = (K + BM - 1) / BM;
-    const int64_t tiles = T * (T + 1) / 2;
+    if (row_tile0 < 0 || row_tile0 > T) return cudaErrorInvalidValue;
+    const int64_t t_off = row_tile0 * (row_tile0 + 1) / 2;
+    const int64_t tiles = T * (T + 1) / 2 - t_off;
+    if (tiles <= 0) return cudaSuccess;
     const int nk = (int)(ldA / BKC);
     LaunchTimer lt(ctx, K_GRAM_TC);
     add_work(ctx, K_GRAM_TC, 2.0 * (double)tiles * BM * BM * (double)ldA * (split ? 3.0 : 1.0));
     if (split)
         k_gram<true><<<(unsigned)tiles, THREADS, Cfg<true>::SMEM_BYTES, ctx_stream(ctx)>>>(map, map_lo, K, nk, C, ldc,
-                                                                                           d_err);
+                                                                                           d_err, t_off);
     else
         k_gram<false><<<(unsigned)tiles, THREADS, Cfg<false>::SMEM_BYTES, ctx_stream(ctx)>>>(map, map_lo, K, nk, C, ldc,
-                                                                                             d_err);
+                                                                                             d_err, t_off);
+    return cudaGetLastError();
+}
+
+// Retained block of a passive Gram gathered from the previous one (one thread per element of the
+// lower triangle, rows over blockIdx.y)
+__global__ void k_gather_gram(const float* __restrict__ Gc, int64_t ldc, const int64_t* __restrict__ cidx, int64_t r0,
+                              float* __restrict__ G, int64_t ldG)
+{
+    for (int64_t a = blockIdx.y; a < r0; a += gridDim.y) {
+        const int64_t ca = cidx[a];
+        for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= a; b += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t cb = cidx[b];
+            G[(size_t)a * ldG + b] = ca >= cb ? Gc[(size_t)ca * ldc + cb] : Gc[(size_t)cb * ldc + ca];
+        }
+    }
+}
+
+cudaError_t gather_gram(sw_ctx* ctx, const float* Gc, int64_t ldc, const int64_t* cidx, int64_t r0, float* G,
+                        int64_t ldG)
+{
+    if (r0 <= 0) return cudaSuccess;
+    LaunchTimer lt(ctx, K_MISC);
+    add_work(ctx, K_MISC, 8.0 * (double)r0 * (double)r0 / 2.0);
+    const unsigned gx = (unsigned)std::min<int64_t>((r0 + 255) / 256, 8);
+    const unsigned gy = (unsigned)std::min<int64_t>(r0, 65535);
+    k_gather_gram<<<dim3(gx, gy), 256, 0, ctx_stream(ctx)>>>(Gc, ldc, cidx, r0, G, ldG);
     return cudaGetLastError();
 }
 

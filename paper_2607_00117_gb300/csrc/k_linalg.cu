@@ -664,9 +664,7 @@ __global__ void __launch_bounds__(256) k_u_times_w_ff(const float* __restrict__ 
     }
 }
 
-// out[i] = sum_r U[i, r] x[r] with x split into (xh, xl); one warp per orbit.  VEC: each lane reads
-// four consecutive rows (16-byte loads), two such loads in flight
-template <bool VEC>
+// out[i] = sum_r U[i, r] x[r] with x split into (xh, xl); one warp per orbit
 __global__ void __launch_bounds__(256) k_ut_times_x_ff(const float* __restrict__ U, int64_t M, int64_t N,
                                                        const float* __restrict__ xh, const float* __restrict__ xl,
                                                        double* __restrict__ out)
@@ -677,51 +675,79 @@ __global__ void __launch_bounds__(256) k_ut_times_x_ff(const float* __restrict__
     for (int64_t i = warp; i < N; i += nwarp) {
         const float* col = U + (size_t)i * M;
         FF s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        if constexpr (VEC) {
-            int64_t r = 4 * lane;
-            for (; r + 128 + 3 < M; r += 256) {
-                const float4 u0 = *reinterpret_cast<const float4*>(col + r);
-                const float4 u1 = *reinterpret_cast<const float4*>(col + r + 128);
-                const float4 h0 = *reinterpret_cast<const float4*>(xh + r);
-                const float4 h1 = *reinterpret_cast<const float4*>(xh + r + 128);
-                const float4 l0 = *reinterpret_cast<const float4*>(xl + r);
-                const float4 l1 = *reinterpret_cast<const float4*>(xl + r + 128);
-                ff_acc(s[0], u0.x, h0.x, l0.x); ff_acc(s[1], u0.y, h0.y, l0.y);
-                ff_acc(s[2], u0.z, h0.z, l0.z); ff_acc(s[3], u0.w, h0.w, l0.w);
-                ff_acc(s[0], u1.x, h1.x, l1.x); ff_acc(s[1], u1.y, h1.y, l1.y);
-                ff_acc(s[2], u1.z, h1.z, l1.z); ff_acc(s[3], u1.w, h1.w, l1.w);
+        int64_t r = lane;
+        for (; r + 96 < M; r += 128) {
+            float u[4], h[4], l[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) ff_renorm(s[q]);
+            for (int q = 0; q < 4; ++q) {
+                u[q] = col[r + 32 * q];
+                h[q] = xh[r + 32 * q];
+                l[q] = xl[r + 32 * q];
             }
-            for (; r + 3 < M; r += 128) {
-                const float4 u0 = *reinterpret_cast<const float4*>(col + r);
-                const float4 h0 = *reinterpret_cast<const float4*>(xh + r);
-                const float4 l0 = *reinterpret_cast<const float4*>(xl + r);
-                ff_acc(s[0], u0.x, h0.x, l0.x); ff_acc(s[1], u0.y, h0.y, l0.y);
-                ff_acc(s[2], u0.z, h0.z, l0.z); ff_acc(s[3], u0.w, h0.w, l0.w);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) ff_renorm(s[q]);
+            for (int q = 0; q < 4; ++q) {
+                ff_acc(s[q], u[q], h[q], l[q]);
+                ff_renorm(s[q]);
             }
-        } else {
-            int64_t r = lane;
-            for (; r + 96 < M; r += 128) {
-                float u[4], h[4], l[4];
+        }
+        for (; r < M; r += 32) {
+            ff_acc(s[0], col[r], xh[r], xl[r]);
+            ff_renorm(s[0]);
+        }
+        double d = (ff_value(s[0]) + ff_value(s[1])) + (ff_value(s[2]) + ff_value(s[3]));
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    u[q] = col[r + 32 * q];
-                    h[q] = xh[r + 32 * q];
-                    l[q] = xl[r + 32 * q];
-                }
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) out[i] = d;
+    }
+}
+
+// The same with x staged in shared memory once per CTA (one persistent 1024-thread CTA per SM) and
+// each lane streaming four consecutive rows of its orbit's column per 16-byte load, four loads in
+// flight; M a multiple of 4, U 16-byte aligned, 8 M bytes of shared memory
+constexpr int UTX_THREADS = 1024;
+__global__ void __launch_bounds__(UTX_THREADS, 1) k_ut_times_x_ff_sm(const float* __restrict__ U, int64_t M, int64_t N,
+                                                                     const float* __restrict__ xh,
+                                                                     const float* __restrict__ xl,
+                                                                     double* __restrict__ out)
+{
+    extern __shared__ float4 utx_sm[];
+    float4* Xh = utx_sm;
+    float4* Xl = utx_sm + M / 4;
+    for (int64_t e = threadIdx.x; e < M / 4; e += UTX_THREADS) {
+        Xh[e] = reinterpret_cast<const float4*>(xh)[e];
+        Xl[e] = reinterpret_cast<const float4*>(xl)[e];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarp = (int64_t)gridDim.x * (UTX_THREADS / 32);
+    for (int64_t i = (int64_t)blockIdx.x * (UTX_THREADS / 32) + (threadIdx.x >> 5); i < N; i += nwarp) {
+        const float4* col = reinterpret_cast<const float4*>(U + (size_t)i * M);
+        FF s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        int64_t c = lane;   // 16-byte chunk of the column
+        const int64_t nch = M / 4;
+        for (; c + 96 < nch; c += 128) {
+            float4 u[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    ff_acc(s[q], u[q], h[q], l[q]);
-                    ff_renorm(s[q]);
-                }
+            for (int q = 0; q < 4; ++q) u[q] = col[c + 32 * q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 h = Xh[c + 32 * q], l = Xl[c + 32 * q];
+                ff_acc(s[0], u[q].x, h.x, l.x);
+                ff_acc(s[1], u[q].y, h.y, l.y);
+                ff_acc(s[2], u[q].z, h.z, l.z);
+                ff_acc(s[3], u[q].w, h.w, l.w);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) ff_renorm(s[k]);
             }
-            for (; r < M; r += 32) {
-                ff_acc(s[0], col[r], xh[r], xl[r]);
-                ff_renorm(s[0]);
-            }
+        }
+        for (; c < nch; c += 32) {
+            const float4 u = col[c], h = Xh[c], l = Xl[c];
+            ff_acc(s[0], u.x, h.x, l.x);
+            ff_acc(s[1], u.y, h.y, l.y);
+            ff_acc(s[2], u.z, h.z, l.z);
+            ff_acc(s[3], u.w, h.w, l.w);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ff_renorm(s[k]);
         }
         double d = (ff_value(s[0]) + ff_value(s[1])) + (ff_value(s[2]) + ff_value(s[3]));
 #pragma unroll
@@ -1249,13 +1275,22 @@ cudaError_t ut_times_x(sw_ctx* ctx, const T* U, int64_t M, int64_t N, const doub
         float *xh, *xl;
         cudaError_t e = split_ff(ctx, xs, M, &xh, &xl);
         if (e) return e;
-        const bool vec = M % 4 == 0 && ((uintptr_t)U & 15) == 0 && ((uintptr_t)xh & 15) == 0 && ((uintptr_t)xl & 15) == 0;
-        if (vec)
-            k_ut_times_x_ff<true><<<cap_grid(N * 32, 256, ctx_sms(ctx) * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xh, xl,
-                                                                                                        out);
+        const size_t smem = (size_t)M * 2 * sizeof(float);
+        const bool vec = M % 4 == 0 && ((uintptr_t)U & 15) == 0 && ((uintptr_t)xh & 15) == 0 &&
+                         ((uintptr_t)xl & 15) == 0 && smem <= 200 * 1024;
+        static size_t smem_set = 0;
+        if (vec && smem > smem_set) {
+            if (cudaFuncSetAttribute(k_ut_times_x_ff_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+                cudaSuccess)
+                smem_set = 200 * 1024;
+            else
+                cudaGetLastError();
+        }
+        if (vec && smem <= smem_set)
+            k_ut_times_x_ff_sm<<<(unsigned)std::min<int64_t>(ctx_sms(ctx), (N + 31) / 32), UTX_THREADS, smem,
+                                 ctx_stream(ctx)>>>(U, M, N, xh, xl, out);
         else
-            k_ut_times_x_ff<false><<<cap_grid(N * 32, 256, ctx_sms(ctx) * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xh,
-                                                                                                         xl, out);
+            k_ut_times_x_ff<<<cap_grid(N * 32, 256, ctx_sms(ctx) * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xh, xl, out);
     } else {
         k_ut_times_x<T><<<cap_grid(N * 32, 256, ctx_sms(ctx) * 64), 256, 0, ctx_stream(ctx)>>>(U, M, N, xs, out);
     }

@@ -238,10 +238,34 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     // the tensor-core factorisation wants 16-byte rows of G and X (TMA)
     const bool fact_tc = sizeof(GT) == 4 && ctx->opt.chol_tc && !ctx->opt.chol_coop && chol_tc_available();
     int64_t ldG = 0;   // leading dimension of the factored set's G and X
-    auto factor = [&](const std::vector<int64_t>& S, bool& ok) -> sw_status {
-        const int64_t nP = (int64_t)S.size();
+    // passive Grams kept between factorisations (tensor-core form): valid within this solve, and
+    // across the warm-started solves of one bootstrap (same matrix and errors)
+    const bool gcache = fact_tc && split;
+    if (!(warm && warm->start) || (int64_t)ws.gc_pos.size() != N) {
+        ws.gc_set.clear();
+        ws.gc_pos.assign(N, -1);
+    }
+    auto factor = [&](const std::vector<int64_t>& S_in, bool& ok) -> sw_status {
+        const int64_t nP = (int64_t)S_in.size();
         ldG = fact_tc ? (nP + 3) / 4 * 4 : nP;
         ok = false;
+        // with a kept Gram: the orbits it holds first (in its order), whole tile rows of them
+        // gathered from it, the rest (and the partial tile row) computed
+        std::vector<int64_t> S;
+        int64_t r0 = 0;
+        if (gcache && !ws.gc_set.empty()) {
+            S.reserve(nP);
+            std::vector<std::pair<int64_t, int64_t>> kept;
+            for (int64_t i : S_in)
+                if (ws.gc_pos[i] >= 0) kept.push_back({ws.gc_pos[i], i});
+            std::sort(kept.begin(), kept.end());
+            for (auto& kv : kept) S.push_back(kv.second);
+            for (int64_t i : S_in)
+                if (ws.gc_pos[i] < 0) S.push_back(i);
+            r0 = (int64_t)kept.size() / 128 * 128;
+        } else {
+            S = S_in;
+        }
         for (int64_t i : P0) pos[i] = -1;
         P0 = S;
         for (int64_t k = 0; k < nP; ++k) pos[S[k]] = k;
@@ -263,12 +287,42 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         AS_CUDA(ctx, (whiten<T, AT>(ctx, Uc, M, nP, V.inv_sig, V.sP, A, Alo, ldA, true)), "whiten");
         double fl = floor_ridge;
         int infoh = 1, gerrh = 0;
+        float* Gn = nullptr;   // the new kept Gram
+        if constexpr (sizeof(AT) == 2) {
+            if (gcache) {
+                const int nx = 1 - ws.gc_cur;
+                AS_TRY(ctx->ensure(&ws.Gc[nx], &ws.Gc_cap[nx], (size_t)nP * ldG * sizeof(float), "kept Gram"));
+                Gn = (float*)ws.Gc[nx];
+                if (r0 > 0) {
+                    std::vector<int64_t> ci(r0);
+                    for (int64_t k = 0; k < r0; ++k) ci[k] = ws.gc_pos[S[k]];
+                    AS_TRY(ctx->ensure(&ws.gcidx, &ws.gcidx_cap, (size_t)r0 * sizeof(int64_t), "kept Gram index"));
+                    AS_CUDA(ctx, cudaMemcpyAsync(ws.gcidx, ci.data(), r0 * sizeof(int64_t), cudaMemcpyHostToDevice, st),
+                            "kept Gram index");
+                    AS_CUDA(ctx, gather_gram(ctx, (const float*)ws.Gc[ws.gc_cur], ws.gc_ld, (const int64_t*)ws.gcidx, r0, Gn,
+                                             ldG),
+                            "kept Gram");
+                    // the host index list must outlive its copy
+                    AS_CUDA(ctx, cudaStreamSynchronize(st), "kept Gram");
+                }
+                AS_CUDA(ctx, gram_tc(ctx, A, Alo, nP, ldA, Gn, gerr, ldG, r0 / 128), "reduced Gram");
+                for (int64_t i : ws.gc_set) ws.gc_pos[i] = -1;
+                ws.gc_set = S;
+                for (int64_t k = 0; k < nP; ++k) ws.gc_pos[S[k]] = k;
+                ws.gc_cur = nx;
+                ws.gc_ld = ldG;
+            }
+        }
         for (int attempt = 0; attempt < 4 && infoh != 0; ++attempt, fl *= 100.0) {
             for (int64_t k = 0; k < nP; ++k) rh[k] = std::max(mu * sh[k] * sh[k], fl);
             AS_CUDA(ctx, cudaMemcpyAsync(V.ridge, rh.data(), nP * sizeof(double), cudaMemcpyHostToDevice, st), "ridge");
             AS_CUDA(ctx, cudaMemsetAsync(info, 0, sizeof(int), st), "memset");
             if constexpr (sizeof(AT) == 2) {
-                AS_CUDA(ctx, gram_tc(ctx, A, Alo, nP, ldA, (float*)G, gerr, ldG), "reduced Gram");
+                if (Gn)
+                    AS_CUDA(ctx, cudaMemcpyAsync(G, Gn, (size_t)nP * ldG * sizeof(float), cudaMemcpyDeviceToDevice, st),
+                            "reduced Gram");
+                else
+                    AS_CUDA(ctx, gram_tc(ctx, A, Alo, nP, ldA, (float*)G, gerr, ldG), "reduced Gram");
             } else {
                 AS_CUDA(ctx, (gemm<GT, true, true>(ctx, K_GRAM_SIMT, nP, nP, ldA, GT(1), (const GT*)A, ldA,
                                                    (const GT*)A, ldA, GT(0), G, ldG, 0)),
@@ -281,7 +335,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
                                                 : cudaErrorNotSupported;
             if constexpr (sizeof(GT) == 4) {
                 if (ce == cudaErrorNotSupported && fact_tc)
-                    ce = cholesky_inverse_tc(ctx, (float*)G, (float*)ws.X, nP, ldG, info, gerr);
+                    ce = cholesky_inverse_tc(ctx, (float*)G, (float*)ws.X, nP, ldG, info, gerr, false);
             }
             if (ce == cudaErrorNotSupported) {
                 cudaGetLastError();

@@ -36,6 +36,7 @@ struct Options {
     int chol_coop = 0;           // Cholesky + inverse in one cooperative launch (0: per-step launches)
     int chol_tc = 1;             // FP32 Cholesky + inverse with tcgen05 trailing updates (0: SIMT, 64-wide)
     int chol_lookahead = 1;      // tensor-core factorisation: bulk updates on a second stream (1) or in line (0)
+    int chol_reserve_sms = 0;    // tensor-core factorisation: SMs the bulk updates leave to the next steps' chain
     int project_bundle = 1;      // orbits per column of sw_project's matrix (bundles accumulated at bin time)
     int matrix_cache = 1;        // keep freed matrix buffers for reuse by the next matrices of this context
     int integrator = 0;          // 0: kick-drift-kick at fixed dt; 1: adaptive Bogacki-Shampine 3(2) in the bar frame
@@ -62,9 +63,17 @@ struct SolveWS {
     void* Hi = nullptr; size_t Hi_cap = 0;        // polish: inverse of its Cholesky factor
     void* pv = nullptr; size_t pv_cap = 0;        // polish: index list and vectors
     void* boot = nullptr; size_t boot_cap = 0;    // bootstrap solves: realisation data and vectors
+    // the last passive Gram of the active set (scaled, before the ridge), kept so that the next
+    // passive set recomputes only the tile rows of its entering orbits: two buffers (the last and
+    // the next), the orbits in the last one's order and each orbit's position in it
+    void* Gc[2] = {nullptr, nullptr}; size_t Gc_cap[2] = {0, 0};
+    void* gcidx = nullptr; size_t gcidx_cap = 0;
+    int gc_cur = 0;
+    int64_t gc_ld = 0;
+    std::vector<int64_t> gc_set, gc_pos;
     const sw_matrix* A_of = nullptr;              // which matrix A was built from
     void release();
-    void forget_matrix(const sw_matrix* U) { if (A_of == U) A_of = nullptr; }
+    void forget_matrix(const sw_matrix* U) { if (A_of == U) A_of = nullptr; gc_set.clear(); }
 };
 
 struct LaunchRec {

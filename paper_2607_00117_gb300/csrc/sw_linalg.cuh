@@ -29,8 +29,10 @@ cudaError_t cholesky_inverse(sw_ctx* ctx, T* G, T* X, T* D, int64_t K, int* d_in
 // FP32 Cholesky (in place) and X = L^{-1} in 128-wide steps with the trailing and inverse updates on
 // the tensor cores (k_chol_tc.cu); cudaErrorNotSupported without the tensor-map encoder; *d_err != 0 if
 // a bounded wait of a tensor-core kernel ran out
-// G and X are K x K with leading dimension ld, a multiple of 4 (16-byte rows for the TMA)
-cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int64_t ld, int* d_info, int* d_err);
+// G and X are K x K with leading dimension ld, a multiple of 4 (16-byte rows for the TMA).  Without
+// keep_L the diagonal blocks of L are not written back (G then holds only the panels below them).
+cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int64_t ld, int* d_info, int* d_err,
+                                bool keep_L = true);
 bool chol_tc_available();
 template <typename T>
 cudaError_t symmetrize(sw_ctx* ctx, const T* G, int64_t K, T* S);
@@ -97,7 +99,7 @@ struct AsWarm {
     bool record = false, start = false;
     std::vector<char> F0;        // passive set of the recorded solve (N flags)
     std::vector<double> w0;      // its weights (N)
-    std::vector<int64_t> P0;     // the factored set (ascending)
+    std::vector<int64_t> P0;     // the factored set, in the order of its factor
     int64_t ld = 0;              // leading dimension of its G and X
     bool have_factor = false;
     double p0_extra = 0.15;      // P0 = F0 plus up to this fraction of |F0| near-active orbits
@@ -119,9 +121,13 @@ sw_status solve_bootstrap(sw_ctx* ctx, const sw_matrix* U, const double* y_dev, 
 // tcgen05 Gram (k_gram_tc.cu): C (K x K, FP32, row-major, lower tiles) = A A^T with A
 // K x ldA BF16 row-major (ldA a multiple of 64, columns beyond the data zero).  With
 // A_lo non-NULL the operand is A + A_lo and the three leading products of the split
-// are accumulated.  d_err receives a non-zero code if a bounded wait ran out.
+// are accumulated.  d_err receives a non-zero code if a bounded wait ran out.  row_tile0 > 0
+// computes only the tile rows from row_tile0 on (rows 128 row_tile0 .. K - 1 of the lower part).
 cudaError_t gram_tc(sw_ctx* ctx, const __nv_bfloat16* A, const __nv_bfloat16* A_lo, int64_t K, int64_t ldA, float* C,
-                    int* d_err, int64_t ldc = 0);
+                    int* d_err, int64_t ldc = 0, int64_t row_tile0 = 0);
+// G[a][b] = Gc[cidx[a]][cidx[b]] (Gc lower-triangular, read symmetrically) for b <= a < r0
+cudaError_t gather_gram(sw_ctx* ctx, const float* Gc, int64_t ldc, const int64_t* cidx, int64_t r0, float* G,
+                        int64_t ldG);
 bool gram_tc_available();
 
 }  // namespace sw
