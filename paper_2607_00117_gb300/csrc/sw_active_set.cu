@@ -514,11 +514,14 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     // merit: objective of the projection max(x, 0) of each iterate; the best is kept
     std::vector<double> zbest(N, 0.0);
     double fproj = 0.0, fbest = 0.0;
+    // reference of the damping test: the best objective since the candidate set last grew (a wider
+    // candidate set starts from a worse passive set than the optimum on the narrower one)
+    double fref = 0.0;
     {
         double f0 = 0.0;
         AS_TRY(evaluate());
         f0 = chi_h[0];
-        fbest = fproj = f0;
+        fbest = fproj = fref = f0;
     }
     // the factor of P0 serves every passive set inside it (the orbits of P0 \ F masked)
     auto factored_covers = [&](const std::vector<int64_t>& S) {
@@ -564,6 +567,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     }
     for (; outer < 1000000 && n_solves < ctx->opt.as_solves; ++outer) {
         std::vector<std::pair<double, int64_t>> neg, enter;   // (violation, orbit)
+        bool widened = false;
         for (int64_t i : F)
             if (zh[i] < 0.0) neg.push_back({-zh[i] * std::sqrt(hh[i]), i});
         for (int64_t i = 0; i < N; ++i)
@@ -584,6 +588,8 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             }
             nC += kc;
             best_nv = N + 1;
+            fref = HUGE_VAL;
+            widened = kc > 0;
             frac = 1.0;
             if (ctx->opt.verbose && kc)
                 fprintf(stderr, "[sw] candidate set widened by %lld to %lld orbits\n", (long long)kc, (long long)nC);
@@ -597,9 +603,10 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         if (nv == 0) { converged = true; break; }
         const int64_t lim = std::max<int64_t>(block, (int64_t)(ctx->opt.as_grow * (double)F.size()));
         if (outer > 0) {
-            if (fproj < fbest * (1.0 - 1e-13) || nv < best_nv) frac = 1.0;
+            if (fproj < fref * (1.0 - 1e-13) || nv < best_nv) frac = 1.0;
             else frac *= 0.5;
             best_nv = std::min(best_nv, nv);
+            if (!widened) fref = std::min(fref, fproj);   // fproj is still the narrower set's
         }
         auto by_violation = [](const std::pair<double, int64_t>& a, const std::pair<double, int64_t>& b) {
             return a.first > b.first;
