@@ -304,8 +304,10 @@ int64_t sw_alloc_count(const sw_ctx* ctx);
  *                           allocation failure, or by setting 0) instead of returning it to the driver (default 1)
  *  "chol_tc" (0/1)          active set, FP32 form: Cholesky and its inverse in 128-wide steps with the trailing and
  *                           inverse updates on the tensor cores (BF16 hi + lo split, default 1); 0: FP32 SIMT updates
+ *  "chol_pdl" (0/1)         tensor-core factorisation: each panel kernel launched programmatically behind its
+ *                           diagonal-block kernel, staging its rows while that block is factored (default 1)
  *  "chol_reserve_sms" (>= 0) tensor-core factorisation: SMs that the bulk trailing and inverse updates leave free
- *                           for the next steps' diagonal-block chain on the context's stream (default 0)
+ *                           for the next steps' diagonal-block chain on the context's stream (default 8)
  *  "integrator" (0/1)       sw_project's integrator: 0 (default) kick-drift-kick at the fixed dt in the inertial
  *                           frame; 1 the paper's adaptive Bogacki-Shampine 3(2) pair (Sec. 2.2.2) in the frame
  *                           rotating with the bar, nsteps accepted steps from a first trial step dt, each sample

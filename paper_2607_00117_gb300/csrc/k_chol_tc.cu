@@ -193,6 +193,9 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
     float* Tb = CT + SB * CTP;      // 2 x TBUF: the sums T_j of an inverse block row, by parity of r
     float* RR = Tb + 2 * TBUF;      // SB: 1 / L_jj of the current sub-block
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    // the panel kernel that follows may start now: it stages its rows of A (final before this
+    // kernel began) and waits for this grid's D before reading it
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // ---- load the lower triangle (16-byte chunks that reach it; the rest of A is never read), all
     // in flight; rows beyond bs are the identity; X = 0
     {
@@ -423,6 +426,9 @@ __global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t
         const int64_t gi = row0 + i;
         As[i * LP + l] = gi < m ? G[(size_t)(r0 + gi) * ld + j0 + l] : 0.f;
     }
+    // D comes from the diagonal-block kernel just before this one (a no-op without a programmatic
+    // launch)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll 4
     for (int e4 = t; e4 < DB * DB / 4; e4 += 256) {
         const int l = (4 * e4) >> 7, c = (4 * e4) & (DB - 1);
@@ -919,8 +925,19 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
             {
                 LaunchTimer lt(ctx, K_TRSM_PANEL);
                 add_work(ctx, K_TRSM_PANEL, (double)m * DB * DB);
-                k_panel128<<<(unsigned)((m + PR - 1) / PR), 256, PANEL_SMEM, st>>>(G, ld, j0, r0, m, Dk[par],
-                                                                                   Ph[par], Pl[par]);
+                // launched programmatically behind the diagonal block: its row staging overlaps it
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)((m + PR - 1) / PR));
+                cfg.blockDim = dim3(256);
+                cfg.dynamicSmemBytes = PANEL_SMEM;
+                cfg.stream = st;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                at[0].val.programmaticStreamSerializationAllowed = ctx->opt.chol_pdl ? 1 : 0;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                e = cudaLaunchKernelEx(&cfg, k_panel128, G, ld, j0, r0, m, (const float*)Dk[par], Ph[par], Pl[par]);
+                if (e) return e;
             }
             if ((e = cudaGetLastError())) return e;
         }

@@ -36,7 +36,8 @@ struct Options {
     int chol_coop = 0;           // Cholesky + inverse in one cooperative launch (0: per-step launches)
     int chol_tc = 1;             // FP32 Cholesky + inverse with tcgen05 trailing updates (0: SIMT, 64-wide)
     int chol_lookahead = 1;      // tensor-core factorisation: bulk updates on a second stream (1) or in line (0)
-    int chol_reserve_sms = 0;    // tensor-core factorisation: SMs the bulk updates leave to the next steps' chain
+    int chol_reserve_sms = 8;    // tensor-core factorisation: SMs the bulk updates leave to the next steps' chain
+    int chol_pdl = 1;            // tensor-core factorisation: panel launched programmatically behind its diagonal block
     int project_bundle = 1;      // orbits per column of sw_project's matrix (bundles accumulated at bin time)
     int matrix_cache = 1;        // keep freed matrix buffers for reuse by the next matrices of this context
     int integrator = 0;          // 0: kick-drift-kick at fixed dt; 1: adaptive Bogacki-Shampine 3(2) in the bar frame

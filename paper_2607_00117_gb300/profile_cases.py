@@ -1,9 +1,10 @@
 """Single-kernel cases for profiler captures: each runs one part of the path through the C-ABI on
 seeded synthetic inputs, small enough for a multi-pass capture (a few GB on the device at most).
 
-    python -m paper_2607_00117_gb300.profile_cases orbit --grid axisym_2k --n-orb 100000 --nsteps 64
-        integrate + project a library (the fused orbit kernel, its finalize pass) on a workload's
-        grid and potential, without the weight solve
+    python -m paper_2607_00117_gb300.profile_cases orbit --grid axisym_2k --potential barred_100k \
+        --n-orb 100000 --nsteps 64
+        integrate + project a library (the fused orbit kernel, its finalize pass) on one workload's
+        grid in another's potential (and pattern speed), without the weight solve
     python -m paper_2607_00117_gb300.profile_cases factor --k 4096 --mode 0
         the active set's preconditioner factorisation (sw_factor_preconditioner) of a shifted,
         Jacobi-scaled passive Gram with near-duplicate column pairs
@@ -31,13 +32,16 @@ def _passive_gram(K: int, seed: int) -> np.ndarray:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["orbit", "factor"])
-    ap.add_argument("--grid", default="axisym_2k", choices=list(inputs.WORKLOADS.keys() - {"batched_64"}))
+    names = sorted(inputs.WORKLOADS.keys() - {"batched_64"})
+    ap.add_argument("--grid", default="axisym_2k", choices=names)
+    ap.add_argument("--potential", default=None, choices=names, help="default: the grid's workload")
     ap.add_argument("--n-orb", type=int, default=100_000)
     ap.add_argument("--nsteps", type=int, default=64)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--k", type=int, default=4096)
     ap.add_argument("--mode", type=int, default=0)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--bundle", type=int, default=1, help="orbit case: orbits per column (bundles at bin time)")
     args = ap.parse_args()
 
     import torch
@@ -50,20 +54,23 @@ def main():
     times = []
     if args.case == "orbit":
         W = inputs.WORKLOADS[args.grid]
-        ctx.set_potential(W["potential"])
+        P = inputs.WORKLOADS[args.potential or args.grid]
+        ctx.set_potential(P["potential"])
+        ctx.set_option("project_bundle", args.bundle)
         ics = inputs.disc_ics(inputs.DISC_HALO, args.n_orb, seed=W["seeds"]["ic"])
         ics_d = torch.from_numpy(ics).to(dev)
         for rep in range(args.reps + 1):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.integrate_library_device(ics_d, W["omega_p"], W["dt"], args.nsteps)
+            ctx.integrate_library_device(ics_d, P["omega_p"], W["dt"], args.nsteps)
             U = ctx.project(dict(W["grid"], gh=0))
             e1.record(stream)
             torch.cuda.synchronize()
             U.free()
             if rep:
                 times.append(e0.elapsed_time(e1))
-        print(json.dumps({"case": "orbit", "grid": args.grid, "n_orb": args.n_orb, "nsteps": args.nsteps,
+        print(json.dumps({"case": "orbit", "grid": args.grid, "potential": args.potential or args.grid,
+                          "n_orb": args.n_orb, "bundle": args.bundle, "nsteps": args.nsteps,
                           "rows": inputs.rows_of(dict(W["grid"], gh=0)), "ms": times}))
     else:
         G = _passive_gram(args.k, 7000 + args.k)

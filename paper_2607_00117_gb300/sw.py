@@ -297,6 +297,7 @@ class Context:
         self.handle = h.value
         self.precision = precision
         self.device = device
+        self.last_status = SW_OK   # status of the last solve_weights call
 
     def _check(self, st: int) -> int:
         if st not in (SW_OK,):
@@ -389,6 +390,7 @@ class Context:
         errors = np.ascontiguousarray(errors, dtype=np.float64)
         w = np.empty(U.N); chi2 = np.empty(3)
         st = lib().sw_solve_weights(self.handle, U.handle, _dp(data), _dp(errors), lam, _dp(w), _dp(chi2))
+        self.last_status = st
         if not (allow_nonconv and st == SW_ENONCONV):
             self._check(st)
         return w, chi2
