@@ -191,19 +191,20 @@ def make_data(sw, torch, W, rank, n_mock=N_MOCK):
 # ---------------------------------------------------------------------------
 # algorithmic work per unit for the roofline of the dominant kernel
 # ---------------------------------------------------------------------------
-# lane-instructions executed per orbit-step by the fused orbit kernel (FP32 form, barred potential,
-# histogram rows, four mirror copies): smsp__inst_executed x threads per instruction / orbit-steps from
-# the ncu capture in profiles/orbit_kernel_fp32_barred.md
-OPS_PER_ORBIT_STEP = 891.0
+# lane-instructions executed per orbit-step by the fused orbit kernel (FP32 form, barred potential, the
+# benchmark's histogram grid, bundles of four accumulated at bin time): smsp__inst_executed x threads per
+# instruction / orbit-steps from the ncu capture in profiles/orbit_kernel_fp32_barred.md
+OPS_PER_ORBIT_STEP = 915.0
 # arithmetic operations of the method per orbit-step, counted from the kernel's formulas: kick-drift-kick
 # with Kahan compensation ~45, the disc + NFW + Long-Murali force ~155 (correctly rounded divisions and
 # square roots counted as one operation each), rotation, mirrors, projection and binning of 4 copies ~170
 ALG_OPS_PER_ORBIT_STEP = 370.0
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel from an ncu capture of the kernel as it
-# stands (null until a capture of the current kernel exists)
-NCU_TRAFFIC_PER_LAUNCH = {}
+# DRAM bytes (read + write) per launch of the dominant kernel from a one-pass ncu capture of the
+# benchmark's own launch (profiles/orbit_kernel_fp32_barred.md); a kernel without a capture of its
+# current form reports null
+NCU_TRAFFIC_PER_LAUNCH = {"orbit_project_bin": 37004726528 + 28198813440}
 
 # kernels launched as a single CTA (a chain of dependent launches): their roofline also
 # states the fraction of one SM's FP32 peak, the most one launch can reach
@@ -509,7 +510,9 @@ def run_sw(args):
     dom = max(kstats, key=lambda k: kstats[k]["ms"])
     sm_mhz = clk["sm_mhz"] if clk else sm_max
     roof = roofline_entry(dom, kstats, hbm, bf16_sus, sm_mhz, n_sm)
-    roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(dom), "peak_source": peak_src,
+    traffic = NCU_TRAFFIC_PER_LAUNCH.get(dom) if (N, S) == (100_000, 10_000) else None
+    roof.update({"kernel": dom, "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu)",
+                 "peak_source": peak_src,
                  "ms_per_launch": kstats[dom]["ms"] / kstats[dom]["launches"],
                  "launch_times": f"CUDA events around each launch on the context's stream, {n_prof} profiled "
                                  f"steps after the timed region"})
@@ -700,7 +703,7 @@ def run_large(args):
     sm_mhz = clk["sm_mhz"] if clk else sm_max
     dom = max(kstats, key=lambda k: kstats[k]["ms"])
     roof = roofline_entry(dom, kstats, hbm, bf16_sus, sm_mhz, n_sm)
-    roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(dom), "peak_source": peak_src})
+    roof.update({"kernel": dom, "traffic": None, "peak_source": peak_src})
     line = {"metric": "orbit-steps/s (whole model evaluations, FP32 batched vs FP64 plain at matched chi^2)",
             "value": N * S * args.steps * world / elapsed, "unit": "orbit-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": 1e3 * elapsed / args.steps,
@@ -802,7 +805,7 @@ def run_batched(args):
     sm_mhz = clk["sm_mhz"] if clk else sm_max
     dom = max(kstats, key=lambda k: kstats[k]["ms"])
     roof = roofline_entry(dom, kstats, hbm, bf16_sus, sm_mhz, torch.cuda.get_device_properties(local).multi_processor_count)
-    roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(dom), "peak_source": peak_src})
+    roof.update({"kernel": dom, "traffic": None, "peak_source": peak_src})
     bo = kstats.get("batch_orbit_bin", {"ms": float("nan")})
     line = {"metric": "orbit-steps/s (whole model evaluations, FP32 batched vs FP64 plain at matched chi^2)",
             "value": ntot * S * args.steps / elapsed, "unit": "orbit-steps/s", "n_gpus": world, "steps": args.steps,

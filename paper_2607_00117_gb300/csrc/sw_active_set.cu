@@ -603,7 +603,10 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         if (nv == 0) { converged = true; break; }
         const int64_t lim = std::max<int64_t>(block, (int64_t)(ctx->opt.as_grow * (double)F.size()));
         if (outer > 0) {
-            if (fproj < fref * (1.0 - 1e-13) || nv < best_nv) frac = 1.0;
+            // damped exchanges: halve the fraction when neither the objective nor the violation count
+            // improved, and let it recover only gradually (x4 per improving step), so that a degenerate
+            // problem does not alternate between full and damped exchanges
+            if (fproj < fref * (1.0 - 1e-13) || nv < best_nv) frac = std::min(1.0, 4.0 * frac);
             else frac *= 0.5;
             best_nv = std::min(best_nv, nv);
             if (!widened) fref = std::min(fref, fproj);   // fproj is still the narrower set's
