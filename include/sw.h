@@ -304,6 +304,9 @@ int64_t sw_alloc_count(const sw_ctx* ctx);
  *                           allocation failure, or by setting 0) instead of returning it to the driver (default 1)
  *  "chol_tc" (0/1)          active set, FP32 form: Cholesky and its inverse in 128-wide steps with the trailing and
  *                           inverse updates on the tensor cores (BF16 hi + lo split, default 1); 0: FP32 SIMT updates
+ *  "boot_p0_extra" (0 .. 4) sw_solve_bootstrap: the factor kept for the realisations covers the plain solve's
+ *                           support plus this fraction of it in near-active orbits (default 0: a wider factored set
+ *                           serves more passive sets but preconditions the masked solves worse)
  *  "chol_pdl" (0/1)         tensor-core factorisation: each panel kernel launched programmatically behind its
  *                           diagonal-block kernel, staging its rows while that block is factored (default 1)
  *  "chol_reserve_sms" (>= 0) tensor-core factorisation: SMs that the bulk trailing and inverse updates leave free

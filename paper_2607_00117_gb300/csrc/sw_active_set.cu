@@ -761,6 +761,7 @@ sw_status solve_bootstrap(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev,
     AS_CUDA(ctx, cudaMemsetAsync(chi, 0, 8 * sizeof(double), st), "memset");
     AS_CUDA(ctx, prep_data(ctx, M, sig_dev, y_dev, inv_sig, ys, bad), "prep data");
     AsWarm warm;
+    warm.p0_extra = ctx->opt.boot_p0_extra;
     warm.record = true;
     sw_status worst = solve_active_set<T, AT, GT>(ctx, Um, y_dev, sig_dev, lam, wb, chi, &warm);
     if (worst != SW_OK && worst != SW_ENONCONV) return worst;

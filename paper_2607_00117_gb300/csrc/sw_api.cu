@@ -1090,6 +1090,9 @@ extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value)
     } else if (!strcmp(key, "project_bundle")) {
         if (!(value >= 1.0 && value <= 1024.0 && value == std::floor(value))) return SW_EINVAL;
         ctx->opt.project_bundle = (int)value;
+    } else if (!strcmp(key, "boot_p0_extra")) {
+        if (!(value >= 0.0 && value <= 4.0)) return SW_EINVAL;
+        ctx->opt.boot_p0_extra = value;
     } else if (!strcmp(key, "chol_pdl")) {
         if (!(value == 0 || value == 1)) return SW_EINVAL;
         ctx->opt.chol_pdl = (int)value;

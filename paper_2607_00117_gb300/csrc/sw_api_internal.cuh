@@ -37,6 +37,7 @@ struct Options {
     int chol_tc = 1;             // FP32 Cholesky + inverse with tcgen05 trailing updates (0: SIMT, 64-wide)
     int chol_lookahead = 1;      // tensor-core factorisation: bulk updates on a second stream (1) or in line (0)
     int chol_reserve_sms = 8;    // tensor-core factorisation: SMs the bulk updates leave to the next steps' chain
+    double boot_p0_extra = 0.0;  // bootstrap: factored set = the plain solve's support plus this fraction of near-active orbits
     int chol_pdl = 1;            // tensor-core factorisation: panel launched programmatically behind its diagonal block
     int project_bundle = 1;      // orbits per column of sw_project's matrix (bundles accumulated at bin time)
     int matrix_cache = 1;        // keep freed matrix buffers for reuse by the next matrices of this context

@@ -102,7 +102,7 @@ struct AsWarm {
     std::vector<int64_t> P0;     // the factored set, in the order of its factor
     int64_t ld = 0;              // leading dimension of its G and X
     bool have_factor = false;
-    double p0_extra = 0.15;      // P0 = F0 plus up to this fraction of |F0| near-active orbits
+    double p0_extra = 0.0;       // P0 = F0 plus up to this fraction of |F0| near-active orbits
     int64_t factorisations = 0;  // factorisations made by the solves of this warm start
 };
 
