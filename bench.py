@@ -199,6 +199,12 @@ OPS_PER_ORBIT_STEP = 915.0
 # with Kahan compensation ~45, the disc + NFW + Long-Murali force ~155 (correctly rounded divisions and
 # square roots counted as one operation each), rotation, mirrors, projection and binning of 4 copies ~170
 ALG_OPS_PER_ORBIT_STEP = 370.0
+# the paper's adaptive integrator (k_orbit_bs3, FP32, barred potential): lane-instructions executed per
+# accepted orbit-step, rejected trials included (ncu capture in profiles/orbit_kernel_fp32_barred.md), and
+# the method's arithmetic per accepted step: three force evaluations (3 x 155), the stage combinations,
+# embedded error and step control (~90) and the step-weighted binning of 4 copies (~170)
+OPS_PER_BS3_STEP = 1897.0
+ALG_OPS_PER_BS3_STEP = 725.0
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel from a one-pass ncu capture of the
@@ -603,9 +609,18 @@ def bs3_leg(sw, torch, W, ics_d, stream, local, n_sm, sm_mhz, nsteps=5000):
     ko = ks.get("orbit_project_bin", {"ms": float("nan")})
     _, status = c.project_stats(n)
     c.close()
+    rate = n * nsteps / (ko["ms"] / 1e3)          # accepted orbit-steps/s of the orbit kernel
+    peak = n_sm * FP32_LANES * sm_mhz * 1e6 / 1e12  # T lane-instructions / s
     return {"orbits": int(n), "accepted_steps": nsteps, "seconds": t,
             "orbit_steps_per_s": n * nsteps / t,
             "orbit_kernel_ms": ko["ms"], "kept_orbits": int((status == 0).sum()),
+            "roofline": {"bound": "alu", "kernel": "orbit_project_bin (k_orbit_bs3)",
+                         "achieved": OPS_PER_BS3_STEP * rate / 1e12, "peak": peak, "unit": "T lane-instructions/s",
+                         "frac": OPS_PER_BS3_STEP * rate / 1e12 / peak,
+                         "algorithmic_frac": ALG_OPS_PER_BS3_STEP * rate / 1e12 / peak,
+                         "note": f"frac counts the {OPS_PER_BS3_STEP:.0f} lane-instructions executed per accepted "
+                                 f"orbit-step (rejected trials included); algorithmic_frac the "
+                                 f"{ALG_OPS_PER_BS3_STEP:.0f} arithmetic operations of an accepted step"},
             "note": "three force evaluations per accepted step (the fourth stage is the next step's first) "
                     "plus three per rejected trial"}
 

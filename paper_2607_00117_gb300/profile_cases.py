@@ -42,6 +42,7 @@ def main():
     ap.add_argument("--mode", type=int, default=0)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--bundle", type=int, default=1, help="orbit case: orbits per column (bundles at bin time)")
+    ap.add_argument("--integrator", type=int, default=0, help="orbit case: 0 kick-drift-kick, 1 the adaptive pair")
     args = ap.parse_args()
 
     import torch
@@ -57,6 +58,7 @@ def main():
         P = inputs.WORKLOADS[args.potential or args.grid]
         ctx.set_potential(P["potential"])
         ctx.set_option("project_bundle", args.bundle)
+        ctx.set_option("integrator", args.integrator)
         ics = inputs.disc_ics(inputs.DISC_HALO, args.n_orb, seed=W["seeds"]["ic"])
         ics_d = torch.from_numpy(ics).to(dev)
         for rep in range(args.reps + 1):
@@ -70,7 +72,8 @@ def main():
             if rep:
                 times.append(e0.elapsed_time(e1))
         print(json.dumps({"case": "orbit", "grid": args.grid, "potential": args.potential or args.grid,
-                          "n_orb": args.n_orb, "bundle": args.bundle, "nsteps": args.nsteps,
+                          "n_orb": args.n_orb, "bundle": args.bundle, "integrator": args.integrator,
+                          "nsteps": args.nsteps,
                           "rows": inputs.rows_of(dict(W["grid"], gh=0)), "ms": times}))
     else:
         G = _passive_gram(args.k, 7000 + args.k)
