@@ -315,21 +315,6 @@ def matched_leg(sw, torch, reps=3, n_seeds=8):
 # ---------------------------------------------------------------------------
 # the oracle arm (CPU, FP64)
 # ---------------------------------------------------------------------------
-def cpu_sample(W, n_orb=N_CPU_SAMPLE):
-    import oracle
-    pot = oracle.make_pot(W["potential"])
-    obs = oracle.make_obs(W["grid"])
-    ics = inputs.disc_ics(W["potential"], n_orb, seed=W["seeds"]["ic"])
-    cores = oracle.max_threads()
-    t0 = time.perf_counter()
-    U, _, _ = oracle.build_matrix(pot, W["omega_p"], W["dt"], W["nsteps"], ics, obs)
-    dt = time.perf_counter() - t0
-    value = n_orb * W["nsteps"] / dt
-    sample = (f"{n_orb} orbits x {W['nsteps']} steps of {WORKLOAD} (integrate + project + bin into the "
-              f"{U.shape[1]}-row matrix, FP64, OpenMP); the weight solve is not in the sample")
-    return value, cores, sample, dt
-
-
 def cpu_single_thread(W, n_orb=64):
     """The same oracle work on one host thread (orbit-steps/s), beside the all-core figure."""
     import oracle
@@ -346,26 +331,67 @@ def cpu_single_thread(W, n_orb=64):
         oracle.set_threads(cores)
 
 
+def reference_model(W, n_orb, data=None):
+    """One whole model evaluation by the oracle on a bounded sample of the workload: n_orb orbits (n_orb / 4
+    bundles of four dithered initial conditions) integrated, projected and binned into the histogram rows,
+    the quality cut, the bundles, the Gauss-Hermite rows and the exact weight solve (whitening, normal
+    equations, Lawson-Hanson).  Without data, builds the sample's own mock data (true weights + noise) and
+    returns it with the evaluation's time."""
+    import oracle
+    grid = W["grid"]
+    pot = oracle.make_pot(W["potential"])
+    obs = oracle.make_obs(grid)
+    nb = W.get("bundle", 1)
+    base = inputs.workload_ics(W["potential"], n_orb // nb, W["seeds"]["ic"], W.get("ics", "disc"))
+    ics = inputs.dither(base, nb, W["seeds"]["dither"], W["potential"]) if nb > 1 else base
+    nd = grid["nR"] * grid["nphi"] * grid["nz"]
+    npix = grid["nx"] * grid["ny"]
+    t0 = time.perf_counter()
+    U, _, status = oracle.build_matrix(pot, W["omega_p"], W["dt"], W["nsteps"], ics, obs)
+    U[status != 0] = 0.0
+    Ub = oracle.bundle(U, nb) if nb > 1 else U
+    if data is None:
+        wt = inputs.true_weights(Ub.shape[0], W["seeds"]["w"])
+        v0s, gh_err = inputs.gh_reference(pixel_moments_from_hist(Ub.T @ wt, grid))
+        Ug = oracle.reduce_gh(Ub, nd, npix, grid["nv"], -grid["vmax"], 2 * grid["vmax"] / grid["nv"], v0s)
+        rows = Ug.T.copy()
+        y0 = rows @ wt
+        blocks = inputs.row_blocks(dict(grid, gh=1))
+        sig = inputs.mock_sigma(y0, blocks, gh_err=gh_err)
+        y = y0 + sig * inputs.noise(len(y0), W["seeds"]["noise"])
+        return (v0s, y, sig), time.perf_counter() - t0
+    v0s, y, sig = data
+    Ug = oracle.reduce_gh(Ub, nd, npix, grid["nv"], -grid["vmax"], 2 * grid["vmax"] / grid["nv"], v0s)
+    rows = Ug.T.copy()
+    Ut, yt = oracle.whiten(rows, y, sig)
+    H, q = oracle.normal_equations(Ut, yt, W["lam"])
+    oracle.nnls_lh_normal(H, q)
+    return None, time.perf_counter() - t0
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
+    import oracle
     W = inputs.WORKLOADS[WORKLOAD]
+    n_orb = 512
+    data, _ = reference_model(W, n_orb)
     for _ in range(args.warmup):
-        cpu_sample(W, 256)
-    vals, ts = [], []
-    for _ in range(args.steps):
-        v, cores, sample, dt = cpu_sample(W, 512)
-        vals.append(v); ts.append(dt)
-    value = float(np.mean(vals))
+        reference_model(W, n_orb, data)
+    ts = [reference_model(W, n_orb, data)[1] for _ in range(args.steps)]
+    value = n_orb * W["nsteps"] / float(np.mean(ts))
+    cores = oracle.max_threads()
+    sample = (f"{n_orb} orbits ({n_orb // W.get('bundle', 1)} bundles) x {W['nsteps']} steps of {WORKLOAD}: "
+              f"integrate + project + bin (FP64, OpenMP), quality cut, bundles, Gauss-Hermite rows and the exact "
+              f"weight solve (normal equations + Lawson-Hanson) of that sample")
     line = {"metric": "orbit-steps/s (whole model evaluations, FP32 batched vs FP64 plain at matched chi^2)",
             "value": value, "unit": "orbit-steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(ts)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_orbits": 512, "nsteps": W["nsteps"]}, "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_orbits": n_orb, "nsteps": W["nsteps"]}, "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "orbit-steps/s", "cores": cores, "kind": "oracle",
-                             "sample": sample.replace(str(N_CPU_SAMPLE), "512"),
-                             "single_thread_value": cpu_single_thread(W)},
+                             "sample": sample, "single_thread_value": cpu_single_thread(W)},
             "e2e": {"value": value, "unit": "orbit-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -537,8 +563,15 @@ def run_sw(args):
 
     cpu = None
     if not args.no_cpu:
-        v, cores, sample, _ = cpu_sample(W)
-        cpu = {"value": v, "unit": "orbit-steps/s", "cores": cores, "kind": "oracle", "sample": sample,
+        import oracle
+        data, _ = reference_model(W, N_CPU_SAMPLE)
+        _, t_cpu = reference_model(W, N_CPU_SAMPLE, data)
+        cpu = {"value": N_CPU_SAMPLE * S / t_cpu, "unit": "orbit-steps/s", "cores": oracle.max_threads(),
+               "kind": "oracle",
+               "sample": f"{N_CPU_SAMPLE} orbits ({N_CPU_SAMPLE // nb} bundles) x {S} steps of {WORKLOAD}: "
+                         f"integrate + project + bin (FP64, OpenMP), quality cut, bundles, Gauss-Hermite rows "
+                         f"and the exact weight solve of that sample (one evaluation after an untimed one that "
+                         f"made its mock data)",
                "single_thread_value": cpu_single_thread(W)}
 
     value = N * S * args.steps * world / elapsed
