@@ -182,6 +182,55 @@ __device__ __forceinline__ void trailing_rest(float* __restrict__ A, int p0, int
     }
 }
 
+// Phase A of k_diag128 for warp 0: Cholesky of the 32 x 32 diagonal sub-block at (c0, c0), one row per
+// lane in registers; writes L_ss back into A (upper part zero), its columns into CT and 1 / L_jj into RR.
+// Kept out of line so that its registers are allocated apart from the rest of the kernel.
+__device__ __noinline__ void warp_factor32(float* __restrict__ A, float* __restrict__ CT, float* __restrict__ RR,
+                                           int c0, int bs, int64_t j0, int* info, int lane)
+{
+    float a[SB];
+#pragma unroll
+    for (int k = 0; k < SB; k += 4) {
+        const float4 v = ld4(A + (c0 + lane) * AP + c0 + k);
+        a[k] = v.x; a[k + 1] = v.y; a[k + 2] = v.z; a[k + 3] = v.w;
+    }
+    float d = __shfl_sync(0xffffffffu, a[0], 0);
+    float rmine = 0.f;   // 1 / L_jj of this lane's column j = lane
+    int bad = 0;         // first non-positive pivot of the sub-block, plus one
+#pragma unroll
+    for (int j = 0; j < SB; ++j) {
+        const bool ok = d > 0.f;
+        bad = (!ok && bad == 0 && c0 + j < bs) ? j + 1 : bad;
+        const float r = rsqrtf(ok ? d : 1e-30f);
+        rmine = lane == j ? r : rmine;
+        const float lij = lane >= j ? a[j] * r : 0.f;
+        a[j] = lij;
+        CT[j * CTP + lane] = lij;
+        if (j + 1 < SB) {
+            // the next pivot: lane j + 1 subtracts its own l_(j+1) j^2, one shuffle broadcasts it
+            const float dn = a[j + 1] - lij * lij;
+            d = __shfl_sync(0xffffffffu, dn, j + 1 < SB ? j + 1 : 0);
+        }
+        // the rest of column j reaches every lane as broadcast reads of its row of CT
+        __syncwarp();
+#pragma unroll
+        for (int k4 = ((j + 1) & ~3); k4 < SB; k4 += 4) {
+            const float4 c = ld4(CT + j * CTP + k4);
+            if (k4 + 0 > j) a[k4 + 0] -= lij * c.x;
+            if (k4 + 1 > j) a[k4 + 1] -= lij * c.y;
+            if (k4 + 2 > j) a[k4 + 2] -= lij * c.z;
+            if (k4 + 3 > j) a[k4 + 3] -= lij * c.w;
+        }
+    }
+    RR[lane] = rmine;
+    if (bad && lane == 0 && info) atomicCAS(info, 0, (int)(j0 + c0 + bad));
+#pragma unroll
+    for (int k = 0; k < SB; k += 4)
+        *reinterpret_cast<float4*>(A + (c0 + lane) * AP + c0 + k) =
+            make_float4(k <= lane ? a[k] : 0.f, k + 1 <= lane ? a[k + 1] : 0.f,
+                        k + 2 <= lane ? a[k + 2] : 0.f, k + 3 <= lane ? a[k + 3] : 0.f);
+}
+
 __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__ G, int64_t ld, int64_t j0, int bs,
                                                              float* __restrict__ D /* D_k^T */, int* info,
                                                              int write_L)
@@ -198,26 +247,29 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // ---- load the lower triangle (16-byte chunks that reach it; the rest of A is never read), all
     // in flight; rows beyond bs are the identity; X = 0
-    {
-        float4 v[16];
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        float4 v[8];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
+        for (int uu = 0; uu < 8; ++uu) {
+            const int u = 8 * half + uu;
             const int e = t + DIAG_THREADS * u, i = e >> 5, l4 = (e & 31) * 4;
             const float* g = G + (size_t)(j0 + i) * ld + j0 + l4;
             if (l4 > i) continue;
             if (i < bs && l4 + 3 < bs) {
-                v[u] = ld4(g);
+                v[uu] = ld4(g);
             } else {
                 float w[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) w[c] = (i < bs && l4 + c < bs) ? g[c] : (i == l4 + c ? 1.f : 0.f);
-                v[u] = make_float4(w[0], w[1], w[2], w[3]);
+                v[uu] = make_float4(w[0], w[1], w[2], w[3]);
             }
         }
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
+        for (int uu = 0; uu < 8; ++uu) {
+            const int u = 8 * half + uu;
             const int e = t + DIAG_THREADS * u, i = e >> 5, l4 = (e & 31) * 4;
-            if (l4 <= i) *reinterpret_cast<float4*>(A + i * AP + l4) = v[u];
+            if (l4 <= i) *reinterpret_cast<float4*>(A + i * AP + l4) = v[uu];
             *reinterpret_cast<float4*>(X + i * AP + l4) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
@@ -227,42 +279,11 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
         const int c0 = SB * s;
         // ======== A
         if (warp == 0) {
-            float a[SB];
-#pragma unroll
-            for (int k = 0; k < SB; k += 4) {
-                const float4 v = ld4(A + (c0 + lane) * AP + c0 + k);
-                a[k] = v.x; a[k + 1] = v.y; a[k + 2] = v.z; a[k + 3] = v.w;
-            }
-            float d = __shfl_sync(0xffffffffu, a[0], 0);
-            float rmine = 0.f;   // 1 / L_jj of this lane's column j = lane
-            int bad = 0;         // first non-positive pivot of the sub-block, plus one
-#pragma unroll
-            for (int j = 0; j < SB; ++j) {
-                const bool ok = d > 0.f;
-                bad = (!ok && bad == 0 && c0 + j < bs) ? j + 1 : bad;
-                const float r = rsqrtf(ok ? d : 1e-30f);
-                rmine = lane == j ? r : rmine;
-                const float lij = lane >= j ? a[j] * r : 0.f;
-                a[j] = lij;
-                CT[j * CTP + lane] = lij;
-                if (j + 1 < SB) {
-                    // the next pivot: lane j + 1 subtracts its own l_(j+1) j^2, one shuffle broadcasts it
-                    const float dn = a[j + 1] - lij * lij;
-                    d = __shfl_sync(0xffffffffu, dn, j + 1 < SB ? j + 1 : 0);
-                }
-#pragma unroll
-                for (int k = j + 1; k < SB; ++k) a[k] -= lij * __shfl_sync(0xffffffffu, lij, k);
-            }
-            RR[lane] = rmine;
-            if (bad && lane == 0 && info) atomicCAS(info, 0, (int)(j0 + c0 + bad));
-#pragma unroll
-            for (int k = 0; k < SB; k += 4)
-                *reinterpret_cast<float4*>(A + (c0 + lane) * AP + c0 + k) =
-                    make_float4(k <= lane ? a[k] : 0.f, k + 1 <= lane ? a[k + 1] : 0.f,
-                                k + 2 <= lane ? a[k + 2] : 0.f, k + 3 <= lane ? a[k + 3] : 0.f);
-        } else {
-            const int tid = t - 32, NT = DIAG_THREADS - 32;
-            auto bar = [] { asm volatile("bar.sync 1, %0;" ::"n"(DIAG_THREADS - 32) : "memory"); };
+            warp_factor32(A, CT, RR, c0, bs, j0, info, lane);
+        } else if (warp != 4) {
+            // warps 1-3 and 5-7 (warp 4 shares warp 0's scheduler and stays idle)
+            const int tid = t - (warp < 4 ? 32 : 64), NT = DIAG_THREADS - 64;
+            auto bar = [] { asm volatile("bar.sync 1, %0;" ::"n"(DIAG_THREADS - 64) : "memory"); };
             // the previous panel's update of columns beyond sub-block s + 1 (columns of s + 1 were done in C)
             if (s >= 1 && s <= 2) trailing_rest(A, c0 - SB, c0 + SB, tid, NT);
             // X_(s-1) j = -X_(s-1)(s-1) T_j, then T_j of block row s (it needs block row s - 1)
