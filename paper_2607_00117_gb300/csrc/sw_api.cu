@@ -515,6 +515,11 @@ GridT<T> make_grid(double incl, double pa, double bar_angle, const sw_pixel_grid
     g.zmin = (T)dens->zmin; g.dz = (T)dz; g.inv_dz = (T)(1.0 / dz);
     g.gh = gh;
     g.ncopy = mirror4 ? 4 : 1;
+    // the copies (-x, -y, +-z) project to (-X, -Y, -V) of the (x, y, -+z) copies: with grids symmetric
+    // about 0 their bins are the reflected ones
+    auto centred = [](double lo, int n, double w) { return std::fabs(lo + 0.5 * n * w) <= 1e-12 * (std::fabs(lo) + w); };
+    g.sym = centred(pix->x0, pix->nx, pix->dx) && centred(pix->y0, pix->ny, pix->dy) &&
+            (gh || centred(vb->v0, vb->nv, vb->dv));
     g.nd = (int64_t)dens->nR * dens->nphi * dens->nz;
     g.npix = (int64_t)pix->nx * pix->ny;
     g.M = g.nd + g.npix + (gh ? 4 * g.npix : g.npix * g.nv);

@@ -42,6 +42,7 @@ struct GridT {
     T dR, inv_dR, inv_dphi, dphi, zmin, inv_dz, dz;
     int nx, ny, nv, nR, nphi, nz;
     int gh, ncopy;
+    int sym;                           // pixel and velocity grids symmetric about 0 (mirror copies by reflection)
     int64_t nd, npix, M;               // rows: density, pixel mass, kinematic block starts at nd + npix
 };
 

@@ -43,6 +43,7 @@ def main():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--bundle", type=int, default=1, help="orbit case: orbits per column (bundles at bin time)")
     ap.add_argument("--integrator", type=int, default=0, help="orbit case: 0 kick-drift-kick, 1 the adaptive pair")
+    ap.add_argument("--drift", action="store_true", help="orbit case: also run the drift-only pass (no binning)")
     args = ap.parse_args()
 
     import torch
@@ -64,7 +65,12 @@ def main():
         for rep in range(args.reps + 1):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.integrate_library_device(ics_d, P["omega_p"], W["dt"], args.nsteps)
+            if args.drift:
+                drift = torch.empty(args.n_orb, dtype=torch.float64, device=dev)
+                status = torch.empty(args.n_orb, dtype=torch.uint8, device=dev)
+                ctx.integrate_library_device(ics_d, P["omega_p"], W["dt"], args.nsteps, drift, status)
+            else:
+                ctx.integrate_library_device(ics_d, P["omega_p"], W["dt"], args.nsteps)
             U = ctx.project(dict(W["grid"], gh=0))
             e1.record(stream)
             torch.cuda.synchronize()
