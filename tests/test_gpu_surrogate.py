@@ -45,9 +45,12 @@ def _setup(env, shape, B, seed):
     return c, emu, X, t
 
 
-@pytest.mark.parametrize("B", [1, 37, 300])
-def test_mlp_forward_and_gradient_vs_oracle(env, orc, B):
+@pytest.mark.parametrize("shape,B", [(SHAPE, 1), (SHAPE, 37), (SHAPE, 300), ((12, 256, 3), 1), ((12, 256, 3), 300)])
+def test_mlp_forward_and_gradient_vs_oracle(env, orc, shape, B):
+    """Forward, BF16 inference and all gradients against the FP64 oracle, at a small network and at the
+    configured emulator (12 -> 256 -> 256 -> 256 -> 1)."""
     torch, sw, surrogate = env
+    SHAPE = shape
     c, emu, X, t = _setup(env, SHAPE, B, 7 + B)
     dev = emu.dev
     Xd, td = torch.from_numpy(X).to(dev), torch.from_numpy(t).to(dev)
