@@ -44,6 +44,7 @@ def main():
     ap.add_argument("--bundle", type=int, default=1, help="orbit case: orbits per column (bundles at bin time)")
     ap.add_argument("--integrator", type=int, default=0, help="orbit case: 0 kick-drift-kick, 1 the adaptive pair")
     ap.add_argument("--drift", action="store_true", help="orbit case: also run the drift-only pass (no binning)")
+    ap.add_argument("--ej-every", type=int, default=0, help="orbit case: steps between Jacobi checks (0: default)")
     args = ap.parse_args()
 
     import torch
@@ -60,6 +61,8 @@ def main():
         ctx.set_potential(P["potential"])
         ctx.set_option("project_bundle", args.bundle)
         ctx.set_option("integrator", args.integrator)
+        if args.ej_every:
+            ctx.set_option("ej_every", args.ej_every)
         ics = inputs.disc_ics(inputs.DISC_HALO, args.n_orb, seed=W["seeds"]["ic"])
         ics_d = torch.from_numpy(ics).to(dev)
         for rep in range(args.reps + 1):
