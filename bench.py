@@ -264,7 +264,7 @@ def matched_leg(sw, torch, reps=3, n_seeds=8):
     """FP32 (Kahan, tensor-core Gram) against plain FP64 on the small axisymmetric workload
     (2 000 orbits x 2 000 steps, 7 300 rows).  The data come from an independent FP64 library;
     each form builds and solves the libraries of n_seeds initial-condition seeds against them.
-    Matched chi^2 (survey reading 26): |chi2_FP32 - chi2_FP64| / chi2_FP64 within
+    Matched chi^2 (the FP32 form meets the FP64 fit): |chi2_FP32 - chi2_FP64| / chi2_FP64 within
     max(1e-4, the spread of chi^2 over the seeds); models/s of each form on the first seed."""
     W = inputs.WORKLOADS["axisym_2k"]
     out = {"workload": "axisym_2k", "ic_seeds": n_seeds}

@@ -29,6 +29,12 @@ inline float __frsqrt_rn(float x) { return 1.0f / std::sqrt(x); }
 inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
 inline float __fdiv_rn(float a, float b) { return a / b; }
 inline float __expf(float x) { return std::exp(x); }
+// rounding-down conversion, saturating like the device instruction (NaN gives 0)
+inline int __float2int_rd(float x) {
+    if (!(x == x)) return 0;
+    const double f = std::floor((double)x);
+    return f >= 2147483647.0 ? INT32_MAX : (f <= -2147483648.0 ? INT32_MIN : (int)f);
+}
 template <class T> inline T atomicAdd(T* p, T v) { T o = *p; *p = o + v; return o; }
 template <class T> inline T atomicMax(T* p, T v) { T o = *p; if (v > o) *p = v; return o; }
 inline long long __double_as_longlong(double d) { long long r; std::memcpy(&r, &d, 8); return r; }

@@ -9,7 +9,7 @@ step sequence; their step sizes differ by rounding only), identical status, drif
 to 1e-9.  FP32: the step controller's decisions depend on the working precision, so
 an orbit's FP32 step sequence can leave the FP64 one; each column is held to the
 oracle's own spread under perturbations of the initial condition, and most columns
-meet the survey's 1e-3 matrix gate outright.  An orbit abandoned before its first
+meet the plain per-orbit L1 gate of 1e-3 outright.  An orbit abandoned before its first
 accepted step keeps an all-zero column."""
 import numpy as np
 import pytest
