@@ -288,6 +288,11 @@ int64_t sw_alloc_count(const sw_ctx* ctx);
  *  "large_solver" (0/1)     above orbit_direct_max orbits: 0 active set (default), 1 ADMM on a working set
  *  "as_block" (>= 1)        active set: KKT violators entering per pivoting step (default 1024)
  *  "as_cg_max" (>= 0)       active set: preconditioned conjugate-gradient steps per reduced solve (default 200)
+ *  "as_border" (0 .. 4096)  active set, FP32 tensor-core form: a passive set that adds at most this many orbits
+ *                           to the factored set extends its factor by bordering (the new block row of the
+ *                           factor's inverse from the kept one) instead of refactoring (default 256; 0: off)
+ *  "as_mask" (0 .. 1)       active set: a factor serves the passive sets inside its factored set that leave at
+ *                           most this fraction of it masked (default 0.02); more masked orbits refactor
  *  "as_cg_tol" (> 0)        active set: CG stops at max|r| <= as_cg_tol * kkt_tol * max|q| (default 0.05)
  *  "as_solves" (>= 1)       active set: cap on pivoting steps (default 400)
  *  "solver" (0/1/2)         0 (default): the active set when lambda > 0, when N <= M, or for libraries above

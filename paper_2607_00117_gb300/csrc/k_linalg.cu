@@ -98,6 +98,88 @@ __global__ void k_whiten_transpose(const T* __restrict__ U, int64_t M, int64_t N
 }
 
 // ---------------------------------------------------------------------------
+// Split-contraction SIMT GEMM for short, wide products: C[m x n] += alpha A op(B),
+// A row-major m x k; BT: B is n x k row-major (A B^T), else k x n row-major (A B).
+// The contraction is cut into slices of kchunk (blockIdx.z) accumulated into C by
+// atomics, so that a product with few rows still fills the GPU.  TRI: B is lower
+// triangular, and each 64-column tile of C contracts only over B's triangle
+// (BT: row c of B holds entries k <= c; else column c of B holds entries k >= c).
+// ---------------------------------------------------------------------------
+template <typename T, bool BT, bool TRI>
+__global__ void __launch_bounds__(256) k_gemm_acc(int64_t m, int64_t n, int64_t k, T alpha, const T* __restrict__ A,
+                                                  int64_t lda, const T* __restrict__ B, int64_t ldb, T* __restrict__ C,
+                                                  int64_t ldc, int64_t kchunk)
+{
+    constexpr int BM = 64, BN = 64, BK = 16;
+    const int64_t bm = (int64_t)blockIdx.y * BM, bn = (int64_t)blockIdx.x * BN;
+    int64_t klo = 0, khi = k;
+    if (TRI) {
+        if (BT) khi = bn + BN < k ? bn + BN : k;
+        else klo = bn;
+    }
+    const int64_t k0 = klo + (int64_t)blockIdx.z * kchunk;
+    const int64_t k1 = k0 + kchunk < khi ? k0 + kchunk : khi;
+    if (k0 >= k1) return;
+    __shared__ T As[BK][BM + 4];
+    __shared__ T Bs[BK][BN + 4];
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int64_t kb = k0; kb < k1; kb += BK) {
+        {
+            const int r = t >> 2, kq = (t & 3) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t gr = bm + r, gk = kb + kq + q;
+                As[kq + q][r] = (gr < m && gk < k1) ? A[(size_t)gr * lda + gk] : T(0);
+            }
+        }
+        if (BT) {
+            const int r = t >> 2, kq = (t & 3) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t gc = bn + r, gk = kb + kq + q;
+                Bs[kq + q][r] = (gc < n && gk < k1) ? B[(size_t)gc * ldb + gk] : T(0);
+            }
+        } else {
+            const int kk = t >> 4, cq = (t & 15) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t gc = bn + cq + q, gk = kb + kk;
+                Bs[kk][cq + q] = (gc < n && gk < k1) ? B[(size_t)gk * ldb + gc] : T(0);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t gr = bm + ty * 4 + i;
+        if (gr >= m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gc = bn + tx * 4 + j;
+            if (gc < n) atomicAdd(C + (size_t)gr * ldc + gc, alpha * acc[i][j]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // SIMT GEMM: C[m x n] = beta C + alpha A op(B); A row-major m x k; BT: B is
 // n x k row-major (C = A B^T), else k x n row-major (C = A B).  LOWER skips
 // 64 x 64 tiles that lie strictly above the diagonal of the global matrix
@@ -1009,6 +1091,25 @@ cudaError_t gemm(sw_ctx* ctx, int kid, int64_t m, int64_t n, int64_t k, T alpha,
     return cudaGetLastError();
 }
 
+template <typename T, bool BT, bool TRI>
+cudaError_t gemm_acc(sw_ctx* ctx, int kid, int64_t m, int64_t n, int64_t k, T alpha, const T* A, int64_t lda,
+                     const T* B, int64_t ldb, T* C, int64_t ldc)
+{
+    if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+    LaunchTimer lt(ctx, kid);
+    add_work(ctx, kid, (TRI ? 1.0 : 2.0) * (double)m * (double)n * (double)k);
+    const int64_t gx = (n + 63) / 64, gy = (m + 63) / 64;
+    // about four CTAs per SM over the tiles; slices of at least 256 (a multiple of 16)
+    const int64_t want = std::max<int64_t>(1, (int64_t)ctx_sms(ctx) * 4 / std::max<int64_t>(1, gx * gy));
+    int64_t kchunk = std::max<int64_t>(256, (k + want - 1) / want);
+    kchunk = (kchunk + 15) / 16 * 16;
+    const int64_t gz = (k + kchunk - 1) / kchunk;
+    if (gz > 65535) return cudaErrorInvalidValue;
+    k_gemm_acc<T, BT, TRI><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), 256, 0, ctx_stream(ctx)>>>(
+        m, n, k, alpha, A, lda, B, ldb, C, ldc, kchunk);
+    return cudaGetLastError();
+}
+
 template <typename T>
 static size_t smem2() { return 2 * sizeof(T) * NB * (NB + 1); }
 
@@ -1389,6 +1490,16 @@ SW_WH(float, float)
 SW_WH(double, double)
 template cudaError_t gemm<float, true, true>(sw_ctx*, int, int64_t, int64_t, int64_t, float, const float*, int64_t,
                                              const float*, int64_t, float, float*, int64_t, int64_t);
+template cudaError_t gemm_acc<float, true, true>(sw_ctx*, int, int64_t, int64_t, int64_t, float, const float*,
+                                                 int64_t, const float*, int64_t, float*, int64_t);
+template cudaError_t gemm_acc<float, false, true>(sw_ctx*, int, int64_t, int64_t, int64_t, float, const float*,
+                                                  int64_t, const float*, int64_t, float*, int64_t);
+template cudaError_t gemm_acc<float, true, false>(sw_ctx*, int, int64_t, int64_t, int64_t, float, const float*,
+                                                  int64_t, const float*, int64_t, float*, int64_t);
+template cudaError_t gemm_acc<double, true, false>(sw_ctx*, int, int64_t, int64_t, int64_t, double,
+                                                   const double*, int64_t, const double*, int64_t, double*, int64_t);
+template cudaError_t gemm<float, false, false>(sw_ctx*, int, int64_t, int64_t, int64_t, float, const float*, int64_t,
+                                               const float*, int64_t, float, float*, int64_t, int64_t);
 template cudaError_t gemm<double, true, true>(sw_ctx*, int, int64_t, int64_t, int64_t, double, const double*,
                                               int64_t, const double*, int64_t, double, double*, int64_t, int64_t);
 template cudaError_t cholesky_inverse<float>(sw_ctx*, float*, float*, float*, int64_t, int*);

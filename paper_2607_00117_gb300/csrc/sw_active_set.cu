@@ -18,10 +18,12 @@
 // matrix with FP64 accumulation.  The preconditioner is the Cholesky factor of
 // the Jacobi-scaled Gram of the factored set P0, formed on the tensor cores
 // (BF16 hi + lo split, FP32 accumulation), factored in FP32 with its triangular
-// inverse kept explicitly.  The solve accepts any F inside P0 (the orbits of
-// P0 outside F masked); every pivoting step refactors on its own passive set,
-// so P0 = F as the loop stands.  The gradient over all N orbits is recomputed
-// in FP64 after every step.
+// inverse kept explicitly.  The solve accepts any F inside P0: the orbits of P0
+// outside F are masked and the preconditioner is corrected to the exact
+// inverse on F (block inverse of P0's).  A pivoting step whose passive set
+// stays inside P0 (a few orbits masked) reuses the factor, one that adds a few
+// orbits extends it by bordering, and any other refactors on its own passive
+// set.  The gradient over all N orbits is recomputed in FP64 after every step.
 #include "sw_linalg.cuh"
 
 #include <algorithm>
@@ -142,6 +144,64 @@ __global__ void k_cg_mask(int64_t n, const double* __restrict__ m, double* __res
         z[i] *= m[i];
 }
 
+// XdT[k][i] = X[i][dpos[k]]: the columns of the factor's inverse at the masked orbits, as rows
+template <typename GT>
+__global__ void k_gather_xcols(const GT* __restrict__ X, int64_t ldx, int64_t K, const int64_t* __restrict__ dpos,
+                               int64_t nD, GT* __restrict__ XdT, int64_t ldt)
+{
+    const int64_t n = nD * K;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / K, i = t - k * K;
+        XdT[(size_t)k * ldt + i] = X[(size_t)i * ldx + dpos[k]];
+    }
+}
+
+// W = H^-1 for a symmetric positive definite n x n matrix H (row-major, lower triangle read), in
+// FP64 on the host: H = C C^T (Cholesky-Crout), Ci = C^-1, W = Ci^T Ci.  false if a pivot is not
+// positive.
+bool spd_inverse(std::vector<double>& H, int64_t n, std::vector<double>& W)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double* hj = &H[(size_t)j * n];
+        double d = hj[j];
+        for (int64_t k = 0; k < j; ++k) d -= hj[k] * hj[k];
+        if (!(d > 0.0)) return false;
+        d = std::sqrt(d);
+        hj[j] = d;
+        for (int64_t i = j + 1; i < n; ++i) {
+            double* hi = &H[(size_t)i * n];
+            double v = hi[j];
+            for (int64_t k = 0; k < j; ++k) v -= hi[k] * hj[k];
+            hi[j] = v / d;
+        }
+    }
+    // Ci by forward substitution, one row at a time: Ci[i][j] = -(sum_{k=j}^{i-1} C[i][k] Ci[k][j]) / C[i][i]
+    std::vector<double> Ci((size_t)n * n, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        const double* hi = &H[(size_t)i * n];
+        double* ci = &Ci[(size_t)i * n];
+        for (int64_t k = 0; k < i; ++k) {
+            const double c = hi[k];
+            const double* ck = &Ci[(size_t)k * n];
+            for (int64_t j = 0; j <= k; ++j) ci[j] -= c * ck[j];
+        }
+        const double inv = 1.0 / hi[i];
+        for (int64_t j = 0; j < i; ++j) ci[j] *= inv;
+        ci[i] = inv;
+    }
+    W.assign((size_t)n * n, 0.0);
+    for (int64_t k = 0; k < n; ++k) {   // W += Ci[k]^T Ci[k] over the rows of Ci
+        const double* ck = &Ci[(size_t)k * n];
+        for (int64_t i = 0; i <= k; ++i) {
+            const double a = ck[i];
+            if (a == 0.0) continue;
+            double* wi = &W[(size_t)i * n];
+            for (int64_t j = 0; j <= k; ++j) wi[j] += a * ck[j];
+        }
+    }
+    return true;
+}
+
 inline int cg_blocks(const sw_ctx* ctx, int64_t n)
 {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + CG_THREADS - 1) / CG_THREADS, (int64_t)ctx_sms(ctx) * 8));
@@ -241,14 +301,22 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     // passive Grams kept between factorisations (tensor-core form): valid within this solve, and
     // across the warm-started solves of one bootstrap (same matrix and errors)
     const bool gcache = fact_tc && split;
+    // bordering (tensor-core form): the factor's buffers keep room for as_border more orbits, so that a
+    // passive set adding a few orbits to the factored set P0 extends P0's factor instead of refactoring
+    const int64_t slack = gcache ? std::max(0, ctx->opt.as_border) : 0;
+    bool p0_ok = false;            // ws.X holds the inverse factor of P0
+    double fl_ok = floor_ridge;    // ridge floor of that factor
+    int n_border = 0;
     if (!(warm && warm->start) || (int64_t)ws.gc_pos.size() != N) {
         ws.gc_set.clear();
         ws.gc_pos.assign(N, -1);
     }
     auto factor = [&](const std::vector<int64_t>& S_in, bool& ok) -> sw_status {
         const int64_t nP = (int64_t)S_in.size();
-        ldG = fact_tc ? (nP + 3) / 4 * 4 : nP;
+        ldG = fact_tc ? (nP + slack + 3) / 4 * 4 : nP;
+        const int64_t room = nP + slack;
         ok = false;
+        p0_ok = false;
         // with a kept Gram: the orbits it holds first (in its order), whole tile rows of them
         // gathered from it, the rest (and the partial tile row) computed
         std::vector<int64_t> S;
@@ -270,11 +338,13 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         P0 = S;
         for (int64_t k = 0; k < nP; ++k) pos[S[k]] = k;
         std::vector<double> sh(nP), rh(nP);
-        AS_TRY(ctx->ensure(&ws.Uc, &ws.Uc_cap, (size_t)nP * M * sizeof(T), "passive columns"));
-        AS_TRY(ctx->ensure(&ws.A, &ws.A_cap, (size_t)nP * ldA * sizeof(AT), "passive matrix"));
-        if (split) AS_TRY(ctx->ensure(&ws.Alo, &ws.Alo_cap, (size_t)nP * ldA * sizeof(AT), "passive matrix (lo)"));
-        AS_TRY(ctx->ensure(&ws.G, &ws.G_cap, (size_t)nP * ldG * sizeof(GT), "reduced Gram"));
-        AS_TRY(ctx->ensure(&ws.X, &ws.X_cap, (size_t)nP * ldG * sizeof(GT), "reduced inverse factor"));
+        // G doubles as the bordering's scratch (two slack x ldG and two slack x slack blocks)
+        const size_t g_elems = std::max((size_t)nP * ldG, (size_t)slack * (2 * ldG + 2 * ((slack + 3) / 4 * 4)));
+        AS_TRY(ctx->ensure(&ws.Uc, &ws.Uc_cap, (size_t)room * M * sizeof(T), "passive columns"));
+        AS_TRY(ctx->ensure(&ws.A, &ws.A_cap, (size_t)room * ldA * sizeof(AT), "passive matrix"));
+        if (split) AS_TRY(ctx->ensure(&ws.Alo, &ws.Alo_cap, (size_t)room * ldA * sizeof(AT), "passive matrix (lo)"));
+        AS_TRY(ctx->ensure(&ws.G, &ws.G_cap, g_elems * sizeof(GT), "reduced Gram"));
+        AS_TRY(ctx->ensure(&ws.X, &ws.X_cap, (size_t)room * ldG * sizeof(GT), "reduced inverse factor"));
         AS_TRY(ctx->ensure(&ws.D, &ws.D_cap, 64 * 64 * sizeof(GT), "block scratch"));
         T* Uc = (T*)ws.Uc;
         AT* A = (AT*)ws.A;
@@ -291,7 +361,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         if constexpr (sizeof(AT) == 2) {
             if (gcache) {
                 const int nx = 1 - ws.gc_cur;
-                AS_TRY(ctx->ensure(&ws.Gc[nx], &ws.Gc_cap[nx], (size_t)nP * ldG * sizeof(float), "kept Gram"));
+                AS_TRY(ctx->ensure(&ws.Gc[nx], &ws.Gc_cap[nx], (size_t)room * ldG * sizeof(float), "kept Gram"));
                 Gn = (float*)ws.Gc[nx];
                 if (r0 > 0) {
                     std::vector<int64_t> ci(r0);
@@ -313,7 +383,9 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
                 ws.gc_ld = ldG;
             }
         }
+        double fl_try = fl;
         for (int attempt = 0; attempt < 4 && infoh != 0; ++attempt, fl *= 100.0) {
+            fl_try = fl;
             for (int64_t k = 0; k < nP; ++k) rh[k] = std::max(mu * sh[k] * sh[k], fl);
             AS_CUDA(ctx, cudaMemcpyAsync(V.ridge, rh.data(), nP * sizeof(double), cudaMemcpyHostToDevice, st), "ridge");
             AS_CUDA(ctx, cudaMemsetAsync(info, 0, sizeof(int), st), "memset");
@@ -354,14 +426,131 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         if (warm) ++warm->factorisations;
         if (infoh != 0) return SW_OK;   // ok = false
         ok = true;
+        p0_ok = true;
+        fl_ok = fl_try;
+        return SW_OK;
+    };
+
+    // orbits the factor's buffers hold at leading dimension ldG
+    auto room_of = [&]() -> int64_t {
+        if (!ldG || !ws.X || !ws.Uc || !ws.A || !ws.Gc[ws.gc_cur]) return 0;
+        int64_t r = (int64_t)(ws.X_cap / ((size_t)ldG * sizeof(GT)));
+        r = std::min(r, (int64_t)(ws.Gc_cap[ws.gc_cur] / ((size_t)ldG * sizeof(float))));
+        r = std::min(r, (int64_t)(ws.Uc_cap / ((size_t)M * sizeof(T))));
+        r = std::min(r, (int64_t)(ws.A_cap / ((size_t)ldA * sizeof(AT))));
+        if (split) r = std::min(r, ws.Alo ? (int64_t)(ws.Alo_cap / ((size_t)ldA * sizeof(AT))) : 0);
+        return r;
+    };
+
+    // ---- bordering: P1 = (P0, E) from the factor of P0.  With A the scaled, shifted Gram and
+    // X0 = L0^-1 (A_00 = L0 L0^T):  L_E0 = A_E0 X0^T,  L_EE L_EE^T = A_EE - L_E0 L_E0^T,  and the
+    // new block row of the inverse  X_E0 = -X_EE L_E0 X0,  X_EE = L_EE^-1.  The rows of the kept
+    // Gram for E come from the tensor-core Gram of the appended tile rows; the leading block of the
+    // factor, and of everything indexed by P0, is unchanged.  ok = false if A_EE - L_E0 L_E0^T is
+    // not positive definite in FP32 (the caller then refactors).
+    auto border = [&](const std::vector<int64_t>& E, bool& ok) -> sw_status {
+        ok = false;
+        if constexpr (sizeof(AT) == 2 && sizeof(GT) == 4) {
+            const int64_t K0 = (int64_t)P0.size(), nE = (int64_t)E.size(), K1 = K0 + nE;
+            const int64_t ldS = (nE + 3) / 4 * 4;
+            T* Uc = (T*)ws.Uc;
+            AT* A = (AT*)ws.A;
+            AT* Alo = (AT*)ws.Alo;
+            float* Gk = (float*)ws.Gc[ws.gc_cur];
+            float* X = (float*)ws.X;
+            float* L21 = (float*)ws.G;   // scratch: the in-place factor is not needed after factoring
+            float* Y = L21 + (size_t)nE * ldG;
+            float* Sm = Y + (size_t)nE * ldG;
+            float* X22 = Sm + (size_t)nE * ldS;
+            std::vector<double> sh(nE), rh(nE);
+            for (int64_t k = 0; k < nE; ++k) {
+                sh[k] = 1.0 / std::sqrt(hh[E[k]] > 0.0 ? hh[E[k]] : 1.0);
+                rh[k] = std::max(mu * sh[k] * sh[k], fl_ok);
+            }
+            AS_CUDA(ctx, cudaMemcpyAsync(V.idx + K0, E.data(), nE * sizeof(int64_t), cudaMemcpyHostToDevice, st), "idx");
+            AS_CUDA(ctx, cudaMemcpyAsync(V.sP + K0, sh.data(), nE * sizeof(double), cudaMemcpyHostToDevice, st), "scales");
+            AS_CUDA(ctx, cudaMemcpyAsync(V.ridge + K0, rh.data(), nE * sizeof(double), cudaMemcpyHostToDevice, st), "ridge");
+            AS_CUDA(ctx, gather_cols<T>(ctx, U, M, V.idx + K0, nE, Uc + (size_t)K0 * M), "gather");
+            AS_CUDA(ctx, (whiten<T, AT>(ctx, Uc + (size_t)K0 * M, M, nE, V.inv_sig, V.sP + K0, A + (size_t)K0 * ldA,
+                                        Alo + (size_t)K0 * ldA, ldA, true)),
+                    "whiten");
+            // the kept Gram's tile rows from the one holding row K0 on (P0's rows there are recomputed)
+            AS_CUDA(ctx, gram_tc(ctx, A, Alo, K1, ldA, Gk, gerr, ldG, K0 / 128), "reduced Gram");
+            for (size_t k = (size_t)K0; k < ws.gc_set.size(); ++k) ws.gc_pos[ws.gc_set[k]] = -1;
+            ws.gc_set.resize(K0);
+            for (int64_t k = 0; k < nE; ++k) {
+                P0.push_back(E[k]);
+                pos[E[k]] = K0 + k;
+                ws.gc_set.push_back(E[k]);
+                ws.gc_pos[E[k]] = K0 + k;
+            }
+            AS_CUDA(ctx, cudaMemsetAsync(X + (size_t)K0 * ldG, 0, (size_t)nE * ldG * sizeof(float), st), "memset");
+            AS_CUDA(ctx, cudaMemsetAsync(L21, 0, (size_t)2 * nE * ldG * sizeof(float), st), "memset");   // L21, Y
+            // L_E0 = A_E0 X0^T (X0 lower triangular)
+            AS_CUDA(ctx, (gemm_acc<float, true, true>(ctx, K_BORDER, nE, K0, K0, 1.f, Gk + (size_t)K0 * ldG, ldG, X,
+                                                      ldG, L21, ldG)),
+                    "border");
+            // S = A_EE + R_E - L_E0 L_E0^T (lower triangle; the factorisation reads no other)
+            AS_CUDA(ctx, cudaMemcpy2DAsync(Sm, ldS * sizeof(float), Gk + (size_t)K0 * ldG + K0, ldG * sizeof(float),
+                                           nE * sizeof(float), nE, cudaMemcpyDeviceToDevice, st),
+                    "border");
+            AS_CUDA(ctx, shift_diag_vec<float>(ctx, Sm, nE, ldS, V.ridge + K0), "ridge");
+            AS_CUDA(ctx, (gemm_acc<float, true, false>(ctx, K_BORDER, nE, nE, K0, -1.f, L21, ldG, L21, ldG, Sm, ldS)),
+                    "border");
+            AS_CUDA(ctx, cudaMemsetAsync(info, 0, sizeof(int), st), "memset");
+            AS_CUDA(ctx, cholesky_inverse_tc(ctx, Sm, X22, nE, ldS, info, gerr, false), "border");
+            // X_E0 = -X_EE (L_E0 X0), X_EE
+            AS_CUDA(ctx, (gemm_acc<float, false, true>(ctx, K_BORDER, nE, K0, K0, 1.f, L21, ldG, X, ldG, Y, ldG)),
+                    "border");
+            AS_CUDA(ctx, (gemm<float, false, false>(ctx, K_BORDER, nE, K0, nE, -1.f, X22, ldS, Y, ldG, 0.f,
+                                                    X + (size_t)K0 * ldG, ldG, 0)),
+                    "border");
+            AS_CUDA(ctx, cudaMemcpy2DAsync(X + (size_t)K0 * ldG + K0, ldG * sizeof(float), X22, ldS * sizeof(float),
+                                           nE * sizeof(float), nE, cudaMemcpyDeviceToDevice, st),
+                    "border");
+            int infoh = 1, gerrh = 0;
+            AS_CUDA(ctx, cudaMemcpyAsync(&infoh, info, sizeof(int), cudaMemcpyDeviceToHost, st), "info");
+            AS_CUDA(ctx, cudaMemcpyAsync(&gerrh, gerr, sizeof(int), cudaMemcpyDeviceToHost, st), "flags");
+            AS_CUDA(ctx, cudaStreamSynchronize(st), "border");
+            if (gerrh) { set_error(ctx, "solve: a tensor-core kernel (Gram or factor update) timed out"); return SW_ETIMEOUT; }
+            ++n_border;
+            ok = infoh == 0;
+        }
+        return SW_OK;
+    };
+
+    // a passive set that adds at most as_border orbits to the factored set, with at most as_mask of the
+    // extended set masked, borders the factor; done = false leaves the refactoring to the caller
+    auto try_border = [&](const std::vector<int64_t>& Fn, bool& done) -> sw_status {
+        done = false;
+        if (!slack || !p0_ok || P0.empty() || ws.gc_ld != ldG) return SW_OK;
+        std::vector<int64_t> E;
+        for (int64_t i : Fn)
+            if (pos[i] < 0) E.push_back(i);
+        const int64_t K0 = (int64_t)P0.size(), nE = (int64_t)E.size(), K1 = K0 + nE;
+        if (nE == 0 || nE > slack || K1 > cap || K1 > ldG || K1 > room_of()) return SW_OK;
+        if ((double)(K1 - (int64_t)Fn.size()) > ctx->opt.as_mask * (double)K1) return SW_OK;
+        const int64_t ldS = (nE + 3) / 4 * 4;
+        if ((size_t)nE * (2 * ldG + 2 * ldS) * sizeof(float) > ws.G_cap) return SW_OK;
+        // the kept Gram must hold P0 in the factor's order
+        if ((int64_t)ws.gc_set.size() < K0) return SW_OK;
+        for (int64_t k = 0; k < K0; ++k)
+            if (ws.gc_set[k] != P0[k]) return SW_OK;
+        bool ok = false;
+        AS_TRY(border(E, ok));
+        if (ctx->opt.verbose > 1)
+            fprintf(stderr, "[sw]   border: %lld orbits appended to %lld, %lld masked%s\n", (long long)nE,
+                    (long long)K0, (long long)(K1 - (int64_t)Fn.size()), ok ? "" : " (not definite: refactor)");
+        if (!ok) p0_ok = false;
+        done = ok;
         return SW_OK;
     };
 
     // ---- (G_F + mu I) x = q_F for a passive set F inside P0, by preconditioned
     // conjugate gradients in the coordinates of P0 with the orbits outside F masked:
-    // the preconditioner is the F block of the inverse of the P0 factor, which differs
-    // from the exact inverse on F by a term of the rank of P0 \ F.  Products use the
-    // stored matrix with FP64 accumulation.  Result in xh (P0 order, zero outside F).
+    // the preconditioner is the inverse on F obtained from the P0 factor (below).
+    // Products use the stored matrix with FP64 accumulation.  Result in xh (P0 order,
+    // zero outside F).
     auto solve_on = [&](const std::vector<int64_t>& F, bool& converged) -> sw_status {
         const int64_t nP = (int64_t)P0.size();
         const T* Uc = (const T*)ws.Uc;
@@ -372,10 +561,73 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         AS_CUDA(ctx, cudaMemcpyAsync(V.mask, mh.data(), nP * sizeof(double), cudaMemcpyHostToDevice, st), "mask");
         AS_CUDA(ctx, gather_vec(ctx, V.q, V.idx, nP, V.qP), "q_P");
         const int nb = cg_blocks(ctx, nP);
-        auto precond = [&](const double* r, double* z) -> sw_status {   // z = m S X^T X S r
+        // The masked orbits D = P0 \ F: with H = A^-1 = X^T X for the scaled, shifted Gram A of P0, the
+        // inverse of A_FF is (H - H_:D H_DD^-1 H_D:)_FF (block inverse), so the preconditioner applies
+        // z = X^T (t - X_:D u), t = X r, u = H_DD^-1 (X_:D^T t): exact on F up to the factor's rounding,
+        // where the masked form alone leaves |D| outlying eigenvalues to the iteration.  H_DD = X_:D^T
+        // X_:D is inverted on the host in FP64; above kMaskExactMax masked orbits the masked form stays.
+        constexpr int64_t kMaskExactMax = 384;
+        int64_t nDc = 0, ldT = 0;
+        GT *XdT = nullptr, *Wd = nullptr, *cD = nullptr, *uD = nullptr;
+        {
+            std::vector<int64_t> dpos;
+            for (int64_t k = 0; k < nP; ++k)
+                if (mh[k] == 0.0) dpos.push_back(k);
+            const int64_t nD = (int64_t)dpos.size();
+            if (nD > 0 && nD <= kMaskExactMax) {
+                ldT = (nP + 3) / 4 * 4;
+                Span sp{nullptr};
+                sp.take<int64_t>(nD);
+                sp.take<GT>(nD * ldT);
+                sp.take<GT>(nD * nD);
+                sp.take<GT>(nD * nD);
+                sp.take<GT>(nD);
+                sp.take<GT>(nD);
+                AS_TRY(ctx->ensure(&ws.Mc, &ws.Mc_cap, sp.used + 256, "masked-orbit correction"));
+                Span sm{(char*)ws.Mc};
+                int64_t* dpos_d = sm.take<int64_t>(nD);
+                XdT = sm.take<GT>(nD * ldT);
+                GT* Hd = sm.take<GT>(nD * nD);
+                Wd = sm.take<GT>(nD * nD);
+                cD = sm.take<GT>(nD);
+                uD = sm.take<GT>(nD);
+                AS_CUDA(ctx, cudaMemcpyAsync(dpos_d, dpos.data(), nD * sizeof(int64_t), cudaMemcpyHostToDevice, st),
+                        "masked orbits");
+                {
+                    LaunchTimer lt(ctx, K_PCG);
+                    k_gather_xcols<GT><<<(unsigned)std::min<int64_t>((nD * nP + 255) / 256, (int64_t)ctx_sms(ctx) * 16),
+                                         256, 0, st>>>(X, ldG, nP, dpos_d, nD, XdT, ldT);
+                }
+                AS_CUDA(ctx, cudaGetLastError(), "masked orbits");
+                AS_CUDA(ctx, cudaMemsetAsync(Hd, 0, (size_t)nD * nD * sizeof(GT), st), "memset");
+                AS_CUDA(ctx, (gemm_acc<GT, true, false>(ctx, K_PCG, nD, nD, nP, GT(1), XdT, ldT, XdT, ldT, Hd, nD)),
+                        "masked orbits");
+                std::vector<GT> hg((size_t)nD * nD);
+                AS_CUDA(ctx, cudaMemcpyAsync(hg.data(), Hd, hg.size() * sizeof(GT), cudaMemcpyDeviceToHost, st),
+                        "masked orbits");
+                AS_CUDA(ctx, cudaStreamSynchronize(st), "masked orbits");
+                std::vector<double> H(hg.begin(), hg.end()), Wh;
+                if (spd_inverse(H, nD, Wh)) {
+                    std::vector<GT> wg(Wh.begin(), Wh.end());
+                    AS_CUDA(ctx, cudaMemcpyAsync(Wd, wg.data(), wg.size() * sizeof(GT), cudaMemcpyHostToDevice, st),
+                            "masked orbits");
+                    AS_CUDA(ctx, cudaStreamSynchronize(st), "masked orbits");
+                    nDc = nD;
+                }
+            }
+        }
+        auto precond = [&](const double* r, double* z) -> sw_status {   // z = m S X^T X S r (corrected)
             AS_CUDA(ctx, scale_to<GT>(ctx, nP, r, V.sP, V.rs), "precondition");
             AS_CUDA(ctx, (rowdot<GT, GT, GT, GT>(ctx, K_TRMV_L, X, nP, nP, ldG, V.rs, V.t1, 1.0, 0.0, true)),
                     "precondition");
+            if (nDc) {
+                AS_CUDA(ctx, (rowdot<GT, GT, GT, GT>(ctx, K_PCG, XdT, nDc, nP, ldT, V.t1, cD, 1.0, 0.0, false)),
+                        "precondition");
+                AS_CUDA(ctx, (rowdot<GT, GT, GT, GT>(ctx, K_PCG, Wd, nDc, nDc, nDc, cD, uD, 1.0, 0.0, false)),
+                        "precondition");
+                AS_CUDA(ctx, (colcomb<GT, GT, GT, GT>(ctx, K_PCG, XdT, nDc, nP, ldT, uD, V.t1, -1.0, false)),
+                        "precondition");
+            }
             AS_CUDA(ctx, cudaMemsetAsync(V.c, 0, nP * sizeof(GT), st), "memset");
             AS_CUDA(ctx, (colcomb<GT, GT, GT, GT>(ctx, K_TRMV_LT, X, nP, nP, ldG, V.t1, V.c, 1.0, true)),
                     "precondition");
@@ -524,11 +776,14 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         fbest = fproj = fref = f0;
     }
     // the factor of P0 serves every passive set inside it (the orbits of P0 \ F masked)
+    // (the recorded factor of a warm start serves every passive set inside it; another factor serves
+    // those that mask at most as_mask of it)
     auto factored_covers = [&](const std::vector<int64_t>& S) {
-        if (!warm || !warm->have_factor || P0.empty()) return false;
+        if (P0.empty() || !p0_ok) return false;
         for (int64_t i : S)
             if (pos[i] < 0) return false;
-        return true;
+        if (warm && warm->have_factor) return true;
+        return (double)((int64_t)P0.size() - (int64_t)S.size()) <= ctx->opt.as_mask * (double)P0.size();
     };
     if (warm && warm->start && (int64_t)warm->F0.size() == N && !warm->P0.empty()) {
         // begin from the recorded passive set, solved against this problem's data with the factor of
@@ -539,6 +794,8 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             P0 = warm->P0;
             ldG = warm->ld;
             for (int64_t k = 0; k < (int64_t)P0.size(); ++k) pos[P0[k]] = k;
+            p0_ok = true;
+            fl_ok = warm->fl;
         } else {
             const std::vector<int64_t> S = warm->P0;
             AS_TRY(factor(S, have));
@@ -636,8 +893,14 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         if (!F.empty()) {
             bool ok = true, conv = false;
             if (!factored_covers(F)) {
-                AS_TRY(factor(F, ok));
-                if (warm) warm->have_factor = false;   // P0 is now this passive set
+                // a bordered factor keeps P0's factor as its leading block: a warm start's recorded
+                // factor survives it
+                bool bordered = false;
+                AS_TRY(try_border(F, bordered));
+                if (!bordered) {
+                    AS_TRY(factor(F, ok));
+                    if (warm) warm->have_factor = false;   // P0 is now this passive set
+                }
             }
             if (!ok) { failed = true; break; }
             AS_TRY(solve_on(F, conv));
@@ -696,6 +959,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         if (!S.empty()) AS_TRY(factor(S, ok));
         warm->P0 = P0;
         warm->ld = ldG;
+        warm->fl = fl_ok;
         warm->have_factor = ok;
     }
     {
@@ -714,8 +978,8 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     ctx->solve_info[6] = outer + 1;
     ctx->solve_info[7] = (double)support;
     if (ctx->opt.verbose)
-        fprintf(stderr, "[sw] active set done: support %lld solves %d factors %d cg %d pg_rel %.3g%s\n",
-                (long long)support, n_solves, n_factor, cg_total, pg_rel, converged ? "" : " (stopped)");
+        fprintf(stderr, "[sw] active set done: support %lld solves %d factors %d borders %d cg %d pg_rel %.3g%s\n",
+                (long long)support, n_solves, n_factor, n_border, cg_total, pg_rel, converged ? "" : " (stopped)");
     if (failed) {
         set_error(ctx, "solve: reduced Gram not positive definite after ridge retries (|F| %zu)", F.size());
         return SW_ENONCONV;

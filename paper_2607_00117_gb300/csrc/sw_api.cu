@@ -17,7 +17,7 @@ const char* kKernelNames[K_COUNT] = {
     "potential_eval", "whiten", "gram_tcgen05", "gram_simt", "shift_diag", "diag_factor_inverse", "panel_gemm",
     "syrk_update", "inverse_block_row", "trinv_update", "gemv_n", "gemv_t", "trmv_l", "trmv_lt", "admm_update",
     "residual", "gradient", "chi2", "misc", "batch_orbit_bin", "mlp_fwd", "mlp_bwd", "adam", "reduce_gh", "pcg", "bundle", "cholesky_inverse",
-    "syrk_update_tcgen05", "trinv_update_tcgen05"};
+    "syrk_update_tcgen05", "trinv_update_tcgen05", "factor_border"};
 
 void set_error(sw_ctx* ctx, const char* fmt, ...)
 {
@@ -1002,7 +1002,8 @@ const int kKernelWorkKind[K_COUNT] = {
     W_BYTES /*gemv_t*/, W_BYTES /*trmv_l*/, W_BYTES /*trmv_lt*/, W_NONE /*admm_update*/, W_BYTES /*residual*/,
     W_BYTES /*gradient*/, W_NONE /*chi2*/, W_NONE /*misc*/, W_ORBIT_STEPS /*batch_orbit*/, W_FLOP_SIMT /*mlp_fwd*/,
     W_FLOP_SIMT /*mlp_bwd*/, W_NONE /*adam*/, W_BYTES /*reduce_gh*/, W_NONE /*pcg*/, W_BYTES /*bundle*/,
-    W_FLOP_SIMT /*cholesky_inverse*/, W_FLOP_TENSOR /*syrk_tc*/, W_FLOP_TENSOR /*trinv_tc*/};
+    W_FLOP_SIMT /*cholesky_inverse*/, W_FLOP_TENSOR /*syrk_tc*/, W_FLOP_TENSOR /*trinv_tc*/,
+    W_FLOP_SIMT /*border*/};
 
 void add_work(sw_ctx* ctx, int kid, double units)
 {
@@ -1095,6 +1096,12 @@ extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value)
     } else if (!strcmp(key, "project_bundle")) {
         if (!(value >= 1.0 && value <= 1024.0 && value == std::floor(value))) return SW_EINVAL;
         ctx->opt.project_bundle = (int)value;
+    } else if (!strcmp(key, "as_border")) {
+        if (!(value >= 0 && value <= 4096 && value == std::floor(value))) return SW_EINVAL;
+        ctx->opt.as_border = (int)value;
+    } else if (!strcmp(key, "as_mask")) {
+        if (!(value >= 0.0 && value <= 1.0)) return SW_EINVAL;
+        ctx->opt.as_mask = value;
     } else if (!strcmp(key, "boot_p0_extra")) {
         if (!(value >= 0.0 && value <= 4.0)) return SW_EINVAL;
         ctx->opt.boot_p0_extra = value;

@@ -44,6 +44,8 @@ struct Options {
     int integrator = 0;          // 0: kick-drift-kick at fixed dt; 1: adaptive Bogacki-Shampine 3(2) in the bar frame
     double bs3_rtol = 1e-4;      // relative tolerance of the adaptive integrator
     int as_cg_max = 200;         // active set: conjugate-gradient steps per reduced solve
+    int as_border = 256;         // active set: at most this many entering orbits appended to the factor (0: refactor)
+    double as_mask = 0.02;       // active set: largest fraction of the factored set masked before refactoring
     double as_cg_tol = 0.05;     // active set: CG stops at max|r| <= as_cg_tol * kkt_tol * max|q|
     int as_solves = 400;         // active set: cap on reduced solves
     bool gram_tc = true;         // tcgen05 BF16 Gram (FP32 path); false: SIMT FP32 Gram
@@ -70,6 +72,7 @@ struct SolveWS {
     // the next), the orbits in the last one's order and each orbit's position in it
     void* Gc[2] = {nullptr, nullptr}; size_t Gc_cap[2] = {0, 0};
     void* gcidx = nullptr; size_t gcidx_cap = 0;
+    void* Mc = nullptr; size_t Mc_cap = 0;        // correction of the masked orbits: X's columns, H_DD^-1
     int gc_cur = 0;
     int64_t gc_ld = 0;
     std::vector<int64_t> gc_set, gc_pos;

@@ -78,7 +78,7 @@ enum KernelId {
     K_WHITEN, K_GRAM_TC, K_GRAM_SIMT, K_SHIFT, K_POTRF_DIAG, K_TRSM_PANEL, K_SYRK_UPDATE,
     K_TRINV_DIAG, K_TRINV_UPDATE, K_GEMV_N, K_GEMV_T, K_TRMV_L, K_TRMV_LT, K_ADMM_UPDATE,
     K_RESID, K_GRAD, K_CHI2, K_MISC, K_BATCH_ORBIT, K_MLP_FWD, K_MLP_BWD, K_ADAM, K_REDUCE_GH, K_PCG, K_BUNDLE, K_CHOL_COOP,
-    K_SYRK_TC, K_TRINV_TC, K_COUNT
+    K_SYRK_TC, K_TRINV_TC, K_BORDER, K_COUNT
 };
 extern const char* kKernelNames[K_COUNT];
 

@@ -19,6 +19,12 @@ cudaError_t div_to(sw_ctx* ctx, int64_t n, const double* a, const double* b, GT*
 template <typename T, bool BT, bool LOWER>
 cudaError_t gemm(sw_ctx* ctx, int kid, int64_t m, int64_t n, int64_t k, T alpha, const T* A, int64_t lda, const T* B,
                  int64_t ldb, T beta, T* C, int64_t ldc, int64_t diag_off);
+// C[m x n] += alpha A op(B), the contraction split into slices accumulated by atomics (C initialised
+// by the caller); TRI: B lower triangular, only its triangle contracted (BT: B n x k, row c holding
+// k <= c; else B k x n, column c holding k >= c)
+template <typename T, bool BT, bool TRI>
+cudaError_t gemm_acc(sw_ctx* ctx, int kid, int64_t m, int64_t n, int64_t k, T alpha, const T* A, int64_t lda,
+                     const T* B, int64_t ldb, T* C, int64_t ldc);
 // Cholesky (in place) and the explicit inverse X = L^{-1} in one cooperative launch (k_chol.cu);
 // cudaErrorNotSupported when the device cannot launch it; *d_err != 0 if a barrier wait ran out
 template <typename T>
@@ -101,6 +107,7 @@ struct AsWarm {
     std::vector<double> w0;      // its weights (N)
     std::vector<int64_t> P0;     // the factored set, in the order of its factor
     int64_t ld = 0;              // leading dimension of its G and X
+    double fl = 0.0;             // ridge floor of its factor
     bool have_factor = false;
     double p0_extra = 0.0;       // P0 = F0 plus up to this fraction of |F0| near-active orbits
     int64_t factorisations = 0;  // factorisations made by the solves of this warm start

@@ -41,7 +41,7 @@ using namespace sw;
 
 void SolveWS::release()
 {
-    void* bufs[] = {A, Alo, G, Gs, X, D, vec, R, H, Hi, pv, Uc, outer, boot, Gc[0], Gc[1], gcidx};
+    void* bufs[] = {A, Alo, G, Gs, X, D, vec, R, H, Hi, pv, Uc, outer, boot, Gc[0], Gc[1], gcidx, Mc};
     for (void* b : bufs)
         if (b) cudaFree(b);
     *this = SolveWS();

@@ -175,6 +175,44 @@ def test_cooperative_factorisation_matches_per_step_launches(sw, orc):
     np.testing.assert_allclose(out[0][0], out[1][0], rtol=1e-4, atol=1e-6 * out[0][0].max())
 
 
+def test_factor_bordering_matches_refactoring(sw, orc):
+    """Pivoting steps that add a few orbits to the factored set extend its factor by bordering
+    (option as_border) and mask the orbits that left it (as_mask) instead of refactoring: the
+    same solution as refactoring at every step, with fewer factorisations and about as many
+    conjugate-gradient steps (the preconditioner is corrected to the exact inverse on the passive
+    set), both meeting the KKT certificate, and the oracle's chi^2."""
+    grid = dict(W1["grid"], nx=8, ny=8, nR=5, nphi=4, nz=3, gh=1, incl=0.9)
+    ics = inputs.disc_ics(BARRED, 1500, seed=205)
+    po = orc.make_pot(BARRED)
+    mom = orc.pixel_moments(po, 40.0, inputs.DT_HALF_MYR, 300, ics, orc.make_obs(grid), np.ones(len(ics)))
+    v0s, gh_err = inputs.gh_reference(mom)
+    out = []
+    for border, mask in ((0, 0.0), (256, 0.1)):
+        c, U = _build(sw, "fp32", BARRED, 40.0, ics, 300, grid, gh_v0s=v0s)
+        c.set_option("orbit_direct_max", 0)
+        c.set_option("as_block", 16)
+        c.set_option("as_border", border)
+        c.set_option("as_mask", mask)
+        Ug = U.copy().T.copy()
+        blocks = inputs.row_blocks(grid)
+        y, sig = _mock(orc, Ug, blocks, gh_err=gh_err)
+        c.reset_stats()
+        w, chi2 = c.solve_weights(U, y, sig, 1.0)
+        info = c.solve_info()
+        assert info["kkt_met"]
+        borders = c.kernel_stats().get("factor_border", {}).get("launches", 0)
+        out.append((w, chi2, borders, info["refine_rounds"], info["admm_iterations"]))
+    print(f"factorisations {out[0][3]}, CG steps {out[0][4]} (refactoring) against {out[1][3]}, {out[1][4]} "
+          f"(bordering, {out[1][2]} border launches)")
+    assert out[0][2] == 0 and out[1][2] > 0
+    assert out[1][3] < out[0][3]
+    assert out[1][4] <= 1.5 * out[0][4] + 10
+    np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-7)
+    np.testing.assert_allclose(out[0][0], out[1][0], rtol=1e-4, atol=1e-6 * out[0][0].max())
+    w_o, chi2_o, H, q = _oracle_solve(orc, Ug, y, sig, 1.0, blocks["dens"][1])
+    np.testing.assert_allclose(out[1][1][:2], chi2_o[:2], rtol=1e-4)
+
+
 def test_solve_working_set_path(sw, orc):
     """The ADMM working-set option for very many orbits on a small problem with
     the direct path disabled: its chi^2 approaches the exact one and its
