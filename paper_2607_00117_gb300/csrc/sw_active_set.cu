@@ -307,6 +307,13 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     bool p0_ok = false;            // ws.X holds the inverse factor of P0
     double fl_ok = floor_ridge;    // ridge floor of that factor
     int n_border = 0;
+    // the masked orbits' correction prepared for the next solve (prepare_mask, below)
+    constexpr int64_t kMaskExactMax = 384;
+    constexpr double kMaskCond = 3e3;
+    int64_t mk_n = 0, mk_ldT = 0;
+    GT *mk_XdT = nullptr, *mk_W = nullptr, *mk_cD = nullptr, *mk_uD = nullptr;
+    bool mk_ready = false;
+    int n_mask_refused = 0;
     if (!(warm && warm->start) || (int64_t)ws.gc_pos.size() != N) {
         ws.gc_set.clear();
         ws.gc_pos.assign(N, -1);
@@ -317,6 +324,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         const int64_t room = nP + slack;
         ok = false;
         p0_ok = false;
+        mk_ready = false;
         // with a kept Gram: the orbits it holds first (in its order), whole tile rows of them
         // gathered from it, the rest (and the partial tile row) computed
         std::vector<int64_t> S;
@@ -446,10 +454,12 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     // X0 = L0^-1 (A_00 = L0 L0^T):  L_E0 = A_E0 X0^T,  L_EE L_EE^T = A_EE - L_E0 L_E0^T,  and the
     // new block row of the inverse  X_E0 = -X_EE L_E0 X0,  X_EE = L_EE^-1.  The rows of the kept
     // Gram for E come from the tensor-core Gram of the appended tile rows; the leading block of the
-    // factor, and of everything indexed by P0, is unchanged.  ok = false if A_EE - L_E0 L_E0^T is
-    // not positive definite in FP32 (the caller then refactors).
+    // factor, and of everything indexed by P0, is unchanged.  ok = false if an entering orbit lies
+    // nearly in the span of P0 (a diagonal of A_EE - L_E0 L_E0^T below 5e-4 of its own) or that
+    // matrix is not positive definite in FP32 (the caller then refactors).
     auto border = [&](const std::vector<int64_t>& E, bool& ok) -> sw_status {
         ok = false;
+        mk_ready = false;
         if constexpr (sizeof(AT) == 2 && sizeof(GT) == 4) {
             const int64_t K0 = (int64_t)P0.size(), nE = (int64_t)E.size(), K1 = K0 + nE;
             const int64_t ldS = (nE + 3) / 4 * 4;
@@ -497,6 +507,20 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             AS_CUDA(ctx, shift_diag_vec<float>(ctx, Sm, nE, ldS, V.ridge + K0), "ridge");
             AS_CUDA(ctx, (gemm_acc<float, true, false>(ctx, K_BORDER, nE, nE, K0, -1.f, L21, ldG, L21, ldG, Sm, ldS)),
                     "border");
+            // every entering orbit must keep kBorderCond of its (unit) scaled norm outside the span of P0:
+            // nearer to it the Schur complement is within the FP32 factor's error of zero (refactor)
+            {
+                constexpr double kBorderCond = 5e-4;
+                std::vector<float> sd(nE);
+                AS_CUDA(ctx, cudaMemcpy2DAsync(sd.data(), sizeof(float), Sm, (ldS + 1) * sizeof(float), sizeof(float), nE,
+                                               cudaMemcpyDeviceToHost, st),
+                        "border");
+                AS_CUDA(ctx, cudaStreamSynchronize(st), "border");
+                double smin = HUGE_VAL;
+                for (int64_t k = 0; k < nE; ++k) smin = std::min(smin, (double)sd[k] / (1.0 + rh[k]));
+                if (ctx->opt.verbose > 1) fprintf(stderr, "[sw]   border: min Schur diagonal %.3g\n", smin);
+                if (!(smin >= kBorderCond)) return SW_OK;
+            }
             AS_CUDA(ctx, cudaMemsetAsync(info, 0, sizeof(int), st), "memset");
             AS_CUDA(ctx, cholesky_inverse_tc(ctx, Sm, X22, nE, ldS, info, gerr, false), "border");
             // X_E0 = -X_EE (L_E0 X0), X_EE
@@ -540,9 +564,85 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         AS_TRY(border(E, ok));
         if (ctx->opt.verbose > 1)
             fprintf(stderr, "[sw]   border: %lld orbits appended to %lld, %lld masked%s\n", (long long)nE,
-                    (long long)K0, (long long)(K1 - (int64_t)Fn.size()), ok ? "" : " (not definite: refactor)");
+                    (long long)K0, (long long)(K1 - (int64_t)Fn.size()), ok ? "" : " (ill-conditioned: refactor)");
         if (!ok) p0_ok = false;
         done = ok;
+        return SW_OK;
+    };
+
+    // ---- correction of the masked orbits D = P0 \ F for the solve on F.  With H = A^-1 = X^T X for
+    // the scaled, shifted Gram A of P0, the inverse of A_FF is (H - H_:D H_DD^-1 H_D:)_FF (block
+    // inverse), so the preconditioner applies z = X^T (t - X_:D u), t = X r, u = H_DD^-1 (X_:D^T t):
+    // exact on F up to the factor's rounding, where the masked form alone leaves |D| outlying
+    // eigenvalues to the iteration.  H_DD = X_:D^T X_:D is inverted on the host in FP64.  ok = false
+    // when the correction cannot be formed accurately: more than kMaskExactMax masked orbits, or a
+    // masked orbit nearly in the span of the others (H_dd = 1 / its squared distance from them, in
+    // units of its unit scaled norm, above kMaskCond: the factor's ~1e-4 relative error would then
+    // dominate the correction).
+    auto prepare_mask = [&](const std::vector<int64_t>& Fs, bool& ok) -> sw_status {
+        ok = false;
+        mk_ready = false;
+        mk_n = 0;
+        const int64_t nP = (int64_t)P0.size();
+        const GT* X = (const GT*)ws.X;
+        std::vector<char> inP(nP, 0);
+        for (int64_t i : Fs) inP[pos[i]] = 1;
+        std::vector<int64_t> dpos;
+        for (int64_t k = 0; k < nP; ++k)
+            if (!inP[k]) dpos.push_back(k);
+        const int64_t nD = (int64_t)dpos.size();
+        if (nD == 0) { ok = mk_ready = true; return SW_OK; }
+        if (nD > kMaskExactMax) return SW_OK;
+        const int64_t ldT = (nP + 3) / 4 * 4;
+        Span sp{nullptr};
+        sp.take<int64_t>(nD);
+        sp.take<GT>(nD * ldT);
+        sp.take<GT>(nD * nD);
+        sp.take<GT>(nD * nD);
+        sp.take<GT>(nD);
+        sp.take<GT>(nD);
+        AS_TRY(ctx->ensure(&ws.Mc, &ws.Mc_cap, sp.used + 256, "masked-orbit correction"));
+        Span sm{(char*)ws.Mc};
+        int64_t* dpos_d = sm.take<int64_t>(nD);
+        GT* XdT = sm.take<GT>(nD * ldT);
+        GT* Hd = sm.take<GT>(nD * nD);
+        GT* Wd = sm.take<GT>(nD * nD);
+        GT* cD = sm.take<GT>(nD);
+        GT* uD = sm.take<GT>(nD);
+        AS_CUDA(ctx, cudaMemcpyAsync(dpos_d, dpos.data(), nD * sizeof(int64_t), cudaMemcpyHostToDevice, st),
+                "masked orbits");
+        {
+            LaunchTimer lt(ctx, K_PCG);
+            k_gather_xcols<GT><<<(unsigned)std::min<int64_t>((nD * nP + 255) / 256, (int64_t)ctx_sms(ctx) * 16), 256,
+                                 0, st>>>(X, ldG, nP, dpos_d, nD, XdT, ldT);
+        }
+        AS_CUDA(ctx, cudaGetLastError(), "masked orbits");
+        AS_CUDA(ctx, cudaMemsetAsync(Hd, 0, (size_t)nD * nD * sizeof(GT), st), "memset");
+        AS_CUDA(ctx, (gemm_acc<GT, true, false>(ctx, K_PCG, nD, nD, nP, GT(1), XdT, ldT, XdT, ldT, Hd, nD)),
+                "masked orbits");
+        std::vector<GT> hg((size_t)nD * nD);
+        AS_CUDA(ctx, cudaMemcpyAsync(hg.data(), Hd, hg.size() * sizeof(GT), cudaMemcpyDeviceToHost, st),
+                "masked orbits");
+        AS_CUDA(ctx, cudaStreamSynchronize(st), "masked orbits");
+        std::vector<double> H(hg.begin(), hg.end()), Wh;
+        double hmax = 0.0;
+        for (int64_t k = 0; k < nD; ++k) hmax = std::max(hmax, H[(size_t)k * nD + k]);
+        if (ctx->opt.verbose > 1) fprintf(stderr, "[sw]   mask: %lld orbits, max H_dd %.3g\n", (long long)nD, hmax);
+        if (!(hmax <= kMaskCond) || !spd_inverse(H, nD, Wh)) {
+            ++n_mask_refused;
+            return SW_OK;
+        }
+        std::vector<GT> wg(Wh.begin(), Wh.end());
+        AS_CUDA(ctx, cudaMemcpyAsync(Wd, wg.data(), wg.size() * sizeof(GT), cudaMemcpyHostToDevice, st),
+                "masked orbits");
+        AS_CUDA(ctx, cudaStreamSynchronize(st), "masked orbits");
+        mk_n = nD;
+        mk_ldT = ldT;
+        mk_XdT = XdT;
+        mk_W = Wd;
+        mk_cD = cD;
+        mk_uD = uD;
+        ok = mk_ready = true;
         return SW_OK;
     };
 
@@ -561,61 +661,10 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         AS_CUDA(ctx, cudaMemcpyAsync(V.mask, mh.data(), nP * sizeof(double), cudaMemcpyHostToDevice, st), "mask");
         AS_CUDA(ctx, gather_vec(ctx, V.q, V.idx, nP, V.qP), "q_P");
         const int nb = cg_blocks(ctx, nP);
-        // The masked orbits D = P0 \ F: with H = A^-1 = X^T X for the scaled, shifted Gram A of P0, the
-        // inverse of A_FF is (H - H_:D H_DD^-1 H_D:)_FF (block inverse), so the preconditioner applies
-        // z = X^T (t - X_:D u), t = X r, u = H_DD^-1 (X_:D^T t): exact on F up to the factor's rounding,
-        // where the masked form alone leaves |D| outlying eigenvalues to the iteration.  H_DD = X_:D^T
-        // X_:D is inverted on the host in FP64; above kMaskExactMax masked orbits the masked form stays.
-        constexpr int64_t kMaskExactMax = 384;
-        int64_t nDc = 0, ldT = 0;
-        GT *XdT = nullptr, *Wd = nullptr, *cD = nullptr, *uD = nullptr;
-        {
-            std::vector<int64_t> dpos;
-            for (int64_t k = 0; k < nP; ++k)
-                if (mh[k] == 0.0) dpos.push_back(k);
-            const int64_t nD = (int64_t)dpos.size();
-            if (nD > 0 && nD <= kMaskExactMax) {
-                ldT = (nP + 3) / 4 * 4;
-                Span sp{nullptr};
-                sp.take<int64_t>(nD);
-                sp.take<GT>(nD * ldT);
-                sp.take<GT>(nD * nD);
-                sp.take<GT>(nD * nD);
-                sp.take<GT>(nD);
-                sp.take<GT>(nD);
-                AS_TRY(ctx->ensure(&ws.Mc, &ws.Mc_cap, sp.used + 256, "masked-orbit correction"));
-                Span sm{(char*)ws.Mc};
-                int64_t* dpos_d = sm.take<int64_t>(nD);
-                XdT = sm.take<GT>(nD * ldT);
-                GT* Hd = sm.take<GT>(nD * nD);
-                Wd = sm.take<GT>(nD * nD);
-                cD = sm.take<GT>(nD);
-                uD = sm.take<GT>(nD);
-                AS_CUDA(ctx, cudaMemcpyAsync(dpos_d, dpos.data(), nD * sizeof(int64_t), cudaMemcpyHostToDevice, st),
-                        "masked orbits");
-                {
-                    LaunchTimer lt(ctx, K_PCG);
-                    k_gather_xcols<GT><<<(unsigned)std::min<int64_t>((nD * nP + 255) / 256, (int64_t)ctx_sms(ctx) * 16),
-                                         256, 0, st>>>(X, ldG, nP, dpos_d, nD, XdT, ldT);
-                }
-                AS_CUDA(ctx, cudaGetLastError(), "masked orbits");
-                AS_CUDA(ctx, cudaMemsetAsync(Hd, 0, (size_t)nD * nD * sizeof(GT), st), "memset");
-                AS_CUDA(ctx, (gemm_acc<GT, true, false>(ctx, K_PCG, nD, nD, nP, GT(1), XdT, ldT, XdT, ldT, Hd, nD)),
-                        "masked orbits");
-                std::vector<GT> hg((size_t)nD * nD);
-                AS_CUDA(ctx, cudaMemcpyAsync(hg.data(), Hd, hg.size() * sizeof(GT), cudaMemcpyDeviceToHost, st),
-                        "masked orbits");
-                AS_CUDA(ctx, cudaStreamSynchronize(st), "masked orbits");
-                std::vector<double> H(hg.begin(), hg.end()), Wh;
-                if (spd_inverse(H, nD, Wh)) {
-                    std::vector<GT> wg(Wh.begin(), Wh.end());
-                    AS_CUDA(ctx, cudaMemcpyAsync(Wd, wg.data(), wg.size() * sizeof(GT), cudaMemcpyHostToDevice, st),
-                            "masked orbits");
-                    AS_CUDA(ctx, cudaStreamSynchronize(st), "masked orbits");
-                    nDc = nD;
-                }
-            }
-        }
+        // the masked orbits' correction, when prepare_mask formed it for this passive set
+        const int64_t nDc = mk_ready ? mk_n : 0, ldT = mk_ldT;
+        GT *XdT = mk_XdT, *Wd = mk_W, *cD = mk_cD, *uD = mk_uD;
+        mk_ready = false;
         auto precond = [&](const double* r, double* z) -> sw_status {   // z = m S X^T X S r (corrected)
             AS_CUDA(ctx, scale_to<GT>(ctx, nP, r, V.sP, V.rs), "precondition");
             AS_CUDA(ctx, (rowdot<GT, GT, GT, GT>(ctx, K_TRMV_L, X, nP, nP, ldG, V.rs, V.t1, 1.0, 0.0, true)),
@@ -710,12 +759,17 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         return SW_OK;
     };
 
-    // exact state of zh over all N: negative gradient gh, projected gradient, chi^2
+    // exact state of zh over all N: negative gradient gh, projected gradient, chi^2.  With wP (the
+    // device copy of zh on P0, in P0's order; zh zero outside P0) U w is formed from P0's gathered
+    // columns instead of the whole matrix.
     double pg_rel = 1.0, chi_h[4] = {0, 0, 0, 0};
-    auto evaluate = [&]() -> sw_status {
+    auto evaluate = [&](const double* wP = nullptr) -> sw_status {
         AS_CUDA(ctx, cudaMemcpyAsync(V.w, zh.data(), N * sizeof(double), cudaMemcpyHostToDevice, st), "w");
         AS_CUDA(ctx, cudaMemsetAsync(V.acc, 0, M * sizeof(double), st), "memset");
-        AS_CUDA(ctx, u_times_w<T>(ctx, U, M, N, V.w, V.acc), "U w");
+        if (wP)
+            AS_CUDA(ctx, u_times_w<T>(ctx, (const T*)ws.Uc, M, (int64_t)P0.size(), wP, V.acc), "U_P w");
+        else
+            AS_CUDA(ctx, u_times_w<T>(ctx, U, M, N, V.w, V.acc), "U w");
         AS_CUDA(ctx, residual(ctx, M, y_dev, V.acc, V.inv_sig, V.e, V.xs), "residual");
         AS_CUDA(ctx, ut_times_x<T>(ctx, U, M, N, V.xs, V.ute), "U^T e");
         AS_CUDA(ctx, cudaMemsetAsync(pgmax, 0, 8, st), "memset");
@@ -805,7 +859,8 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             for (int64_t i = 0; i < N; ++i)
                 if (warm->F0[i]) { inF[i] = 1; F.push_back(i); }
         if (!F.empty()) {
-            bool conv = false;
+            bool conv = false, mok = false;
+            AS_TRY(prepare_mask(F, mok));   // masked-only without it
             AS_TRY(solve_on(F, conv));
             std::fill(zh.begin(), zh.end(), 0.0);
             for (int64_t i : F) zh[i] = xh[pos[i]];
@@ -818,7 +873,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
                 fbest = fproj;
                 for (int64_t i = 0; i < N; ++i) zbest[i] = std::max(zh[i], 0.0);
             }
-            AS_TRY(evaluate());
+            AS_TRY(evaluate(V.x));
             evaluated = true;
         }
     }
@@ -890,20 +945,31 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         for (int64_t i = 0; i < N; ++i)
             if (inF[i]) F.push_back(i);
         std::fill(zh.begin(), zh.end(), 0.0);
+        bool solved = false;   // V.x holds zh on P0
         if (!F.empty()) {
             bool ok = true, conv = false;
-            if (!factored_covers(F)) {
-                // a bordered factor keeps P0's factor as its leading block: a warm start's recorded
-                // factor survives it
+            // the factor of P0 serves F when it covers F and the masked orbits' correction can be formed
+            // (a warm start's recorded factor also runs masked-only); else it is bordered by the entering
+            // orbits; else F is factored.  A bordered factor keeps P0's factor as its leading block: a
+            // warm start's recorded factor survives it.
+            bool ready = false;
+            if (factored_covers(F)) {
+                bool mok = false;
+                AS_TRY(prepare_mask(F, mok));
+                ready = mok || (warm && warm->have_factor);
+            }
+            if (!ready) {
                 bool bordered = false;
                 AS_TRY(try_border(F, bordered));
-                if (!bordered) {
-                    AS_TRY(factor(F, ok));
-                    if (warm) warm->have_factor = false;   // P0 is now this passive set
-                }
+                if (bordered) AS_TRY(prepare_mask(F, ready));
+            }
+            if (!ready) {
+                AS_TRY(factor(F, ok));
+                if (warm) warm->have_factor = false;   // P0 is now this passive set
             }
             if (!ok) { failed = true; break; }
             AS_TRY(solve_on(F, conv));
+            solved = true;
             for (int64_t i : F) zh[i] = xh[pos[i]];
             buf.assign(P0.size(), 0.0);
             for (int64_t i : F) buf[pos[i]] = std::max(zh[i], 0.0);
@@ -917,7 +983,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             fbest = fproj;
             for (int64_t i = 0; i < N; ++i) zbest[i] = std::max(zh[i], 0.0);
         }
-        AS_TRY(evaluate());
+        AS_TRY(evaluate(solved ? V.x : nullptr));
         evaluated = true;
     }
     if (!converged) {   // return the best projected iterate
@@ -978,8 +1044,11 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
     ctx->solve_info[6] = outer + 1;
     ctx->solve_info[7] = (double)support;
     if (ctx->opt.verbose)
-        fprintf(stderr, "[sw] active set done: support %lld solves %d factors %d borders %d cg %d pg_rel %.3g%s\n",
-                (long long)support, n_solves, n_factor, n_border, cg_total, pg_rel, converged ? "" : " (stopped)");
+        fprintf(stderr,
+                "[sw] active set done: support %lld solves %d factors %d borders %d (masks refused %d) cg %d "
+                "pg_rel %.3g%s\n",
+                (long long)support, n_solves, n_factor, n_border, n_mask_refused, cg_total, pg_rel,
+                converged ? "" : " (stopped)");
     if (failed) {
         set_error(ctx, "solve: reduced Gram not positive definite after ridge retries (|F| %zu)", F.size());
         return SW_ENONCONV;
