@@ -314,6 +314,9 @@ int64_t sw_alloc_count(const sw_ctx* ctx);
  *                           serves more passive sets but preconditions the masked solves worse)
  *  "chol_pdl" (0/1)         tensor-core factorisation: each panel kernel launched programmatically behind its
  *                           diagonal-block kernel, staging its rows while that block is factored (default 1)
+ *  "chol_super" (0/1)       tensor-core factorisation: two 128-wide diagonal blocks per step, their panels side by
+ *                           side, so that the trailing matrix and the inverse take one rank-256 update per two
+ *                           blocks (default 1); 0: a rank-128 update per block
  *  "chol_reserve_sms" (>= 0) tensor-core factorisation: SMs that the bulk trailing and inverse updates leave free
  *                           for the next steps' diagonal-block chain on the context's stream (default 8)
  *  "integrator" (0/1)       sw_project's integrator: 0 (default) kick-drift-kick at the fixed dt in the inertial

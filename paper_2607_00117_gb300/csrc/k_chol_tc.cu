@@ -424,7 +424,8 @@ constexpr size_t DIAG_SMEM = sizeof(float) * (2 * DB * AP + SB * CTP + 2 * TBUF 
 
 // ---------------------------------------------------------------------------
 // 2. Panel: P = A D^T for m rows below the diagonal block (A = G[r0 + i][j0 ..
-// j0 + 127]), in place in G, and its BF16 hi + lo halves (m x 128 row-major).
+// j0 + 127]), in place in G, and its BF16 hi + lo halves (m x 128, rows pst
+// elements apart: 128, or 256 when two panels share a row).
 // 32 rows per CTA of 256 threads; thread (tr, tc) = (t / 16, t % 16) computes
 // rows 2 tr, 2 tr + 1 and columns 4 tc .. 4 tc + 3 and 64 + 4 tc .. 64 + 4 tc +
 // 3 (two 16-byte loads of a row of D^T in distinct bank groups).  D arrives
@@ -434,7 +435,8 @@ constexpr int PR = 32;
 constexpr int DTP = DB + 4;   // padded row of DT (16-byte aligned, conflict-free float4 rows)
 __global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t ld, int64_t j0, int64_t r0,
                                                   int64_t m, const float* __restrict__ Dt,
-                                                  __nv_bfloat16* __restrict__ Ph, __nv_bfloat16* __restrict__ Pl)
+                                                  __nv_bfloat16* __restrict__ Ph, __nv_bfloat16* __restrict__ Pl,
+                                                  int pst)
 {
     extern __shared__ __align__(16) float sm[];
     float* DT = sm;              // DB x DTP
@@ -492,8 +494,8 @@ __global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t
                 hw[q / 2] = (uint32_t)__bfloat16_as_ushort(h.x) | ((uint32_t)__bfloat16_as_ushort(h.y) << 16);
                 lw[q / 2] = (uint32_t)__bfloat16_as_ushort(lo.x) | ((uint32_t)__bfloat16_as_ushort(lo.y) << 16);
             }
-            *reinterpret_cast<uint2*>(Ph + (size_t)gi * DB + c) = make_uint2(hw[0], hw[1]);
-            *reinterpret_cast<uint2*>(Pl + (size_t)gi * DB + c) = make_uint2(lw[0], lw[1]);
+            *reinterpret_cast<uint2*>(Ph + (size_t)gi * pst + c) = make_uint2(hw[0], hw[1]);
+            *reinterpret_cast<uint2*>(Pl + (size_t)gi * pst + c) = make_uint2(lw[0], lw[1]);
         }
     }
 }
@@ -503,7 +505,7 @@ constexpr size_t PANEL_SMEM = sizeof(float) * (PR * LP + DB * DTP);
 // ---------------------------------------------------------------------------
 // 4. Block row of the inverse: X[j0 + i][c] <- sum_l D[i][l] X[j0 + l][c] for
 // the ncols leading columns (in place), and its transpose as BF16 hi + lo
-// halves: XT[c][i] (ncols x 128 row-major).  32 columns per CTA of 256
+// halves: XT[c][i] (ncols x 128, rows xst elements apart: 128 or 256).  32 columns per CTA of 256
 // threads; thread (trow, tcol) = (t / 16, t % 16) computes rows 8 trow .. 8
 // trow + 7 and columns 2 tcol, 2 tcol + 1.  D arrives transposed (Dt[l][i] =
 // D[i][l]) and is staged by 16-byte copies.
@@ -512,7 +514,8 @@ constexpr int TC = 32;
 constexpr int SSP = TC + 4;
 __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t ld, int64_t j0, int bs,
                                                  int64_t ncols, const float* __restrict__ Dt,
-                                                 __nv_bfloat16* __restrict__ XTh, __nv_bfloat16* __restrict__ XTl)
+                                                 __nv_bfloat16* __restrict__ XTh, __nv_bfloat16* __restrict__ XTl,
+                                                 int xst)
 {
     extern __shared__ __align__(16) float sm[];
     float* DT = sm;                   // DB x DTP
@@ -571,9 +574,9 @@ __global__ void __launch_bounds__(256) k_trmm128(float* __restrict__ X, int64_t 
         const int cc = e >> 4, ch = e & 15;
         const int64_t gc = c0 + cc;
         if (gc >= ncols) continue;
-        *reinterpret_cast<uint4*>(XTh + (size_t)gc * DB + ch * 8) =
+        *reinterpret_cast<uint4*>(XTh + (size_t)gc * xst + ch * 8) =
             *reinterpret_cast<const uint4*>(Th + cc * (DB + 8) + ch * 8);
-        *reinterpret_cast<uint4*>(XTl + (size_t)gc * DB + ch * 8) =
+        *reinterpret_cast<uint4*>(XTl + (size_t)gc * xst + ch * 8) =
             *reinterpret_cast<const uint4*>(Tl + cc * (DB + 8) + ch * 8);
     }
 }
@@ -823,11 +826,11 @@ static bool make_cmap(CUtensorMap* map, float* C, int64_t K, int64_t ld)
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// rows x 128 BF16, row-major (256-byte rows): boxes of 64 x 128 with the 128-byte swizzle
-static bool make_map(CUtensorMap* map, const __nv_bfloat16* A, int64_t rows)
+// rows x width BF16, row-major (width 128 or 256): boxes of 64 x 128 with the 128-byte swizzle
+static bool make_map(CUtensorMap* map, const __nv_bfloat16* A, int64_t rows, int64_t width = DB)
 {
-    cuuint64_t dims[2] = {(cuuint64_t)DB, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)DB * 2};
+    cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)width * 2};
     cuuint32_t box[2] = {BKC, BM};
     cuuint32_t estr[2] = {1, 1};
     return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)A, dims, strides, box, estr,
@@ -868,9 +871,10 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
     cudaStream_t sb = la && ctx->stream2 ? ctx->stream2 : st;   // the bulk updates' stream
     const bool two = sb != st;
     // dependency events: rings of 3 for "panel k done" (P), "rest of the trailing update k done"
-    // (R) and "step k's bulk work done" (B); no dependency reaches further back than two steps
-    if (two && ctx->dep_events.size() < 9) {
-        while (ctx->dep_events.size() < 9) {
+    // (R), "step k's bulk work done" (B) and, in 256-wide super-steps, "second panel done" (Q); no
+    // dependency reaches further back than two steps
+    if (two && ctx->dep_events.size() < 12) {
+        while (ctx->dep_events.size() < 12) {
             cudaEvent_t ev;
             if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return cudaErrorUnknown;
             ctx->dep_events.push_back(ev);
@@ -879,24 +883,81 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
     auto evP = [&](int64_t k) { return ctx->dep_events[0 + k % 3]; };
     auto evR = [&](int64_t k) { return ctx->dep_events[3 + k % 3]; };
     auto evB = [&](int64_t k) { return ctx->dep_events[6 + k % 3]; };
-    // scratch, double-buffered by step parity where the two streams overlap: D_k (128 x 128 FP32)
-    // and the panel's BF16 halves (K x 128 each); the inverse block row's halves (K x 128 each)
+    auto evQ = [&](int64_t k) { return ctx->dep_events[9 + k % 3]; };
+    // scratch, double-buffered by step parity where the two streams overlap: the D blocks (128 x 128
+    // FP32; two per super-step) and the panels' BF16 halves (K x W each); the inverse block rows'
+    // halves (K x W each), W = 128, or 256 for two panels side by side
+    const bool sup = ctx->opt.chol_super != 0;
+    const int W = sup ? 2 * DB : DB;
+    const int nd = sup ? 4 : 2;
     const size_t dbytes = (size_t)DB * DB * sizeof(float);
-    const size_t hbytes = ((size_t)K * DB * sizeof(__nv_bfloat16) + 255) & ~(size_t)255;
-    if (ctx->ensure(&ctx->d_chol_tc, &ctx->chol_tc_cap, 2 * dbytes + 6 * hbytes + 256, "factor scratch") != SW_OK)
+    const size_t hbytes = ((size_t)K * W * sizeof(__nv_bfloat16) + 255) & ~(size_t)255;
+    if (ctx->ensure(&ctx->d_chol_tc, &ctx->chol_tc_cap, nd * dbytes + 6 * hbytes + 256, "factor scratch") != SW_OK)
         return cudaErrorMemoryAllocation;
     char* base = (char*)ctx->d_chol_tc;
-    float* Dk[2] = {(float*)base, (float*)(base + dbytes)};
-    __nv_bfloat16* Ph[2] = {(__nv_bfloat16*)(base + 2 * dbytes), (__nv_bfloat16*)(base + 2 * dbytes + hbytes)};
-    __nv_bfloat16* Pl[2] = {(__nv_bfloat16*)(base + 2 * dbytes + 2 * hbytes),
-                            (__nv_bfloat16*)(base + 2 * dbytes + 3 * hbytes)};
-    __nv_bfloat16* XTh = (__nv_bfloat16*)(base + 2 * dbytes + 4 * hbytes);
-    __nv_bfloat16* XTl = (__nv_bfloat16*)(base + 2 * dbytes + 5 * hbytes);
+    float* Dk[4] = {(float*)base, (float*)(base + dbytes), (float*)(base + 2 * dbytes), (float*)(base + 3 * dbytes)};
+    char* hb = base + nd * dbytes;
+    __nv_bfloat16* Ph[2] = {(__nv_bfloat16*)hb, (__nv_bfloat16*)(hb + hbytes)};
+    __nv_bfloat16* Pl[2] = {(__nv_bfloat16*)(hb + 2 * hbytes), (__nv_bfloat16*)(hb + 3 * hbytes)};
+    __nv_bfloat16* XTh = (__nv_bfloat16*)(hb + 4 * hbytes);
+    __nv_bfloat16* XTl = (__nv_bfloat16*)(hb + 5 * hbytes);
     CUtensorMap mph[2], mpl[2], mxh, mxl, mg, mx;
     for (int b = 0; b < 2; ++b)
-        if (!make_map(&mph[b], Ph[b], K) || !make_map(&mpl[b], Pl[b], K)) return cudaErrorInvalidValue;
-    if (!make_map(&mxh, XTh, K) || !make_map(&mxl, XTl, K) || !make_cmap(&mg, G, K, ld) || !make_cmap(&mx, X, K, ld))
+        if (!make_map(&mph[b], Ph[b], K, W) || !make_map(&mpl[b], Pl[b], K, W)) return cudaErrorInvalidValue;
+    if (!make_map(&mxh, XTh, K, W) || !make_map(&mxl, XTl, K, W) || !make_cmap(&mg, G, K, ld) ||
+        !make_cmap(&mx, X, K, ld))
         return cudaErrorInvalidValue;
+    const unsigned grid_cap = (unsigned)ctx_sms(ctx);
+    // the bulk updates (stream B) may leave SMs free for the next steps' chain on stream A
+    const unsigned bulk_cap = (unsigned)std::max(1, ctx_sms(ctx) - (two ? ctx->opt.chol_reserve_sms : 0));
+    auto tc_launch = [&](cudaStream_t s, int kid, bool lower, const CUtensorMap& a, const CUtensorMap& al,
+                         const CUtensorMap& bm, const CUtensorMap& bl, const CUtensorMap& c, int cx0, int cy0,
+                         int ra0, int rb0, int64_t tiles, int64_t tiles_n, double flops,
+                         int depth = DB) -> cudaError_t {
+        if (tiles <= 0) return cudaSuccess;
+        LaunchTimer lt(ctx, kid, s);
+        add_work(ctx, kid, flops);
+        const unsigned g = (unsigned)std::min<int64_t>(tiles, s == st ? grid_cap : bulk_cap);
+        if (lower)
+            k_tc_sub<true><<<g, SUB_THREADS, SUB_SMEM, s>>>(a, al, bm, bl, c, cx0, cy0, ra0, rb0, tiles, tiles_n,
+                                                           depth / BKC, d_err);
+        else
+            k_tc_sub<false><<<g, SUB_THREADS, SUB_SMEM, s>>>(a, al, bm, bl, c, cx0, cy0, ra0, rb0, tiles, tiles_n,
+                                                            depth / BKC, d_err);
+        return cudaGetLastError();
+    };
+    auto diag_launch = [&](int64_t j0, int bs, float* D) -> cudaError_t {
+        LaunchTimer lt(ctx, K_POTRF_DIAG);
+        add_work(ctx, K_POTRF_DIAG, 2.0 * (double)bs * bs * bs / 3.0);
+        k_diag128<<<1, DIAG_THREADS, DIAG_SMEM, st>>>(G, ld, j0, bs, D, d_info, keep_L ? 1 : 0);
+        return cudaGetLastError();
+    };
+    // the panel is launched programmatically behind its diagonal block: its row staging overlaps it
+    auto panel_launch = [&](int64_t j0, int64_t r0, int64_t m, const float* D, __nv_bfloat16* ph,
+                            __nv_bfloat16* pl) -> cudaError_t {
+        if (m <= 0) return cudaSuccess;
+        LaunchTimer lt(ctx, K_TRSM_PANEL);
+        add_work(ctx, K_TRSM_PANEL, (double)m * DB * DB);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)((m + PR - 1) / PR));
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = PANEL_SMEM;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = ctx->opt.chol_pdl ? 1 : 0;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_panel128, G, ld, j0, r0, m, D, ph, pl, W);
+        return e ? e : cudaGetLastError();
+    };
+    auto trmm_launch = [&](int64_t j0, int bs, int64_t ncols, const float* D, __nv_bfloat16* xh,
+                           __nv_bfloat16* xl) -> cudaError_t {
+        LaunchTimer lt(ctx, K_TRINV_DIAG, sb);
+        add_work(ctx, K_TRINV_DIAG, (double)bs * bs * (double)ncols);
+        k_trmm128<<<(unsigned)((ncols + TC - 1) / TC), 256, TRMM_SMEM, sb>>>(X, ld, j0, bs, ncols, D, xh, xl, W);
+        return cudaGetLastError();
+    };
     cudaError_t e;
     // X = I
     if ((e = cudaMemsetAsync(X, 0, (size_t)K * ld * sizeof(float), st))) return e;
@@ -904,30 +965,96 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
         LaunchTimer lt(ctx, K_MISC);
         k_unit_diag<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(X, K, ld);
     }
-    const unsigned grid_cap = (unsigned)ctx_sms(ctx);
-    // the bulk updates (stream B) may leave SMs free for the next steps' chain on stream A
-    const unsigned bulk_cap = (unsigned)std::max(1, ctx_sms(ctx) - (two ? ctx->opt.chol_reserve_sms : 0));
-    auto tc_launch = [&](cudaStream_t s, int kid, bool lower, const CUtensorMap& a, const CUtensorMap& al,
-                         const CUtensorMap& bm, const CUtensorMap& bl, const CUtensorMap& c, int cx0, int cy0,
-                         int ra0, int rb0, int64_t tiles, int64_t tiles_n, double flops) -> cudaError_t {
-        if (tiles <= 0) return cudaSuccess;
-        LaunchTimer lt(ctx, kid, s);
-        add_work(ctx, kid, flops);
-        const unsigned g = (unsigned)std::min<int64_t>(tiles, s == st ? grid_cap : bulk_cap);
-        if (lower)
-            k_tc_sub<true><<<g, SUB_THREADS, SUB_SMEM, s>>>(a, al, bm, bl, c, cx0, cy0, ra0, rb0, tiles, tiles_n,
-                                                           DB / BKC, d_err);
-        else
-            k_tc_sub<false><<<g, SUB_THREADS, SUB_SMEM, s>>>(a, al, bm, bl, c, cx0, cy0, ra0, rb0, tiles, tiles_n,
-                                                            DB / BKC, d_err);
-        return cudaGetLastError();
-    };
+    const int64_t nb = (K + DB - 1) / DB;
+    if (sup) {
+        // 256-wide super-steps: blocks a = 2 s and b = 2 s + 1.  The panels of a and b sit side by side
+        // in the rows of P (row g - r0a for global row g >= r0a; P_a in columns 0 .. 127, P_b in 128 ..
+        // 255 from row 128 on), so the trailing matrix and the inverse's rows below b take one
+        // rank-256 update per super-step: one read-modify-write pass where 128-wide steps make two.
+        //   chain (stream A): diag a, panel a, block column b -= P_a P_a^T (rank 128), diag b, panel b,
+        //                     block column a + 2 -= [P_a P_b][P_a P_b]^T (rank 256);
+        //   bulk (stream B):  X_a <- D_a X_a, the rest of the trailing matrix (rank 256), block row b of
+        //                     the inverse -= L_ba X_a (rank 128), X_b <- D_b X_b, the rows below b
+        //                     -= [L_ia L_ib][X_a; X_b] (rank 256).
+        // XT holds the transposed block rows side by side (X_a in columns 0 .. 127, zero in the rows of
+        // block b; X_b in 128 .. 255).
+        const int64_t ns = (nb + 1) / 2;
+        for (int64_t si = 0; si < ns; ++si) {
+            const int64_t ka = 2 * si, kbb = 2 * si + 1;
+            const bool hasb = kbb < nb;
+            const int64_t j0a = ka * DB;
+            const int bsa = (int)(K - j0a < DB ? K - j0a : DB);
+            const int64_t r0a = j0a + bsa, ma = K - r0a;
+            const int64_t j0b = r0a;
+            const int bsb = hasb ? (int)(K - j0b < DB ? K - j0b : DB) : 0;
+            const int64_t r0b = j0b + bsb, mb = hasb ? K - r0b : 0;
+            const int par = (int)(si & 1);
+            float* Da = Dk[2 * par];
+            float* Db = Dk[2 * par + 1];
+            const int64_t Ta = (ma + BM - 1) / BM, Tb = (mb + BM - 1) / BM;
+            // ---- chain
+            // the buffers of parity par were last read by super-step si - 2's bulk work
+            if (two && si >= 2 && (e = cudaStreamWaitEvent(st, evB(si - 2), 0))) return e;
+            if ((e = diag_launch(j0a, bsa, Da))) return e;
+            if ((e = panel_launch(j0a, r0a, ma, Da, Ph[par], Pl[par]))) return e;
+            if (two && (e = cudaEventRecord(evP(si), st))) return e;
+            if (hasb) {
+                // block column b, last updated by super-step si - 1's rest
+                if (two && si >= 1 && (e = cudaStreamWaitEvent(st, evR(si - 1), 0))) return e;
+                if ((e = tc_launch(st, K_SYRK_TC, false, mph[par], mpl[par], mph[par], mpl[par], mg, (int)r0a, (int)r0a,
+                                   0, 0, Ta, 1, 2.0 * (double)ma * std::min<int64_t>(ma, BN) * DB, DB)))
+                    return e;
+                if ((e = diag_launch(j0b, bsb, Db))) return e;
+                // P_b from row 128 of P, columns 128 .. 255 (mb > 0 only when block b is full)
+                if ((e = panel_launch(j0b, r0b, mb, Db, Ph[par] + (size_t)DB * W + DB, Pl[par] + (size_t)DB * W + DB)))
+                    return e;
+                if (two && (e = cudaEventRecord(evQ(si), st))) return e;
+                if (mb > 0 &&
+                    (e = tc_launch(st, K_SYRK_TC, false, mph[par], mpl[par], mph[par], mpl[par], mg, (int)r0b,
+                                   (int)r0b, DB, DB, Tb, 1, 2.0 * (double)mb * std::min<int64_t>(mb, BN) * 2 * DB,
+                                   2 * DB)))
+                    return e;
+            }
+            // ---- bulk
+            if (two && (e = cudaStreamWaitEvent(sb, evP(si), 0))) return e;
+            if ((e = trmm_launch(j0a, bsa, r0a, Da, XTh, XTl))) return e;
+            if (hasb) {
+                // X_a has no entries in the columns of block b
+                if ((e = cudaMemset2DAsync(XTh + (size_t)r0a * W, (size_t)W * 2, 0, (size_t)DB * 2, (size_t)bsb, sb)) ||
+                    (e = cudaMemset2DAsync(XTl + (size_t)r0a * W, (size_t)W * 2, 0, (size_t)DB * 2, (size_t)bsb, sb)))
+                    return e;
+                if (two && (e = cudaStreamWaitEvent(sb, evQ(si), 0))) return e;
+                if (Tb > 1) {
+                    const int64_t T1 = Tb - 1;
+                    const double mr = (double)(mb - BN);
+                    if ((e = tc_launch(sb, K_SYRK_TC, true, mph[par], mpl[par], mph[par], mpl[par], mg, (int)(r0b + BN),
+                                       (int)(r0b + BN), 2 * DB, 2 * DB, T1 * (T1 + 1) / 2, T1,
+                                       mr * (mr + 1.0) * 2 * DB, 2 * DB)))
+                        return e;
+                }
+            }
+            if (two && (e = cudaEventRecord(evR(si), sb))) return e;
+            if (hasb) {
+                const int64_t Tna = (r0a + BN - 1) / BN, Tnb = (r0b + BN - 1) / BN;
+                // block row b of the inverse: X_b -= L_ba X_a
+                if ((e = tc_launch(sb, K_TRINV_TC, false, mph[par], mpl[par], mxh, mxl, mx, 0, (int)j0b, 0, 0, Tna, Tna,
+                                   2.0 * (double)bsb * (double)r0a * DB, DB)))
+                    return e;
+                if ((e = trmm_launch(j0b, bsb, r0b, Db, XTh + DB, XTl + DB))) return e;
+                if (mb > 0 && (e = tc_launch(sb, K_TRINV_TC, false, mph[par], mpl[par], mxh, mxl, mx, 0, (int)r0b, DB, 0,
+                                             Tb * Tnb, Tnb, 2.0 * (double)mb * (double)r0b * 2 * DB, 2 * DB)))
+                    return e;
+            }
+            if (two && (e = cudaEventRecord(evB(si), sb))) return e;
+        }
+        if (two && (e = cudaStreamWaitEvent(st, evB(ns - 1), 0))) return e;
+        return cudaSuccess;
+    }
     // Step k.  Stream A (the context's): diagonal block, panel and the trailing update's first
     // tile column (the next diagonal block's column), the chain every later step waits for.
     // Stream B: the rest of the trailing update, the inverse's block row and its update of the
     // rows below -- the bulk work, which overlaps the next steps' chain.  Without a second
     // stream everything runs in this order on A.
-    const int64_t nb = (K + DB - 1) / DB;
     for (int64_t kb = 0; kb < nb; ++kb) {
         const int64_t j0 = kb * DB;
         const int bs = (int)(K - j0 < DB ? K - j0 : DB);
@@ -957,7 +1084,7 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
                 at[0].val.programmaticStreamSerializationAllowed = ctx->opt.chol_pdl ? 1 : 0;
                 cfg.attrs = at;
                 cfg.numAttrs = 1;
-                e = cudaLaunchKernelEx(&cfg, k_panel128, G, ld, j0, r0, m, (const float*)Dk[par], Ph[par], Pl[par]);
+                e = cudaLaunchKernelEx(&cfg, k_panel128, G, ld, j0, r0, m, (const float*)Dk[par], Ph[par], Pl[par], DB);
                 if (e) return e;
             }
             if ((e = cudaGetLastError())) return e;
@@ -983,7 +1110,8 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
         {
             LaunchTimer lt(ctx, K_TRINV_DIAG, sb);
             add_work(ctx, K_TRINV_DIAG, (double)bs * bs * (double)r0);
-            k_trmm128<<<(unsigned)((r0 + TC - 1) / TC), 256, TRMM_SMEM, sb>>>(X, ld, j0, bs, r0, Dk[par], XTh, XTl);
+            k_trmm128<<<(unsigned)((r0 + TC - 1) / TC), 256, TRMM_SMEM, sb>>>(X, ld, j0, bs, r0, Dk[par], XTh, XTl,
+                                                                             DB);
         }
         if ((e = cudaGetLastError())) return e;
         if (m > 0) {
