@@ -314,6 +314,9 @@ int64_t sw_alloc_count(const sw_ctx* ctx);
  *                           serves more passive sets but preconditions the masked solves worse)
  *  "chol_pdl" (0/1)         tensor-core factorisation: each panel kernel launched programmatically behind its
  *                           diagonal-block kernel, staging its rows while that block is factored (default 1)
+ *  "chol_panel_tc" (0/1)    tensor-core factorisation, 256-wide steps: each panel P = A D^T on the tensor cores from
+ *                           the BF16 hi + lo split of A and D (1), or in FP32 SIMT (default 0: as fast, and the
+ *                           FP32 panel keeps the preconditioner closer, fewer conjugate-gradient steps)
  *  "chol_super" (0/1)       tensor-core factorisation: two 128-wide diagonal blocks per step, their panels side by
  *                           side, so that the trailing matrix and the inverse take one rank-256 update per two
  *                           blocks (default 1); 0: a rank-128 update per block

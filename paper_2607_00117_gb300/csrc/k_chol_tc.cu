@@ -42,6 +42,25 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
     lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
+// eight FP32 values as their BF16 hi and lo halves, 16 bytes each (element 2q in the low half of word q)
+__device__ __forceinline__ void split8(const float (&v)[8], uint4& h, uint4& l)
+{
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(v[2 * q] - __low2float(hh), v[2 * q + 1] - __high2float(hh));
+        hw[q] = (uint32_t)__bfloat16_as_ushort(hh.x) | ((uint32_t)__bfloat16_as_ushort(hh.y) << 16);
+        lw[q] = (uint32_t)__bfloat16_as_ushort(ll.x) | ((uint32_t)__bfloat16_as_ushort(ll.y) << 16);
+    }
+    h = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    l = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
+// byte offset of the 16-byte chunk j (elements 8 j .. 8 j + 7) of row r in a 128 x 64 BF16 box with the
+// 128-byte swizzle (the layout a TMA load with that swizzle produces, which the UMMA descriptor reads)
+__device__ __forceinline__ int sw128_off(int r, int j) { return r * 128 + ((j ^ (r & 7)) << 4); }
+
 // ---------------------------------------------------------------------------
 // 1. Diagonal block: Cholesky and triangular inverse, blocked by 32 inside the
 // CTA (256 threads).  The block sits in shared memory (A, row pitch AP; rows
@@ -233,7 +252,7 @@ __device__ __noinline__ void warp_factor32(float* __restrict__ A, float* __restr
 
 __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__ G, int64_t ld, int64_t j0, int bs,
                                                              float* __restrict__ D /* D_k^T */, int* info,
-                                                             int write_L)
+                                                             int write_L, uint4* __restrict__ Dsw)
 {
     extern __shared__ __align__(16) float sm[];
     float* A = sm;                  // DB x AP: the block, then L
@@ -418,6 +437,25 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag128(float* __restrict__
             D[(l4 + 3) * DB + c] = cin && l4 + 3 <= c ? v.w : 0.f;
         }
     }
+    // D as the tensor-core panel's B operand (Dsw non-NULL): the BF16 hi and lo halves of D[c][l] (zero
+    // for l > c or c >= bs), rows c, in four 128 x 64 boxes of 16 KB -- hi l < 64, hi l >= 64, lo l < 64,
+    // lo l >= 64 -- in the 128-byte-swizzled layout, so that one flat copy puts them in shared memory
+    if (Dsw) {
+#pragma unroll 2
+        for (int u = t; u < DB * 16; u += DIAG_THREADS) {
+            const int c = u >> 4, j16 = u & 15, b = j16 >> 3, j = j16 & 7, l0 = 8 * j16;
+            const float4 x0 = ld4(X + c * AP + l0), x1 = ld4(X + c * AP + l0 + 4);
+            const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = (c < bs && l0 + q <= c) ? xv[q] : 0.f;
+            uint4 h, l;
+            split8(v, h, l);
+            const int off = sw128_off(c, j) >> 4;
+            Dsw[b * 1024 + off] = h;
+            Dsw[(2 + b) * 1024 + off] = l;
+        }
+    }
 }
 
 constexpr size_t DIAG_SMEM = sizeof(float) * (2 * DB * AP + SB * CTP + 2 * TBUF + SB);
@@ -501,6 +539,140 @@ __global__ void __launch_bounds__(256) k_panel128(float* __restrict__ G, int64_t
 }
 
 constexpr size_t PANEL_SMEM = sizeof(float) * (PR * LP + DB * DTP);
+
+// ---------------------------------------------------------------------------
+// 2'. Panel on the tensor cores: the same P = A D^T, one 128-row tile per CTA of 128
+// threads.  The CTA splits its rows of A (FP32, final before the diagonal block began,
+// so staged before the programmatic wait) into BF16 hi + lo halves in the 128-byte-
+// swizzled K-major layout, copies the diagonal kernel's split D (Dsw) in one bulk copy,
+// and one thread issues the three leading products of the split (hi hi, hi lo, lo hi)
+// into a 128-column TMEM accumulator; each warp then drains its 32 rows, writing P in
+// place into G and its own BF16 halves.  Waits are bounded: on expiry the CTA records an
+// error, waits for its products once more (bounded), frees TMEM and returns.
+// ---------------------------------------------------------------------------
+constexpr int PT_BOX = 128 * 64 * 2;                    // one 128 x 64 BF16 box
+constexpr int PT_SMEM = 8 * PT_BOX + 1024 + 64;
+__global__ void __launch_bounds__(128, 1) k_panel_tc(float* __restrict__ G, int64_t ld, int64_t j0, int64_t r0,
+                                                     int64_t m, const uint4* __restrict__ Dsw,
+                                                     __nv_bfloat16* __restrict__ Ph, __nv_bfloat16* __restrict__ Pl,
+                                                     int pst, int* err)
+{
+    extern __shared__ unsigned char smraw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    unsigned char* Ahi = base;                 // boxes: columns 0 .. 63, 64 .. 127
+    unsigned char* Alo = base + 2 * PT_BOX;
+    unsigned char* Bop = base + 4 * PT_BOX;    // D: hi 0 .. 63, hi 64 .. 127, lo 0 .. 63, lo 64 .. 127
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + 8 * PT_BOX);   // [0] the copy of D, [1] the products
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    volatile int* go = reinterpret_cast<volatile int*>(tslot + 1);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * 128;
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // A: sixteen (row, 8-column chunk) units per thread, a warp covering two rows with 512-byte reads
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+        const int u = t + 128 * k, i = u >> 4, j16 = u & 15;
+        const int64_t gi = row0 + i;
+        float v[8];
+        if (gi < m) {
+            const float* g = G + (size_t)(r0 + gi) * ld + j0 + 8 * j16;
+            const float4 a0 = *reinterpret_cast<const float4*>(g), a1 = *reinterpret_cast<const float4*>(g + 4);
+            v[0] = a0.x; v[1] = a0.y; v[2] = a0.z; v[3] = a0.w; v[4] = a1.x; v[5] = a1.y; v[6] = a1.z; v[7] = a1.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = 0.f;
+        }
+        uint4 h, l;
+        split8(v, h, l);
+        const int off = (j16 >> 3) * PT_BOX + sw128_off(i, j16 & 7);
+        *reinterpret_cast<uint4*>(Ahi + off) = h;
+        *reinterpret_cast<uint4*>(Alo + off) = l;
+    }
+    // D comes from the diagonal-block kernel just before this one
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    fence_proxy_async_smem();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    if (t == 0) {
+        mbar_expect_tx(&bar[0], 4 * PT_BOX);
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         su32(Bop)),
+                     "l"((uint64_t)Dsw), "r"(4 * PT_BOX), "r"(su32(&bar[0]))
+                     : "memory");
+        int ok = mbar_wait(&bar[0], 0) ? 1 : 0;
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = idesc_bf16(128, 128);
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const uint64_t da = smem_desc(su32(Ahi + b * PT_BOX)), dal = smem_desc(su32(Alo + b * PT_BOX));
+                const uint64_t db = smem_desc(su32(Bop + b * PT_BOX)), dbl = smem_desc(su32(Bop + (2 + b) * PT_BOX));
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    umma(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (b | k) != 0);
+                    umma(tmem, da + (uint64_t)(2 * k), dbl + (uint64_t)(2 * k), idesc, 1u);
+                    umma(tmem, dal + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, 1u);
+                }
+            }
+            umma_commit(&bar[1]);
+        } else {
+            atomicExch(err, 1);
+            mbar_wait(&bar[0], 0);   // the copy may still be in flight: one more bounded wait
+        }
+        *go = ok;
+    }
+    __syncthreads();
+    if (*go) {
+        if (!mbar_wait(&bar[1], 0)) {
+            if (lane == 0) atomicExch(err, 1);
+            mbar_wait(&bar[1], 0);   // its products still run: give them one more bounded wait
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int i = 32 * warp + lane;
+            const int64_t gi = row0 + i;
+#pragma unroll 1
+            for (int c0 = 0; c0 < DB; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+                if (gi < m) {
+                    float* g = G + (size_t)(r0 + gi) * ld + j0 + c0;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        *reinterpret_cast<float4*>(g + 4 * q) =
+                            make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                        __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float f[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) f[e] = __uint_as_float(v[8 * q + e]);
+                        uint4 h, l;
+                        split8(f, h, l);
+                        *reinterpret_cast<uint4*>(Ph + (size_t)gi * pst + c0 + 8 * q) = h;
+                        *reinterpret_cast<uint4*>(Pl + (size_t)gi * pst + c0 + 8 * q) = l;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+    }
+}
 
 // ---------------------------------------------------------------------------
 // 4. Block row of the inverse: X[j0 + i][c] <- sum_l D[i][l] X[j0 + l][c] for
@@ -854,6 +1026,7 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
         cudaError_t e;
         if ((e = cudaFuncSetAttribute(k_diag128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DIAG_SMEM)) ||
             (e = cudaFuncSetAttribute(k_panel128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM)) ||
+            (e = cudaFuncSetAttribute(k_panel_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, PT_SMEM)) ||
             (e = cudaFuncSetAttribute(k_trmm128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TRMM_SMEM)) ||
             (e = cudaFuncSetAttribute(k_tc_sub<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SUB_SMEM)) ||
             (e = cudaFuncSetAttribute(k_tc_sub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SUB_SMEM)))
@@ -892,11 +1065,18 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
     const int nd = sup ? 4 : 2;
     const size_t dbytes = (size_t)DB * DB * sizeof(float);
     const size_t hbytes = ((size_t)K * W * sizeof(__nv_bfloat16) + 255) & ~(size_t)255;
-    if (ctx->ensure(&ctx->d_chol_tc, &ctx->chol_tc_cap, nd * dbytes + 6 * hbytes + 256, "factor scratch") != SW_OK)
+    // with the tensor-core panel, each D also as its swizzled BF16 split (4 boxes of 16 KB)
+    const bool ptc = ctx->opt.chol_panel_tc != 0;
+    const size_t swbytes = ptc ? (size_t)4 * PT_BOX : 0;
+    if (ctx->ensure(&ctx->d_chol_tc, &ctx->chol_tc_cap, nd * (dbytes + swbytes) + 6 * hbytes + 256, "factor scratch") !=
+        SW_OK)
         return cudaErrorMemoryAllocation;
     char* base = (char*)ctx->d_chol_tc;
     float* Dk[4] = {(float*)base, (float*)(base + dbytes), (float*)(base + 2 * dbytes), (float*)(base + 3 * dbytes)};
-    char* hb = base + nd * dbytes;
+    uint4* Dsw[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (ptc)
+        for (int i = 0; i < nd; ++i) Dsw[i] = (uint4*)(base + nd * dbytes + i * swbytes);
+    char* hb = base + nd * (dbytes + swbytes);
     __nv_bfloat16* Ph[2] = {(__nv_bfloat16*)hb, (__nv_bfloat16*)(hb + hbytes)};
     __nv_bfloat16* Pl[2] = {(__nv_bfloat16*)(hb + 2 * hbytes), (__nv_bfloat16*)(hb + 3 * hbytes)};
     __nv_bfloat16* XTh = (__nv_bfloat16*)(hb + 4 * hbytes);
@@ -926,29 +1106,37 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
                                                             depth / BKC, d_err);
         return cudaGetLastError();
     };
-    auto diag_launch = [&](int64_t j0, int bs, float* D) -> cudaError_t {
+    auto diag_launch = [&](int64_t j0, int bs, int slot) -> cudaError_t {
         LaunchTimer lt(ctx, K_POTRF_DIAG);
         add_work(ctx, K_POTRF_DIAG, 2.0 * (double)bs * bs * bs / 3.0);
-        k_diag128<<<1, DIAG_THREADS, DIAG_SMEM, st>>>(G, ld, j0, bs, D, d_info, keep_L ? 1 : 0);
+        k_diag128<<<1, DIAG_THREADS, DIAG_SMEM, st>>>(G, ld, j0, bs, Dk[slot], d_info, keep_L ? 1 : 0, Dsw[slot]);
         return cudaGetLastError();
     };
     // the panel is launched programmatically behind its diagonal block: its row staging overlaps it
-    auto panel_launch = [&](int64_t j0, int64_t r0, int64_t m, const float* D, __nv_bfloat16* ph,
+    auto panel_launch = [&](int64_t j0, int64_t r0, int64_t m, int slot, __nv_bfloat16* ph,
                             __nv_bfloat16* pl) -> cudaError_t {
         if (m <= 0) return cudaSuccess;
         LaunchTimer lt(ctx, K_TRSM_PANEL);
         add_work(ctx, K_TRSM_PANEL, (double)m * DB * DB);
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)((m + PR - 1) / PR));
-        cfg.blockDim = dim3(256);
-        cfg.dynamicSmemBytes = PANEL_SMEM;
         cfg.stream = st;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         at[0].val.programmaticStreamSerializationAllowed = ctx->opt.chol_pdl ? 1 : 0;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, k_panel128, G, ld, j0, r0, m, D, ph, pl, W);
+        cudaError_t e;
+        if (ptc) {
+            cfg.gridDim = dim3((unsigned)((m + 127) / 128));
+            cfg.blockDim = dim3(128);
+            cfg.dynamicSmemBytes = PT_SMEM;
+            e = cudaLaunchKernelEx(&cfg, k_panel_tc, G, ld, j0, r0, m, (const uint4*)Dsw[slot], ph, pl, W, d_err);
+        } else {
+            cfg.gridDim = dim3((unsigned)((m + PR - 1) / PR));
+            cfg.blockDim = dim3(256);
+            cfg.dynamicSmemBytes = PANEL_SMEM;
+            e = cudaLaunchKernelEx(&cfg, k_panel128, G, ld, j0, r0, m, (const float*)Dk[slot], ph, pl, W);
+        }
         return e ? e : cudaGetLastError();
     };
     auto trmm_launch = [&](int64_t j0, int bs, int64_t ncols, const float* D, __nv_bfloat16* xh,
@@ -989,14 +1177,15 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
             const int bsb = hasb ? (int)(K - j0b < DB ? K - j0b : DB) : 0;
             const int64_t r0b = j0b + bsb, mb = hasb ? K - r0b : 0;
             const int par = (int)(si & 1);
-            float* Da = Dk[2 * par];
-            float* Db = Dk[2 * par + 1];
+            const int sa = 2 * par, sbk = 2 * par + 1;
+            float* Da = Dk[sa];
+            float* Db = Dk[sbk];
             const int64_t Ta = (ma + BM - 1) / BM, Tb = (mb + BM - 1) / BM;
             // ---- chain
             // the buffers of parity par were last read by super-step si - 2's bulk work
             if (two && si >= 2 && (e = cudaStreamWaitEvent(st, evB(si - 2), 0))) return e;
-            if ((e = diag_launch(j0a, bsa, Da))) return e;
-            if ((e = panel_launch(j0a, r0a, ma, Da, Ph[par], Pl[par]))) return e;
+            if ((e = diag_launch(j0a, bsa, sa))) return e;
+            if ((e = panel_launch(j0a, r0a, ma, sa, Ph[par], Pl[par]))) return e;
             if (two && (e = cudaEventRecord(evP(si), st))) return e;
             if (hasb) {
                 // block column b, last updated by super-step si - 1's rest
@@ -1004,9 +1193,9 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
                 if ((e = tc_launch(st, K_SYRK_TC, false, mph[par], mpl[par], mph[par], mpl[par], mg, (int)r0a, (int)r0a,
                                    0, 0, Ta, 1, 2.0 * (double)ma * std::min<int64_t>(ma, BN) * DB, DB)))
                     return e;
-                if ((e = diag_launch(j0b, bsb, Db))) return e;
+                if ((e = diag_launch(j0b, bsb, sbk))) return e;
                 // P_b from row 128 of P, columns 128 .. 255 (mb > 0 only when block b is full)
-                if ((e = panel_launch(j0b, r0b, mb, Db, Ph[par] + (size_t)DB * W + DB, Pl[par] + (size_t)DB * W + DB)))
+                if ((e = panel_launch(j0b, r0b, mb, sbk, Ph[par] + (size_t)DB * W + DB, Pl[par] + (size_t)DB * W + DB)))
                     return e;
                 if (two && (e = cudaEventRecord(evQ(si), st))) return e;
                 if (mb > 0 &&
@@ -1065,7 +1254,7 @@ cudaError_t cholesky_inverse_tc(sw_ctx* ctx, float* G, float* X, int64_t K, int6
         {
             LaunchTimer lt(ctx, K_POTRF_DIAG);
             add_work(ctx, K_POTRF_DIAG, 2.0 * (double)bs * bs * bs / 3.0);
-            k_diag128<<<1, DIAG_THREADS, DIAG_SMEM, st>>>(G, ld, j0, bs, Dk[par], d_info, keep_L ? 1 : 0);
+            k_diag128<<<1, DIAG_THREADS, DIAG_SMEM, st>>>(G, ld, j0, bs, Dk[par], d_info, keep_L ? 1 : 0, nullptr);
         }
         if ((e = cudaGetLastError())) return e;
         const int64_t T = (m + BM - 1) / BM;

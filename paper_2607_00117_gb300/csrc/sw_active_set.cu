@@ -27,6 +27,7 @@
 #include "sw_linalg.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -413,10 +414,15 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             AS_CUDA(ctx, cudaMemsetAsync(cerr, 0, sizeof(int), st), "memset");
             cudaError_t ce = ctx->opt.chol_coop ? cholesky_inverse_coop<GT>(ctx, G, (GT*)ws.X, nP, info, cerr)
                                                 : cudaErrorNotSupported;
+            // verbose > 2: the host's enqueue time of the factorisation against its time to completion
+            const bool timed = ctx->opt.verbose > 2;
+            if (timed) AS_CUDA(ctx, cudaStreamSynchronize(st), "reduced factor");
+            const auto th0 = std::chrono::steady_clock::now();
             if constexpr (sizeof(GT) == 4) {
                 if (ce == cudaErrorNotSupported && fact_tc)
                     ce = cholesky_inverse_tc(ctx, (float*)G, (float*)ws.X, nP, ldG, info, gerr, false);
             }
+            const auto th1 = std::chrono::steady_clock::now();
             if (ce == cudaErrorNotSupported) {
                 cudaGetLastError();
                 ce = ldG == nP ? cholesky_inverse<GT>(ctx, G, (GT*)ws.X, (GT*)ws.D, nP, info) : cudaErrorInvalidValue;
@@ -427,6 +433,10 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             AS_CUDA(ctx, cudaMemcpyAsync(&gerrh, gerr, sizeof(int), cudaMemcpyDeviceToHost, st), "flags");
             AS_CUDA(ctx, cudaMemcpyAsync(&cerrh, cerr, sizeof(int), cudaMemcpyDeviceToHost, st), "flags");
             AS_CUDA(ctx, cudaStreamSynchronize(st), "reduced factor");
+            if (timed)
+                fprintf(stderr, "[sw]   factor K %lld: enqueued in %.2f ms, done in %.2f ms\n", (long long)nP,
+                        std::chrono::duration<double, std::milli>(th1 - th0).count(),
+                        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count());
             if (gerrh) { set_error(ctx, "solve: a tensor-core kernel (Gram or factor update) timed out"); return SW_ETIMEOUT; }
             if (cerrh) { set_error(ctx, "solve: a grid barrier of the Cholesky kernel timed out"); return SW_ETIMEOUT; }
         }
@@ -877,7 +887,15 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             evaluated = true;
         }
     }
+    // verbose > 2: wall time of each phase of a pivoting step (host decisions, factor, solve, objective,
+    // evaluation), each phase ending at a synchronisation
+    auto wall = [] { return std::chrono::steady_clock::now(); };
+    auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+        return std::chrono::duration<double, std::milli>(b - a).count();
+    };
     for (; outer < 1000000 && n_solves < ctx->opt.as_solves; ++outer) {
+        const auto w0 = wall();
+        auto w1 = w0, w2 = w0, w3 = w0, w4 = w0;
         std::vector<std::pair<double, int64_t>> neg, enter;   // (violation, orbit)
         bool widened = false;
         for (int64_t i : F)
@@ -946,6 +964,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             if (inF[i]) F.push_back(i);
         std::fill(zh.begin(), zh.end(), 0.0);
         bool solved = false;   // V.x holds zh on P0
+        w1 = wall();
         if (!F.empty()) {
             bool ok = true, conv = false;
             // the factor of P0 serves F when it covers F and the masked orbits' correction can be formed
@@ -968,7 +987,9 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
                 if (warm) warm->have_factor = false;   // P0 is now this passive set
             }
             if (!ok) { failed = true; break; }
+            w2 = wall();
             AS_TRY(solve_on(F, conv));
+            w3 = wall();
             solved = true;
             for (int64_t i : F) zh[i] = xh[pos[i]];
             buf.assign(P0.size(), 0.0);
@@ -976,6 +997,7 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
             AS_CUDA(ctx, cudaMemcpyAsync(V.xa, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, st),
                     "x+");
             AS_TRY(objective_P0(V.xa, fproj));
+            w4 = wall();
         } else {
             fproj = fbest;
         }
@@ -985,6 +1007,9 @@ sw_status solve_active_set(sw_ctx* ctx, const sw_matrix* Um, const double* y_dev
         }
         AS_TRY(evaluate(solved ? V.x : nullptr));
         evaluated = true;
+        if (ctx->opt.verbose > 2 && solved)
+            fprintf(stderr, "[sw]   step %d (ms): host %.2f, factor %.2f, solve %.2f, objective %.2f, evaluation %.2f\n",
+                    outer, ms(w0, w1), ms(w1, w2), ms(w2, w3), ms(w3, w4), ms(w4, wall()));
     }
     if (!converged) {   // return the best projected iterate
         zh = zbest;

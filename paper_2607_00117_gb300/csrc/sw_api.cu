@@ -1105,6 +1105,9 @@ extern "C" sw_status sw_set_option(sw_ctx* ctx, const char* key, double value)
     } else if (!strcmp(key, "boot_p0_extra")) {
         if (!(value >= 0.0 && value <= 4.0)) return SW_EINVAL;
         ctx->opt.boot_p0_extra = value;
+    } else if (!strcmp(key, "chol_panel_tc")) {
+        if (!(value == 0 || value == 1)) return SW_EINVAL;
+        ctx->opt.chol_panel_tc = (int)value;
     } else if (!strcmp(key, "chol_super")) {
         if (!(value == 0 || value == 1)) return SW_EINVAL;
         ctx->opt.chol_super = (int)value;

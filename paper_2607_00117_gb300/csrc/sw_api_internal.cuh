@@ -39,6 +39,7 @@ struct Options {
     int chol_reserve_sms = 8;    // tensor-core factorisation: SMs the bulk updates leave to the next steps' chain
     double boot_p0_extra = 0.0;  // bootstrap: factored set = the plain solve's support plus this fraction of near-active orbits
     int chol_pdl = 1;            // tensor-core factorisation: panel launched programmatically behind its diagonal block
+    int chol_panel_tc = 0;       // tensor-core factorisation: panels on the tensor cores (BF16 hi + lo split) or FP32 SIMT
     int chol_super = 1;          // tensor-core factorisation: 256-wide super-steps (rank-256 bulk updates) or 128-wide steps
     int project_bundle = 1;      // orbits per column of sw_project's matrix (bundles accumulated at bin time)
     int matrix_cache = 1;        // keep freed matrix buffers for reuse by the next matrices of this context

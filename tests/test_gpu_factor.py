@@ -86,3 +86,25 @@ def test_factor_reports_nonpositive_pivot(ctx):
     assert info == 151
     L, X, info = ctx.factor_preconditioner(G.astype(np.float32), 1)
     assert info == 151
+
+
+@pytest.mark.parametrize("K", [300, 640, 1000])
+@pytest.mark.parametrize("variant", [(0, 0), (1, 0), (1, 1)])
+def test_factor_step_variants(K, variant):
+    """The tensor-core form's schedules: 128-wide steps (chol_super 0), 256-wide super-steps with
+    rank-256 bulk updates and SIMT panels (1, chol_panel_tc 0) or panels on the tensor cores (1, 1).
+    Each meets the tensor-core gate; the variants agree with one another to it."""
+    from paper_2607_00117_gb300 import sw as swmod
+    swmod.lib(build_if_missing=True)
+    G = passive_gram(K, 7200 + K)
+    c = swmod.Context(0, "fp32")
+    c.set_option("chol_super", variant[0])
+    c.set_option("chol_panel_tc", variant[1])
+    L, X, info = c.factor_preconditioner(G, 0)
+    assert info == 0
+    back_L, back_X, fwd_L, cond, upper = _errs(G, L, X)
+    tol = (K + 2) * U32 + 2.0 ** -16 * np.sqrt(K)
+    print(f"K={K} super={variant[0]} panel_tc={variant[1]}: backward {back_L:.3g}, {back_X:.3g} (tol {tol:.3g}); "
+          f"forward {fwd_L:.3g}")
+    assert upper == 0.0
+    assert back_L <= tol and back_X <= tol
