@@ -878,9 +878,20 @@ __global__ void __launch_bounds__(256) k_colnorm2(const T* __restrict__ U, int64
     for (int64_t i = warp; i < N; i += nwarp) {
         const T* col = U + (size_t)i * M;
         double s = 0.0;
-        for (int64_t r = lane; r < M; r += 32) {
-            double v = (double)col[r] * inv_sig[r];
-            s += v * v;
+        if constexpr (sizeof(T) == 4) {
+            // FP32 products, each lane's sum in FP32 (a few hundred terms, ~1e-6 relative: the norms set
+            // the Jacobi scaling and the ranking of violators), the warp's total in FP64
+            float sf = 0.f;
+            for (int64_t r = lane; r < M; r += 32) {
+                const float v = col[r] * (float)inv_sig[r];
+                sf = fmaf(v, v, sf);
+            }
+            s = (double)sf;
+        } else {
+            for (int64_t r = lane; r < M; r += 32) {
+                double v = (double)col[r] * inv_sig[r];
+                s += v * v;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
