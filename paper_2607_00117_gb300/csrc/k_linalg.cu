@@ -818,9 +818,11 @@ __global__ void __launch_bounds__(UTX_THREADS, 1) k_ut_times_x_ff_sm(const float
                 ff_acc(s[1], u[q].y, h.y, l.y);
                 ff_acc(s[2], u[q].z, h.z, l.z);
                 ff_acc(s[3], u[q].w, h.w, l.w);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) ff_renorm(s[k]);
             }
+            // four terms per sum between renormalisations (as in k_u_times_w_ff): s.l stays within
+            // a few units of the last place of s.h
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ff_renorm(s[k]);
         }
         for (; c < nch; c += 32) {
             const float4 u = col[c], h = Xh[c], l = Xl[c];
