@@ -194,7 +194,7 @@ def make_data(sw, torch, W, rank, n_mock=N_MOCK):
 # lane-instructions executed per orbit-step by the fused orbit kernel (FP32 form, barred potential, the
 # benchmark's histogram grid, bundles of four accumulated at bin time): smsp__inst_executed x threads per
 # instruction / orbit-steps from the ncu capture in profiles/orbit_kernel_fp32_barred.md
-OPS_PER_ORBIT_STEP = 870.0
+OPS_PER_ORBIT_STEP = 832.0
 # arithmetic operations of the method per orbit-step, counted from the kernel's formulas: kick-drift-kick
 # with Kahan compensation ~45, the disc + NFW + Long-Murali force ~155 (correctly rounded divisions and
 # square roots counted as one operation each), rotation, mirrors, projection and binning of 4 copies ~170
@@ -210,7 +210,7 @@ ALG_OPS_PER_BS3_STEP = 725.0
 # DRAM bytes (read + write) per launch of the dominant kernel from a one-pass ncu capture of the
 # benchmark's own launch (profiles/orbit_kernel_fp32_barred.md); a kernel without a capture of its
 # current form reports null
-NCU_TRAFFIC_PER_LAUNCH = {"orbit_project_bin": 37405249792 + 28910736896}
+NCU_TRAFFIC_PER_LAUNCH = {}
 
 # kernels launched as a single CTA (a chain of dependent launches): their roofline also
 # states the fraction of one SM's FP32 peak, the most one launch can reach
