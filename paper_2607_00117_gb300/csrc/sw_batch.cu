@@ -38,6 +38,7 @@ struct sw_batch {
     std::vector<sw_matrix> views;
     bool models_set = false, tuned = false, have_graph = false;
     int threads = 128, grid = 0, ej_every = 8;   // grid: set from the device's SM count at creation
+    int pot = 0;                                  // 1: every model is disc + halo + Long-Murali bar (FP32 kernel)
     std::vector<double> tune_ms;   // per candidate, in candidate order
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -82,7 +83,7 @@ cudaError_t enqueue(sw_batch* b, int64_t nsteps)
     cudaError_t e = cudaMemsetAsync(b->U, 0, (size_t)b->M * b->ntot * sizeof(T), st);
     if (!e) e = cudaMemsetAsync(b->next, 0, sizeof(int), st);
     if (!e)
-        e = launch_batch_orbit_bin<T>(st, b->threads, b->grid, b->gh, (const ModelT<T>*)b->models, b->items,
+        e = launch_batch_orbit_bin<T>(st, b->threads, b->grid, b->gh, b->pot, (const ModelT<T>*)b->models, b->items,
                                       b->n_items, b->next, (const T*)b->soa, b->ntot, nsteps, b->ej_every, b->drift,
                                       b->status);
     if (!e) e = launch_zero_flagged<T>(ctx, b->U, b->M, b->ntot, b->status);
@@ -245,6 +246,20 @@ sw_status set_models_impl(sw_batch* b, const sw_potential_params* pots, const do
     if (!e) e = cudaStreamSynchronize(st);
     if (aos) cudaFree(aos);
     if (e) return ctx->cuda_fail(e, "batch model upload");
+    // the kernel's potential layout: a captured graph holds the kernel of the layout it was captured with
+    int pot = sizeof(T) == 4 ? 1 : 0;
+    for (int k = 0; k < K && pot; ++k) {
+        const FieldT<T>& f = ms[k].f;
+        if (!(f.has_disc && f.has_halo && f.has_bar && f.bar_kind == 0 && f.test_kind == 0)) pot = 0;
+    }
+    if (pot != b->pot && b->have_graph) {
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        b->have_graph = false;
+    }
+    b->pot = pot;
     b->models_set = true;
     return SW_OK;
 }

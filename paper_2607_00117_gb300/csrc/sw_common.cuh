@@ -131,9 +131,10 @@ cudaError_t launch_reduce_gh(sw_ctx* ctx, const void* Uh, int64_t Mh, int64_t N,
                              const void* W, void* Ug, int64_t Mg);
 template <typename T>
 cudaError_t launch_bundle(sw_ctx* ctx, const void* U, int64_t M, int64_t Nb, int n, void* out);
-// persistent multi-model launch: threads per CTA in {64, 128, 256}, grid CTAs
+// persistent multi-model launch: threads per CTA in {64, 128, 256}, grid CTAs; pot = 1 (FP32 only) when
+// every model is disc + halo + Long-Murali bar with no test fixture
 template <typename T>
-cudaError_t launch_batch_orbit_bin(cudaStream_t st, int threads, int grid, int gh, const ModelT<T>* models,
+cudaError_t launch_batch_orbit_bin(cudaStream_t st, int threads, int grid, int gh, int pot, const ModelT<T>* models,
                                    const int2* items, int n_items, int* next, const T* soa, int64_t ld,
                                    int64_t nsteps, int ej_every, double* drift, uint8_t* status);
 
