@@ -194,7 +194,7 @@ def make_data(sw, torch, W, rank, n_mock=N_MOCK):
 # lane-instructions executed per orbit-step by the fused orbit kernel (FP32 form, barred potential, the
 # benchmark's histogram grid, bundles of four accumulated at bin time): smsp__inst_executed x threads per
 # instruction / orbit-steps from the ncu capture in profiles/orbit_kernel_fp32_barred.md
-OPS_PER_ORBIT_STEP = 830.0
+OPS_PER_ORBIT_STEP = 726.0
 # arithmetic operations of the method per orbit-step, counted from the kernel's formulas: kick-drift-kick
 # with Kahan compensation ~45, the disc + NFW + Long-Murali force ~155 (correctly rounded divisions and
 # square roots counted as one operation each), rotation, mirrors, projection and binning of 4 copies ~170

@@ -3,7 +3,8 @@
 // Dehnen-Aly bar can be compared with the oracle without a GPU.  Input file: 10 model
 // scalars (disc M, a, b; M_DM, R_s; bar M, L, b, c; bar_kind), the 8-point Gauss-Legendre
 // rule's 4 positive nodes and 4 weights, n, then n x 3 bar-frame points (doubles).
-// Output: for FP64 then FP32, phi (n) and acceleration (n x 3), as doubles.
+// Output: for FP64, FP32 and the FP32 kernels' fixed layout (FP32 again where the model is not
+// disc + halo + Long-Murali bar), phi (n) and acceleration (n x 3), as doubles.
 #include "bs3_host.h"
 
 #include <cstdio>
@@ -26,13 +27,14 @@ static FieldT<T> make(const double* P, const double* gl)
     return f;
 }
 
-template <typename T>
+template <typename T, int POT = POT_ANY>
 static void eval(const FieldT<T>& f, const std::vector<double>& xyz, int64_t n, FILE* out)
 {
     std::vector<double> phi(n), acc(3 * n);
     for (int64_t i = 0; i < n; ++i) {
         T ax, ay, az, ph, xb, yb;
-        field<T>(f, T(1), T(0), (T)xyz[3 * i], (T)xyz[3 * i + 1], (T)xyz[3 * i + 2], ax, ay, az, ph, true, xb, yb);
+        field<T, POT>(f, T(1), T(0), (T)xyz[3 * i], (T)xyz[3 * i + 1], (T)xyz[3 * i + 2], ax, ay, az, ph, true, xb,
+                      yb);
         phi[i] = ph; acc[3 * i] = ax; acc[3 * i + 1] = ay; acc[3 * i + 2] = az;
     }
     fwrite(phi.data(), sizeof(double), n, out);
@@ -56,6 +58,12 @@ int main(int argc, char** argv)
     if (!out) return 6;
     eval<double>(make<double>(P, gl), xyz, n, out);
     eval<float>(make<float>(P, gl), xyz, n, out);
+    // the fixed disc + halo + Long-Murali layout of the FP32 kernels, where the model is that layout
+    const FieldT<float> f32 = make<float>(P, gl);
+    if (f32.has_disc && f32.has_halo && f32.has_bar && f32.bar_kind == 0)
+        eval<float, POT_DHL>(f32, xyz, n, out);
+    else
+        eval<float>(f32, xyz, n, out);
     fclose(out);
     return 0;
 }

@@ -58,7 +58,7 @@ def _run(harness, orc, p, xyz):
     raw = np.fromfile(fout, dtype=np.float64)
     n = len(xyz)
     out = []
-    for k in range(2):
+    for k in range(3):
         blk = raw[4 * n * k:4 * n * (k + 1)]
         out.append((blk[:n], blk[n:].reshape(n, 3)))
     return out
@@ -69,12 +69,14 @@ def test_field_device_functions_match_oracle(orc, harness, pot):
     p = PAPER_BAR if pot == "paper_bar" else dict(inputs.DISC_HALO, **inputs.BAR)
     xyz = _points(301, 1000)
     phi_o, acc_o = orc.potential(orc.make_pot(p), xyz)
-    (phi64, acc64), (phi32, acc32) = _run(harness, orc, p, xyz)
+    (phi64, acc64), (phi32, acc32), (phid, accd) = _run(harness, orc, p, xyz)
     scale = _scale(acc_o)
     np.testing.assert_allclose(phi64, phi_o, rtol=1e-11)
     assert np.all(np.abs(acc64 - acc_o) <= 1e-12 * scale), (np.abs(acc64 - acc_o) / scale).max()
-    np.testing.assert_allclose(phi32, phi_o, rtol=1e-6)
-    assert np.all(np.abs(acc32 - acc_o) <= 3e-5 * scale), (np.abs(acc32 - acc_o) / scale).max()
+    # FP32, and the fixed disc + halo + Long-Murali layout of the FP32 kernels (its branch-free forms)
+    for ph, ac in ((phi32, acc32), (phid, accd)):
+        np.testing.assert_allclose(ph, phi_o, rtol=1e-6)
+        assert np.all(np.abs(ac - acc_o) <= 3e-5 * scale), (np.abs(ac - acc_o) / scale).max()
 
 
 def _scale(acc):
