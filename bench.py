@@ -210,7 +210,7 @@ ALG_OPS_PER_BS3_STEP = 725.0
 # DRAM bytes (read + write) per launch of the dominant kernel from a one-pass ncu capture of the
 # benchmark's own launch (profiles/orbit_kernel_fp32_barred.md); a kernel without a capture of its
 # current form reports null
-NCU_TRAFFIC_PER_LAUNCH = {}
+NCU_TRAFFIC_PER_LAUNCH = {"orbit_project_bin": 34821034240 + 26780705536}
 
 # kernels launched as a single CTA (a chain of dependent launches): their roofline also
 # states the fraction of one SM's FP32 peak, the most one launch can reach
