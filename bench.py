@@ -194,10 +194,10 @@ def make_data(sw, torch, W, rank, n_mock=N_MOCK):
 # lane-instructions executed per orbit-step by the fused orbit kernel (FP32 form, barred potential, the
 # benchmark's histogram grid, bundles of four accumulated at bin time): smsp__inst_executed x threads per
 # instruction / orbit-steps from the ncu capture in profiles/orbit_kernel_fp32_barred.md
-OPS_PER_ORBIT_STEP = 726.0
+OPS_PER_ORBIT_STEP = 728.5
 # arithmetic operations of the method per orbit-step, counted from the kernel's formulas: kick-drift-kick
-# with Kahan compensation ~45, the disc + NFW + Long-Murali force ~155 (correctly rounded divisions and
-# square roots counted as one operation each), rotation, mirrors, projection and binning of 4 copies ~170
+# with Kahan compensation ~45, the disc + NFW + Long-Murali force ~155 (divisions and square roots counted
+# as one operation each), rotation, mirrors, projection and binning of 4 copies ~170
 ALG_OPS_PER_ORBIT_STEP = 370.0
 # the paper's adaptive integrator (k_orbit_bs3, FP32, barred potential): lane-instructions executed per
 # accepted orbit-step, rejected trials included (ncu capture in profiles/orbit_kernel_fp32_barred.md), and
@@ -210,7 +210,7 @@ ALG_OPS_PER_BS3_STEP = 725.0
 # DRAM bytes (read + write) per launch of the dominant kernel from a one-pass ncu capture of the
 # benchmark's own launch (profiles/orbit_kernel_fp32_barred.md); a kernel without a capture of its
 # current form reports null
-NCU_TRAFFIC_PER_LAUNCH = {"orbit_project_bin": 34821034240 + 26780705536}
+NCU_TRAFFIC_PER_LAUNCH = {"orbit_project_bin": 34970118912 + 26922181888}
 
 # kernels launched as a single CTA (a chain of dependent launches): their roofline also
 # states the fraction of one SM's FP32 peak, the most one launch can reach
