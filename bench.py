@@ -369,6 +369,18 @@ def reference_model(W, n_orb, data=None):
     return None, time.perf_counter() - t0
 
 
+def reference_config(W, world):
+    """Our arm's `config` for the default workload (the reference arm reports on the same
+    configuration; each of its steps is the bounded sample its cpu_baseline names)."""
+    grid, nb = W["grid"], W.get("bundle", 1)
+    npix = grid["nx"] * grid["ny"]
+    nd = grid["nR"] * grid["nphi"] * grid["nz"]
+    return {"workload": WORKLOAD, "ics": W.get("ics", "disc"), "n_orb": W["n_orb"], "bundles": W["n_orb"] // nb,
+            "dithers_per_bundle": nb, "nsteps": W["nsteps"], "rows_histogram": nd + npix * (1 + grid["nv"]),
+            "rows_solve": nd + 5 * npix, "parallelism": f"replicas x{world}",
+            "l2": "inputs and U far larger than L2 (bundled U 8.7 GB)"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -389,7 +401,7 @@ def run_reference(args):
             "value": value, "unit": "orbit-steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(ts)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_orbits": n_orb, "nsteps": W["nsteps"]}, "impl": "reference",
+            "config": reference_config(W, world), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "orbit-steps/s", "cores": cores, "kind": "oracle",
                              "sample": sample, "single_thread_value": cpu_single_thread(W)},
             "e2e": {"value": value, "unit": "orbit-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

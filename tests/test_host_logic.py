@@ -55,3 +55,15 @@ def test_roofline_entry_arithmetic():
     assert math.isclose(g["frac"], 1.0) and math.isclose(g["method_frac"], 1.0 / 3.0)
     y = bench.roofline_entry("syrk_update_tcgen05", st3, 6000.0, 1500.0, 2070.0, 152)
     assert math.isclose(y["frac"], 1.0 / 3.0) and math.isclose(y["tensor_pipe_frac"], 1.0)
+
+
+def test_reference_arm_reports_the_workload_rows(orc):
+    """The reference arm's config is the workload's: its row counts are those of the oracle's
+    observation grids (the histogram matrix, and the Gauss-Hermite rows the solve uses)."""
+    import bench
+    W = inputs.WORKLOADS[bench.WORKLOAD]
+    c = bench.reference_config(W, 1)
+    assert c["rows_histogram"] == orc.n_rows(orc.make_obs(W["grid"]))
+    assert c["rows_solve"] == orc.n_rows(orc.make_obs(dict(W["grid"], gh=1)))
+    assert c["bundles"] * c["dithers_per_bundle"] == c["n_orb"] == W["n_orb"]
+    assert c["parallelism"] == "replicas x1"
